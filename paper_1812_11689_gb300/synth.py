@@ -1,0 +1,156 @@
+"""Seeded synthetic workloads shaped like the paper's kNN benchmarks.
+
+This module holds no arithmetic of the method itself: it only draws point
+sets (NumPy ``Generator(PCG64(seed))``) that both the CUDA path and the CPU
+oracle consume.  The paper evaluates on UCI / Olivetti datasets (Sec. 5,
+Tables 1-2) that are not available here; these distributions stand in for
+them, one per workload:
+
+* ``mix5_d10``      n=2,000, d=10: 5-component isotropic Gaussian mixture,
+                    means ~ N(0, 9 I), unit variance, equal weights.
+* ``aniso20_d64``   n=200,000, d=64: 20-component mixture, means ~ N(0, 9 I),
+                    covariance Q diag(lam) Q^T, Q Haar (QR of a Gaussian with
+                    sign fix), lam log-uniform in [0.01, 1].
+* ``subspace16_d128`` n=1,000,000, d=128: x = B z + eps, B (128 x 16)
+                    orthonormal, z ~ N(0, I_16), eps ~ N(0, 0.01^2 I).
+* ``student3_d32``  n=500,000, d=32: x_j = s_j * t_3, s_j log-uniform in
+                    [0.1, 10] (heavy tails).
+* ``mix50_d96``     n=2,000,000, d=96: 50-component isotropic mixture, unit
+                    variance, means ~ N(0, 9 I); plus request streams of new
+                    points from the same mixture (sizes log-uniform in
+                    [1, 4096]).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Workload:
+    name: str
+    n: int
+    d: int
+    n_trees: int
+    leaf_max: int
+    k: int
+    n_try: int = 5
+    extra: dict = field(default_factory=dict)
+
+
+WORKLOADS = {
+    "mix5_d10": Workload("mix5_d10", 2000, 10, 10, 50, 5),
+    "aniso20_d64": Workload("aniso20_d64", 200_000, 64, 40, 128, 10),
+    "subspace16_d128": Workload("subspace16_d128", 1_000_000, 128, 64, 256, 20),
+    "student3_d32": Workload("student3_d32", 500_000, 32, 128, 64, 10,
+                             extra={"t_sweep": [1, 2, 4, 8, 16, 32, 64, 128]}),
+    "mix50_d96": Workload("mix50_d96", 2_000_000, 96, 32, 128, 10,
+                          extra={"k_set": [10, 50], "max_request": 4096}),
+}
+
+
+def _rng(seed: int, stream: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64([seed, stream]))
+
+
+def _haar(rng: np.random.Generator, d: int) -> np.ndarray:
+    q, r = np.linalg.qr(rng.standard_normal((d, d)))
+    return q * np.sign(np.diag(r))[None, :]
+
+
+class _Mixture:
+    """Gaussian mixture with per-component affine maps x = mu + A z."""
+
+    def __init__(self, means: np.ndarray, maps: list | None):
+        self.means = means
+        self.maps = maps
+
+    def sample(self, rng: np.random.Generator, n: int) -> np.ndarray:
+        c, d = self.means.shape
+        comp = rng.integers(0, c, size=n)
+        z = rng.standard_normal((n, d))
+        if self.maps is not None:
+            out = np.empty((n, d))
+            for k in range(c):
+                sel = comp == k
+                out[sel] = z[sel] @ self.maps[k].T
+            z = out
+        return (z + self.means[comp]).astype(np.float32)
+
+
+def _mixture_for(name: str, d: int, rng: np.random.Generator) -> _Mixture:
+    if name == "mix5_d10":
+        return _Mixture(3.0 * rng.standard_normal((5, d)), None)
+    if name == "aniso20_d64":
+        means = 3.0 * rng.standard_normal((20, d))
+        maps = []
+        for _ in range(20):
+            q = _haar(rng, d)
+            lam = np.exp(rng.uniform(np.log(0.01), np.log(1.0), size=d))
+            maps.append(q * np.sqrt(lam)[None, :])
+        return _Mixture(means, maps)
+    if name == "mix50_d96":
+        return _Mixture(3.0 * rng.standard_normal((50, d)), None)
+    raise KeyError(name)
+
+
+def make(name: str, seed: int = 0, n: int | None = None) -> np.ndarray:
+    """Data matrix X (n x d, float32, row-major) of workload `name`.
+
+    `n` overrides the workload's size (same distribution, fewer points) for
+    tests that need a smaller instance of the same shape.
+    """
+    w = WORKLOADS[name]
+    n = w.n if n is None else int(n)
+    rng = _rng(seed, 0)
+    if name in ("mix5_d10", "aniso20_d64", "mix50_d96"):
+        mix = _mixture_for(name, w.d, rng)
+        return mix.sample(_rng(seed, 1), n)
+    if name == "subspace16_d128":
+        B, _ = np.linalg.qr(rng.standard_normal((w.d, 16)))
+        r2 = _rng(seed, 1)
+        z = r2.standard_normal((n, 16))
+        eps = 0.01 * r2.standard_normal((n, w.d))
+        return (z @ B.T + eps).astype(np.float32)
+    if name == "student3_d32":
+        s = np.exp(rng.uniform(np.log(0.1), np.log(10.0), size=w.d))
+        t = _rng(seed, 1).standard_t(3, size=(n, w.d))
+        return (t * s[None, :]).astype(np.float32)
+    raise KeyError(name)
+
+
+def queries(name: str, m: int, seed: int = 0, stream: int = 7) -> np.ndarray:
+    """m new points from the same distribution as `make(name, seed)`."""
+    w = WORKLOADS[name]
+    rng = _rng(seed, 0)
+    if name in ("mix5_d10", "aniso20_d64", "mix50_d96"):
+        mix = _mixture_for(name, w.d, rng)
+        return mix.sample(_rng(seed, stream), m)
+    return make_like(name, m, seed, stream)
+
+
+def make_like(name: str, m: int, seed: int, stream: int) -> np.ndarray:
+    w = WORKLOADS[name]
+    rng = _rng(seed, 0)
+    if name == "subspace16_d128":
+        B, _ = np.linalg.qr(rng.standard_normal((w.d, 16)))
+        r2 = _rng(seed, stream)
+        return (r2.standard_normal((m, 16)) @ B.T
+                + 0.01 * r2.standard_normal((m, w.d))).astype(np.float32)
+    if name == "student3_d32":
+        s = np.exp(rng.uniform(np.log(0.1), np.log(10.0), size=w.d))
+        return (_rng(seed, stream).standard_t(3, size=(m, w.d)) * s[None, :]).astype(np.float32)
+    raise KeyError(name)
+
+
+def request_sizes(count: int, seed: int = 0, max_size: int = 4096) -> np.ndarray:
+    """Request sizes floor(exp(U(0, ln(max+1)))) clamped to [1, max]."""
+    u = _rng(seed, 11).uniform(0.0, np.log(max_size + 1.0), size=count)
+    return np.clip(np.floor(np.exp(u)), 1, max_size).astype(np.int64)
+
+
+def poisson_arrivals(count: int, rate_per_s: float, seed: int = 0) -> np.ndarray:
+    """Arrival times (seconds from 0) of a Poisson process of the given rate."""
+    gaps = _rng(seed, 12).exponential(1.0 / rate_per_s, size=count)
+    return np.cumsum(gaps)
