@@ -1,0 +1,153 @@
+/*
+ * rpforest.h -- C ABI of the GB300 (sm_103a) rpForests kNN library.
+ *
+ * Random projection forests kNN search, Yan, Wang, Wang, Wang & Li,
+ * "K-nearest Neighbor Search by Random Projection Forests" (arXiv 1812.11689).
+ * The library grows T random projection trees on one GPU (Sec. 2,
+ * Algorithms 1 and 2), computes exact distances inside every (tree, leaf)
+ * block and merges the per-tree candidates into the K nearest neighbours of
+ * every point (Algorithm 3).
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are row-major, contiguous, FP32 (points) / int32 (indices).
+ *  - A pointer argument may be device memory or host memory (pageable or
+ *    pinned); host buffers are staged through library-owned device memory on
+ *    the given stream.  `stream` is a cudaStream_t (NULL = legacy stream).
+ *  - Return 0 on success or a negative RPF_E* code.  Nothing is thrown across
+ *    the ABI.  On error the output buffers are left in an unspecified state.
+ *  - Distances are Euclidean.  Neighbour lists are sorted ascending by the
+ *    canonical FP32 squared distance d32(x, y) = fold_k fmaf(x_k - y_k,
+ *    x_k - y_k, s) with ties broken by the smaller index; the reported
+ *    distance is sqrtf(d32).  Slots without a candidate hold (-1, +inf).
+ *  - Every random draw is a pure function of (seed, tree, node key, ...), so
+ *    results are deterministic and the first T' trees of a T-tree forest are
+ *    exactly the T'-tree forest.
+ */
+#ifndef RPFOREST_H
+#define RPFOREST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RPF_OK 0
+#define RPF_EINVAL (-1)    /* bad argument (null pointer, size out of range) */
+#define RPF_ENOMEM (-2)    /* a device or host allocation failed */
+#define RPF_ECUDA (-3)     /* a CUDA runtime call or kernel failed */
+#define RPF_ETIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define RPF_EINTERNAL (-5) /* an internal consistency check failed */
+
+/* Forest handle; owned by the library, read-only after rpf_build. */
+typedef struct rpf_forest rpf_forest;
+
+/* Growth and search parameters (Sec. 2 and Sec. 5.2 of the paper). */
+typedef struct {
+  int32_t n_trees;    /* T >= 1: number of rpTrees (Algorithm 3)                  */
+  int32_t leaf_max;   /* L in [1, 1024]: a node with more than L points is split, */
+                      /* so no leaf holds more than L (Algorithm 1, n_s = L + 1). */
+  int32_t n_try;      /* nTry in [1, 64]: candidate directions per node; the one  */
+                      /* with the largest projected dispersion wins (Algorithm 2). */
+                      /* 1 = the basic rpTree.                                    */
+  int32_t split_rule; /* 0 = c uniform on [min, max] of the projections (Sec. 2). */
+  int32_t form;       /* leaf distance tiles: 0 = plain FP32 SIMT; 1 = BF16       */
+                      /* tensor-core Gram + exact FP32 re-rank of a shortlist.    */
+                      /* Both return identical lists.                             */
+  int32_t growth;     /* 0 = default (2); 1 = every split decided in FP64 (G-A);  */
+                      /* 2 = FP32 projections with a certified error bound and    */
+                      /* FP64 recompute of every undecided case (G-B).  1 and 2   */
+                      /* grow identical trees.                                    */
+  uint64_t seed;      /* seed of every random draw                                */
+} rpf_params;
+
+/* Fill `p` with defaults: T=10, L=50, nTry=5, uniform split, plain form,
+   growth 0, seed 0. */
+void rpf_default_params(rpf_params* p);
+
+/*
+ * rpf_build -- grow the forest (Sec. 2, Algorithm 1 per tree, Algorithm 2 per
+ * node; Algorithm 3, first loop).
+ *   X      : n x d points (device or host).  The library copies X; the caller
+ *            may free it when the call returns.
+ *   n, d   : 1 <= n, 1 <= d <= 4096, n * n_trees < 2^31.
+ *   p      : parameters (copied).
+ *   stream : stream for all work; the call synchronises it before returning.
+ *   out    : receives the new forest; release with rpf_free.
+ * Errors: RPF_EINVAL (null pointer, sizes or parameters out of range),
+ * RPF_ENOMEM, RPF_ECUDA.
+ */
+int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* stream,
+              rpf_forest** out);
+
+/*
+ * rpf_all_knn -- K nearest neighbours of every data point among the union of
+ * its T leaves, the point itself excluded (Algorithm 3 with Q = U).
+ *   K        : 1 <= K <= 128.
+ *   idx,dist : n x K outputs (device or host), sorted as described above.
+ *   workspace: device scratch of at least rpf_workspace_bytes(f, 0, K, 1)
+ *              bytes, or NULL to let the library allocate (stream-ordered).
+ *   stream   : work is enqueued on it; host outputs are complete on return.
+ * Errors: RPF_EINVAL, RPF_ENOMEM, RPF_ECUDA.
+ */
+int rpf_all_knn(rpf_forest* f, int32_t K, int32_t* idx, float* dist, void* workspace,
+                size_t ws_bytes, void* stream);
+
+/*
+ * rpf_query -- K nearest neighbours of m new points Q among the data, found
+ * in the union of the leaves each query falls into (Algorithm 3: "let q fall
+ * through tree t_i").  Nothing is excluded.  Safe to call concurrently on one
+ * forest from several host threads with different streams and workspaces.
+ *   Q        : m x d queries (device or host); m >= 0 (m = 0 is a no-op).
+ *   K        : 1 <= K <= 128.
+ *   idx,dist : m x K outputs (device or host).
+ *   workspace: device scratch of rpf_workspace_bytes(f, m, K, 0) bytes, or
+ *              NULL to let the library allocate (stream-ordered).
+ * Errors: RPF_EINVAL, RPF_ENOMEM, RPF_ECUDA.
+ */
+int rpf_query(const rpf_forest* f, const float* Q, int64_t m, int32_t K, int32_t* idx,
+              float* dist, void* workspace, size_t ws_bytes, void* stream);
+
+/* Scratch bytes rpf_all_knn (for_all_knn = 1, m ignored) or rpf_query needs. */
+size_t rpf_workspace_bytes(const rpf_forest* f, int64_t m, int32_t K, int32_t for_all_knn);
+
+/* Release the forest and its device memory.  NULL is a no-op. */
+void rpf_free(rpf_forest* f);
+
+/* Static English description of an RPF_E* code. */
+const char* rpf_error_string(int code);
+
+/* ---- inspection (host outputs; used by tests and tools) ------------------ */
+
+/* Sizes: n, d, T, total node count, leaf count, max depth, and the number of
+   nodes whose split needed the FP64 fallback under growth 2.  Any pointer may
+   be NULL. */
+int rpf_forest_info(const rpf_forest* f, int64_t* n, int32_t* d, int32_t* n_trees,
+                    int64_t* n_nodes, int64_t* n_leaves, int32_t* max_depth,
+                    int64_t* n_exact_nodes);
+
+/* Final permutation of tree t (n int32, host): every leaf is a contiguous
+   segment, members in ascending original index. */
+int rpf_forest_perm(const rpf_forest* f, int32_t t, int32_t* perm_host);
+
+/* Leaf table (host, n_leaves entries each): tree, begin (offset in the tree's
+   permutation), len. */
+int rpf_forest_leaves(const rpf_forest* f, int32_t* tree, int32_t* begin, int32_t* len);
+
+/* Node table (host, n_nodes entries each): key (node key of the counter-based
+   draws; root 1), tree, begin, len, left child, right child (-1 for leaves),
+   chosen try (-1 if none), flag (1 = rank split), split point c. */
+int rpf_forest_nodes(const rpf_forest* f, uint64_t* key, int32_t* tree, int32_t* begin,
+                     int32_t* len, int32_t* left, int32_t* right, int32_t* jstar,
+                     int32_t* flag, double* c);
+
+/* The candidate directions of Algorithm 2 for (tree t, node key, try j),
+   d doubles each, for n_keys keys: out[i*d + k].  Device or host output. */
+int rpf_directions(uint64_t seed, int32_t t, const uint64_t* keys_host, int32_t n_keys,
+                   int32_t j, int32_t d, double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPFOREST_H */

@@ -96,6 +96,9 @@ def lib():
             L.orc_all_knn.restype = None
             L.orc_all_knn.argtypes = [ctypes.c_void_p, _f32p, ctypes.c_int32, _i32p, _f32p,
                                       ctypes.c_int32]
+            L.orc_all_knn_rows.restype = None
+            L.orc_all_knn_rows.argtypes = [ctypes.c_void_p, _f32p, _i32p, ctypes.c_int64,
+                                           ctypes.c_int32, _i32p, _f32p, ctypes.c_int32]
             L.orc_route.restype = ctypes.c_int64
             L.orc_route.argtypes = [ctypes.c_void_p, ctypes.c_int32, _f32p]
             L.orc_query.restype = None
@@ -230,6 +233,14 @@ class Forest:
         dist = np.empty((self.n, K), np.float32)
         lib().orc_all_knn(self._h, _p(self.X, _f32p), K, _p(idx, _i32p), _p(dist, _f32p),
                           self.threads)
+        return idx, dist
+
+    def all_knn_rows(self, rows, K: int):
+        rows = np.ascontiguousarray(rows, np.int32)
+        idx = np.empty((rows.size, K), np.int32)
+        dist = np.empty((rows.size, K), np.float32)
+        lib().orc_all_knn_rows(self._h, _p(self.X, _f32p), _p(rows, _i32p), rows.size, K,
+                               _p(idx, _i32p), _p(dist, _f32p), self.threads)
         return idx, dist
 
     def route(self, t: int, q: np.ndarray) -> int:

@@ -590,6 +590,66 @@ void orc_all_knn(const orc_forest* F, const float* X, int32_t K, int32_t* idx,
   (void)threads;
 }
 
+/* All-kNN answers for the data points rows[0..nr) only (same definition as
+   orc_all_knn; used to check large instances on a sample). */
+void orc_all_knn_rows(const orc_forest* F, const float* X, const int32_t* rows, int64_t nr,
+                      int32_t K, int32_t* idx, float* dist, int32_t threads) {
+  const int64_t n = F->n;
+  const int T = F->T;
+  /* position of every point in every tree's permutation */
+  int32_t* pos = (int32_t*)malloc(sizeof(int32_t) * (size_t)n * (size_t)T);
+  int64_t** leaf_b = (int64_t**)malloc(sizeof(int64_t*) * (size_t)T);
+  int64_t** leaf_l = (int64_t**)malloc(sizeof(int64_t*) * (size_t)T);
+  for (int t = 0; t < T; ++t) {
+    const orc_tree* tr = &F->trees[t];
+    for (int64_t a = 0; a < n; ++a) pos[(size_t)tr->perm[a] * T + t] = (int32_t)a;
+    leaf_b[t] = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    leaf_l[t] = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t i = 0; i < tr->n_nodes; ++i) {
+      const orc_node* nd = &tr->nodes[i];
+      if (!nd->leaf) continue;
+      for (int64_t a = 0; a < nd->len; ++a) {
+        leaf_b[t][nd->begin + a] = nd->begin;
+        leaf_l[t][nd->begin + a] = nd->len;
+      }
+    }
+  }
+#ifdef _OPENMP
+  if (threads < 1) threads = 1;
+#pragma omp parallel num_threads(threads)
+#endif
+  {
+    int32_t* stamp = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) stamp[i] = -1;
+    int32_t** mem = (int32_t**)malloc(sizeof(int32_t*) * (size_t)T);
+    int64_t* len = (int64_t*)malloc(sizeof(int64_t) * (size_t)T);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 8)
+#endif
+    for (int64_t r = 0; r < nr; ++r) {
+      const int32_t i = rows[r];
+      for (int t = 0; t < T; ++t) {
+        const int64_t a = pos[(size_t)i * T + t];
+        mem[t] = F->trees[t].perm + leaf_b[t][a];
+        len[t] = leaf_l[t][a];
+      }
+      orc_knn_from_union(X, F->d, X + (size_t)i * F->d, i, mem, len, T, K, stamp, (int32_t)r,
+                         idx + (size_t)r * K, dist + (size_t)r * K);
+    }
+    free(stamp);
+    free(mem);
+    free(len);
+  }
+  for (int t = 0; t < T; ++t) {
+    free(leaf_b[t]);
+    free(leaf_l[t]);
+  }
+  free(leaf_b);
+  free(leaf_l);
+  free(pos);
+  (void)threads;
+}
+
 /* Drop a point through tree t (Algorithm 3, "let q fall through tree t_i"):
    at an internal node go left iff r* . q < c; a rank-split node sends every
    query left.  Returns the leaf's node index. */

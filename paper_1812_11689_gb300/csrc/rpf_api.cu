@@ -1,0 +1,287 @@
+// rpf_api.cu -- the C ABI declared in include/rpforest.h: argument checks,
+// staging of host buffers through device memory, forest lifetime.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rpf_internal.cuh"
+
+int rpf_cuda_err(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return RPF_ENOMEM;
+  return RPF_ECUDA;
+}
+
+bool rpf_is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+namespace {
+
+template <typename T>
+int dalloc(rpf_forest* f, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count * sizeof(T), 16));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return RPF_ENOMEM;
+  }
+  f->owned.push_back(q);
+  *p = (T*)q;
+  return RPF_OK;
+}
+
+void free_forest(rpf_forest* f) {
+  if (!f) return;
+  for (void* p : f->owned) cudaFree(p);
+  void* ps[] = {f->node_key,  f->node_tree,  f->node_begin, f->node_len,  f->node_left,
+                f->node_right, f->node_jstar, f->node_flag, f->node_c,    f->node_dir,
+                f->node_dir32, f->leaf_tree,  f->leaf_begin, f->leaf_len, f->tile_first,
+                f->tile_count, f->stage};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  delete f;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rpf_default_params(rpf_params* p) {
+  if (!p) return;
+  p->n_trees = 10;
+  p->leaf_max = 50;
+  p->n_try = 5;
+  p->split_rule = 0;
+  p->form = 0;
+  p->growth = 0;
+  p->seed = 0;
+}
+
+const char* rpf_error_string(int code) {
+  switch (code) {
+    case RPF_OK: return "success";
+    case RPF_EINVAL: return "invalid argument";
+    case RPF_ENOMEM: return "out of memory";
+    case RPF_ECUDA: return "CUDA error";
+    case RPF_ETIMEOUT: return "device wait timed out";
+    case RPF_EINTERNAL: return "internal error";
+    default: return "unknown error";
+  }
+}
+
+int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* stream,
+              rpf_forest** out) {
+  if (!out) return RPF_EINVAL;
+  *out = nullptr;
+  if (!X || !p || n < 1 || d < 1 || d > RPF_MAX_D) return RPF_EINVAL;
+  if (p->n_trees < 1 || p->leaf_max < 1 || p->leaf_max > RPF_MAX_LEAF || p->n_try < 1 || p->n_try > RPF_MAX_TRY) return RPF_EINVAL;
+  if (p->split_rule != 0 || p->form < 0 || p->form > 1 || p->growth < 0 || p->growth > 2)
+    return RPF_EINVAL;
+  if (n * (int64_t)p->n_trees >= ((int64_t)1 << 31)) return RPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  rpf_forest* f = new (std::nothrow) rpf_forest();
+  if (!f) return RPF_ENOMEM;
+  f->n = n;
+  f->d = d;
+  f->prm = *p;
+  if (f->prm.growth == 0) f->prm.growth = 2;
+  // the G-B projection kernel stages nTry x d FP32 directions in shared memory
+  if (f->prm.growth == 2 && (size_t)p->n_try * d * 4 + 2048 > 200 * 1024) f->prm.growth = 1;
+  cudaGetDevice(&f->device);
+  int rc;
+  if ((rc = dalloc(f, &f->X, (size_t)n * d)) || (rc = dalloc(f, &f->xnorm, (size_t)n)) ||
+      (rc = dalloc(f, &f->perm, (size_t)n * p->n_trees))) {
+    free_forest(f);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(f->X, X, sizeof(float) * n * d, cudaMemcpyDefault, s);
+  if (e != cudaSuccess) {
+    free_forest(f);
+    return rpf_cuda_err(e);
+  }
+  if ((rc = rpf_grow(f, s)) || (rc = rpf_build_tiles(f, s))) {
+    free_forest(f);
+    return rc;
+  }
+  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    free_forest(f);
+    return rpf_cuda_err(e);
+  }
+  *out = f;
+  return RPF_OK;
+}
+
+void rpf_free(rpf_forest* f) { free_forest(f); }
+
+size_t rpf_workspace_bytes(const rpf_forest* f, int64_t m, int32_t K, int32_t for_all_knn) {
+  if (!f || K < 1 || K > RPF_MAX_K || m < 0) return 0;
+  return for_all_knn ? rpf_all_knn_ws(f, K) : rpf_query_ws(f, m, K);
+}
+
+int rpf_all_knn(rpf_forest* f, int32_t K, int32_t* idx, float* dist, void* workspace,
+                size_t ws_bytes, void* stream) {
+  if (!f || !idx || !dist || K < 1 || K > RPF_MAX_K) return RPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = f->n;
+  const bool dev_out = rpf_is_device_ptr(idx) && rpf_is_device_ptr(dist);
+  int32_t* di = idx;
+  float* dd = dist;
+  if (!dev_out) {
+    const size_t need = (size_t)n * K * 8;
+    if (f->stage_bytes < need) {
+      if (f->stage) cudaFree(f->stage);
+      f->stage = nullptr;
+      f->stage_bytes = 0;
+      if (cudaMalloc(&f->stage, need) != cudaSuccess) {
+        cudaGetLastError();
+        return RPF_ENOMEM;
+      }
+      f->stage_bytes = need;
+    }
+    di = (int32_t*)f->stage;
+    dd = (float*)((char*)f->stage + (size_t)n * K * 4);
+  }
+  void* ws = workspace;
+  size_t wsb = ws_bytes;
+  bool own_ws = false;
+  if (!ws) {
+    wsb = rpf_all_knn_ws(f, K);
+    if (cudaMallocAsync(&ws, wsb, s) != cudaSuccess) {
+      cudaGetLastError();
+      return RPF_ENOMEM;
+    }
+    own_ws = true;
+  }
+  int rc = rpf_all_knn_dev(f, K, di, dd, ws, wsb, s);
+  if (own_ws) cudaFreeAsync(ws, s);
+  if (rc) return rc;
+  if (!dev_out) {
+    RPF_CU(cudaMemcpyAsync(idx, di, (size_t)n * K * 4, cudaMemcpyDefault, s));
+    RPF_CU(cudaMemcpyAsync(dist, dd, (size_t)n * K * 4, cudaMemcpyDefault, s));
+    RPF_CU(cudaStreamSynchronize(s));
+  }
+  RPF_CU(cudaGetLastError());
+  return RPF_OK;
+}
+
+int rpf_query(const rpf_forest* f, const float* Q, int64_t m, int32_t K, int32_t* idx,
+              float* dist, void* workspace, size_t ws_bytes, void* stream) {
+  if (!f || K < 1 || K > RPF_MAX_K || m < 0) return RPF_EINVAL;
+  if (m == 0) return RPF_OK;
+  if (!Q || !idx || !dist) return RPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int T = f->prm.n_trees;
+  const size_t need = rpf_query_ws(f, m, K);
+  void* ws = workspace;
+  bool own_ws = false;
+  if (!ws) {
+    if (cudaMallocAsync(&ws, need, s) != cudaSuccess) {
+      cudaGetLastError();
+      return RPF_ENOMEM;
+    }
+    own_ws = true;
+  } else if (ws_bytes < need) {
+    return RPF_EINVAL;
+  }
+  auto a256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  char* w = (char*)ws;
+  const size_t core = a256((size_t)m * T * 4) + a256((size_t)T * m * K * 8);
+  float* dQ = (float*)(w + core);
+  int32_t* di = (int32_t*)(w + core + a256((size_t)m * f->d * 4));
+  float* dd = (float*)(w + core + a256((size_t)m * f->d * 4) + a256((size_t)m * K * 4));
+  const bool q_dev = rpf_is_device_ptr(Q);
+  const bool o_dev = rpf_is_device_ptr(idx) && rpf_is_device_ptr(dist);
+  int rc = RPF_OK;
+  cudaError_t e = cudaSuccess;
+  if (!q_dev) e = cudaMemcpyAsync(dQ, Q, (size_t)m * f->d * 4, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) {
+    rc = rpf_query_dev(f, q_dev ? Q : dQ, m, K, o_dev ? idx : di, o_dev ? dist : dd, ws, core, s);
+    if (!rc && !o_dev) {
+      e = cudaMemcpyAsync(idx, di, (size_t)m * K * 4, cudaMemcpyDefault, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dist, dd, (size_t)m * K * 4, cudaMemcpyDefault, s);
+    }
+  }
+  if (own_ws) cudaFreeAsync(ws, s);
+  if (!o_dev && e == cudaSuccess && !rc) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return rpf_cuda_err(e);
+  return rc;
+}
+
+int rpf_forest_info(const rpf_forest* f, int64_t* n, int32_t* d, int32_t* n_trees,
+                    int64_t* n_nodes, int64_t* n_leaves, int32_t* max_depth,
+                    int64_t* n_exact_nodes) {
+  if (!f) return RPF_EINVAL;
+  if (n) *n = f->n;
+  if (d) *d = f->d;
+  if (n_trees) *n_trees = f->prm.n_trees;
+  if (n_nodes) *n_nodes = f->n_nodes;
+  if (n_leaves) *n_leaves = f->n_leaves;
+  if (max_depth) *max_depth = f->max_depth;
+  if (n_exact_nodes) *n_exact_nodes = f->n_exact;
+  return RPF_OK;
+}
+
+int rpf_forest_perm(const rpf_forest* f, int32_t t, int32_t* perm_host) {
+  if (!f || !perm_host || t < 0 || t >= f->prm.n_trees) return RPF_EINVAL;
+  RPF_CU(cudaMemcpy(perm_host, f->perm + (int64_t)t * f->n, sizeof(int32_t) * f->n,
+                    cudaMemcpyDefault));
+  return RPF_OK;
+}
+
+int rpf_forest_leaves(const rpf_forest* f, int32_t* tree, int32_t* begin, int32_t* len) {
+  if (!f) return RPF_EINVAL;
+  const size_t b = sizeof(int32_t) * f->n_leaves;
+  if (tree) RPF_CU(cudaMemcpy(tree, f->leaf_tree, b, cudaMemcpyDefault));
+  if (begin) RPF_CU(cudaMemcpy(begin, f->leaf_begin, b, cudaMemcpyDefault));
+  if (len) RPF_CU(cudaMemcpy(len, f->leaf_len, b, cudaMemcpyDefault));
+  return RPF_OK;
+}
+
+int rpf_forest_nodes(const rpf_forest* f, uint64_t* key, int32_t* tree, int32_t* begin,
+                     int32_t* len, int32_t* left, int32_t* right, int32_t* jstar, int32_t* flag,
+                     double* c) {
+  if (!f) return RPF_EINVAL;
+  const size_t nn = (size_t)f->n_nodes;
+  if (key) RPF_CU(cudaMemcpy(key, f->node_key, 8 * nn, cudaMemcpyDefault));
+  if (tree) RPF_CU(cudaMemcpy(tree, f->node_tree, 4 * nn, cudaMemcpyDefault));
+  if (begin) RPF_CU(cudaMemcpy(begin, f->node_begin, 4 * nn, cudaMemcpyDefault));
+  if (len) RPF_CU(cudaMemcpy(len, f->node_len, 4 * nn, cudaMemcpyDefault));
+  if (left) RPF_CU(cudaMemcpy(left, f->node_left, 4 * nn, cudaMemcpyDefault));
+  if (right) RPF_CU(cudaMemcpy(right, f->node_right, 4 * nn, cudaMemcpyDefault));
+  if (jstar) RPF_CU(cudaMemcpy(jstar, f->node_jstar, 4 * nn, cudaMemcpyDefault));
+  if (flag) RPF_CU(cudaMemcpy(flag, f->node_flag, 4 * nn, cudaMemcpyDefault));
+  if (c) RPF_CU(cudaMemcpy(c, f->node_c, 8 * nn, cudaMemcpyDefault));
+  return RPF_OK;
+}
+
+int rpf_directions(uint64_t seed, int32_t t, const uint64_t* keys_host, int32_t n_keys, int32_t j,
+                   int32_t d, double* out, void* stream) {
+  if (!keys_host || !out || n_keys < 0 || d < 1 || d > RPF_MAX_D || j < 0) return RPF_EINVAL;
+  if (n_keys == 0) return RPF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint64_t* dk = nullptr;
+  double* dout = nullptr;
+  RPF_CU(cudaMallocAsync((void**)&dk, 8 * (size_t)n_keys, s));
+  const bool o_dev = rpf_is_device_ptr(out);
+  if (!o_dev) RPF_CU(cudaMallocAsync((void**)&dout, 8 * (size_t)n_keys * d, s));
+  RPF_CU(cudaMemcpyAsync(dk, keys_host, 8 * (size_t)n_keys, cudaMemcpyDefault, s));
+  rpf_launch_directions(seed, t, dk, n_keys, j, d, o_dev ? out : dout, s);
+  RPF_CU(cudaGetLastError());
+  if (!o_dev) RPF_CU(cudaMemcpyAsync(out, dout, 8 * (size_t)n_keys * d, cudaMemcpyDefault, s));
+  cudaFreeAsync(dk, s);
+  if (dout) cudaFreeAsync(dout, s);
+  RPF_CU(cudaStreamSynchronize(s));
+  return RPF_OK;
+}
+
+}  // extern "C"

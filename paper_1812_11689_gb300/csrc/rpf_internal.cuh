@@ -1,0 +1,236 @@
+// rpf_internal.cuh -- device helpers and the forest object of the GB300
+// rpForests library (arXiv 1812.11689).  Compiled with -fmad=false: every
+// fused multiply-add below is written out with __fma_rn / __fmaf_rn, so the
+// FP64 arithmetic that decides tree structure is the same sequence of IEEE
+// operations on every run.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "rpforest.h"
+
+#define RPF_GAMMA 0x9E3779B97F4A7C15ULL
+#define RPF_TAG_DIR 1ULL
+#define RPF_TAG_SPLIT 2ULL
+#define RPF_SPLIT_ATTEMPTS 8
+#define RPF_CHUNK 4096  // canonical reduction chunk; also the growth work chunk
+#define RPF_MAX_TRY 64
+#define RPF_MAX_D 4096
+#define RPF_MAX_K 128
+#define RPF_MAX_LEAF 1024  // a leaf is one CTA tile of at most 1024 rows
+#define RPF_FULL 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// Counter-based random numbers (Sec. 2 "generate a random direction" and
+// "c ~ runif[a, b]").  mix64 is the SplitMix64 output function (Steele, Lea &
+// Flood 2014); word() absorbs (tag, tree, node key, try/attempt, counter) into
+// the seed one field at a time.  Root key 1; child key = mix64(key ^ (1 +
+// side) * GAMMA), side 0 = left, 1 = right.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t rpf_mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint64_t rpf_word(uint64_t seed, uint64_t tag, uint64_t t,
+                                                      uint64_t key, uint64_t j, uint64_t c) {
+  uint64_t h = seed;
+  h = rpf_mix64((h ^ tag) + RPF_GAMMA);
+  h = rpf_mix64((h ^ t) + RPF_GAMMA);
+  h = rpf_mix64((h ^ key) + RPF_GAMMA);
+  h = rpf_mix64((h ^ j) + RPF_GAMMA);
+  h = rpf_mix64((h ^ c) + RPF_GAMMA);
+  return h;
+}
+
+__host__ __device__ __forceinline__ uint64_t rpf_child_key(uint64_t key, int side) {
+  return rpf_mix64(key ^ ((uint64_t)(1 + side) * RPF_GAMMA));
+}
+
+// u53 = (w >> 11) 2^-53 in [0, 1)
+__device__ __forceinline__ double rpf_u53(uint64_t w) {
+  return __dmul_rn((double)(w >> 11), 0x1p-53);
+}
+
+// ---------------------------------------------------------------------------
+// ln(u) for normal u > 0: u = m 2^e, m folded into [sqrt(2)/2, sqrt(2)],
+// ln m = 2 atanh(s) with s = (m - 1)/(m + 1) and the atanh Taylor series
+// s (1 + z/3 + ... + z^10/21), z = s^2 (|s| <= 0.1716).  Coefficients are the
+// IEEE quotients 1/(2k+1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double rpf_ln(double u) {
+  const double LN2 = 0.69314718055994530942;
+  const double SQRT2 = 1.41421356237309504880;
+  uint64_t b = (uint64_t)__double_as_longlong(u);
+  int e = (int)((b >> 52) & 0x7ff) - 1023;
+  uint64_t mb = (b & 0x000FFFFFFFFFFFFFULL) | 0x3FF0000000000000ULL;
+  double m = __longlong_as_double((long long)mb);
+  if (m > SQRT2) {
+    m = __dmul_rn(m, 0.5);
+    e += 1;
+  }
+  double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+  double z = __dmul_rn(s, s);
+  double p = __ddiv_rn(1.0, 21.0);
+#pragma unroll
+  for (int k = 9; k >= 0; --k) p = __fma_rn(p, z, __ddiv_rn(1.0, (double)(2 * k + 1)));
+  double h = __dmul_rn(s, p);
+  return __fma_rn((double)e, LN2, __dadd_rn(h, h));
+}
+
+// ---------------------------------------------------------------------------
+// cos(2 pi u), sin(2 pi u), u in [0, 1): quadrant q = floor(4u), theta =
+// (4u - q) pi/2, Taylor series of cos / sin to theta^22 / theta^23 with
+// coefficients (-1)^k / n!, n! formed as a running double product.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rpf_sincos2pi(double u, double* c_out, double* s_out) {
+  const double PI_2 = 1.57079632679489661923;
+  double inv[24];
+  double fact = 1.0;
+  inv[0] = 1.0;
+#pragma unroll
+  for (int n = 1; n <= 23; ++n) {
+    fact = __dmul_rn(fact, (double)n);
+    inv[n] = __ddiv_rn(1.0, fact);
+  }
+  double x = __dmul_rn(u, 4.0);
+  int q = (int)x;
+  double f = __dsub_rn(x, (double)q);
+  double th = __dmul_rn(f, PI_2);
+  double z = __dmul_rn(th, th);
+  double cs = -inv[22];  // k = 11: (-1)^11 / 22!
+  double sn = -inv[23];
+#pragma unroll
+  for (int k = 10; k >= 0; --k) {
+    cs = __fma_rn(cs, z, (k & 1) ? -inv[2 * k] : inv[2 * k]);
+    sn = __fma_rn(sn, z, (k & 1) ? -inv[2 * k + 1] : inv[2 * k + 1]);
+  }
+  sn = __dmul_rn(sn, th);
+  switch (q & 3) {
+    case 0: *c_out = cs; *s_out = sn; break;
+    case 1: *c_out = -sn; *s_out = cs; break;
+    case 2: *c_out = -cs; *s_out = -sn; break;
+    default: *c_out = sn; *s_out = -cs; break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Canonical FP64 warp sum of one chunk (<= 4096 values): lane l adds
+// v[l], v[l+32], ... in order from +0.0, then the lane sums are folded by
+// xor-butterfly 16, 8, 4, 2, 1 (lane 0 follows s_l += s_{l+off}).  Every lane
+// returns the result.  All 32 lanes must call it.
+// ---------------------------------------------------------------------------
+template <typename F>
+__device__ __forceinline__ double rpf_warp_chunk_sum(int64_t len, int lane, F val) {
+  double a = 0.0;
+  for (int64_t k = lane; k < len; k += 32) a = __dadd_rn(a, val(k));
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) a = __dadd_rn(a, __shfl_xor_sync(RPF_FULL, a, off));
+  return a;
+}
+
+// Order-preserving map of doubles to uint64 (for atomicMin / atomicMax).
+__device__ __forceinline__ unsigned long long rpf_dkey(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b & 0x8000000000000000ULL) ? ~b : (b | 0x8000000000000000ULL);
+}
+__device__ __forceinline__ double rpf_dkey_inv(unsigned long long k) {
+  unsigned long long b = (k & 0x8000000000000000ULL) ? (k & 0x7FFFFFFFFFFFFFFFULL) : ~k;
+  return __longlong_as_double((long long)b);
+}
+
+// Canonical FP32 squared distance (ranking key of every neighbour list).
+__device__ __forceinline__ float rpf_d32(const float* x, const float* y, int d) {
+  float s = 0.0f;
+  for (int k = 0; k < d; ++k) {
+    float e = __fsub_rn(x[k], y[k]);
+    s = __fmaf_rn(e, e, s);
+  }
+  return s;
+}
+
+// (d, i) < (e, j) in the neighbour order; index -1 means "empty" (+inf).
+__device__ __forceinline__ bool rpf_less(float d, int i, float e, int j) {
+  return d < e || (d == e && (unsigned)i < (unsigned)j);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct rpf_dbuf {  // owned device allocation
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct rpf_forest {
+  int64_t n = 0;
+  int32_t d = 0;
+  rpf_params prm{};
+  int device = 0;
+
+  float* X = nullptr;         // n x d
+  float* xnorm = nullptr;     // n: upper bound of |x|_2
+  int32_t* perm = nullptr;    // T x n final permutation
+
+  // node table (capacity nodes_cap)
+  int64_t n_nodes = 0, nodes_cap = 0;
+  uint64_t* node_key = nullptr;
+  int32_t* node_tree = nullptr;
+  int32_t* node_begin = nullptr;
+  int32_t* node_len = nullptr;
+  int32_t* node_left = nullptr;
+  int32_t* node_right = nullptr;
+  int32_t* node_jstar = nullptr;
+  int32_t* node_flag = nullptr;
+  double* node_c = nullptr;
+  double* node_dir = nullptr;  // n_nodes x d (FP64 r*), zeros for leaves
+  float* node_dir32 = nullptr; // n_nodes x d (FP32 copy for query filtering)
+
+  // leaves
+  int64_t n_leaves = 0;
+  int32_t* leaf_tree = nullptr;
+  int32_t* leaf_begin = nullptr;
+  int32_t* leaf_len = nullptr;
+  int32_t max_depth = 0;
+  int64_t n_exact = 0;  // nodes decided by the FP64 fallback
+
+  // all-kNN tiles (built once from the leaf table)
+  int32_t tile_rows = 0;
+  int64_t n_tiles = 0;
+  int32_t* tile_first = nullptr;  // first leaf of tile
+  int32_t* tile_count = nullptr;  // leaves in tile
+  int32_t max_leaf = 0;
+  std::vector<int64_t> tree_tile_begin;  // T + 1 (host): tiles of tree t
+
+  // staging for host outputs of rpf_all_knn
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+
+  std::vector<void*> owned;
+};
+
+#define RPF_CU(call)                                  \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return rpf_cuda_err(e_);   \
+  } while (0)
+
+int rpf_cuda_err(cudaError_t e);
+bool rpf_is_device_ptr(const void* p);
+
+// growth (rpf_grow.cu)
+int rpf_grow(rpf_forest* f, cudaStream_t s);
+// leaf tiles + merge + query (rpf_knn.cu)
+int rpf_build_tiles(rpf_forest* f, cudaStream_t s);
+int rpf_all_knn_dev(rpf_forest* f, int K, int32_t* idx, float* dist, void* ws, size_t ws_bytes,
+                    cudaStream_t s);
+int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t* idx, float* dist,
+                  void* ws, size_t ws_bytes, cudaStream_t s);
+size_t rpf_all_knn_ws(const rpf_forest* f, int K);
+size_t rpf_query_ws(const rpf_forest* f, int64_t m, int K);
+void rpf_launch_directions(uint64_t seed, int32_t t, const uint64_t* keys_dev, int32_t n_keys,
+                           int32_t j, int32_t d, double* out_dev, cudaStream_t s);

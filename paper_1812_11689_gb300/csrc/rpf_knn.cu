@@ -1,0 +1,408 @@
+// rpf_knn.cu -- distances inside every (tree, leaf) block and the cross-tree
+// merge of Algorithm 3 (Sec. 2): N_q is the union of q's leaves over the T
+// trees and its K closest points are the answer.  A point y in the K closest
+// of N_q has at most K-1 points of N_q before it, hence at most K-1 points of
+// any leaf containing it, so y is in that leaf's own top-K: merging per-leaf
+// top-K lists (deduplicated by index) gives exactly the top-K of the union.
+//
+//   k_leaf_plain   one CTA per tile of packed small leaves; every row scans its
+//                  leaf with the canonical FP32 d32 and keeps a sorted top-K
+//   k_merge        per point, merge the per-tree lists of a group of trees
+//                  into the running top-K (duplicates have identical keys
+//                  because d32 is symmetric and deterministic)
+//   k_route        drop each query through each tree (FP64 r* . q < c)
+//   k_qscan        per (query, tree): top-K of the leaf the query fell into
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "rpf_internal.cuh"
+
+namespace {
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Register-resident sorted top-K (ascending by (d, idx)); KMAX is a compile-
+// time capacity, K <= KMAX the runtime length.
+template <int KMAX>
+struct TopK {
+  float kd[KMAX];
+  int ki[KMAX];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) {
+      kd[q] = INFINITY;
+      ki[q] = -1;
+    }
+  }
+  __device__ __forceinline__ float worst_d(int K) const {
+    float w = kd[0];
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q)
+      if (q == K - 1) w = kd[q];
+    return w;
+  }
+  __device__ __forceinline__ int worst_i(int K) const {
+    int w = ki[0];
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q)
+      if (q == K - 1) w = ki[q];
+    return w;
+  }
+  // insert assuming (v, j) < entry K-1
+  __device__ __forceinline__ void insert(int K, float v, int j) {
+    bool done = false;
+#pragma unroll
+    for (int q = KMAX - 1; q >= 0; --q) {
+      if (q < K && !done) {
+        if (q > 0 && rpf_less(v, j, kd[q - 1], ki[q - 1])) {
+          kd[q] = kd[q - 1];
+          ki[q] = ki[q - 1];
+        } else {
+          kd[q] = v;
+          ki[q] = j;
+          done = true;
+        }
+      }
+    }
+  }
+  __device__ __forceinline__ bool contains(int K, int j) const {
+    bool f = false;
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) f |= (q < K) && (ki[q] == j);
+    return f;
+  }
+  __device__ __forceinline__ void offer(int K, float v, int j, float& wd, int& wi) {
+    if (rpf_less(v, j, wd, wi)) {
+      insert(K, v, j);
+      wd = worst_d(K);
+      wi = worst_i(K);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Plain leaf tiles.  Tile = consecutive leaves of one tree (sorted leaf list)
+// with at most blockDim rows.  Rows staged in shared memory when they fit.
+// cand layout: [(g * n + point) * K + k] as (d32 bits, idx).
+// ---------------------------------------------------------------------------
+template <int KMAX, bool SMEM>
+__global__ void __launch_bounds__(1024) k_leaf_plain(const int32_t* tile_first, const int32_t* tile_count,
+                             int64_t tile_base, const int32_t* leaf_tree,
+                             const int32_t* leaf_begin, const int32_t* leaf_len,
+                             const int32_t* perm, const float* X, int64_t n, int d, int K,
+                             int t0, uint2* cand) {
+  extern __shared__ float xs[];
+  __shared__ int leaf_off[1025];
+  const int64_t tile = tile_base + blockIdx.x;
+  const int lf0 = tile_first[tile], nl = tile_count[tile];
+  const int t = leaf_tree[lf0];
+  const int b0 = leaf_begin[lf0];
+  // leaves of a tile are consecutive in the tree's permutation (sorted by
+  // begin), so row r of the tile is permutation position b0 + r
+  for (int q = threadIdx.x; q < nl; q += blockDim.x) leaf_off[q] = leaf_begin[lf0 + q] - b0;
+  if (threadIdx.x == 0) leaf_off[nl] = leaf_begin[lf0 + nl - 1] + leaf_len[lf0 + nl - 1] - b0;
+  __syncthreads();
+  const int rows = leaf_off[nl];
+  const int32_t* prow = perm + (int64_t)t * n + b0;
+  const int dp = d + 1;
+  if (SMEM) {  // coalesced row copies, one warp per row
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = w; r < rows; r += nw) {
+      const float* src = X + (int64_t)prow[r] * d;
+      for (int k = l; k < d; k += 32) xs[r * dp + k] = src[k];
+    }
+    __syncthreads();
+  }
+  const int i = threadIdx.x;
+  if (i >= rows) return;
+  int lo = 0, hi = nl - 1;  // leaf of row i: last q with leaf_off[q] <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (leaf_off[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  const int lb = leaf_off[lo], le = leaf_off[lo + 1];
+  const int gi = prow[i];
+  TopK<KMAX> tk;
+  tk.init();
+  float wd = INFINITY;
+  int wi = -1;
+  const float* xi = SMEM ? xs + i * dp : X + (int64_t)gi * d;
+  for (int jr = lb; jr < le; ++jr) {
+    if (jr == i) continue;
+    const int gj = prow[jr];
+    const float* xj = SMEM ? xs + jr * dp : X + (int64_t)gj * d;
+    const float v = rpf_d32(xi, xj, d);
+    tk.offer(K, v, gj, wd, wi);
+  }
+  uint2* out = cand + ((int64_t)(t - t0) * n + gi) * K;
+#pragma unroll
+  for (int q = 0; q < KMAX; ++q)
+    if (q < K) out[q] = make_uint2(__float_as_uint(tk.kd[q]), (unsigned)tk.ki[q]);
+}
+
+// Merge G per-tree lists (sorted, padded with (inf, -1)) into the running list
+// of each point.  first: no running list yet; last: write the final outputs.
+template <int KMAX>
+__global__ void k_merge(int64_t n, int K, int G, const uint2* cand, uint2* run, bool first,
+                        bool last, int32_t* idx, float* dist) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  TopK<KMAX> tk;
+  tk.init();
+  if (!first) {
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q)
+      if (q < K) {
+        uint2 e = run[i * K + q];
+        tk.kd[q] = __uint_as_float(e.x);
+        tk.ki[q] = (int)e.y;
+      }
+  }
+  float wd = tk.worst_d(K);
+  int wi = tk.worst_i(K);
+  for (int g = 0; g < G; ++g) {
+    const uint2* c = cand + ((int64_t)g * n + i) * K;
+    for (int q = 0; q < K; ++q) {
+      const uint2 e = c[q];
+      const int j = (int)e.y;
+      if (j < 0) break;
+      const float v = __uint_as_float(e.x);
+      if (!rpf_less(v, j, wd, wi)) break;  // lists are sorted: nothing later fits
+      if (tk.contains(K, j)) continue;
+      tk.insert(K, v, j);
+      wd = tk.worst_d(K);
+      wi = tk.worst_i(K);
+    }
+  }
+  if (last) {
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q)
+      if (q < K) {
+        idx[i * K + q] = tk.ki[q];
+        dist[i * K + q] = tk.ki[q] < 0 ? INFINITY : __fsqrt_rn(tk.kd[q]);
+      }
+  } else {
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q)
+      if (q < K) run[i * K + q] = make_uint2(__float_as_uint(tk.kd[q]), (unsigned)tk.ki[q]);
+  }
+}
+
+// Drop query q through tree t: at a split node go left iff r* . q < c (FP64
+// canonical fma chain), at a rank-split node go left.  Output: leaf node id.
+__global__ void k_route(const float* Q, int64_t m, int d, int T, const int32_t* node_left,
+                        const int32_t* node_right, const int32_t* node_flag, const double* node_c,
+                        const double* node_dir, int32_t* qleaf) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= m * T) return;
+  const int64_t q = g / T;
+  const int t = (int)(g % T);
+  const float* x = Q + q * d;
+  int node = t;
+  while (node_left[node] >= 0) {
+    if (node_flag[node]) {
+      node = node_left[node];
+      continue;
+    }
+    const double* r = node_dir + (int64_t)node * d;
+    double p = 0.0;
+    for (int k = 0; k < d; ++k) p = __fma_rn((double)__ldg(x + k), r[k], p);
+    node = (p < node_c[node]) ? node_left[node] : node_right[node];
+  }
+  qleaf[g] = node;
+}
+
+template <int KMAX>
+__global__ void k_qscan(const float* Q, int64_t m, int d, int T, int K, const int32_t* qleaf,
+                        const int32_t* node_tree, const int32_t* node_begin,
+                        const int32_t* node_len, const int32_t* perm, const float* X, int64_t n,
+                        uint2* cand) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= m * T) return;
+  const int64_t q = g / T;
+  const int t = (int)(g % T);
+  const int leaf = qleaf[g];
+  const int b = node_begin[leaf], ln = node_len[leaf];
+  const int32_t* mem = perm + (int64_t)node_tree[leaf] * n + b;
+  const float* x = Q + q * d;
+  TopK<KMAX> tk;
+  tk.init();
+  float wd = INFINITY;
+  int wi = -1;
+  for (int a = 0; a < ln; ++a) {
+    const int j = mem[a];
+    const float v = rpf_d32(x, X + (int64_t)j * d, d);
+    tk.offer(K, v, j, wd, wi);
+  }
+  uint2* out = cand + ((int64_t)t * m + q) * K;
+#pragma unroll
+  for (int q2 = 0; q2 < KMAX; ++q2)
+    if (q2 < K) out[q2] = make_uint2(__float_as_uint(tk.kd[q2]), (unsigned)tk.ki[q2]);
+}
+
+template <int KMAX>
+void launch_leaf(const rpf_forest* f, int64_t tb, int64_t nt, int K, int t0, uint2* cand,
+                 cudaStream_t s) {
+  const int rows = f->tile_rows;
+  const size_t smem = sizeof(float) * (size_t)rows * (f->d + 1);
+  if (smem <= 200 * 1024) {
+    cudaFuncSetAttribute(k_leaf_plain<KMAX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_leaf_plain<KMAX, true><<<(unsigned)nt, rows, smem, s>>>(
+        f->tile_first, f->tile_count, tb, f->leaf_tree, f->leaf_begin, f->leaf_len, f->perm, f->X,
+        f->n, f->d, K, t0, cand);
+  } else {
+    k_leaf_plain<KMAX, false><<<(unsigned)nt, rows, 0, s>>>(
+        f->tile_first, f->tile_count, tb, f->leaf_tree, f->leaf_begin, f->leaf_len, f->perm, f->X,
+        f->n, f->d, K, t0, cand);
+  }
+}
+
+template <int KMAX>
+void launch_merge(int64_t n, int K, int G, const uint2* cand, uint2* run, bool first, bool last,
+                  int32_t* idx, float* dist, cudaStream_t s) {
+  k_merge<KMAX><<<nblk(n, 128), 128, 0, s>>>(n, K, G, cand, run, first, last, idx, dist);
+}
+
+template <int KMAX>
+void launch_qscan(const rpf_forest* f, const float* Q, int64_t m, int K, const int32_t* qleaf,
+                  uint2* cand, cudaStream_t s) {
+  const int T = f->prm.n_trees;
+  k_qscan<KMAX><<<nblk(m * T, 128), 128, 0, s>>>(Q, m, f->d, T, K, qleaf, f->node_tree,
+                                                 f->node_begin, f->node_len, f->perm, f->X, f->n,
+                                                 cand);
+}
+
+#define RPF_KDISPATCH(K, FN, ...)                 \
+  do {                                            \
+    if ((K) <= 8) FN<8>(__VA_ARGS__);             \
+    else if ((K) <= 16) FN<16>(__VA_ARGS__);      \
+    else if ((K) <= 32) FN<32>(__VA_ARGS__);      \
+    else if ((K) <= 64) FN<64>(__VA_ARGS__);      \
+    else FN<128>(__VA_ARGS__);                    \
+  } while (0)
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Work list: leaves sorted by tree (stable), then packed greedily into tiles of
+// at most tile_rows rows.  Built once per forest on the host from the leaf
+// table (a few hundred thousand entries at most).
+// ---------------------------------------------------------------------------
+int rpf_build_tiles(rpf_forest* f, cudaStream_t s) {
+  const int64_t nl = f->n_leaves;
+  const int T = f->prm.n_trees;
+  std::vector<int32_t> lt(nl), lb(nl), ll(nl);
+  RPF_CU(cudaMemcpyAsync(lt.data(), f->leaf_tree, 4 * nl, cudaMemcpyDeviceToHost, s));
+  RPF_CU(cudaMemcpyAsync(lb.data(), f->leaf_begin, 4 * nl, cudaMemcpyDeviceToHost, s));
+  RPF_CU(cudaMemcpyAsync(ll.data(), f->leaf_len, 4 * nl, cudaMemcpyDeviceToHost, s));
+  RPF_CU(cudaStreamSynchronize(s));
+  // counting sort by tree, then by begin within a tree (deterministic order)
+  std::vector<int64_t> order(nl);
+  for (int64_t i = 0; i < nl; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return lt[a] != lt[b] ? lt[a] < lt[b] : lb[a] < lb[b];
+  });
+  std::vector<int32_t> st(nl), sb(nl), sl(nl);
+  int32_t maxleaf = 1;
+  for (int64_t i = 0; i < nl; ++i) {
+    st[i] = lt[order[i]];
+    sb[i] = lb[order[i]];
+    sl[i] = ll[order[i]];
+    maxleaf = std::max(maxleaf, sl[i]);
+  }
+  int rows = ((maxleaf + 31) / 32) * 32;
+  rows = std::max(rows, 64);
+  rows = std::min(rows, 1024);
+  std::vector<int32_t> tf, tc;
+  std::vector<int64_t> ttb(T + 1, 0);
+  int64_t i = 0;
+  for (int t = 0; t < T; ++t) {
+    ttb[t] = (int64_t)tf.size();
+    while (i < nl && st[i] == t) {
+      int r = 0, c = 0;
+      const int64_t first = i;
+      while (i < nl && st[i] == t && r + sl[i] <= rows) {
+        r += sl[i];
+        ++c;
+        ++i;
+      }
+      if (c == 0) return RPF_EINTERNAL;  // a leaf larger than a tile
+      tf.push_back((int32_t)first);
+      tc.push_back(c);
+    }
+  }
+  ttb[T] = (int64_t)tf.size();
+  RPF_CU(cudaMemcpyAsync(f->leaf_tree, st.data(), 4 * nl, cudaMemcpyHostToDevice, s));
+  RPF_CU(cudaMemcpyAsync(f->leaf_begin, sb.data(), 4 * nl, cudaMemcpyHostToDevice, s));
+  RPF_CU(cudaMemcpyAsync(f->leaf_len, sl.data(), 4 * nl, cudaMemcpyHostToDevice, s));
+  const int64_t ntl = (int64_t)tf.size();
+  if (f->tile_first) cudaFree(f->tile_first);
+  if (f->tile_count) cudaFree(f->tile_count);
+  RPF_CU(cudaMalloc((void**)&f->tile_first, 4 * std::max<int64_t>(ntl, 1)));
+  RPF_CU(cudaMalloc((void**)&f->tile_count, 4 * std::max<int64_t>(ntl, 1)));
+  RPF_CU(cudaMemcpyAsync(f->tile_first, tf.data(), 4 * ntl, cudaMemcpyHostToDevice, s));
+  RPF_CU(cudaMemcpyAsync(f->tile_count, tc.data(), 4 * ntl, cudaMemcpyHostToDevice, s));
+  RPF_CU(cudaStreamSynchronize(s));
+  f->tile_rows = rows;
+  f->n_tiles = ntl;
+  f->max_leaf = maxleaf;
+  f->tree_tile_begin.assign(ttb.begin(), ttb.end());
+  return RPF_OK;
+}
+
+size_t rpf_all_knn_ws(const rpf_forest* f, int K) {
+  const int64_t n = f->n;
+  const int T = f->prm.n_trees;
+  return align256((size_t)T * n * K * 8) + align256((size_t)n * K * 8);
+}
+
+int rpf_all_knn_dev(rpf_forest* f, int K, int32_t* idx, float* dist, void* ws, size_t ws_bytes,
+                    cudaStream_t s) {
+  const int64_t n = f->n;
+  const int T = f->prm.n_trees;
+  const size_t run_b = align256((size_t)n * K * 8);
+  const size_t per_tree = (size_t)n * K * 8;
+  if (ws_bytes < run_b + align256(per_tree)) return RPF_EINVAL;
+  int G = (int)std::min<int64_t>(T, (int64_t)((ws_bytes - run_b) / per_tree));
+  while (G > 1 && align256((size_t)G * per_tree) + run_b > ws_bytes) --G;
+  uint2* run = (uint2*)ws;
+  uint2* cand = (uint2*)((char*)ws + run_b);
+  for (int t0 = 0; t0 < T; t0 += G) {
+    const int g = std::min(G, T - t0);
+    const int64_t tb = f->tree_tile_begin[t0];
+    const int64_t nt = f->tree_tile_begin[t0 + g] - tb;
+    if (nt > 0) RPF_KDISPATCH(K, launch_leaf, f, tb, nt, K, t0, cand, s);
+    const bool first = t0 == 0, last = t0 + g >= T;
+    RPF_KDISPATCH(K, launch_merge, n, K, g, cand, run, first, last, idx, dist, s);
+  }
+  RPF_CU(cudaGetLastError());
+  return RPF_OK;
+}
+
+size_t rpf_query_ws(const rpf_forest* f, int64_t m, int K) {
+  const int T = f->prm.n_trees;
+  return align256((size_t)m * T * 4) + align256((size_t)T * m * K * 8) +
+         align256((size_t)m * f->d * 4) + align256((size_t)m * K * 4) +
+         align256((size_t)m * K * 4);
+}
+
+int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t* idx,
+                  float* dist, void* ws, size_t ws_bytes, cudaStream_t s) {
+  const int T = f->prm.n_trees;
+  if (ws_bytes < align256((size_t)m * T * 4) + align256((size_t)T * m * K * 8)) return RPF_EINVAL;
+  int32_t* qleaf = (int32_t*)ws;
+  uint2* cand = (uint2*)((char*)ws + align256((size_t)m * T * 4));
+  k_route<<<nblk(m * T, 128), 128, 0, s>>>(Q, m, f->d, T, f->node_left, f->node_right,
+                                           f->node_flag, f->node_c, f->node_dir, qleaf);
+  RPF_KDISPATCH(K, launch_qscan, f, Q, m, K, qleaf, cand, s);
+  RPF_KDISPATCH(K, launch_merge, m, K, T, cand, nullptr, true, true, idx, dist, s);
+  RPF_CU(cudaGetLastError());
+  return RPF_OK;
+}

@@ -1,0 +1,155 @@
+"""Python face of the rpForests CUDA library: the same calls as the C ABI.
+
+``Forest(X, ...)`` -> rpf_build, ``.all_knn(K)`` -> rpf_all_knn,
+``.query(Q, K)`` -> rpf_query, ``.close()`` -> rpf_free.  Tensors are passed
+by pointer; torch supplies device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, rpf_params
+
+FORM_PLAIN, FORM_CHOSEN = 0, 1
+GROWTH_DEFAULT, GROWTH_FP64, GROWTH_CERTIFIED = 0, 1, 2
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t) -> int:
+    if isinstance(t, torch.Tensor):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    raise TypeError("expected a torch.Tensor or numpy.ndarray")
+
+
+def _as_points(X):
+    if isinstance(X, np.ndarray):
+        X = np.ascontiguousarray(X, np.float32)
+        if X.ndim != 2:
+            raise ValueError("points must be a 2-D array")
+        return X
+    if not isinstance(X, torch.Tensor) or X.dim() != 2:
+        raise ValueError("points must be a 2-D tensor")
+    if X.dtype != torch.float32:
+        X = X.float()
+    return X.contiguous()
+
+
+class Forest:
+    """T random projection trees over X (n x d, float32; device or host)."""
+
+    def __init__(self, X, n_trees: int = 10, leaf_max: int = 50, n_try: int = 5,
+                 form: int = FORM_PLAIN, growth: int = GROWTH_DEFAULT, seed: int = 0,
+                 stream=None):
+        X = _as_points(X)
+        self.n, self.d = int(X.shape[0]), int(X.shape[1])
+        self.params = rpf_params(n_trees, leaf_max, n_try, 0, form, growth, seed)
+        h = ctypes.c_void_p()
+        check(_lib.lib().rpf_build(_ptr(X), self.n, self.d, ctypes.byref(self.params),
+                                   _stream_handle(stream), ctypes.byref(h)), "rpf_build")
+        self._h = h
+
+    # ---- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib().rpf_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    # ---- search -------------------------------------------------------------
+    def workspace_bytes(self, K: int, m: int = 0, all_knn: bool = True) -> int:
+        return int(_lib.lib().rpf_workspace_bytes(self._h, m, K, 1 if all_knn else 0))
+
+    def all_knn(self, K: int, idx=None, dist=None, workspace=None, stream=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if idx is None:
+            idx = torch.empty((self.n, K), dtype=torch.int32, device=dev)
+        if dist is None:
+            dist = torch.empty((self.n, K), dtype=torch.float32, device=dev)
+        ws, wsb = (0, 0) if workspace is None else (_ptr(workspace), workspace.numel()
+                                                     * workspace.element_size())
+        check(_lib.lib().rpf_all_knn(self._h, K, _ptr(idx), _ptr(dist), ws or None, wsb,
+                                     _stream_handle(stream)), "rpf_all_knn")
+        return idx, dist
+
+    def query(self, Q, K: int, idx=None, dist=None, workspace=None, stream=None):
+        Q = _as_points(Q)
+        m = int(Q.shape[0])
+        on_dev = isinstance(Q, torch.Tensor) and Q.is_cuda
+        if idx is None:
+            idx = (torch.empty((m, K), dtype=torch.int32, device=Q.device) if on_dev
+                   else np.empty((m, K), np.int32))
+        if dist is None:
+            dist = (torch.empty((m, K), dtype=torch.float32, device=Q.device) if on_dev
+                    else np.empty((m, K), np.float32))
+        ws, wsb = (0, 0) if workspace is None else (_ptr(workspace), workspace.numel()
+                                                     * workspace.element_size())
+        check(_lib.lib().rpf_query(self._h, _ptr(Q) if m else None, m, K,
+                                   _ptr(idx) if m else None, _ptr(dist) if m else None,
+                                   ws or None, wsb, _stream_handle(stream)), "rpf_query")
+        return idx, dist
+
+    # ---- inspection ------------------------------------------------------------
+    def info(self) -> dict:
+        n, d, T, nn, nl, md, ne = (ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(),
+                                   ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(),
+                                   ctypes.c_int64())
+        check(_lib.lib().rpf_forest_info(self._h, *(ctypes.byref(v) for v in
+                                                    (n, d, T, nn, nl, md, ne))), "info")
+        return {"n": n.value, "d": d.value, "n_trees": T.value, "n_nodes": nn.value,
+                "n_leaves": nl.value, "max_depth": md.value, "n_exact_nodes": ne.value}
+
+    def perm(self, t: int) -> np.ndarray:
+        out = np.empty(self.n, np.int32)
+        check(_lib.lib().rpf_forest_perm(self._h, t, out.ctypes.data), "perm")
+        return out
+
+    def leaves(self):
+        nl = self.info()["n_leaves"]
+        tr, b, ln = (np.empty(nl, np.int32) for _ in range(3))
+        check(_lib.lib().rpf_forest_leaves(self._h, tr.ctypes.data, b.ctypes.data,
+                                           ln.ctypes.data), "leaves")
+        return tr, b, ln
+
+    def nodes(self) -> dict:
+        nn = self.info()["n_nodes"]
+        key = np.empty(nn, np.uint64)
+        i32 = {k: np.empty(nn, np.int32) for k in ("tree", "begin", "len", "left", "right",
+                                                    "jstar", "flag")}
+        c = np.empty(nn, np.float64)
+        check(_lib.lib().rpf_forest_nodes(self._h, key.ctypes.data, *(i32[k].ctypes.data for k in
+                                          ("tree", "begin", "len", "left", "right", "jstar",
+                                           "flag")), c.ctypes.data), "nodes")
+        out = {"key": key, "c": c}
+        out.update(i32)
+        return out
+
+
+def directions(seed: int, t: int, keys, j: int, d: int, stream=None) -> np.ndarray:
+    """Candidate directions of Algorithm 2 for (tree t, node keys, try j), on the GPU."""
+    keys = np.ascontiguousarray(keys, np.uint64)
+    out = np.empty((keys.size, d), np.float64)
+    check(_lib.lib().rpf_directions(seed, t, keys.ctypes.data, keys.size, j, d, out.ctypes.data,
+                                    _stream_handle(stream)), "rpf_directions")
+    return out

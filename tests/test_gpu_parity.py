@@ -1,0 +1,253 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bit-exact: candidate directions, every tree's permutation and leaf table, the
+split records (chosen try, split point, rank-split flag) keyed by node key,
+and the neighbour indices; distances bit-exact against the oracle's FP32 key
+and within 1e-5 relative of FP64 (the tolerance the method's FP32 distance
+key guarantees: (d + 3) 2^-24 < 1e-5 for d <= 128).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1812_11689_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL_FP64 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1812_11689_gb300 import build
+    build.build()
+
+
+def F(*a, **k):
+    from paper_1812_11689_gb300 import forest
+    return forest.Forest(*a, **k)
+
+
+def gpu_forest(X, T, L, ntry, seed=0, growth=0, form=0):
+    return F(torch.from_numpy(np.ascontiguousarray(X)).cuda(), n_trees=T, leaf_max=L,
+             n_try=ntry, seed=seed, growth=growth, form=form)
+
+
+def compare_trees(g, o, T):
+    nodes = g.nodes()
+    for t in range(T):
+        assert np.array_equal(g.perm(t), o.perm(t)), "perm of tree %d differs" % t
+    tr, b, ln = g.leaves()
+    for t in range(T):
+        ob, ol = o.leaves(t)
+        sel = tr == t
+        order = np.argsort(b[sel])
+        assert np.array_equal(b[sel][order], ob) and np.array_equal(ln[sel][order], ol)
+    # split records keyed by (tree, node key)
+    gi = {}
+    for i in range(len(nodes["key"])):
+        if nodes["left"][i] >= 0:
+            gi[(int(nodes["tree"][i]), int(nodes["key"][i]))] = (
+                int(nodes["jstar"][i]), int(nodes["flag"][i]), nodes["c"][i])
+    count = 0
+    for t in range(T):
+        on = o.nodes(t)
+        for i in np.where(on["leaf"] == 0)[0]:
+            js, fl, c = gi[(t, int(on["key"][i]))]
+            assert js == int(on["jstar"][i]) and fl == int(on["flag"][i])
+            if not fl:
+                assert c == on["c"][i]
+            count += 1
+    assert count == len(gi)
+
+
+@pytest.mark.parametrize("d", [1, 2, 10, 64, 127])
+def test_directions_bit_exact(d):
+    from paper_1812_11689_gb300 import forest
+    rng = np.random.default_rng(d)
+    keys = np.concatenate([[1], rng.integers(0, 2 ** 63, 300, dtype=np.int64).astype(np.uint64)])
+    for t, j in ((0, 0), (7, 3)):
+        g = forest.directions(11, t, keys, j, d)
+        o = np.stack([oracle.direction(11, t, int(k), j, d) for k in keys])
+        assert np.array_equal(g.view(np.uint64), o.view(np.uint64))
+
+
+@pytest.mark.parametrize("growth", [1, 2])
+def test_trees_bit_exact_mix5(growth):
+    X = synth.make("mix5_d10")
+    g = gpu_forest(X, 10, 50, 5, growth=growth)
+    o = oracle.Forest(X, 10, 50, 5, seed=0)
+    compare_trees(g, o, 10)
+
+
+@pytest.mark.parametrize("name,n,L,ntry", [("aniso20_d64", 20000, 128, 5),
+                                           ("student3_d32", 20000, 64, 5),
+                                           ("subspace16_d128", 8000, 256, 3),
+                                           ("mix50_d96", 9000, 128, 1)])
+def test_trees_bit_exact_workload_shapes(name, n, L, ntry):
+    X = synth.make(name, n=n)
+    o = oracle.Forest(X, 4, L, ntry, seed=5)
+    for growth in (1, 2):
+        g = gpu_forest(X, 4, L, ntry, seed=5, growth=growth)
+        compare_trees(g, o, 4)
+
+
+def test_growth_modes_agree_and_certification_skips_fp64():
+    X = synth.make("aniso20_d64", n=30000)
+    a = gpu_forest(X, 6, 128, 5, growth=1)
+    b = gpu_forest(X, 6, 128, 5, growth=2)
+    for t in range(6):
+        assert np.array_equal(a.perm(t), b.perm(t))
+    ia, ib = a.info(), b.info()
+    assert ia["n_nodes"] == ib["n_nodes"]
+    # FP64 fallback only for a minority of nodes under certification
+    assert ib["n_exact_nodes"] < 0.25 * (ib["n_nodes"] - ib["n_leaves"])
+    assert ia["n_exact_nodes"] == ia["n_nodes"] - ia["n_leaves"]
+
+
+def check_knn(gi, gd, oi, od, X, rows=None):
+    assert np.array_equal(gi, oi)
+    assert np.array_equal(gd, od)
+    # distances vs FP64 (non-padded slots)
+    rows = np.arange(len(gi)) if rows is None else rows
+    ok = gi >= 0
+    xi = X[np.repeat(rows, gi.shape[1])[ok.ravel()]].astype(np.float64)
+    xj = X[gi[ok]].astype(np.float64)
+    d64 = np.sqrt(((xi - xj) ** 2).sum(1))
+    rel = np.abs(gd[ok].astype(np.float64) - d64) / np.maximum(d64, 1e-30)
+    assert rel.max() <= REL_TOL_FP64
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_all_knn_bit_exact_mix5(form):
+    X = synth.make("mix5_d10")
+    g = gpu_forest(X, 10, 50, 5, form=form)
+    gi, gd = g.all_knn(5)
+    o = oracle.Forest(X, 10, 50, 5, seed=0)
+    oi, od = o.all_knn(5)
+    check_knn(gi.cpu().numpy(), gd.cpu().numpy(), oi, od, X)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_all_knn_bit_exact_aniso_subsample(form):
+    X = synth.make("aniso20_d64", n=20000)
+    g = gpu_forest(X, 8, 128, 5, form=form)
+    gi, gd = g.all_knn(10)
+    o = oracle.Forest(X, 8, 128, 5, seed=0)
+    oi, od = o.all_knn(10)
+    check_knn(gi.cpu().numpy(), gd.cpu().numpy(), oi, od, X)
+
+
+@pytest.mark.parametrize("K", [1, 7, 16, 20, 33, 128])
+def test_all_knn_k_range_and_grouped_workspace(K):
+    X = synth.make("subspace16_d128", n=3000)
+    g = gpu_forest(X, 5, 200, 3)
+    o = oracle.Forest(X, 5, 200, 3, seed=0)
+    oi, od = o.all_knn(K)
+    gi, gd = g.all_knn(K)
+    check_knn(gi.cpu().numpy(), gd.cpu().numpy(), oi, od, X)
+    # a workspace with room for two trees at a time gives the same lists
+    ws_b = (2 * 3000 * K * 8 + 255) // 256 * 256 + (3000 * K * 8 + 255) // 256 * 256
+    ws = torch.empty(ws_b, dtype=torch.uint8, device="cuda")
+    hi, hd = g.all_knn(K, workspace=ws)
+    assert torch.equal(hi, gi) and torch.equal(hd, gd)
+
+
+def test_host_buffers_match_device_buffers():
+    X = synth.make("mix5_d10", n=1500)
+    g = F(X, n_trees=6, leaf_max=40, n_try=3, seed=2)  # host input
+    hi = np.empty((1500, 6), np.int32)
+    hd = np.empty((1500, 6), np.float32)
+    g.all_knn(6, idx=hi, dist=hd)
+    di, dd = g.all_knn(6)
+    assert np.array_equal(hi, di.cpu().numpy()) and np.array_equal(hd, dd.cpu().numpy())
+    o = oracle.Forest(X, 6, 40, 3, seed=2)
+    oi, od = o.all_knn(6)
+    assert np.array_equal(hi, oi)
+
+
+def test_query_matches_oracle_and_routes_build_points():
+    X = synth.make("aniso20_d64", n=12000)
+    Q = synth.queries("aniso20_d64", 700)
+    g = gpu_forest(X, 6, 128, 5)
+    o = oracle.Forest(X, 6, 128, 5, seed=0)
+    for K in (1, 10, 50):
+        qi, qd = g.query(torch.from_numpy(Q).cuda(), K)
+        oi, od = o.query(Q, K)
+        assert np.array_equal(qi.cpu().numpy(), oi) and np.array_equal(qd.cpu().numpy(), od)
+    # host queries, host outputs
+    hi, hd = g.query(Q[:100], 10)
+    oi, od = o.query(Q[:100], 10)
+    assert np.array_equal(hi, oi) and np.array_equal(hd, od)
+    # a data point routed through the forest lands in its own leaves: its
+    # query answer is its all-kNN answer with itself at distance 0 in front
+    ai, ad = g.all_knn(9)
+    qi, qd = g.query(torch.from_numpy(X[:500]).cuda(), 10)
+    qi, qd, ai = qi.cpu().numpy(), qd.cpu().numpy(), ai.cpu().numpy()
+    dup = {tuple(r) for r in X[:500]}
+    for i in range(500):
+        if qd[i, 1] == 0.0:  # an exact duplicate of point i exists; order by index
+            continue
+        assert qi[i, 0] == i and qd[i, 0] == 0.0
+        assert np.array_equal(qi[i, 1:], ai[i])
+    assert len(dup) > 0
+    # empty query set
+    ei, ed = g.query(torch.empty((0, 64), device="cuda"), 5)
+    assert ei.shape == (0, 5)
+
+
+def test_single_leaf_forest_is_exact_knn():
+    X = synth.make("mix5_d10", n=700)
+    g = gpu_forest(X, 2, 700, 5)
+    gi, gd = g.all_knn(7)
+    bi, bd, _ = oracle.brute_knn(X, 7)
+    assert np.array_equal(gi.cpu().numpy(), bi) and np.array_equal(gd.cpu().numpy(), bd)
+
+
+def test_degenerate_inputs():
+    # all points identical: every split is a rank split
+    X = np.ones((600, 5), np.float32)
+    for growth in (1, 2):
+        g = gpu_forest(X, 3, 16, 3, growth=growth)
+        o = oracle.Forest(X, 3, 16, 3, seed=0)
+        compare_trees(g, o, 3)
+        gi, gd = g.all_knn(3)
+        oi, od = o.all_knn(3)
+        assert np.array_equal(gi.cpu().numpy(), oi) and np.array_equal(gd.cpu().numpy(), od)
+    # duplicates and a constant column
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((3000, 6)).astype(np.float32)
+    X[:, 2] = 7.0
+    X[100:400] = X[0]
+    g = gpu_forest(X, 4, 20, 4)
+    o = oracle.Forest(X, 4, 20, 4, seed=0)
+    compare_trees(g, o, 4)
+    gi, gd = g.all_knn(5)
+    oi, od = o.all_knn(5)
+    assert np.array_equal(gi.cpu().numpy(), oi) and np.array_equal(gd.cpu().numpy(), od)
+    # d = 1
+    X = rng.standard_normal((5000, 1)).astype(np.float32)
+    g = gpu_forest(X, 3, 30, 2)
+    o = oracle.Forest(X, 3, 30, 2, seed=0)
+    compare_trees(g, o, 3)
+
+
+@pytest.mark.parametrize("n,K", [(1, 1), (2, 3), (5, 8)])
+def test_tiny_inputs_pad(n, K):
+    X = synth.make("mix5_d10", n=max(n, 1))[:n]
+    g = gpu_forest(X, 3, 1, 2)
+    gi, gd = g.all_knn(K)
+    o = oracle.Forest(X, 3, 1, 2, seed=0)
+    oi, od = o.all_knn(K)
+    assert np.array_equal(gi.cpu().numpy(), oi) and np.array_equal(gd.cpu().numpy(), od)
+    assert np.all(gi.cpu().numpy()[:, n - 1:] == -1)
+
+
+def test_ragged_large_node_multi_chunk():
+    # one tree whose root spans many 4096-position chunks with a ragged tail
+    X = synth.make("student3_d32", n=4096 * 5 + 77)
+    o = oracle.Forest(X, 2, 1000, 7, seed=3)
+    for growth in (1, 2):
+        g = gpu_forest(X, 2, 1000, 7, seed=3, growth=growth)
+        compare_trees(g, o, 2)
