@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""All-kNN throughput of the GB300 rpForests library (one JSON line).
+
+A step is one pass of the whole hot path over one synthetic data set: grow T
+random projection trees (rpf_build) and answer all-kNN for every point
+(rpf_all_knn).  value = points answered per second (n / step time), inputs
+resident in HBM, L2 flushed between steps.  e2e = the same through the C ABI
+with host buffers (pinned X in, pinned idx/dist out, copies inside the timed
+region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the CPU oracle (the plain C restatement of the paper's
+algorithms) on the host cores, on a bounded sample of the same workload, and
+scales it to the full workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="aniso20_d64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--profile-step", action="store_true",
+                    help="one warm-up step and one step of the chosen form, nothing else "
+                         "(the command the ncu summaries under profiles/ are taken from)")
+    return ap.parse_args()
+
+
+def dist_env():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            j = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm_bandwidth_gbs"):
+                if k in j:
+                    return float(j[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(X, w, threads, t_sample=16, rows_sample=20000, seed=0):
+    import oracle
+    oracle.build()
+    n = X.shape[0]
+    Ts = min(t_sample, w.n_trees)
+    t0 = time.perf_counter()
+    F = oracle.Forest(X, Ts, w.leaf_max, w.n_try, seed=seed, threads=threads)
+    t_grow = time.perf_counter() - t0
+    rows = np.random.default_rng(seed).choice(n, size=min(rows_sample, n), replace=False)
+    rows = np.sort(rows).astype(np.int32)
+    t0 = time.perf_counter()
+    F.all_knn_rows(rows, w.k)
+    t_rows = time.perf_counter() - t0
+    # growth cost is linear in T (trees are independent); search cost is
+    # linear in the answered rows and in T (union size ~ T leaves)
+    t_full = t_grow * (w.n_trees / Ts) + t_rows * (n / len(rows)) * (w.n_trees / Ts)
+    sample = ("%d of %d trees grown on all %d points, all-kNN for %d sampled points over "
+              "those trees; scaled by trees and points" % (Ts, w.n_trees, n, len(rows)))
+    return {"value": n / t_full, "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": sample, "sample_seconds": t_grow + t_rows, "scaled_seconds": t_full}
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.strip().splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def roofline(trace, w, fo, n, hbm_peak, peak_kind):
+    """Roofline of the kernel with the largest share of the timed steps."""
+    if not trace:
+        return None, None
+    top = max(trace, key=lambda k: trace[k]["ms"])
+    t = trace[top]
+    nodes = fo.nodes()
+    internal = nodes["left"] >= 0
+    active = int(nodes["len"][internal].sum())  # point-levels projected per build
+    d, T, K, nt = w.d, w.n_trees, w.k, w.n_try
+    # algorithmic bytes per build / per all-kNN for each kernel
+    per_step = {
+        "k_proj32": active * (4 * d + 4 + 4 + 4 * nt),       # X row, perm, |x|, p32 out
+        "k_proj64": active * (4 * d + 4 + 8 * nt),
+        "k_side_count": active * (4 + 4 + 1),                 # p32*, perm, side
+        "k_scatter": active * (1 + 4 + 4),                    # side, perm in, perm out
+        "k_var32": active * (4 * nt),
+        "k_leaf_plain": n * T * (4 * d + 4 + 8 * K),          # rows, perm, per-tree lists
+        "k_leaf_bf16": n * T * (4 * d + 4 + 8 * K),
+        "k_merge": n * (T * 8 * K + 8 * K),                   # per-tree lists, outputs
+    }
+    steps = t.get("steps", 1)
+    bytes_total = per_step.get(top)
+    if bytes_total is None:
+        return top, None
+    bytes_per_launch = bytes_total * steps / t["launches"]
+    ms_per_launch = t["ms"] / t["launches"]
+    ach = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9
+    return top, {"kernel": top, "bound": "hbm", "achieved": round(ach, 1),
+                 "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+                 "peak_source": peak_kind, "traffic": None,
+                 "algorithmic_bytes_per_launch": int(bytes_per_launch),
+                 "ms_per_launch": round(ms_per_launch, 5), "launches": t["launches"],
+                 "share": None}
+
+
+def run_gb300(args, rank, world, local_rank):
+    import torch
+    from paper_1812_11689_gb300 import forest, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.WORKLOADS[args.workload]
+    X = synth.make(args.workload, seed=args.seed + rank)
+    n, d = X.shape
+    Xd = torch.from_numpy(X).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+    kw = dict(n_trees=w.n_trees, leaf_max=w.leaf_max, n_try=w.n_try, seed=args.seed)
+    ws = {}
+
+    def step(form):
+        f = forest.Forest(Xd, form=form, **kw)
+        if form not in ws:
+            ws[form] = torch.empty(f.workspace_bytes(w.k), dtype=torch.uint8, device=dev)
+        out = f.all_knn(w.k, workspace=ws[form])
+        return f, out
+
+    def timed(form, K, trace=False):
+        times, b_ms, a_ms = [], [], []
+        for _ in range(K):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            f = forest.Forest(Xd, form=form, **kw)
+            e1.record(stream)
+            f.all_knn(w.k, workspace=ws[form])
+            e2.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e2))
+            b_ms.append(e0.elapsed_time(e1))
+            a_ms.append(e1.elapsed_time(e2))
+            f.close()
+        return times, b_ms, a_ms
+
+    chosen, plain = forest.FORM_CHOSEN, forest.FORM_PLAIN
+    for _ in range(args.warmup):
+        for form in (chosen, plain):
+            f, _ = step(form)
+            f.close()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    forest.Trace.read()
+    forest.Trace.enable(True)
+    l0 = forest.Trace.launch_count()
+    times, b_ms, a_ms = timed(chosen, args.steps, trace=True)
+    l1 = forest.Trace.launch_count()
+    forest.Trace.enable(False)
+    trace = forest.Trace.read()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * n / (ms_step * 1e-3)
+
+    # plain FP32 form on the same workload
+    p_times, p_b, p_a = timed(plain, args.steps)
+    p_ms = sum(p_times) / len(p_times)
+
+    # end to end through the C ABI with host buffers
+    Xh = torch.from_numpy(X).pin_memory()
+    ih = torch.empty((n, w.k), dtype=torch.int32).pin_memory()
+    dh = torch.empty((n, w.k), dtype=torch.float32).pin_memory()
+    e2e_t = []
+    for it in range(args.steps + 1):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = forest.Forest(Xh, form=chosen, **kw)
+        f.all_knn(w.k, idx=ih, dist=dh, workspace=ws[chosen])
+        torch.cuda.synchronize()
+        if it:
+            e2e_t.append(time.perf_counter() - t0)
+        f.close()
+    e2e_s = sum(e2e_t) / len(e2e_t)
+
+    # accuracy: chosen == plain bit for bit; missing rate vs exact brute force
+    fc, (ci, cd) = step(chosen)
+    fp, (pi, pd) = step(plain)
+    same = bool(torch.equal(ci, pi) and torch.equal(cd, pd))
+    rows = torch.from_numpy(np.sort(np.random.default_rng(1).choice(n, 2000, replace=False))
+                            .astype(np.int32)).to(dev)
+    bi, bd = forest.brute_knn(Xd, Xd[rows.long()].contiguous(), w.k, self_idx=rows)
+    ci_s, cd_s = ci[rows.long()].cpu().numpy(), cd[rows.long()].cpu().numpy()
+    bi, bd = bi.cpu().numpy(), bd.cpu().numpy()
+    miss = sum(len(set(bi[r]) - set(ci_s[r])) for r in range(len(bi))) / float(bi.size)
+    disc = float((cd_s[:, -1].mean() - bd[:, -1].mean()) / bd[:, -1].mean())
+    info = fc.info()
+
+    hbm_peak, peak_kind = peaks()
+    for k in trace:
+        trace[k]["steps"] = args.steps
+    top, roof = roofline(trace, w, fc, n, hbm_peak, peak_kind)
+    if roof is not None:
+        tot = sum(v["ms"] for v in trace.values())
+        roof["share"] = round(trace[top]["ms"] / tot, 4) if tot else None
+    fc.close()
+    fp.close()
+
+    line = {
+        "metric": "all-kNN queries/s at <=1% missing rate (chosen vs plain FP32 form)",
+        "value": round(value, 1),
+        "unit": "queries/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "d": d, "n_trees": w.n_trees,
+                   "leaf_max": w.leaf_max, "k": w.k, "n_try": w.n_try, "form": "chosen",
+                   "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "stage_ms": {"build": round(sum(b_ms) / len(b_ms), 3),
+                     "all_knn": round(sum(a_ms) / len(a_ms), 3)},
+        "plain": {"value": round(world * n / (p_ms * 1e-3), 1), "ms_per_step": round(p_ms, 3),
+                  "stage_ms": {"build": round(sum(p_b) / len(p_b), 3),
+                               "all_knn": round(sum(p_a) / len(p_a), 3)}},
+        "chosen_equals_plain": same,
+        "missing_rate": round(miss, 5),
+        "knn_distance_discrepancy": round(disc, 6),
+        "accuracy_sample": "2000 points vs exact brute force (rpf_brute_knn)",
+        "forest": info,
+        "e2e": {"value": round(world * n / e2e_s, 1), "unit": "queries/s",
+                "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(n * w.k * 8)},
+        "gpu_launches": int((l1 - l0) / args.steps),
+        "gpu_launches_per_step": True,
+        "roofline": roof,
+        "kernels_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in
+                                sorted(trace.items(), key=lambda kv: -kv[1]["ms"])},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(X, w, os.cpu_count() or 1)
+    return line
+
+
+def run_profile_step(args):
+    import torch
+    from paper_1812_11689_gb300 import forest, synth
+    w = synth.WORKLOADS[args.workload]
+    X = torch.from_numpy(synth.make(args.workload, seed=args.seed)).cuda()
+    kw = dict(n_trees=w.n_trees, leaf_max=w.leaf_max, n_try=w.n_try, seed=args.seed,
+              form=forest.FORM_CHOSEN)
+    counts = []
+    for _ in range(2):
+        l0 = forest.Trace.launch_count()
+        f = forest.Forest(X, **kw)
+        f.all_knn(w.k)
+        torch.cuda.synchronize()
+        counts.append(forest.Trace.launch_count() - l0)
+        f.close()
+    return {"profile_step": True, "workload": args.workload, "launches_per_step": counts}
+
+
+def run_reference(args, rank, world):
+    from paper_1812_11689_gb300 import synth
+    if rank != 0:
+        return None
+    w = synth.WORKLOADS[args.workload]
+    X = synth.make(args.workload, seed=args.seed)
+    threads = os.cpu_count() or 1
+    res = []
+    for _ in range(args.warmup):
+        oracle_sample(X, w, threads, t_sample=4, rows_sample=5000)
+    for _ in range(args.steps):
+        res.append(oracle_sample(X, w, threads, t_sample=4, rows_sample=5000))
+    v = statistics.median(r["value"] for r in res)
+    cb = dict(res[-1])
+    cb["value"] = v
+    return {"impl": "reference", "metric": "all-kNN queries/s at <=1% missing rate "
+            "(chosen vs plain FP32 form)", "value": round(v, 2), "unit": "queries/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * w.n / v, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": w.n, "d": w.d, "n_trees": w.n_trees,
+                       "leaf_max": w.leaf_max, "k": w.k, "n_try": w.n_try},
+            "cpu_baseline": cb,
+            "e2e": {"value": round(v, 2), "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "gb300" else "gloo"
+        if args.impl == "gb300":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend=backend)
+    if args.profile_step:
+        line = run_profile_step(args)
+    elif args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_gb300(args, rank, world, local_rank)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -118,6 +118,33 @@ void rpf_free(rpf_forest* f);
 /* Static English description of an RPF_E* code. */
 const char* rpf_error_string(int code);
 
+/*
+ * rpf_brute_knn -- exact kNN by brute force under the same (d32, index) order:
+ * for each of the m rows of Q, the K nearest of the n rows of X, skipping
+ * index self[i] for row i when self is not NULL (all-kNN ground truth).  This
+ * is the ground truth of the missing rate and kNN-distance metrics of Sec. 5.1.
+ *   X (n x d), Q (m x d), self (m), idx / dist (m x K): device or host.
+ * Errors: RPF_EINVAL, RPF_ENOMEM, RPF_ECUDA.
+ */
+int rpf_brute_knn(const float* X, int64_t n, int32_t d, const float* Q, int64_t m,
+                  const int32_t* self, int32_t K, int32_t* idx, float* dist, void* stream);
+
+/* ---- tracing ---------------------------------------------------------------- */
+
+/* Turn per-kernel timing on (1) or off (0).  When on, every kernel launch of
+   the library is bracketed by a CUDA event pair on its launching stream. */
+int rpf_trace_enable(int on);
+
+/* Kernels launched by the library since it was loaded (always counted). */
+int64_t rpf_launch_count(void);
+
+/* Per-kernel totals of the events recorded since the last read (waits for
+   them): up to max_names entries of name (48 bytes each, NUL-terminated),
+   timed launches and total milliseconds; n_names receives the number of
+   kernel names known.  Clears the recorded events. */
+int rpf_trace_read(int32_t max_names, char* names, int64_t* launches, double* ms,
+                   int32_t* n_names);
+
 /* ---- inspection (host outputs; used by tests and tools) ------------------ */
 
 /* Sizes: n, d, T, total node count, leaf count, max depth, and the number of

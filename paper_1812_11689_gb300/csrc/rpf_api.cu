@@ -284,4 +284,45 @@ int rpf_directions(uint64_t seed, int32_t t, const uint64_t* keys_host, int32_t 
   return RPF_OK;
 }
 
+int rpf_brute_knn(const float* X, int64_t n, int32_t d, const float* Q, int64_t m,
+                  const int32_t* self, int32_t K, int32_t* idx, float* dist, void* stream) {
+  if (!X || n < 1 || d < 1 || d > RPF_MAX_D || m < 0 || K < 1 || K > RPF_MAX_K) return RPF_EINVAL;
+  if (m == 0) return RPF_OK;
+  if (!Q || !idx || !dist || n >= ((int64_t)1 << 31)) return RPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // stage host buffers through one stream-ordered device block
+  const bool xd = rpf_is_device_ptr(X), qd = rpf_is_device_ptr(Q);
+  const bool sd = !self || rpf_is_device_ptr(self);
+  const bool od = rpf_is_device_ptr(idx) && rpf_is_device_ptr(dist);
+  auto a256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t bx = xd ? 0 : a256((size_t)n * d * 4), bq = qd ? 0 : a256((size_t)m * d * 4);
+  const size_t bs = sd ? 0 : a256((size_t)m * 4), bo = od ? 0 : 2 * a256((size_t)m * K * 4);
+  char* w = nullptr;
+  if (bx + bq + bs + bo) {
+    if (cudaMallocAsync((void**)&w, bx + bq + bs + bo, s) != cudaSuccess) {
+      cudaGetLastError();
+      return RPF_ENOMEM;
+    }
+  }
+  const float* Xd = xd ? X : (const float*)w;
+  const float* Qd = qd ? Q : (const float*)(w + bx);
+  const int32_t* Sd = sd ? self : (const int32_t*)(w + bx + bq);
+  int32_t* Id = od ? idx : (int32_t*)(w + bx + bq + bs);
+  float* Dd = od ? dist : (float*)(w + bx + bq + bs + bo / 2);
+  cudaError_t e = cudaSuccess;
+  if (!xd) e = cudaMemcpyAsync((void*)Xd, X, (size_t)n * d * 4, cudaMemcpyDefault, s);
+  if (e == cudaSuccess && !qd) e = cudaMemcpyAsync((void*)Qd, Q, (size_t)m * d * 4, cudaMemcpyDefault, s);
+  if (e == cudaSuccess && !sd) e = cudaMemcpyAsync((void*)Sd, self, (size_t)m * 4, cudaMemcpyDefault, s);
+  int rc = RPF_OK;
+  if (e == cudaSuccess) rc = rpf_brute_dev(Xd, n, d, Qd, m, Sd, K, Id, Dd, s);
+  if (e == cudaSuccess && !rc && !od) {
+    e = cudaMemcpyAsync(idx, Id, (size_t)m * K * 4, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dist, Dd, (size_t)m * K * 4, cudaMemcpyDefault, s);
+  }
+  if (w) cudaFreeAsync(w, s);
+  if (e == cudaSuccess && !od) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return rpf_cuda_err(e);
+  return rc;
+}
+
 }  // extern "C"

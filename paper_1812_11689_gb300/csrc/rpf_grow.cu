@@ -982,9 +982,9 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
   // undecided nodes under G-B
   RPF_TRY(talloc((void**)&p64, sizeof(double) * Tn * ntry));
 
-  k_init_perm<<<nblk(Tn, 256), 256, 0, s>>>(perm_a, n, T);
-  k_init_perm<<<nblk(Tn, 256), 256, 0, s>>>(fo->perm, n, T);
-  k_xnorm<<<nblk(n, 256), 256, 0, s>>>(fo->X, n, d, fo->xnorm);
+  RPF_LAUNCH("k_init_perm", s, k_init_perm<<<nblk(Tn, 256), 256, 0, s>>>(perm_a, n, T));
+  RPF_LAUNCH("k_init_perm", s, k_init_perm<<<nblk(Tn, 256), 256, 0, s>>>(fo->perm, n, T));
+  RPF_LAUNCH("k_xnorm", s, k_xnorm<<<nblk(n, 256), 256, 0, s>>>(fo->X, n, d, fo->xnorm));
 
   // node table: roots 0..T-1
   auto ensure_nodes = [&](int64_t need) -> int {
@@ -1180,71 +1180,71 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     uint64_t* fr_key = lv.fr_key[cur];
     int32_t *ch_node = lv.ch_node[cur], *ch_start = lv.ch_start[cur], *ch_len = lv.ch_len[cur];
 
-    k_dirs<<<nblk((int64_t)F * ntry, 128), 128, 0, s>>>(Fi, ntry, d, seed, fr_tree, fr_key,
-                                                          lv.dir64, lv.dir32);
+    RPF_LAUNCH("k_dirs", s, k_dirs<<<nblk((int64_t)F * ntry, 128), 128, 0, s>>>(Fi, ntry, d, seed, fr_tree, fr_key,
+                                                          lv.dir64, lv.dir32));
     if (growth == 2) {
       const size_t smem = sizeof(float) * ((size_t)ntry * d + kBlock);
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_proj32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_proj32<<<Ci, kBlock, smem, s>>>(ch_node, ch_start, ch_len, fr_tree, fr_begin, fo->X,
+      RPF_LAUNCH("k_proj32", s, k_proj32<<<Ci, kBlock, smem, s>>>(ch_node, ch_start, ch_len, fr_tree, fr_begin, fo->X,
                                         perm_cur, fo->xnorm, n, Tn, d, ntry, lv.dir32, p32,
-                                        lv.cp_s1, lv.cp_min32, lv.cp_max32, lv.cp_xmax);
-      k_stats32<<<nblk(F, 128), 128, 0, s>>>(Fi, ntry, d, fr_cb, fr_nc, fr_len, lv.cp_s1,
+                                        lv.cp_s1, lv.cp_min32, lv.cp_max32, lv.cp_xmax));
+      RPF_LAUNCH("k_stats32", s, k_stats32<<<nblk(F, 128), 128, 0, s>>>(Fi, ntry, d, fr_cb, fr_nc, fr_len, lv.cp_s1,
                                              lv.cp_min32, lv.cp_max32, lv.cp_xmax, lv.fr_mu,
-                                             lv.fr_min32, lv.fr_max32, lv.fr_rad);
-      k_var32<<<Ci, kBlock, 0, s>>>(ch_node, ch_start, ch_len, fr_tree, fr_begin, n, Tn, ntry, p32,
-                                    lv.fr_mu, lv.cp_s2, lv.cp_s1);
-      k_certify<<<nblk(F, 128), 128, 0, s>>>(Fi, ntry, fr_cb, fr_nc, fr_len, lv.cp_s2, lv.cp_s1,
+                                             lv.fr_min32, lv.fr_max32, lv.fr_rad));
+      RPF_LAUNCH("k_var32", s, k_var32<<<Ci, kBlock, 0, s>>>(ch_node, ch_start, ch_len, fr_tree, fr_begin, n, Tn, ntry, p32,
+                                    lv.fr_mu, lv.cp_s2, lv.cp_s1));
+      RPF_LAUNCH("k_certify", s, k_certify<<<nblk(F, 128), 128, 0, s>>>(Fi, ntry, fr_cb, fr_nc, fr_len, lv.cp_s2, lv.cp_s1,
                                              lv.fr_mu, lv.fr_rad, lv.fr_min32, lv.fr_max32,
                                              lv.fr_exact, lv.fr_jstar, lv.fr_tl, lv.fr_tr,
-                                             lv.fr_akey, lv.fr_bkey, lv.fr_vhat);
-      k_cand<<<Ci, kBlock, 0, s>>>(ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact,
+                                             lv.fr_akey, lv.fr_bkey, lv.fr_vhat));
+      RPF_LAUNCH("k_cand", s, k_cand<<<Ci, kBlock, 0, s>>>(ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact,
                                    lv.fr_jstar, lv.fr_tl, lv.fr_tr, fo->X, perm_cur, n, Tn, d,
-                                   ntry, p32, lv.dir64, lv.fr_akey, lv.fr_bkey);
-      k_cand_finish<<<nblk(F, 128), 128, 0, s>>>(Fi, lv.fr_exact, lv.fr_akey, lv.fr_bkey, lv.fr_a,
-                                                 lv.fr_b);
+                                   ntry, p32, lv.dir64, lv.fr_akey, lv.fr_bkey));
+      RPF_LAUNCH("k_cand_finish", s, k_cand_finish<<<nblk(F, 128), 128, 0, s>>>(Fi, lv.fr_exact, lv.fr_akey, lv.fr_bkey, lv.fr_a,
+                                                 lv.fr_b));
     } else {
-      k_fill_i32<<<nblk(F, 256), 256, 0, s>>>(lv.fr_exact, F, 1);
-      k_fill_i32<<<nblk(F, 256), 256, 0, s>>>((int32_t*)lv.fr_rad, F, 0);
+      RPF_LAUNCH("k_fill_i32", s, k_fill_i32<<<nblk(F, 256), 256, 0, s>>>(lv.fr_exact, F, 1));
+      RPF_LAUNCH("k_fill_i32", s, k_fill_i32<<<nblk(F, 256), 256, 0, s>>>((int32_t*)lv.fr_rad, F, 0));
     }
     // exact path (all nodes under G-A; undecided nodes under G-B)
-    k_proj64<<<Ci, kBlock, 0, s>>>(ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact,
-                                   fo->X, perm_cur, n, Tn, d, ntry, lv.dir64, p64);
-    k_csum_chunks<<<nblk((int64_t)C * ntry * 32, 256), 256, 0, s>>>(
+    RPF_LAUNCH("k_proj64", s, k_proj64<<<Ci, kBlock, 0, s>>>(ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact,
+                                   fo->X, perm_cur, n, Tn, d, ntry, lv.dir64, p64));
+    RPF_LAUNCH("k_csum_chunks", s, k_csum_chunks<<<nblk((int64_t)C * ntry * 32, 256), 256, 0, s>>>(
         0, Ci, ntry, ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, n, Tn, p64,
-        lv.fr_mu, lv.cp_sum, lv.cp_min, lv.cp_max);
-    k_csum_nodes<<<nblk((int64_t)F * 32, 256), 256, 0, s>>>(
+        lv.fr_mu, lv.cp_sum, lv.cp_min, lv.cp_max));
+    RPF_LAUNCH("k_csum_nodes", s, k_csum_nodes<<<nblk((int64_t)F * 32, 256), 256, 0, s>>>(
         0, Fi, ntry, fr_cb, fr_nc, fr_len, lv.fr_exact, lv.cp_sum, lv.cp_min, lv.cp_max, lv.fr_mu,
-        lv.fr_min, lv.fr_max, lv.fr_jstar, lv.fr_a, lv.fr_b);
-    k_csum_chunks<<<nblk((int64_t)C * ntry * 32, 256), 256, 0, s>>>(
+        lv.fr_min, lv.fr_max, lv.fr_jstar, lv.fr_a, lv.fr_b));
+    RPF_LAUNCH("k_csum_chunks", s, k_csum_chunks<<<nblk((int64_t)C * ntry * 32, 256), 256, 0, s>>>(
         1, Ci, ntry, ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, n, Tn, p64,
-        lv.fr_mu, lv.cp_sum, lv.cp_min, lv.cp_max);
-    k_csum_nodes<<<nblk((int64_t)F * 32, 256), 256, 0, s>>>(
+        lv.fr_mu, lv.cp_sum, lv.cp_min, lv.cp_max));
+    RPF_LAUNCH("k_csum_nodes", s, k_csum_nodes<<<nblk((int64_t)F * 32, 256), 256, 0, s>>>(
         1, Fi, ntry, fr_cb, fr_nc, fr_len, lv.fr_exact, lv.cp_sum, lv.cp_min, lv.cp_max, lv.fr_mu,
-        lv.fr_min, lv.fr_max, lv.fr_jstar, lv.fr_a, lv.fr_b);
-    k_count_exact<<<nblk(F, 256), 256, 0, s>>>(Fi, lv.fr_exact, d_exact);
-    k_split<<<nblk(F, 128), 128, 0, s>>>(Fi, ntry, d, seed, fr_node, fr_tree, fr_key, lv.fr_jstar,
+        lv.fr_min, lv.fr_max, lv.fr_jstar, lv.fr_a, lv.fr_b));
+    RPF_LAUNCH("k_count_exact", s, k_count_exact<<<nblk(F, 256), 256, 0, s>>>(Fi, lv.fr_exact, d_exact));
+    RPF_LAUNCH("k_split", s, k_split<<<nblk(F, 128), 128, 0, s>>>(Fi, ntry, d, seed, fr_node, fr_tree, fr_key, lv.fr_jstar,
                                          lv.fr_a, lv.fr_b, lv.fr_rad, lv.fr_c, lv.fr_flag,
                                          lv.fr_tl, lv.fr_tr, fo->node_jstar, fo->node_flag,
-                                         fo->node_c);
-    k_store_dirs<<<Fi, 128, 0, s>>>(Fi, ntry, d, fr_node, lv.fr_jstar, lv.fr_flag, lv.dir64,
-                                    fo->node_dir, fo->node_dir32);
-    k_side_count<<<Ci, kBlock, 0, s>>>(ch_node, ch_start, ch_len, fr_tree, fr_begin, fr_len,
+                                         fo->node_c));
+    RPF_LAUNCH("k_store_dirs", s, k_store_dirs<<<Fi, 128, 0, s>>>(Fi, ntry, d, fr_node, lv.fr_jstar, lv.fr_flag, lv.dir64,
+                                    fo->node_dir, fo->node_dir32));
+    RPF_LAUNCH("k_side_count", s, k_side_count<<<Ci, kBlock, 0, s>>>(ch_node, ch_start, ch_len, fr_tree, fr_begin, fr_len,
                                        lv.fr_exact, lv.fr_jstar, lv.fr_flag, lv.fr_c, lv.fr_tl,
                                        lv.fr_tr, fo->X, perm_cur, n, Tn, d, ntry, p32, p64,
-                                       lv.dir64, side, lv.ch_nleft);
-    k_node_scan<<<nblk(F, 128), 128, 0, s>>>(
+                                       lv.dir64, side, lv.ch_nleft));
+    RPF_LAUNCH("k_node_scan", s, k_node_scan<<<nblk(F, 128), 128, 0, s>>>(
         Fi, L, fo->n_nodes, fr_node, fr_tree, fr_begin, fr_len, fr_key, fr_cb, fr_nc, lv.ch_nleft,
         lv.ch_loff, lv.fr_nl, fo->node_key, fo->node_tree, fo->node_begin, fo->node_len,
-        fo->node_left, fo->node_right, fo->node_jstar, fo->node_flag, fo->node_c);
-    k_scatter<<<Ci, kBlock, 0, s>>>(ch_node, ch_start, ch_len, lv.ch_loff, fr_tree, fr_begin,
-                                    fr_len, lv.fr_nl, L, n, side, perm_cur, perm_nxt, fo->perm);
+        fo->node_left, fo->node_right, fo->node_jstar, fo->node_flag, fo->node_c));
+    RPF_LAUNCH("k_scatter", s, k_scatter<<<Ci, kBlock, 0, s>>>(ch_node, ch_start, ch_len, lv.ch_loff, fr_tree, fr_begin,
+                                    fr_len, lv.fr_nl, L, n, side, perm_cur, perm_nxt, fo->perm));
     const int nxt = cur ^ 1;
-    k_frontier<<<1, 1024, 0, s>>>(
+    RPF_LAUNCH("k_frontier", s, k_frontier<<<1, 1024, 0, s>>>(
         Fi, L, fo->n_nodes, fr_tree, fr_begin, fr_len, fr_key, lv.fr_nl, lv.fr_node[nxt],
         lv.fr_tree[nxt], lv.fr_begin[nxt], lv.fr_len[nxt], lv.fr_key[nxt], lv.fr_cb[nxt],
         lv.fr_nc[nxt], lv.ch_node[nxt], lv.ch_start[nxt], lv.ch_len[nxt], fo->n_leaves,
-        fo->leaf_tree, fo->leaf_begin, fo->leaf_len, d_cnt);
+        fo->leaf_tree, fo->leaf_begin, fo->leaf_len, d_cnt));
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt, d_cnt, sizeof(Counts), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1277,5 +1277,5 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
 
 void rpf_launch_directions(uint64_t seed, int32_t t, const uint64_t* keys_dev, int32_t n_keys,
                            int32_t j, int32_t d, double* out_dev, cudaStream_t s) {
-  k_dirs_keys<<<nblk(n_keys, 64), 64, 0, s>>>(seed, t, keys_dev, n_keys, j, d, out_dev);
+  RPF_LAUNCH("k_dirs_keys", s, k_dirs_keys<<<nblk(n_keys, 64), 64, 0, s>>>(seed, t, keys_dev, n_keys, j, d, out_dev));
 }

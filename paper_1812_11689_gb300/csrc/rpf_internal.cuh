@@ -213,6 +213,20 @@ struct rpf_forest {
   std::vector<void*> owned;
 };
 
+// Launch accounting (rpf_trace.cu): RPF_LAUNCH(name, stream, kernel<<<...>>>(...));
+struct rpf_trace_scope {
+  rpf_trace_scope(const char* name, cudaStream_t s);
+  ~rpf_trace_scope();
+  cudaStream_t s_;
+  int id_ = 0;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+#define RPF_LAUNCH(name, stream, ...)          \
+  do {                                         \
+    rpf_trace_scope rpf_ts_((name), (stream)); \
+    __VA_ARGS__;                               \
+  } while (0)
+
 #define RPF_CU(call)                                  \
   do {                                                \
     cudaError_t e_ = (call);                          \
@@ -230,6 +244,8 @@ int rpf_all_knn_dev(rpf_forest* f, int K, int32_t* idx, float* dist, void* ws, s
                     cudaStream_t s);
 int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t* idx, float* dist,
                   void* ws, size_t ws_bytes, cudaStream_t s);
+int rpf_brute_dev(const float* X, int64_t n, int d, const float* Q, int64_t m,
+                  const int32_t* self, int K, int32_t* idx, float* dist, cudaStream_t s);
 size_t rpf_all_knn_ws(const rpf_forest* f, int K);
 size_t rpf_query_ws(const rpf_forest* f, int64_t m, int K);
 void rpf_launch_directions(uint64_t seed, int32_t t, const uint64_t* keys_dev, int32_t n_keys,

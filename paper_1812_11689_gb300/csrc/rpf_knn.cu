@@ -246,6 +246,41 @@ __global__ void k_qscan(const float* Q, int64_t m, int d, int T, int K, const in
     if (q2 < K) out[q2] = make_uint2(__float_as_uint(tk.kd[q2]), (unsigned)tk.ki[q2]);
 }
 
+// Exact kNN by brute force (ground truth for the Sec. 5.1 metrics): one
+// thread per query row, every data row in order; all threads of a block read
+// the same data row at a time (broadcast).
+template <int KMAX>
+__global__ void k_brute(const float* X, int64_t n, int d, const float* Q, int64_t m,
+                        const int32_t* self, int K, int32_t* idx, float* dist) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = q < m;
+  const float* x = X;
+  const float* y = Q + (live ? q : 0) * d;
+  const int me = (live && self) ? self[q] : -1;
+  TopK<KMAX> tk;
+  tk.init();
+  float wd = INFINITY;
+  int wi = -1;
+  for (int64_t j = 0; j < n; ++j) {
+    if ((int)j == me) continue;
+    const float v = rpf_d32(y, x + j * d, d);
+    tk.offer(K, v, (int)j, wd, wi);
+  }
+  if (!live) return;
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k)
+    if (k < K) {
+      idx[q * K + k] = tk.ki[k];
+      dist[q * K + k] = tk.ki[k] < 0 ? INFINITY : __fsqrt_rn(tk.kd[k]);
+    }
+}
+
+template <int KMAX>
+void launch_brute(const float* X, int64_t n, int d, const float* Q, int64_t m,
+                  const int32_t* self, int K, int32_t* idx, float* dist, cudaStream_t s) {
+  RPF_LAUNCH("k_brute", s, k_brute<KMAX><<<nblk(m, 64), 64, 0, s>>>(X, n, d, Q, m, self, K, idx, dist));
+}
+
 template <int KMAX>
 void launch_leaf(const rpf_forest* f, int64_t tb, int64_t nt, int K, int t0, uint2* cand,
                  cudaStream_t s) {
@@ -254,29 +289,29 @@ void launch_leaf(const rpf_forest* f, int64_t tb, int64_t nt, int K, int t0, uin
   if (smem <= 200 * 1024) {
     cudaFuncSetAttribute(k_leaf_plain<KMAX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    k_leaf_plain<KMAX, true><<<(unsigned)nt, rows, smem, s>>>(
+    RPF_LAUNCH("k_leaf_plain", s, k_leaf_plain<KMAX, true><<<(unsigned)nt, rows, smem, s>>>(
         f->tile_first, f->tile_count, tb, f->leaf_tree, f->leaf_begin, f->leaf_len, f->perm, f->X,
-        f->n, f->d, K, t0, cand);
+        f->n, f->d, K, t0, cand));
   } else {
-    k_leaf_plain<KMAX, false><<<(unsigned)nt, rows, 0, s>>>(
+    RPF_LAUNCH("k_leaf_plain", s, k_leaf_plain<KMAX, false><<<(unsigned)nt, rows, 0, s>>>(
         f->tile_first, f->tile_count, tb, f->leaf_tree, f->leaf_begin, f->leaf_len, f->perm, f->X,
-        f->n, f->d, K, t0, cand);
+        f->n, f->d, K, t0, cand));
   }
 }
 
 template <int KMAX>
 void launch_merge(int64_t n, int K, int G, const uint2* cand, uint2* run, bool first, bool last,
                   int32_t* idx, float* dist, cudaStream_t s) {
-  k_merge<KMAX><<<nblk(n, 128), 128, 0, s>>>(n, K, G, cand, run, first, last, idx, dist);
+  RPF_LAUNCH("k_merge", s, k_merge<KMAX><<<nblk(n, 128), 128, 0, s>>>(n, K, G, cand, run, first, last, idx, dist));
 }
 
 template <int KMAX>
 void launch_qscan(const rpf_forest* f, const float* Q, int64_t m, int K, const int32_t* qleaf,
                   uint2* cand, cudaStream_t s) {
   const int T = f->prm.n_trees;
-  k_qscan<KMAX><<<nblk(m * T, 128), 128, 0, s>>>(Q, m, f->d, T, K, qleaf, f->node_tree,
+  RPF_LAUNCH("k_qscan", s, k_qscan<KMAX><<<nblk(m * T, 128), 128, 0, s>>>(Q, m, f->d, T, K, qleaf, f->node_tree,
                                                  f->node_begin, f->node_len, f->perm, f->X, f->n,
-                                                 cand);
+                                                 cand));
 }
 
 #define RPF_KDISPATCH(K, FN, ...)                 \
@@ -399,10 +434,17 @@ int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t
   if (ws_bytes < align256((size_t)m * T * 4) + align256((size_t)T * m * K * 8)) return RPF_EINVAL;
   int32_t* qleaf = (int32_t*)ws;
   uint2* cand = (uint2*)((char*)ws + align256((size_t)m * T * 4));
-  k_route<<<nblk(m * T, 128), 128, 0, s>>>(Q, m, f->d, T, f->node_left, f->node_right,
-                                           f->node_flag, f->node_c, f->node_dir, qleaf);
+  RPF_LAUNCH("k_route", s, k_route<<<nblk(m * T, 128), 128, 0, s>>>(Q, m, f->d, T, f->node_left, f->node_right,
+                                           f->node_flag, f->node_c, f->node_dir, qleaf));
   RPF_KDISPATCH(K, launch_qscan, f, Q, m, K, qleaf, cand, s);
   RPF_KDISPATCH(K, launch_merge, m, K, T, cand, nullptr, true, true, idx, dist, s);
+  RPF_CU(cudaGetLastError());
+  return RPF_OK;
+}
+
+int rpf_brute_dev(const float* X, int64_t n, int d, const float* Q, int64_t m,
+                  const int32_t* self, int K, int32_t* idx, float* dist, cudaStream_t s) {
+  RPF_KDISPATCH(K, launch_brute, X, n, d, Q, m, self, K, idx, dist, s);
   RPF_CU(cudaGetLastError());
   return RPF_OK;
 }

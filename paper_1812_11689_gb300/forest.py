@@ -153,3 +153,56 @@ def directions(seed: int, t: int, keys, j: int, d: int, stream=None) -> np.ndarr
     check(_lib.lib().rpf_directions(seed, t, keys.ctypes.data, keys.size, j, d, out.ctypes.data,
                                     _stream_handle(stream)), "rpf_directions")
     return out
+
+
+def brute_knn(X, Q, K: int, self_idx=None, stream=None):
+    """Exact kNN of the rows of Q among X on the GPU (d32 key, index ties)."""
+    X = _as_points(X)
+    Q = _as_points(Q)
+    m = int(Q.shape[0])
+    on_dev = isinstance(Q, torch.Tensor) and Q.is_cuda
+    if on_dev:
+        idx = torch.empty((m, K), dtype=torch.int32, device=Q.device)
+        dist = torch.empty((m, K), dtype=torch.float32, device=Q.device)
+    else:
+        idx, dist = np.empty((m, K), np.int32), np.empty((m, K), np.float32)
+    sp = None
+    if self_idx is not None:
+        if isinstance(self_idx, np.ndarray):
+            self_idx = np.ascontiguousarray(self_idx, np.int32)
+        else:
+            self_idx = self_idx.to(torch.int32).contiguous()
+        sp = _ptr(self_idx)
+    check(_lib.lib().rpf_brute_knn(_ptr(X), int(X.shape[0]), int(X.shape[1]),
+                                   _ptr(Q) if m else None, m, sp, K,
+                                   _ptr(idx) if m else None, _ptr(dist) if m else None,
+                                   _stream_handle(stream)), "rpf_brute_knn")
+    return idx, dist
+
+
+class Trace:
+    """Per-kernel CUDA-event timing of the library's launches (rpf_trace_*)."""
+
+    @staticmethod
+    def enable(on: bool = True):
+        _lib.lib().rpf_trace_enable(1 if on else 0)
+
+    @staticmethod
+    def launch_count() -> int:
+        return int(_lib.lib().rpf_launch_count())
+
+    @staticmethod
+    def read() -> dict:
+        cap = 256
+        names = ctypes.create_string_buffer(48 * cap)
+        launches = np.zeros(cap, np.int64)
+        ms = np.zeros(cap, np.float64)
+        k = ctypes.c_int32()
+        check(_lib.lib().rpf_trace_read(cap, names, launches.ctypes.data, ms.ctypes.data,
+                                        ctypes.byref(k)), "rpf_trace_read")
+        out = {}
+        for i in range(min(k.value, cap)):
+            nm = names.raw[48 * i:48 * i + 48].split(b"\0", 1)[0].decode()
+            if launches[i]:
+                out[nm] = {"launches": int(launches[i]), "ms": float(ms[i])}
+        return out

@@ -251,3 +251,33 @@ def test_ragged_large_node_multi_chunk():
     for growth in (1, 2):
         g = gpu_forest(X, 2, 1000, 7, seed=3, growth=growth)
         compare_trees(g, o, 2)
+
+
+def test_brute_knn_matches_oracle_brute_force():
+    from paper_1812_11689_gb300 import forest
+    X = synth.make("aniso20_d64", n=6000)
+    rows = np.arange(0, 6000, 7, dtype=np.int32)
+    gi, gd = forest.brute_knn(torch.from_numpy(X).cuda(), torch.from_numpy(X[rows]).cuda(), 10,
+                              self_idx=torch.from_numpy(rows).cuda())
+    oi, od, _ = oracle.brute_knn(X, 10, rows=rows)
+    assert np.array_equal(gi.cpu().numpy(), oi) and np.array_equal(gd.cpu().numpy(), od)
+    Q = synth.queries("aniso20_d64", 50)
+    hi, hd = forest.brute_knn(X, Q, 3)  # host buffers, no exclusion
+    oi, od, _ = oracle.brute_knn(X, 3, Q=Q)
+    assert np.array_equal(hi, oi) and np.array_equal(hd, od)
+
+
+def test_trace_counts_and_times_launches():
+    from paper_1812_11689_gb300 import forest
+    X = synth.make("mix5_d10", n=3000)
+    forest.Trace.read()
+    forest.Trace.enable(True)
+    l0 = forest.Trace.launch_count()
+    f = gpu_forest(X, 4, 50, 3)
+    f.all_knn(5)
+    l1 = forest.Trace.launch_count()
+    forest.Trace.enable(False)
+    tr = forest.Trace.read()
+    assert l1 - l0 == sum(v["launches"] for v in tr.values())
+    assert tr["k_leaf_plain"]["launches"] >= 1 and tr["k_merge"]["launches"] >= 1
+    assert all(v["ms"] >= 0.0 for v in tr.values())
