@@ -68,10 +68,10 @@ def lib():
             L.orc_child_key.argtypes = [_u64, ctypes.c_int]
             L.orc_u53.restype = ctypes.c_double
             L.orc_u53.argtypes = [_u64]
-            L.orc_ln.restype = ctypes.c_double
-            L.orc_ln.argtypes = [ctypes.c_double]
-            L.orc_sincos2pi.restype = None
-            L.orc_sincos2pi.argtypes = [ctypes.c_double, _f64p, _f64p]
+            L.orc_lnf.restype = ctypes.c_float
+            L.orc_lnf.argtypes = [ctypes.c_float]
+            L.orc_sincos2pif.restype = None
+            L.orc_sincos2pif.argtypes = [ctypes.c_float, _f32p, _f32p]
             L.orc_direction.restype = None
             L.orc_direction.argtypes = [_u64, _u64, _u64, _u64, ctypes.c_int, _f64p]
             L.orc_proj.restype = ctypes.c_double
@@ -140,14 +140,14 @@ def u53(w: int) -> float:
     return float(lib().orc_u53(w))
 
 
-def ln(u: float) -> float:
-    return float(lib().orc_ln(u))
+def lnf(u: float) -> np.float32:
+    return np.float32(lib().orc_lnf(np.float32(u)))
 
 
-def sincos2pi(u: float):
-    c, s = ctypes.c_double(), ctypes.c_double()
-    lib().orc_sincos2pi(u, ctypes.byref(c), ctypes.byref(s))
-    return c.value, s.value
+def sincos2pif(u: float):
+    c, s = ctypes.c_float(), ctypes.c_float()
+    lib().orc_sincos2pif(np.float32(u), ctypes.byref(c), ctypes.byref(s))
+    return np.float32(c.value), np.float32(s.value)
 
 
 def direction(seed: int, t: int, key: int, j: int, d: int) -> np.ndarray:

@@ -20,8 +20,9 @@
  *   randomness  : every random draw is a pure function of (seed, tree, node
  *                 key, ...) through a SplitMix64 chain, so the order in which
  *                 Algorithm 1 picks nodes from its working set is irrelevant.
- *   direction   : r = g / |g|, g ~ N(0, I_d) by Box-Muller on our own ln and
- *                 sin/cos series (no libm transcendental is used).
+ *   direction   : r = g * (1 / |g|), g ~ N(0, I_d) by FP32 Box-Muller on our
+ *                 own FP32 ln and sin/cos series (no libm transcendental);
+ *                 |g| and r in FP64.
  *   projection  : p = fold_k fma((double)x_k, r_k, p) from +0.0 (FP64).
  *   dispersion  : V = canonical-order sum of (p - mu)^2 with mu = S / m and
  *                 S the canonical-order sum of p (argmax of V == argmax SD).
@@ -77,44 +78,45 @@ uint64_t orc_child_key(uint64_t key, int side) {
 double orc_u53(uint64_t w) { return (double)(w >> 11) * 0x1p-53; }
 
 /* ------------------------------------------------------------------------- */
-/* Natural logarithm on (0, inf) for normal inputs: u = m * 2^e with m in     */
-/* [sqrt(2)/2, sqrt(2)], ln m = 2 atanh(s), s = (m-1)/(m+1), the atanh series */
-/* s (1 + z/3 + z^2/5 + ... + z^10/21), z = s^2, |s| <= 0.1716 (Taylor).      */
+/* Natural logarithm in FP32 for normal u > 0: u = m 2^e with m folded into   */
+/* [sqrt(2)/2, sqrt(2)], ln m = 2 atanh(s), s = (m-1)/(m+1), and the atanh    */
+/* Taylor series s (1 + z/3 + z^2/5 + ... + z^5/11), z = s^2 <= 0.0295.       */
+/* Coefficients are the FP32 roundings of the double quotients 1/(2k+1).      */
 /* ------------------------------------------------------------------------- */
-static const double ORC_LN2 = 0.69314718055994530942;
-static const double ORC_SQRT2 = 1.41421356237309504880;
-#define ORC_LN_TERMS 11 /* coefficients 1/(2k+1), k = 0..10 */
+static const float ORC_LN2F = 0.693147180559945309f;
+static const float ORC_SQRT2F = 1.41421356237309504f;
+#define ORC_LN_TERMS 6 /* k = 0..5 */
 
-double orc_ln(double u) {
-  uint64_t b;
-  memcpy(&b, &u, 8);
-  int e = (int)((b >> 52) & 0x7ff) - 1023;
-  uint64_t mb = (b & 0x000FFFFFFFFFFFFFULL) | 0x3FF0000000000000ULL;
-  double m;
-  memcpy(&m, &mb, 8);
-  if (m > ORC_SQRT2) {
-    m = m * 0.5;
+float orc_lnf(float u) {
+  uint32_t b;
+  memcpy(&b, &u, 4);
+  int e = (int)((b >> 23) & 0xff) - 127;
+  uint32_t mb = (b & 0x007FFFFFu) | 0x3F800000u;
+  float m;
+  memcpy(&m, &mb, 4);
+  if (m > ORC_SQRT2F) {
+    m = m * 0.5f;
     e += 1;
   }
-  double s = (m - 1.0) / (m + 1.0);
-  double z = s * s;
-  double p = 1.0 / (double)(2 * (ORC_LN_TERMS - 1) + 1);
-  for (int k = ORC_LN_TERMS - 2; k >= 0; --k) p = fma(p, z, 1.0 / (double)(2 * k + 1));
-  double h = s * p;
-  return fma((double)e, ORC_LN2, h + h);
+  float s = (m - 1.0f) / (m + 1.0f);
+  float z = s * s;
+  float p = (float)(1.0 / (double)(2 * (ORC_LN_TERMS - 1) + 1));
+  for (int k = ORC_LN_TERMS - 2; k >= 0; --k) p = fmaf(p, z, (float)(1.0 / (double)(2 * k + 1)));
+  float h = s * p;
+  return fmaf((float)e, ORC_LN2F, h + h);
 }
 
 /* ------------------------------------------------------------------------- */
-/* cos(2 pi u) and sin(2 pi u) for u in [0, 1): quadrant q = floor(4u),       */
-/* theta = (4u - q) * pi/2 in [0, pi/2), Taylor series of cos and sin to      */
-/* theta^22 and theta^23 (12 terms each), coefficients (-1)^k / n! with n!    */
-/* formed as a running double product.                                        */
+/* cos(2 pi u) and sin(2 pi u) in FP32 for u in [0, 1): quadrant q =          */
+/* floor(4u), theta = (4u - q) pi/2 in [0, pi/2), Taylor series of cos and    */
+/* sin to theta^12 and theta^13 (7 terms each).  Coefficients (-1)^k / n! are */
+/* the FP32 roundings of 1 / (running double product n!).                    */
 /* ------------------------------------------------------------------------- */
-static const double ORC_PI_2 = 1.57079632679489661923;
-#define ORC_TRIG_TERMS 12
+static const float ORC_PI_2F = 1.57079632679489662f;
+#define ORC_TRIG_TERMS 7
 
-static void orc_trig_coefs(double* cosc, double* sinc) {
-  double inv[2 * ORC_TRIG_TERMS + 1];
+static void orc_trig_coefs(float* cosc, float* sinc) {
+  double inv[2 * ORC_TRIG_TERMS];
   double fact = 1.0;
   inv[0] = 1.0;
   for (int n = 1; n <= 2 * ORC_TRIG_TERMS - 1; ++n) {
@@ -122,24 +124,24 @@ static void orc_trig_coefs(double* cosc, double* sinc) {
     inv[n] = 1.0 / fact;
   }
   for (int k = 0; k < ORC_TRIG_TERMS; ++k) {
-    cosc[k] = (k & 1) ? -inv[2 * k] : inv[2 * k];
-    sinc[k] = (k & 1) ? -inv[2 * k + 1] : inv[2 * k + 1];
+    cosc[k] = (float)((k & 1) ? -inv[2 * k] : inv[2 * k]);
+    sinc[k] = (float)((k & 1) ? -inv[2 * k + 1] : inv[2 * k + 1]);
   }
 }
 
-void orc_sincos2pi(double u, double* c_out, double* s_out) {
-  double cosc[ORC_TRIG_TERMS], sinc[ORC_TRIG_TERMS];
+void orc_sincos2pif(float u, float* c_out, float* s_out) {
+  float cosc[ORC_TRIG_TERMS], sinc[ORC_TRIG_TERMS];
   orc_trig_coefs(cosc, sinc);
-  double x = u * 4.0;
+  float x = u * 4.0f;
   int q = (int)x;
-  double f = x - (double)q;
-  double th = f * ORC_PI_2;
-  double z = th * th;
-  double cs = cosc[ORC_TRIG_TERMS - 1];
-  double sn = sinc[ORC_TRIG_TERMS - 1];
+  float f = x - (float)q;
+  float th = f * ORC_PI_2F;
+  float z = th * th;
+  float cs = cosc[ORC_TRIG_TERMS - 1];
+  float sn = sinc[ORC_TRIG_TERMS - 1];
   for (int k = ORC_TRIG_TERMS - 2; k >= 0; --k) {
-    cs = fma(cs, z, cosc[k]);
-    sn = fma(sn, z, sinc[k]);
+    cs = fmaf(cs, z, cosc[k]);
+    sn = fmaf(sn, z, sinc[k]);
   }
   sn = sn * th;
   switch (q & 3) {
@@ -152,21 +154,22 @@ void orc_sincos2pi(double u, double* c_out, double* s_out) {
 
 /* ------------------------------------------------------------------------- */
 /* Random direction for (tree t, node key, try j): Sec. 2, "generate a random */
-/* direction" of Algorithms 1 and 2.  g_{2i}, g_{2i+1} by Box-Muller from the  */
-/* words c = 2i and c = 2i+1; r = g / sqrt(sum_k g_k^2) (sequential fma sum). */
+/* direction" of Algorithms 1 and 2.  g_{2i}, g_{2i+1} by Box-Muller in FP32  */
+/* from the top 24 bits of words c = 2i and c = 2i+1; then in FP64           */
+/* |g| = sqrt(sum_k g_k^2) (sequential fma) and r_k = g_k * (1 / |g|).       */
 /* ------------------------------------------------------------------------- */
 void orc_direction(uint64_t seed, uint64_t t, uint64_t key, uint64_t j, int d,
                    double* r) {
   for (int i = 0; 2 * i < d; ++i) {
     uint64_t w1 = orc_word(seed, ORC_TAG_DIR, t, key, j, (uint64_t)(2 * i));
     uint64_t w2 = orc_word(seed, ORC_TAG_DIR, t, key, j, (uint64_t)(2 * i + 1));
-    double u1 = (double)((w1 >> 11) + 1) * 0x1p-53; /* (0, 1] */
-    double u2 = (double)(w2 >> 11) * 0x1p-53;       /* [0, 1) */
-    double rho = sqrt(-2.0 * orc_ln(u1));
-    double c, s;
-    orc_sincos2pi(u2, &c, &s);
-    r[2 * i] = rho * c;
-    if (2 * i + 1 < d) r[2 * i + 1] = rho * s;
+    float u1 = (float)((w1 >> 40) + 1) * 0x1p-24f; /* (0, 1] */
+    float u2 = (float)(w2 >> 40) * 0x1p-24f;       /* [0, 1) */
+    float rho = sqrtf(-2.0f * orc_lnf(u1));
+    float c, s;
+    orc_sincos2pif(u2, &c, &s);
+    r[2 * i] = (double)(rho * c);
+    if (2 * i + 1 < d) r[2 * i + 1] = (double)(rho * s);
   }
   double ss = 0.0;
   for (int k = 0; k < d; ++k) ss = fma(r[k], r[k], ss);
@@ -176,7 +179,8 @@ void orc_direction(uint64_t seed, uint64_t t, uint64_t key, uint64_t j, int d,
     r[0] = 1.0;
     return;
   }
-  for (int k = 0; k < d; ++k) r[k] = r[k] / nrm;
+  double inv = 1.0 / nrm;
+  for (int k = 0; k < d; ++k) r[k] = r[k] * inv;
 }
 
 /* Projection coefficient r . x (Sec. 2, "projection coefficient"). */
