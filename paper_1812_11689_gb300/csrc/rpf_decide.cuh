@@ -23,44 +23,46 @@
 
 #include "rpf_internal.cuh"
 
-// Box-Muller direction for (tree t, node key, try j) into r[0..d) (FP64).
-// Generates pairs [i0, i1) only when called cooperatively; the sequential
-// normalisation is rpf_dir_normalise.
+// Box-Muller pair i of the direction for (tree t, node key, try j): FP32
+// from the top 24 bits of the words 2i and 2i+1 (u1 in (0, 1], u2 in [0, 1)).
 __device__ __forceinline__ void rpf_gauss_pair(uint64_t seed, uint64_t t, uint64_t key, uint64_t j,
-                                               int i, double* g0, double* g1) {
-  uint64_t w1 = rpf_word(seed, RPF_TAG_DIR, t, key, j, (uint64_t)(2 * i));
-  uint64_t w2 = rpf_word(seed, RPF_TAG_DIR, t, key, j, (uint64_t)(2 * i + 1));
-  double u1 = __dmul_rn((double)((w1 >> 11) + 1), 0x1p-53);
-  double u2 = __dmul_rn((double)(w2 >> 11), 0x1p-53);
-  double rho = __dsqrt_rn(__dmul_rn(-2.0, rpf_ln(u1)));
-  double c, s;
-  rpf_sincos2pi(u2, &c, &s);
-  *g0 = __dmul_rn(rho, c);
-  *g1 = __dmul_rn(rho, s);
+                                               int i, float* g0, float* g1) {
+  const uint64_t w1 = rpf_word(seed, RPF_TAG_DIR, t, key, j, (uint64_t)(2 * i));
+  const uint64_t w2 = rpf_word(seed, RPF_TAG_DIR, t, key, j, (uint64_t)(2 * i + 1));
+  const float u1 = __fmul_rn((float)((w1 >> 40) + 1), 0x1p-24f);
+  const float u2 = __fmul_rn((float)(w2 >> 40), 0x1p-24f);
+  const float rho = __fsqrt_rn(__fmul_rn(-2.0f, rpf_lnf(u1)));
+  float c, s;
+  rpf_sincos2pif(u2, &c, &s);
+  *g0 = __fmul_rn(rho, c);
+  *g1 = __fmul_rn(rho, s);
 }
 
-// sequential canonical norm, then r_k = g_k / |g| (one thread)
-__device__ __forceinline__ double rpf_dir_norm(const double* g, int d) {
+// 1 / |g| with |g| = sqrt(sequential fma sum of g_k^2) in FP64; 0 if g = 0
+__device__ __forceinline__ double rpf_inv_norm(const double* g, int d) {
   double ss = 0.0;
   for (int k = 0; k < d; ++k) ss = __fma_rn(g[k], g[k], ss);
-  return __dsqrt_rn(ss);
+  const double nrm = __dsqrt_rn(ss);
+  return nrm == 0.0 ? 0.0 : __ddiv_rn(1.0, nrm);
 }
 
+// Direction r (FP64) for (tree t, node key, try j): r_k = g_k * (1 / |g|);
+// the unreachable all-zero draw gives e_0.  One thread.
 __device__ __forceinline__ void rpf_gen_direction(uint64_t seed, uint64_t t, uint64_t key, uint64_t j,
                                                   int d, double* r) {
   for (int i = 0; 2 * i < d; ++i) {
-    double g0, g1;
+    float g0, g1;
     rpf_gauss_pair(seed, t, key, j, i, &g0, &g1);
-    r[2 * i] = g0;
-    if (2 * i + 1 < d) r[2 * i + 1] = g1;
+    r[2 * i] = (double)g0;
+    if (2 * i + 1 < d) r[2 * i + 1] = (double)g1;
   }
-  const double nrm = rpf_dir_norm(r, d);
-  if (nrm == 0.0) {
+  const double inv = rpf_inv_norm(r, d);
+  if (inv == 0.0) {
     for (int k = 0; k < d; ++k) r[k] = 0.0;
     r[0] = 1.0;
     return;
   }
-  for (int k = 0; k < d; ++k) r[k] = __ddiv_rn(r[k], nrm);
+  for (int k = 0; k < d; ++k) r[k] = __dmul_rn(r[k], inv);
 }
 
 // canonical FP64 projection

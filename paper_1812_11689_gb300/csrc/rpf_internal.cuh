@@ -56,60 +56,78 @@ __device__ __forceinline__ double rpf_u53(uint64_t w) {
   return __dmul_rn((double)(w >> 11), 0x1p-53);
 }
 
-// ---------------------------------------------------------------------------
-// ln(u) for normal u > 0: u = m 2^e, m folded into [sqrt(2)/2, sqrt(2)],
-// ln m = 2 atanh(s) with s = (m - 1)/(m + 1) and the atanh Taylor series
-// s (1 + z/3 + ... + z^10/21), z = s^2 (|s| <= 0.1716).  Coefficients are the
-// IEEE quotients 1/(2k+1).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double rpf_ln(double u) {
-  const double LN2 = 0.69314718055994530942;
-  const double SQRT2 = 1.41421356237309504880;
-  uint64_t b = (uint64_t)__double_as_longlong(u);
-  int e = (int)((b >> 52) & 0x7ff) - 1023;
-  uint64_t mb = (b & 0x000FFFFFFFFFFFFFULL) | 0x3FF0000000000000ULL;
-  double m = __longlong_as_double((long long)mb);
-  if (m > SQRT2) {
-    m = __dmul_rn(m, 0.5);
-    e += 1;
-  }
-  double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
-  double z = __dmul_rn(s, s);
-  double p = __ddiv_rn(1.0, 21.0);
-#pragma unroll
-  for (int k = 9; k >= 0; --k) p = __fma_rn(p, z, __ddiv_rn(1.0, (double)(2 * k + 1)));
-  double h = __dmul_rn(s, p);
-  return __fma_rn((double)e, LN2, __dadd_rn(h, h));
+// Coefficients of the FP32 series below, fixed at compile time from their
+// definitions: 1/(2k+1) (atanh series) and (-1)^k / n! (cos / sin series,
+// n! a running double product), each rounded once to FP32.
+constexpr float rpf_lnc(int k) { return (float)(1.0 / (double)(2 * k + 1)); }
+constexpr double rpf_inv_fact(int n) {
+  double f = 1.0;
+  for (int i = 1; i <= n; ++i) f = f * (double)i;
+  return 1.0 / f;
+}
+constexpr float rpf_cosc(int k) { return (float)((k & 1) ? -rpf_inv_fact(2 * k) : rpf_inv_fact(2 * k)); }
+constexpr float rpf_sinc(int k) {
+  return (float)((k & 1) ? -rpf_inv_fact(2 * k + 1) : rpf_inv_fact(2 * k + 1));
 }
 
 // ---------------------------------------------------------------------------
-// cos(2 pi u), sin(2 pi u), u in [0, 1): quadrant q = floor(4u), theta =
-// (4u - q) pi/2, Taylor series of cos / sin to theta^22 / theta^23 with
-// coefficients (-1)^k / n!, n! formed as a running double product.
+// ln(u) in FP32 for normal u > 0: u = m 2^e, m folded into [sqrt(2)/2,
+// sqrt(2)], ln m = 2 atanh(s), s = (m - 1)/(m + 1), atanh Taylor series
+// s (1 + z/3 + ... + z^5/11), z = s^2 <= 0.0295.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void rpf_sincos2pi(double u, double* c_out, double* s_out) {
-  const double PI_2 = 1.57079632679489661923;
-  double inv[24];
-  double fact = 1.0;
-  inv[0] = 1.0;
-#pragma unroll
-  for (int n = 1; n <= 23; ++n) {
-    fact = __dmul_rn(fact, (double)n);
-    inv[n] = __ddiv_rn(1.0, fact);
+__device__ __forceinline__ float rpf_lnf(float u) {
+  const float LN2F = 0.693147180559945309f;
+  const float SQRT2F = 1.41421356237309504f;
+  uint32_t b = __float_as_uint(u);
+  int e = (int)((b >> 23) & 0xff) - 127;
+  float m = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
+  if (m > SQRT2F) {
+    m = __fmul_rn(m, 0.5f);
+    e += 1;
   }
-  double x = __dmul_rn(u, 4.0);
+  float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+  float z = __fmul_rn(s, s);
+  constexpr float L0 = rpf_lnc(0), L1 = rpf_lnc(1), L2 = rpf_lnc(2), L3 = rpf_lnc(3);
+  constexpr float L4 = rpf_lnc(4), L5 = rpf_lnc(5);
+  float p = L5;
+  p = __fmaf_rn(p, z, L4);
+  p = __fmaf_rn(p, z, L3);
+  p = __fmaf_rn(p, z, L2);
+  p = __fmaf_rn(p, z, L1);
+  p = __fmaf_rn(p, z, L0);
+  float h = __fmul_rn(s, p);
+  return __fmaf_rn((float)e, LN2F, __fadd_rn(h, h));
+}
+
+// ---------------------------------------------------------------------------
+// cos(2 pi u), sin(2 pi u) in FP32, u in [0, 1): quadrant q = floor(4u),
+// theta = (4u - q) pi/2, Taylor series of cos / sin to theta^12 / theta^13.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rpf_sincos2pif(float u, float* c_out, float* s_out) {
+  const float PI_2F = 1.57079632679489662f;
+  float x = __fmul_rn(u, 4.0f);
   int q = (int)x;
-  double f = __dsub_rn(x, (double)q);
-  double th = __dmul_rn(f, PI_2);
-  double z = __dmul_rn(th, th);
-  double cs = -inv[22];  // k = 11: (-1)^11 / 22!
-  double sn = -inv[23];
-#pragma unroll
-  for (int k = 10; k >= 0; --k) {
-    cs = __fma_rn(cs, z, (k & 1) ? -inv[2 * k] : inv[2 * k]);
-    sn = __fma_rn(sn, z, (k & 1) ? -inv[2 * k + 1] : inv[2 * k + 1]);
-  }
-  sn = __dmul_rn(sn, th);
+  float f = __fsub_rn(x, (float)q);
+  float th = __fmul_rn(f, PI_2F);
+  float z = __fmul_rn(th, th);
+  constexpr float C0 = rpf_cosc(0), C1 = rpf_cosc(1), C2 = rpf_cosc(2), C3 = rpf_cosc(3);
+  constexpr float C4 = rpf_cosc(4), C5 = rpf_cosc(5), C6 = rpf_cosc(6);
+  constexpr float S0 = rpf_sinc(0), S1 = rpf_sinc(1), S2 = rpf_sinc(2), S3 = rpf_sinc(3);
+  constexpr float S4 = rpf_sinc(4), S5 = rpf_sinc(5), S6 = rpf_sinc(6);
+  float cs = C6, sn = S6;
+  cs = __fmaf_rn(cs, z, C5);
+  sn = __fmaf_rn(sn, z, S5);
+  cs = __fmaf_rn(cs, z, C4);
+  sn = __fmaf_rn(sn, z, S4);
+  cs = __fmaf_rn(cs, z, C3);
+  sn = __fmaf_rn(sn, z, S3);
+  cs = __fmaf_rn(cs, z, C2);
+  sn = __fmaf_rn(sn, z, S2);
+  cs = __fmaf_rn(cs, z, C1);
+  sn = __fmaf_rn(sn, z, S1);
+  cs = __fmaf_rn(cs, z, C0);
+  sn = __fmaf_rn(sn, z, S0);
+  sn = __fmul_rn(sn, th);
   switch (q & 3) {
     case 0: *c_out = cs; *s_out = sn; break;
     case 1: *c_out = -sn; *s_out = cs; break;

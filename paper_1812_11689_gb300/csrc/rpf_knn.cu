@@ -338,15 +338,18 @@ int rpf_build_tiles(rpf_forest* f, cudaStream_t s) {
   RPF_CU(cudaMemcpyAsync(lb.data(), f->leaf_begin, 4 * nl, cudaMemcpyDeviceToHost, s));
   RPF_CU(cudaMemcpyAsync(ll.data(), f->leaf_len, 4 * nl, cudaMemcpyDeviceToHost, s));
   RPF_CU(cudaStreamSynchronize(s));
-  // counting sort by tree, then by begin within a tree (deterministic order)
-  std::vector<int64_t> order(nl);
-  for (int64_t i = 0; i < nl; ++i) order[i] = i;
+  // drop unused slots (len 0), then sort by tree and by begin within a tree
+  std::vector<int64_t> order;
+  order.reserve(nl);
+  for (int64_t i = 0; i < nl; ++i)
+    if (ll[i] > 0) order.push_back(i);
   std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
     return lt[a] != lt[b] ? lt[a] < lt[b] : lb[a] < lb[b];
   });
-  std::vector<int32_t> st(nl), sb(nl), sl(nl);
+  const int64_t nv = (int64_t)order.size();
+  std::vector<int32_t> st(nv), sb(nv), sl(nv);
   int32_t maxleaf = 1;
-  for (int64_t i = 0; i < nl; ++i) {
+  for (int64_t i = 0; i < nv; ++i) {
     st[i] = lt[order[i]];
     sb[i] = lb[order[i]];
     sl[i] = ll[order[i]];
@@ -360,10 +363,10 @@ int rpf_build_tiles(rpf_forest* f, cudaStream_t s) {
   int64_t i = 0;
   for (int t = 0; t < T; ++t) {
     ttb[t] = (int64_t)tf.size();
-    while (i < nl && st[i] == t) {
+    while (i < nv && st[i] == t) {
       int r = 0, c = 0;
       const int64_t first = i;
-      while (i < nl && st[i] == t && r + sl[i] <= rows) {
+      while (i < nv && st[i] == t && r + sl[i] <= rows) {
         r += sl[i];
         ++c;
         ++i;
@@ -374,9 +377,10 @@ int rpf_build_tiles(rpf_forest* f, cudaStream_t s) {
     }
   }
   ttb[T] = (int64_t)tf.size();
-  RPF_CU(cudaMemcpyAsync(f->leaf_tree, st.data(), 4 * nl, cudaMemcpyHostToDevice, s));
-  RPF_CU(cudaMemcpyAsync(f->leaf_begin, sb.data(), 4 * nl, cudaMemcpyHostToDevice, s));
-  RPF_CU(cudaMemcpyAsync(f->leaf_len, sl.data(), 4 * nl, cudaMemcpyHostToDevice, s));
+  RPF_CU(cudaMemcpyAsync(f->leaf_tree, st.data(), 4 * nv, cudaMemcpyHostToDevice, s));
+  RPF_CU(cudaMemcpyAsync(f->leaf_begin, sb.data(), 4 * nv, cudaMemcpyHostToDevice, s));
+  RPF_CU(cudaMemcpyAsync(f->leaf_len, sl.data(), 4 * nv, cudaMemcpyHostToDevice, s));
+  f->n_leaves = nv;
   const int64_t ntl = (int64_t)tf.size();
   if (f->tile_first) cudaFree(f->tile_first);
   if (f->tile_count) cudaFree(f->tile_count);

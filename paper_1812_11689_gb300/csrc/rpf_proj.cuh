@@ -1,0 +1,153 @@
+// rpf_proj.cuh -- centred FP32 projections and their block statistics,
+// shared by the level-synchronous and the CTA-local growth kernels.
+//
+// Statistics of the FP32 projections q' of a node for one try: S1 = sum q',
+// S2 = sum q'^2, A = sum |q'|, min, max.  Every thread accumulates at most 16
+// points in FP32, the warp folds with a butterfly in FP32, and thread 0 adds
+// the warp partials in FP64; the error analysis in rpf_certify assumes this
+// depth (RPF_STAT_DEPTH).
+#pragma once
+
+#include "rpf_internal.cuh"
+
+// q'_j(x) = fl32-dot(r32_j, fl32(x - o)) for up to 4 points (gid < 0: none)
+// and tries [j0, j0 + nj) (r32 of try j0 at sr, stride d); nn = FP32 sum of
+// squares of fl32(x - o) when want_nn.
+template <int TG>
+__device__ __forceinline__ void rpf_proj4(const float* __restrict__ X, int d, const int (&gid)[4],
+                                          const float* so, const float* sr, int nj,
+                                          float (&acc)[4][TG], float (&nn)[4], bool want_nn) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    nn[p] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < TG; ++q) acc[p][q] = 0.0f;
+  }
+  if ((d & 3) == 0) {
+    for (int k = 0; k < d; k += 4) {
+      const float4 o4 = *reinterpret_cast<const float4*>(so + k);
+      float4 r4[TG];
+#pragma unroll
+      for (int q = 0; q < TG; ++q)
+        if (q < nj) r4[q] = *reinterpret_cast<const float4*>(sr + q * d + k);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        if (gid[p] < 0) continue;
+        const float4 x4 = __ldg(reinterpret_cast<const float4*>(X + (int64_t)gid[p] * d + k));
+        const float e0 = __fsub_rn(x4.x, o4.x), e1 = __fsub_rn(x4.y, o4.y);
+        const float e2 = __fsub_rn(x4.z, o4.z), e3 = __fsub_rn(x4.w, o4.w);
+        if (want_nn) {
+          nn[p] = __fmaf_rn(e0, e0, nn[p]);
+          nn[p] = __fmaf_rn(e1, e1, nn[p]);
+          nn[p] = __fmaf_rn(e2, e2, nn[p]);
+          nn[p] = __fmaf_rn(e3, e3, nn[p]);
+        }
+#pragma unroll
+        for (int q = 0; q < TG; ++q) {
+          if (q < nj) {
+            float a = acc[p][q];
+            a = __fmaf_rn(e0, r4[q].x, a);
+            a = __fmaf_rn(e1, r4[q].y, a);
+            a = __fmaf_rn(e2, r4[q].z, a);
+            a = __fmaf_rn(e3, r4[q].w, a);
+            acc[p][q] = a;
+          }
+        }
+      }
+    }
+  } else {
+    for (int k = 0; k < d; ++k) {
+      const float ok = so[k];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        if (gid[p] < 0) continue;
+        const float e = __fsub_rn(__ldg(X + (int64_t)gid[p] * d + k), ok);
+        if (want_nn) nn[p] = __fmaf_rn(e, e, nn[p]);
+#pragma unroll
+        for (int q = 0; q < TG; ++q)
+          if (q < nj) acc[p][q] = __fmaf_rn(e, sr[q * d + k], acc[p][q]);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void rpf_stat_add(float v, float& s1, float& s2, float& a1, float& mn,
+                                             float& mx) {
+  s1 = __fadd_rn(s1, v);
+  s2 = __fmaf_rn(v, v, s2);
+  a1 = __fadd_rn(a1, fabsf(v));
+  mn = fminf(mn, v);
+  mx = fmaxf(mx, v);
+}
+
+// Block reduction of per-thread statistics for nj tries into o*[q] (written
+// by thread 0; visible to all threads after the trailing barrier).
+// red: 8 warps x TG x 5 floats of shared memory.
+template <int TG>
+__device__ __forceinline__ void rpf_block_stats(int nj, float (&s1)[TG], float (&s2)[TG],
+                                                float (&a1)[TG], float (&mn)[TG], float (&mx)[TG],
+                                                float* red, double* o1, double* o2, double* oa,
+                                                float* omn, float* omx) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < TG; ++q) {
+    if (q >= nj) continue;
+    float a = s1[q], b = s2[q], c = a1[q], lo = mn[q], hi = mx[q];
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      a = __fadd_rn(a, __shfl_xor_sync(RPF_FULL, a, off));
+      b = __fadd_rn(b, __shfl_xor_sync(RPF_FULL, b, off));
+      c = __fadd_rn(c, __shfl_xor_sync(RPF_FULL, c, off));
+      lo = fminf(lo, __shfl_xor_sync(RPF_FULL, lo, off));
+      hi = fmaxf(hi, __shfl_xor_sync(RPF_FULL, hi, off));
+    }
+    if (lane == 0) {
+      float* r = red + (w * TG + q) * 5;
+      r[0] = a;
+      r[1] = b;
+      r[2] = c;
+      r[3] = lo;
+      r[4] = hi;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int q = 0; q < nj; ++q) {
+      double A = 0.0, B = 0.0, C = 0.0;
+      float lo = INFINITY, hi = -INFINITY;
+      for (int u = 0; u < nw; ++u) {
+        const float* r = red + (u * TG + q) * 5;
+        A = __dadd_rn(A, (double)r[0]);
+        B = __dadd_rn(B, (double)r[1]);
+        C = __dadd_rn(C, (double)r[2]);
+        lo = fminf(lo, r[3]);
+        hi = fmaxf(hi, r[4]);
+      }
+      o1[q] = A;
+      o2[q] = B;
+      oa[q] = C;
+      omn[q] = lo;
+      omx[q] = hi;
+    }
+  }
+  __syncthreads();
+}
+
+// Block-wide max of a non-negative float, returned to every thread.
+// red: at least 33 floats of shared memory (not in use by the caller).
+__device__ __forceinline__ float rpf_block_max(float v, float* red) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) v = fmaxf(v, __shfl_xor_sync(RPF_FULL, v, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.0f;
+    for (int u = 0; u < (int)(blockDim.x >> 5); ++u) m = fmaxf(m, red[u]);
+    red[32] = m;
+  }
+  __syncthreads();
+  const float r = red[32];
+  __syncthreads();
+  return r;
+}

@@ -1,0 +1,500 @@
+// rpf_subtree.cu -- phase B of rpTree growth: one CTA grows the whole subtree
+// of a node of at most 4096 points (Sec. 2, Algorithm 1 with Algorithm 2 for
+// every split), with no launch or host round trip per level.
+//
+// The subtree's permutation segment lives in shared memory.  Nodes are taken
+// depth first from a small stack; after a split the larger child is pushed
+// first so the smaller one is processed next, which keeps the stack depth
+// below log2(4096) + 2.  Per node the CTA
+//   1. draws the nTry candidate directions (FP32 Box-Muller, FP64 normalise)
+//   2. takes o = the node's first member and b_j = p64(o, r_j)
+//   3. projects every point: q' = fl32-dot(r32, fl32(x - o)), error radius,
+//      block statistics (FP32 per thread, FP64 across warps)
+//   4. certifies Algorithm 2's choice, or recomputes the node in FP64 with the
+//      canonical reduction (one chunk: the node has <= 4096 points)
+//   5. finds the exact min / max (FP64 on the few candidates), draws c
+//   6. decides every point's side (certified from q', else FP64) and
+//      partitions the segment stably
+//   7. records the node and its children; leaves are written to the final
+//      permutation, inner children pushed.
+// Node ids and leaf slots come from ranges reserved per subtree (2m - 2 ids,
+// m leaf slots for m points), so the layout is deterministic.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "rpf_decide.cuh"
+#include "rpf_proj.cuh"
+
+namespace {
+
+constexpr int kB = 256;
+constexpr int kSubN = RPF_CHUNK;
+constexpr int kStack = 24;
+
+struct SubState {
+  uint64_t key;
+  int nb, m, id;
+  int exact, js, flag, nl;
+  double a, b, c;
+  float tl, tr, rad, wlo, whi;
+  unsigned long long akey, bkey;
+  int top, next_id, id_end, next_leaf, leaf_end;
+  int leafL, leafR, err;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+struct SubLayout {
+  size_t sP, sT, sSide, r64, r32, so, sbase, sS1, sS2, sA, sinv, smn, smx, red, total;
+};
+
+__host__ __device__ inline SubLayout sub_layout(int d, int ntry, int TG) {
+  SubLayout l{};
+  size_t o = 0;
+  l.sP = o;
+  o = align16(o + 4 * (size_t)kSubN);
+  l.sT = o;
+  o = align16(o + 4 * (size_t)kSubN);
+  l.sSide = o;
+  o = align16(o + (size_t)kSubN);
+  l.r64 = o;
+  o = align16(o + 8 * (size_t)ntry * d);
+  l.r32 = o;
+  o = align16(o + 4 * (size_t)ntry * d);
+  l.so = o;
+  o = align16(o + 4 * (size_t)d);
+  l.sbase = o;
+  o = align16(o + 8 * (size_t)ntry);
+  l.sS1 = o;
+  o = align16(o + 8 * (size_t)ntry);
+  l.sS2 = o;
+  o = align16(o + 8 * (size_t)ntry);
+  l.sA = o;
+  o = align16(o + 8 * (size_t)ntry);
+  l.sinv = o;
+  o = align16(o + 8 * (size_t)ntry);
+  l.smn = o;
+  o = align16(o + 4 * (size_t)ntry);
+  l.smx = o;
+  o = align16(o + 4 * (size_t)ntry);
+  l.red = o;
+  o = align16(o + 4 * (size_t)(8 * TG * 5 + 40));
+  l.total = o;
+  return l;
+}
+
+template <int TG>
+__global__ void __launch_bounds__(kB, 2) k_subtree(
+    const int32_t* it_node, const int32_t* it_tree, const int32_t* it_begin, const int32_t* it_len,
+    const uint64_t* it_key, const int32_t* it_nbase, const int32_t* it_lbase,
+    const float* __restrict__ X, const float* __restrict__ xnorm, int64_t n, int64_t Tn, int d,
+    int ntry, int L, uint64_t seed, int exact_only, int32_t* perm_final, float* p32, double* p64,
+    uint64_t* node_key, int32_t* node_tree, int32_t* node_begin, int32_t* node_len,
+    int32_t* node_left, int32_t* node_right, int32_t* node_jstar, int32_t* node_flag,
+    double* node_c, int32_t* leaf_tree, int32_t* leaf_begin, int32_t* leaf_len,
+    unsigned long long* d_exact, int* d_err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const SubLayout lay = sub_layout(d, ntry, TG);
+  int32_t* sP = reinterpret_cast<int32_t*>(smraw + lay.sP);
+  int32_t* sT = reinterpret_cast<int32_t*>(smraw + lay.sT);
+  uint8_t* sSide = smraw + lay.sSide;
+  double* r64 = reinterpret_cast<double*>(smraw + lay.r64);
+  float* r32 = reinterpret_cast<float*>(smraw + lay.r32);
+  float* so = reinterpret_cast<float*>(smraw + lay.so);
+  double* sbase = reinterpret_cast<double*>(smraw + lay.sbase);
+  double* sS1 = reinterpret_cast<double*>(smraw + lay.sS1);
+  double* sS2 = reinterpret_cast<double*>(smraw + lay.sS2);
+  double* sA = reinterpret_cast<double*>(smraw + lay.sA);
+  double* sinv = reinterpret_cast<double*>(smraw + lay.sinv);
+  float* smn = reinterpret_cast<float*>(smraw + lay.smn);
+  float* smx = reinterpret_cast<float*>(smraw + lay.smx);
+  float* red = reinterpret_cast<float*>(smraw + lay.red);
+  __shared__ SubState S;
+  __shared__ int st_nb[kStack], st_m[kStack], st_id[kStack];
+  __shared__ uint64_t st_key[kStack];
+  __shared__ int wsc[kB / 32];
+  __shared__ int tile_tot;
+
+  const int it = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int t = it_tree[it];
+  const int m0 = it_len[it];
+  const int64_t pbase = (int64_t)t * n + it_begin[it];
+  for (int i = tid; i < m0; i += kB) sP[i] = perm_final[pbase + i];
+  if (tid == 0) {
+    S.top = 1;
+    st_nb[0] = 0;
+    st_m[0] = m0;
+    st_id[0] = it_node[it];
+    st_key[0] = it_key[it];
+    S.next_id = it_nbase[it];
+    S.id_end = it_nbase[it] + 2 * m0 - 2;
+    S.next_leaf = it_lbase[it];
+    S.leaf_end = it_lbase[it] + m0;
+    S.err = 0;
+  }
+  __syncthreads();
+  const int npairs = (d + 1) / 2;
+
+  while (true) {
+    if (tid == 0) {
+      if (S.top == 0 || S.err) {
+        S.m = -1;
+      } else {
+        const int k = --S.top;
+        S.nb = st_nb[k];
+        S.m = st_m[k];
+        S.id = st_id[k];
+        S.key = st_key[k];
+      }
+    }
+    __syncthreads();
+    if (S.m < 0) break;
+    const int nb = S.nb, m = S.m, id = S.id;
+    const uint64_t key = S.key;
+
+    // 1. candidate directions
+    for (int idx = tid; idx < ntry * npairs; idx += kB) {
+      const int j = idx / npairs, i = idx - j * npairs;
+      float g0, g1;
+      rpf_gauss_pair(seed, (uint64_t)t, key, (uint64_t)j, i, &g0, &g1);
+      r64[j * d + 2 * i] = (double)g0;
+      if (2 * i + 1 < d) r64[j * d + 2 * i + 1] = (double)g1;
+    }
+    __syncthreads();
+    for (int j = tid; j < ntry; j += kB) sinv[j] = rpf_inv_norm(r64 + j * d, d);
+    __syncthreads();
+    for (int idx = tid; idx < ntry * d; idx += kB) {
+      const int j = idx / d, k = idx - j * d;
+      const double inv = sinv[j];
+      const double v = inv == 0.0 ? (k == 0 ? 1.0 : 0.0) : __dmul_rn(r64[idx], inv);
+      r64[idx] = v;
+      r32[idx] = __double2float_rn(v);
+    }
+    __syncthreads();
+
+    // 2. centre o and the base projections b_j
+    const int og = sP[nb];
+    const float* xo = X + (int64_t)og * d;
+    for (int k = tid; k < d; k += kB) so[k] = xo[k];
+    for (int j = tid; j < ntry; j += kB) sbase[j] = rpf_p64(xo, r64 + j * d, d);
+    __syncthreads();
+    const float on = xnorm[og];
+
+    // 3. centred FP32 projections and statistics
+    float radmax = 0.0f;
+    if (!exact_only) {
+      for (int j0 = 0; j0 < ntry; j0 += TG) {
+        const int nj = min(TG, ntry - j0);
+        float s1[TG], s2[TG], a1[TG], mn[TG], mx[TG];
+#pragma unroll
+        for (int q = 0; q < TG; ++q) {
+          s1[q] = s2[q] = a1[q] = 0.0f;
+          mn[q] = INFINITY;
+          mx[q] = -INFINITY;
+        }
+        for (int u0 = 0; u0 * kB < m; u0 += 4) {
+          int gid[4], pos[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            pos[p] = tid + kB * (u0 + p);
+            gid[p] = pos[p] < m ? sP[nb + pos[p]] : -1;
+          }
+          float acc[4][TG], nn[4];
+          rpf_proj4<TG>(X, d, gid, so, r32 + j0 * d, nj, acc, nn, j0 == 0);
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            if (gid[p] < 0) continue;
+            if (j0 == 0) radmax = fmaxf(radmax, rpf_point_rad(d, nn[p], xnorm[gid[p]], on));
+#pragma unroll
+            for (int q = 0; q < TG; ++q) {
+              if (q < nj) {
+                const float v = acc[p][q];
+                p32[(int64_t)(j0 + q) * Tn + pbase + nb + pos[p]] = v;
+                rpf_stat_add(v, s1[q], s2[q], a1[q], mn[q], mx[q]);
+              }
+            }
+          }
+        }
+        rpf_block_stats<TG>(nj, s1, s2, a1, mn, mx, red, sS1 + j0, sS2 + j0, sA + j0, smn + j0,
+                            smx + j0);
+      }
+      radmax = rpf_block_max(radmax, red);
+    }
+
+    // 4. certify the choice of Algorithm 2
+    if (tid == 0) {
+      const int w = exact_only ? -1 : rpf_certify(ntry, (double)m, sS1, sS2, sA, sbase, (double)radmax);
+      S.exact = w < 0;
+      S.js = w;
+      S.rad = radmax;
+      if (w >= 0) {
+        const float r2 = __fmul_ru(2.0f, radmax);
+        S.wlo = __fadd_ru(smn[w], r2);
+        S.whi = __fsub_rd(smx[w], r2);
+        S.akey = rpf_dkey(INFINITY);
+        S.bkey = rpf_dkey(-INFINITY);
+      }
+    }
+    __syncthreads();
+
+    if (S.exact) {
+      // canonical FP64 projections and statistics
+      for (int i = tid; i < m; i += kB) {
+        const float* x = X + (int64_t)sP[nb + i] * d;
+        for (int j = 0; j < ntry; ++j)
+          p64[(int64_t)j * Tn + pbase + nb + i] = rpf_p64(x, r64 + j * d, d);
+      }
+      __syncthreads();
+      if (warp == 0) {
+        double best = 0.0;
+        int js = -1;
+        for (int j = 0; j < ntry; ++j) {
+          const double* p = p64 + (int64_t)j * Tn + pbase + nb;
+          const double Ssum = rpf_warp_chunk_sum(m, lane, [&](int64_t k) { return p[k]; });
+          const double mu = __ddiv_rn(Ssum, (double)m);
+          const double V = rpf_warp_chunk_sum(m, lane, [&](int64_t k) {
+            const double e = __dsub_rn(p[k], mu);
+            return __dmul_rn(e, e);
+          });
+          if (V > best) {
+            best = V;
+            js = j;
+          }
+        }
+        double a = INFINITY, b = -INFINITY;
+        if (js >= 0) {
+          const double* p = p64 + (int64_t)js * Tn + pbase + nb;
+          for (int k = lane; k < m; k += 32) {
+            a = fmin(a, p[k]);
+            b = fmax(b, p[k]);
+          }
+          for (int off = 16; off >= 1; off >>= 1) {
+            a = fmin(a, __shfl_xor_sync(RPF_FULL, a, off));
+            b = fmax(b, __shfl_xor_sync(RPF_FULL, b, off));
+          }
+        }
+        if (lane == 0) {
+          S.js = js;
+          S.a = a;
+          S.b = b;
+          atomicAdd(d_exact, 1ULL);
+        }
+      }
+      __syncthreads();
+    } else {
+      // exact min / max among the candidates the bound leaves
+      const int w = S.js;
+      const float lo = S.wlo, hi = S.whi;
+      const float* p = p32 + (int64_t)w * Tn + pbase + nb;
+      for (int i = tid; i < m; i += kB) {
+        const float v = p[i];
+        const bool ca = v <= lo, cb = v >= hi;
+        if (!ca && !cb) continue;
+        const double q = rpf_p64(X + (int64_t)sP[nb + i] * d, r64 + w * d, d);
+        if (ca) atomicMin(&S.akey, rpf_dkey(q));
+        if (cb) atomicMax(&S.bkey, rpf_dkey(q));
+      }
+      __syncthreads();
+      if (tid == 0) {
+        S.a = rpf_dkey_inv(S.akey);
+        S.b = rpf_dkey_inv(S.bkey);
+      }
+      __syncthreads();
+    }
+
+    // 5. split point and node record
+    if (tid == 0) {
+      const int js = S.js;
+      double c = NAN;
+      const int acc = js >= 0 ? rpf_split_point(seed, (uint64_t)t, key, S.a, S.b, &c) : 0;
+      S.c = c;
+      S.flag = acc ? 0 : 1;
+      if (acc && !S.exact) {
+        float tl, tr;
+        rpf_side_thresholds(c, sbase[js], (double)S.rad, &tl, &tr);
+        S.tl = tl;
+        S.tr = tr;
+      }
+      node_jstar[id] = js;
+      node_flag[id] = acc ? 0 : 1;
+      node_c[id] = c;
+    }
+    __syncthreads();
+
+    // 6. sides and the stable partition
+    {
+      const int js = S.js, flag = S.flag, exact = S.exact;
+      const double c = S.c;
+      const float tl = S.tl, tr = S.tr;
+      int cnt = 0;
+      for (int i = tid; i < m; i += kB) {
+        bool left;
+        if (flag) {
+          left = i < (m >> 1);
+        } else if (exact) {
+          left = p64[(int64_t)js * Tn + pbase + nb + i] < c;
+        } else {
+          const float v = p32[(int64_t)js * Tn + pbase + nb + i];
+          if (v < tl) left = true;
+          else if (v >= tr) left = false;
+          else left = rpf_p64(X + (int64_t)sP[nb + i] * d, r64 + js * d, d) < c;
+        }
+        sSide[i] = left ? 1 : 0;
+        cnt += left ? 1 : 0;
+      }
+      for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(RPF_FULL, cnt, off);
+      if (lane == 0) wsc[warp] = cnt;
+      __syncthreads();
+      if (tid == 0) {
+        int s = 0;
+        for (int u = 0; u < kB / 32; ++u) s += wsc[u];
+        S.nl = s;
+      }
+      __syncthreads();
+      const int nl = S.nl;
+      int carryL = 0;
+      for (int t0 = 0; t0 < m; t0 += kB) {
+        const int i = t0 + tid;
+        const int s = i < m ? sSide[i] : 0;
+        int x = s;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int y = __shfl_up_sync(RPF_FULL, x, off);
+          if (lane >= off) x += y;
+        }
+        if (lane == 31) wsc[warp] = x;
+        __syncthreads();
+        if (tid == 0) {
+          int r = 0;
+          for (int u = 0; u < kB / 32; ++u) {
+            const int v = wsc[u];
+            wsc[u] = r;
+            r += v;
+          }
+          tile_tot = r;
+        }
+        __syncthreads();
+        if (i < m) {
+          const int lbefore = carryL + x - s + wsc[warp];
+          const int dst = s ? lbefore : nl + (i - lbefore);
+          sT[nb + dst] = sP[nb + i];
+        }
+        carryL += tile_tot;
+        __syncthreads();
+      }
+      for (int i = tid; i < m; i += kB) sP[nb + i] = sT[nb + i];
+      __syncthreads();
+    }
+
+    // 7. children
+    if (tid == 0) {
+      const int nl = S.nl;
+      const int mL = nl, mR = m - nl;
+      const int idL = S.next_id, idR = S.next_id + 1;
+      if (idR >= S.id_end) S.err = 1;  // reserved range [nbase, nbase + 2 m0 - 2)
+      if (!S.err) {
+        S.next_id += 2;
+        node_left[id] = idL;
+        node_right[id] = idR;
+        const int bL = it_begin[it] + nb, bR = bL + nl;
+        node_key[idL] = rpf_child_key(key, 0);
+        node_key[idR] = rpf_child_key(key, 1);
+        node_tree[idL] = node_tree[idR] = t;
+        node_begin[idL] = bL;
+        node_begin[idR] = bR;
+        node_len[idL] = mL;
+        node_len[idR] = mR;
+        node_left[idL] = node_right[idL] = node_left[idR] = node_right[idR] = -1;
+        node_jstar[idL] = node_jstar[idR] = -1;
+        node_flag[idL] = node_flag[idR] = 0;
+        node_c[idL] = node_c[idR] = NAN;
+        S.leafL = mL <= L;
+        S.leafR = mR <= L;
+        if (S.leafL) {
+          const int ls = S.next_leaf++;
+          leaf_tree[ls] = t;
+          leaf_begin[ls] = bL;
+          leaf_len[ls] = mL;
+        }
+        if (S.leafR) {
+          const int ls = S.next_leaf++;
+          leaf_tree[ls] = t;
+          leaf_begin[ls] = bR;
+          leaf_len[ls] = mR;
+        }
+        if (S.next_leaf > S.leaf_end || S.top + 2 > kStack) {
+          S.err = 1;
+        } else {
+          // push the larger inner child first: the smaller one is popped next
+          const bool Lfirst = mL >= mR;
+          for (int pass = 0; pass < 2; ++pass) {
+            const bool isL = (pass == 0) == Lfirst;
+            if (isL && !S.leafL) {
+              st_nb[S.top] = nb;
+              st_m[S.top] = mL;
+              st_id[S.top] = idL;
+              st_key[S.top] = rpf_child_key(key, 0);
+              ++S.top;
+            } else if (!isL && !S.leafR) {
+              st_nb[S.top] = nb + nl;
+              st_m[S.top] = mR;
+              st_id[S.top] = idR;
+              st_key[S.top] = rpf_child_key(key, 1);
+              ++S.top;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (S.err) break;
+    if (S.leafL)
+      for (int i = tid; i < S.nl; i += kB) perm_final[pbase + nb + i] = sP[nb + i];
+    if (S.leafR)
+      for (int i = tid; i < m - S.nl; i += kB) perm_final[pbase + nb + S.nl + i] = sP[nb + S.nl + i];
+    __syncthreads();
+  }
+  if (tid == 0 && S.err) atomicExch(d_err, 1);
+}
+
+}  // namespace
+
+bool rpf_subtree_fits(int d, int ntry) {
+  return sub_layout(d, ntry, 8).total <= 200 * 1024;
+}
+
+int rpf_grow_subtrees(rpf_forest* fo, int64_t n_items, const int32_t* it_node,
+                      const int32_t* it_tree, const int32_t* it_begin, const int32_t* it_len,
+                      const uint64_t* it_key, const int32_t* it_nbase, const int32_t* it_lbase,
+                      float* p32, double* p64, unsigned long long* d_exact, int* d_err,
+                      cudaStream_t s) {
+  const int d = fo->d, ntry = fo->prm.n_try, L = fo->prm.leaf_max;
+  const int64_t n = fo->n, Tn = n * fo->prm.n_trees;
+  const int exact_only = fo->prm.growth == 1 ? 1 : 0;
+  const int TG = ntry <= 5 ? ntry : 8;
+  const size_t smem = sub_layout(d, ntry, TG).total;
+  if (smem > 200 * 1024) return RPF_EINVAL;
+#define RPF_SUB(TGV)                                                                              \
+  do {                                                                                            \
+    cudaFuncSetAttribute(k_subtree<TGV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    RPF_LAUNCH("k_subtree", s, k_subtree<TGV><<<(unsigned)n_items, kB, smem, s>>>(                \
+        it_node, it_tree, it_begin, it_len, it_key, it_nbase, it_lbase, fo->X, fo->xnorm, n, Tn,  \
+        d, ntry, L, fo->prm.seed, exact_only, fo->perm, p32, p64, fo->node_key, fo->node_tree,    \
+        fo->node_begin, fo->node_len, fo->node_left, fo->node_right, fo->node_jstar,              \
+        fo->node_flag, fo->node_c, fo->leaf_tree, fo->leaf_begin, fo->leaf_len, d_exact, d_err)); \
+  } while (0)
+  switch (TG) {
+    case 1: RPF_SUB(1); break;
+    case 2: RPF_SUB(2); break;
+    case 3: RPF_SUB(3); break;
+    case 4: RPF_SUB(4); break;
+    case 5: RPF_SUB(5); break;
+    default: RPF_SUB(8); break;
+  }
+#undef RPF_SUB
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RPF_OK : rpf_cuda_err(e);
+}
