@@ -22,7 +22,7 @@
  *                 Algorithm 1 picks nodes from its working set is irrelevant.
  *   direction   : r = g * (1 / |g|), g ~ N(0, I_d) by FP32 Box-Muller on our
  *                 own FP32 ln and sin/cos series (no libm transcendental);
- *                 |g| and r in FP64.
+ *                 |g| and r in FP32 (r stored as doubles).
  *   projection  : p = fold_k fma((double)x_k, r_k, p) from +0.0 (FP64).
  *   dispersion  : V = canonical-order sum of (p - mu)^2 with mu = S / m and
  *                 S the canonical-order sum of p (argmax of V == argmax SD).
@@ -154,12 +154,14 @@ void orc_sincos2pif(float u, float* c_out, float* s_out) {
 
 /* ------------------------------------------------------------------------- */
 /* Random direction for (tree t, node key, try j): Sec. 2, "generate a random */
-/* direction" of Algorithms 1 and 2.  g_{2i}, g_{2i+1} by Box-Muller in FP32  */
-/* from the top 24 bits of words c = 2i and c = 2i+1; then in FP64           */
-/* |g| = sqrt(sum_k g_k^2) (sequential fma) and r_k = g_k * (1 / |g|).       */
+/* direction" of Algorithms 1 and 2, all in FP32: g_{2i}, g_{2i+1} by         */
+/* Box-Muller from the top 24 bits of words c = 2i and c = 2i+1; then         */
+/* s = sequential fmaf sum of g_k^2, inv = 1 / sqrtf(s), r_k = g_k * inv.     */
+/* r is returned as doubles (exactly the FP32 values).                        */
 /* ------------------------------------------------------------------------- */
 void orc_direction(uint64_t seed, uint64_t t, uint64_t key, uint64_t j, int d,
                    double* r) {
+  float* g = (float*)malloc(sizeof(float) * (size_t)(d + 1));
   for (int i = 0; 2 * i < d; ++i) {
     uint64_t w1 = orc_word(seed, ORC_TAG_DIR, t, key, j, (uint64_t)(2 * i));
     uint64_t w2 = orc_word(seed, ORC_TAG_DIR, t, key, j, (uint64_t)(2 * i + 1));
@@ -168,19 +170,20 @@ void orc_direction(uint64_t seed, uint64_t t, uint64_t key, uint64_t j, int d,
     float rho = sqrtf(-2.0f * orc_lnf(u1));
     float c, s;
     orc_sincos2pif(u2, &c, &s);
-    r[2 * i] = (double)(rho * c);
-    if (2 * i + 1 < d) r[2 * i + 1] = (double)(rho * s);
+    g[2 * i] = rho * c;
+    if (2 * i + 1 < d) g[2 * i + 1] = rho * s;
   }
-  double ss = 0.0;
-  for (int k = 0; k < d; ++k) ss = fma(r[k], r[k], ss);
-  double nrm = sqrt(ss);
-  if (nrm == 0.0) { /* unreachable in practice: every Gaussian pair zero */
+  float ss = 0.0f;
+  for (int k = 0; k < d; ++k) ss = fmaf(g[k], g[k], ss);
+  if (ss == 0.0f) { /* unreachable in practice: every Gaussian pair zero */
     for (int k = 0; k < d; ++k) r[k] = 0.0;
     r[0] = 1.0;
+    free(g);
     return;
   }
-  double inv = 1.0 / nrm;
-  for (int k = 0; k < d; ++k) r[k] = r[k] * inv;
+  float inv = 1.0f / sqrtf(ss);
+  for (int k = 0; k < d; ++k) r[k] = (double)(g[k] * inv);
+  free(g);
 }
 
 /* Projection coefficient r . x (Sec. 2, "projection coefficient"). */
