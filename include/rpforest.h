@@ -164,7 +164,8 @@ int rpf_forest_leaves(const rpf_forest* f, int32_t* tree, int32_t* begin, int32_
 
 /* Node table (host, n_nodes entries each): key (node key of the counter-based
    draws; root 1), tree, begin, len, left child, right child (-1 for leaves),
-   chosen try (-1 if none), flag (1 = rank split), split point c. */
+   chosen try (-1 if none), flags (bit 0: rank split; bit 1: the split was
+   decided by the FP64 fallback), split point c. */
 int rpf_forest_nodes(const rpf_forest* f, uint64_t* key, int32_t* tree, int32_t* begin,
                      int32_t* len, int32_t* left, int32_t* right, int32_t* jstar,
                      int32_t* flag, double* c);

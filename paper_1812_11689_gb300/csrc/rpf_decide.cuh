@@ -3,7 +3,8 @@
 //
 // Exact definitions (what the CPU oracle computes):
 //   direction r_j   : Box-Muller N(0, I) from the node's counter words,
-//                     normalised in FP64 (Algorithms 1-2, "random direction")
+//                     normalised, all in FP32 (Algorithms 1-2, "random
+//                     direction"); r is an FP32 vector
 //   projection      : p64(x, r) = fold_k fma((double)x_k, r_k, p) from +0.0
 //   dispersion V_j  : canonical-order FP64 sum of (p - mu)^2, mu = S / m
 //   choice          : first j with V_j > best, best starting at 0 (Alg. 2)
@@ -14,10 +15,11 @@
 // Fast path (FP32, certified): for o = the node's first member,
 //   q'_j(x) = fl32-dot(r32_j, fl32(x - o)),   b_j = p64(o, r_j),
 //   |q'_j(x) - (p64_j(x) - b_j)| <= rad(x)
-//     rad(x) = kappa_d |x - o|_2 + (d + 2) 2^-53 1.02 (|x| + |o|),
+//     rad(x) = kappa_d |x - o|_2 + (d + 40) 2^-53 1.02 (|x| + |o|),
 //     kappa_d = (d + 4) 2^-24 1.0625
-// (fma-chain dot-product bound, rounding of r and of x - o to FP32, and the
-// FP64 projections' own bound; Cauchy-Schwarz with |r| <= 1 + d 2^-53).
+// (fma-chain dot-product bound, rounding of x - o to FP32, and the
+// FP64 projections' own bound -- b_j may be summed in any order of depth
+// <= d + 38; Cauchy-Schwarz with |r| <= 1 + d 2^-53).
 // Decisions are taken from q' when the bound separates them, else in FP64.
 #pragma once
 
@@ -38,31 +40,26 @@ __device__ __forceinline__ void rpf_gauss_pair(uint64_t seed, uint64_t t, uint64
   *g1 = __fmul_rn(rho, s);
 }
 
-// 1 / |g| with |g| = sqrt(sequential fma sum of g_k^2) in FP64; 0 if g = 0
-__device__ __forceinline__ double rpf_inv_norm(const double* g, int d) {
-  double ss = 0.0;
-  for (int k = 0; k < d; ++k) ss = __fma_rn(g[k], g[k], ss);
-  const double nrm = __dsqrt_rn(ss);
-  return nrm == 0.0 ? 0.0 : __ddiv_rn(1.0, nrm);
+// 1 / |g| in FP32: |g| = sqrtf(sequential fmaf sum of g_k^2); 0 if g = 0
+__device__ __forceinline__ float rpf_inv_norm32(const float* g, int d) {
+  float ss = 0.0f;
+  for (int k = 0; k < d; ++k) ss = __fmaf_rn(g[k], g[k], ss);
+  return ss == 0.0f ? 0.0f : __fdiv_rn(1.0f, __fsqrt_rn(ss));
 }
 
-// Direction r (FP64) for (tree t, node key, try j): r_k = g_k * (1 / |g|);
-// the unreachable all-zero draw gives e_0.  One thread.
+// Direction r for (tree t, node key, try j), all in FP32: r_k = g_k * (1/|g|);
+// the unreachable all-zero draw gives e_0.  One thread; g is scratch for d
+// floats; r receives the FP32 values widened to FP64.
 __device__ __forceinline__ void rpf_gen_direction(uint64_t seed, uint64_t t, uint64_t key, uint64_t j,
-                                                  int d, double* r) {
+                                                  int d, float* g, double* r) {
   for (int i = 0; 2 * i < d; ++i) {
     float g0, g1;
     rpf_gauss_pair(seed, t, key, j, i, &g0, &g1);
-    r[2 * i] = (double)g0;
-    if (2 * i + 1 < d) r[2 * i + 1] = (double)g1;
+    g[2 * i] = g0;
+    if (2 * i + 1 < d) g[2 * i + 1] = g1;
   }
-  const double inv = rpf_inv_norm(r, d);
-  if (inv == 0.0) {
-    for (int k = 0; k < d; ++k) r[k] = 0.0;
-    r[0] = 1.0;
-    return;
-  }
-  for (int k = 0; k < d; ++k) r[k] = __dmul_rn(r[k], inv);
+  const float inv = rpf_inv_norm32(g, d);
+  for (int k = 0; k < d; ++k) r[k] = inv == 0.0f ? (k == 0 ? 1.0 : 0.0) : (double)__fmul_rn(g[k], inv);
 }
 
 // canonical FP64 projection
@@ -78,49 +75,61 @@ __device__ __forceinline__ float rpf_kappa(int d) { return (float)(d + 4) * 0x1p
 // of fl(x - o), xn / on = upper bounds of |x| and |o|
 __device__ __forceinline__ float rpf_point_rad(int d, float nn, float xn, float on) {
   const float nrm = __fmul_ru(__fsqrt_ru(nn), 1.0f + (float)(d + 4) * 0x1p-24f);
-  const float e64 = __fmul_ru((float)(d + 2) * 0x1p-53f * 1.02f, __fadd_ru(xn, on));
+  const float e64 = __fmul_ru((float)(d + 40) * 0x1p-53f * 1.02f, __fadd_ru(xn, on));
   return __fmaf_ru(rpf_kappa(d), nrm, e64);
 }
 
-// gamma_h for the FP32 statistics: <= 16 sequential terms per thread, a warp
-// butterfly (5) and a sequential merge of the 8 warp partials (8)
-#define RPF_STAT_DEPTH 30
+// gamma_h for the FP32 statistics: at most 32 sequential terms per thread,
+// a warp butterfly (5) and an FP32 merge of at most 8 warp partials.
+#define RPF_STAT_DEPTH 45
 
-// Certify Algorithm 2's choice from the FP32 statistics.  Inputs per try j:
-// S1 = sum q', S2 = sum q'^2, A = sum |q'| (FP32 accumulated, FP64 across
-// chunks), base b_j; node size m and radius rad.  Returns the certified
-// winner, or -1 when the bounds do not separate it (exact path).
-__device__ __forceinline__ int rpf_certify(int ntry, double m, const double* S1, const double* S2,
-                                           const double* A, const double* base, double rad) {
+// Bounds of sqrt(V_j) (the canonical FP64 dispersion of Algorithm 2) from the
+// FP32 statistics of try j: S1 = sum q', S2 = sum q'^2, A = sum |q'|
+// (<= RPF_STAT_DEPTH roundings on any path), node size m, radius rad, and
+// babs >= |b_j| (|o| bounds it).  With Vhat = S2 - S1^2 / m:
+//   |Vhat - V_q| <= EV   (FP32 sums: gamma (S2 + 2|S1| A / m + gamma A^2 / m),
+//                         plus 1e-14 S2 for the FP64 arithmetic here)
+//   |sqrt(V_q) - sqrt(V_p)| <= sqrt(m) rad    (sqrt of a centred sum of
+//                         squares is 1-Lipschitz in the vector of projections)
+//   |sqrt(V) - sqrt(V_p)| <= 1e-12 sqrt(V) + sqrt(m) 1e-13 (|b| + A/m + rad)
+//                         (the canonical FP64 reduction itself)
+// all error terms doubled.  lo / hi are rounded outwards in FP32.
+__device__ __forceinline__ void rpf_try_bounds(int m, double inv_m, double S1, double S2,
+                                               double A, double babs, float rad, double* vhat,
+                                               float* lo, float* hi) {
   const double u = 0x1p-24;
   const double gam = RPF_STAT_DEPTH * u / (1.0 - RPF_STAT_DEPTH * u);
-  const double sm = sqrt(m);
+  const double V = S2 - S1 * (S1 * inv_m);
+  const double Am = A * (1.0 + 2.0 * gam);
+  const double EV =
+      2.0 * (gam * (S2 + 2.0 * fabs(S1) * Am * inv_m + gam * Am * Am * inv_m) + 1e-14 * fabs(S2)) +
+      0x1p-50 * S1 * S1 * inv_m;
+  const float sqm = __fsqrt_ru(__int2float_ru(m));
+  const float vup = __fsqrt_ru(__double2float_ru(fmax(V + EV, 0.0)));
+  const float lip = __fmul_ru(__fmul_ru(2.0f, sqm), rad);
+  const float mid = __fadd_ru(__double2float_ru(fabs(babs) + Am * inv_m), rad);
+  const float e64 = __fmul_ru(2.0f, __fadd_ru(__fmul_ru(1e-12f, vup), __fmul_ru(__fmul_ru(sqm, 1e-13f), mid)));
+  const float err = __fadd_ru(lip, e64);
+  *vhat = V;
+  *hi = __fadd_ru(vup, err);
+  *lo = __fsub_rd(__fsqrt_rd(__double2float_rd(fmax(V - EV, 0.0))), err);
+}
+
+// Certified winner of Algorithm 2 from per-try bounds: the first argmax w of
+// Vhat, accepted iff lo_w > 0 and lo_w > hi_k for every k != w (then V_w is
+// the unique maximum and positive, so Algorithm 2 picks w); else -1.
+__device__ __forceinline__ int rpf_certify_select(int ntry, const double* vhat, const float* lo,
+                                                  const float* hi) {
   int w = -1;
   double vb = -1.0;
-  for (int j = 0; j < ntry; ++j) {
-    const double V = S2[j] - S1[j] * S1[j] / m;
-    if (V > vb) {
-      vb = V;
+  for (int j = 0; j < ntry; ++j)
+    if (vhat[j] > vb) {
+      vb = vhat[j];
       w = j;
     }
-  }
-  if (w < 0) return -1;
-  double lo_w = 0.0, hi_other = -1.0;
-  for (int j = 0; j < ntry; ++j) {
-    const double V = S2[j] - S1[j] * S1[j] / m;
-    const double Am = A[j] * (1.0 + 2.0 * gam);
-    const double EV = 2.0 * (gam * (S2[j] + 2.0 * fabs(S1[j]) * Am / m + gam * Am * Am / m) +
-                             1e-14 * fabs(S2[j]));
-    const double lip = 2.0 * sm * rad;
-    const double e64 = 2.0 * (1e-12 * sqrt(fmax(V, 0.0)) + sm * 1e-13 * (fabs(base[j]) + Am / m + rad));
-    if (j == w) {
-      lo_w = sqrt(fmax(V - EV, 0.0)) - lip - e64;
-    } else {
-      const double hi = sqrt(fmax(V + EV, 0.0)) + lip + e64;
-      hi_other = fmax(hi_other, hi);
-    }
-  }
-  if (!(lo_w > 0.0) || !(lo_w > hi_other)) return -1;
+  if (w < 0 || !(lo[w] > 0.0f)) return -1;
+  for (int j = 0; j < ntry; ++j)
+    if (j != w && !(lo[w] > hi[j])) return -1;
   return w;
 }
 

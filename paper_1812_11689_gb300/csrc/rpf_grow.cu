@@ -112,9 +112,9 @@ __global__ void k_dirs_a(int F, int ntry, int d, uint64_t seed, int64_t n, const
   if (g >= (int64_t)F * ntry) return;
   const int f = (int)(g / ntry), j = (int)(g % ntry);
   double* r = dir64 + g * d;
-  rpf_gen_direction(seed, (uint64_t)fr_tree[f], fr_key[f], (uint64_t)j, d, r);
   float* r32 = dir32 + g * d;
-  for (int k = 0; k < d; ++k) r32[k] = __double2float_rn(r[k]);
+  rpf_gen_direction(seed, (uint64_t)fr_tree[f], fr_key[f], (uint64_t)j, d, r32, r);
+  for (int k = 0; k < d; ++k) r32[k] = (float)r[k];
   const int32_t og = perm_cur[(int64_t)fr_tree[f] * n + fr_begin[f]];
   fr_base[g] = rpf_p64(X + (int64_t)og * d, r, d);
   if (j == 0) fr_ogid[f] = og;
@@ -125,7 +125,10 @@ __global__ void k_dirs_keys(uint64_t seed, int32_t t, const uint64_t* keys, int 
                             double* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nk) return;
-  rpf_gen_direction(seed, (uint64_t)t, keys[i], (uint64_t)j, d, out + (int64_t)i * d);
+  // the FP32 draw is staged in the upper half of the output row's bytes
+  double* r = out + (int64_t)i * d;
+  float* g = reinterpret_cast<float*>(r) + d;
+  rpf_gen_direction(seed, (uint64_t)t, keys[i], (uint64_t)j, d, g, r);
 }
 
 template <int TG>
@@ -203,7 +206,10 @@ __global__ void k_certify_a(int F, int ntry, int exact_only, const int32_t* fr_c
   float rad = 0.0f;
   for (int c = cb; c < cb + nc; ++c) rad = fmaxf(rad, cp_rad[c]);
   fr_rad[f] = rad;
-  double S1[RPF_MAX_TRY], S2[RPF_MAX_TRY], A[RPF_MAX_TRY];
+  double vh[RPF_MAX_TRY];
+  float lo_[RPF_MAX_TRY], hi_[RPF_MAX_TRY];
+  const int m = fr_len[f];
+  const double inv_m = 1.0 / (double)m;
   for (int j = 0; j < ntry; ++j) {
     double a = 0.0, b = 0.0, e = 0.0;
     for (int c = cb; c < cb + nc; ++c) {
@@ -211,13 +217,9 @@ __global__ void k_certify_a(int F, int ntry, int exact_only, const int32_t* fr_c
       b = __dadd_rn(b, cp_s2[(int64_t)c * ntry + j]);
       e = __dadd_rn(e, cp_a[(int64_t)c * ntry + j]);
     }
-    S1[j] = a;
-    S2[j] = b;
-    A[j] = e;
+    rpf_try_bounds(m, inv_m, a, b, e, fr_base[(int64_t)f * ntry + j], rad, &vh[j], &lo_[j], &hi_[j]);
   }
-  const int w = exact_only ? -1
-                           : rpf_certify(ntry, (double)fr_len[f], S1, S2, A,
-                                         fr_base + (int64_t)f * ntry, (double)rad);
+  const int w = exact_only ? -1 : rpf_certify_select(ntry, vh, lo_, hi_);
   if (w < 0) {
     fr_exact[f] = 1;
     return;
@@ -271,16 +273,29 @@ __global__ void k_cand_finish(int F, const int32_t* fr_exact, const unsigned lon
 }
 
 // --- exact path: canonical FP64 projections and statistics (Algorithm 2) ---
+// Chunks of exact nodes, listed so that their FP64 work spreads over the GPU.
+__global__ void k_exact_list(int C, const int32_t* ch_node, const int32_t* fr_exact, int32_t* list,
+                             int32_t* count) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C || !fr_exact[ch_node[c]]) return;
+  list[atomicAdd(count, 1)] = c;
+}
+
+// Grid-stride over (listed chunk, slice of 256 positions): canonical FP64
+// projections of every try.
 __global__ void __launch_bounds__(kBlock) k_proj64(
-    const int32_t* ch_node, const int32_t* ch_start, const int32_t* ch_len, const int32_t* fr_tree,
-    const int32_t* fr_begin, const int32_t* fr_exact, const float* X, const int32_t* perm_cur,
-    int64_t n, int64_t Tn, int d, int ntry, const double* dir64, double* p64) {
-  const int c = blockIdx.x;
-  const int f = ch_node[c];
-  if (!fr_exact[f]) return;
-  const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
-  const int len = ch_len[c];
-  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    const int32_t* list, const int32_t* count, const int32_t* ch_node, const int32_t* ch_start,
+    const int32_t* ch_len, const int32_t* fr_tree, const int32_t* fr_begin, const float* X,
+    const int32_t* perm_cur, int64_t n, int64_t Tn, int d, int ntry, const double* dir64,
+    double* p64) {
+  constexpr int kSlices = RPF_CHUNK / kBlock;
+  const int total = *count * kSlices;
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int c = list[item / kSlices], sl = item % kSlices;
+    const int i = sl * kBlock + threadIdx.x;
+    if (i >= ch_len[c]) continue;
+    const int f = ch_node[c];
+    const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
     const float* x = X + (int64_t)perm_cur[base + i] * d;
     for (int j = 0; j < ntry; ++j)
       p64[(int64_t)j * Tn + base + i] = rpf_p64(x, dir64 + ((int64_t)f * ntry + j) * d, d);
@@ -416,7 +431,7 @@ __global__ void k_split_a(int F, int ntry, uint64_t seed, const int32_t* fr_node
   }
   const int id = fr_node[f];
   node_jstar[id] = js;
-  node_flag[id] = acc ? 0 : 1;
+  node_flag[id] = (acc ? 0 : 1) | (fr_exact[f] ? 2 : 0);
   node_c[id] = c;
 }
 
@@ -809,15 +824,15 @@ __global__ void k_node_dirs(int64_t N, int d, uint64_t seed, const uint64_t* key
   if (i >= N) return;
   double* r = dir + i * d;
   float* r32 = dir32 + i * d;
-  if (left[i] < 0 || flag[i] || jstar[i] < 0) {
+  if (left[i] < 0 || (flag[i] & 1) || jstar[i] < 0) {
     for (int k = 0; k < d; ++k) {
       r[k] = 0.0;
       r32[k] = 0.0f;
     }
     return;
   }
-  rpf_gen_direction(seed, (uint64_t)tree[i], key[i], (uint64_t)jstar[i], d, r);
-  for (int k = 0; k < d; ++k) r32[k] = __double2float_rn(r[k]);
+  rpf_gen_direction(seed, (uint64_t)tree[i], key[i], (uint64_t)jstar[i], d, r32, r);
+  for (int k = 0; k < d; ++k) r32[k] = (float)r[k];
 }
 
 }  // namespace
@@ -904,6 +919,8 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
   RPF_TRY(talloc((void**)&d_cnt, sizeof(Counts)));
   RPF_TRY(talloc((void**)&d_exact, sizeof(unsigned long long)));
   RPF_TRY(talloc((void**)&d_err, sizeof(int)));
+  int32_t* ex_count = nullptr;
+  RPF_TRY(talloc((void**)&ex_count, sizeof(int32_t)));
   RPF_TRYCU(cudaMemsetAsync(d_exact, 0, sizeof(unsigned long long), s));
   RPF_TRYCU(cudaMemsetAsync(d_err, 0, sizeof(int), s));
   if (cudaMallocHost((void**)&h_cnt, sizeof(Counts)) != cudaSuccess) {
@@ -1131,9 +1148,13 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
         lv.fr_whi, fo->X, perm_cur, n, Tn, d, ntry, p32, lv.dir64, lv.fr_akey, lv.fr_bkey));
     RPF_LAUNCH("k_cand_finish", s, k_cand_finish<<<nblk(F, 128), 128, 0, s>>>(
         Fi, lv.fr_exact, lv.fr_akey, lv.fr_bkey, lv.fr_a, lv.fr_b));
-    RPF_LAUNCH("k_proj64", s, k_proj64<<<Ci, kBlock, 0, s>>>(
-        ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, fo->X, perm_cur, n, Tn, d,
-        ntry, lv.dir64, p64));
+    // the exact-chunk list borrows ch_loff, which k_node_scan fills later
+    RPF_TRYCU(cudaMemsetAsync(ex_count, 0, sizeof(int32_t), s));
+    RPF_LAUNCH("k_exact_list", s, k_exact_list<<<nblk(C, 256), 256, 0, s>>>(
+        Ci, ch_node, lv.fr_exact, lv.ch_loff, ex_count));
+    RPF_LAUNCH("k_proj64", s, k_proj64<<<4 * 152, kBlock, 0, s>>>(
+        lv.ch_loff, ex_count, ch_node, ch_start, ch_len, fr_tree, fr_begin, fo->X, perm_cur, n,
+        Tn, d, ntry, lv.dir64, p64));
     for (int pass = 0; pass < 2; ++pass) {
       RPF_LAUNCH("k_csum_chunks", s, k_csum_chunks<<<nblk(C * ntry * 32, 256), 256, 0, s>>>(
           pass, Ci, ntry, ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, n, Tn, p64,

@@ -206,7 +206,7 @@ __global__ void k_route(const float* Q, int64_t m, int d, int T, const int32_t* 
   const float* x = Q + q * d;
   int node = t;
   while (node_left[node] >= 0) {
-    if (node_flag[node]) {
+    if (node_flag[node] & 1) {  // rank split: every query goes left
       node = node_left[node];
       continue;
     }

@@ -2,10 +2,10 @@
 // shared by the level-synchronous and the CTA-local growth kernels.
 //
 // Statistics of the FP32 projections q' of a node for one try: S1 = sum q',
-// S2 = sum q'^2, A = sum |q'|, min, max.  Every thread accumulates at most 16
-// points in FP32, the warp folds with a butterfly in FP32, and thread 0 adds
-// the warp partials in FP64; the error analysis in rpf_certify assumes this
-// depth (RPF_STAT_DEPTH).
+// S2 = sum q'^2, A = sum |q'|, min, max.  Every thread accumulates at most 32
+// points in FP32, the warp folds with a butterfly in FP32, and one thread per
+// try adds the (at most 8) warp partials in FP32; the error analysis of
+// rpf_try_bounds assumes this depth (RPF_STAT_DEPTH).
 #pragma once
 
 #include "rpf_internal.cuh"
@@ -81,7 +81,7 @@ __device__ __forceinline__ void rpf_stat_add(float v, float& s1, float& s2, floa
 }
 
 // Block reduction of per-thread statistics for nj tries into o*[q] (written
-// by thread 0; visible to all threads after the trailing barrier).
+// by thread q; visible to all threads after the trailing barrier).
 // red: 8 warps x TG x 5 floats of shared memory.
 template <int TG>
 __device__ __forceinline__ void rpf_block_stats(int nj, float (&s1)[TG], float (&s2)[TG],
@@ -111,22 +111,23 @@ __device__ __forceinline__ void rpf_block_stats(int nj, float (&s1)[TG], float (
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if ((int)threadIdx.x < nj) {  // one thread per try
     const int nw = blockDim.x >> 5;
-    for (int q = 0; q < nj; ++q) {
-      double A = 0.0, B = 0.0, C = 0.0;
+    const int q = threadIdx.x;
+    {
+      float A = 0.0f, B = 0.0f, C = 0.0f;
       float lo = INFINITY, hi = -INFINITY;
       for (int u = 0; u < nw; ++u) {
         const float* r = red + (u * TG + q) * 5;
-        A = __dadd_rn(A, (double)r[0]);
-        B = __dadd_rn(B, (double)r[1]);
-        C = __dadd_rn(C, (double)r[2]);
+        A = __fadd_rn(A, r[0]);
+        B = __fadd_rn(B, r[1]);
+        C = __fadd_rn(C, r[2]);
         lo = fminf(lo, r[3]);
         hi = fmaxf(hi, r[4]);
       }
-      o1[q] = A;
-      o2[q] = B;
-      oa[q] = C;
+      o1[q] = (double)A;
+      o2[q] = (double)B;
+      oa[q] = (double)C;
       omn[q] = lo;
       omx[q] = hi;
     }

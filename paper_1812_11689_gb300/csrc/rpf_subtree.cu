@@ -18,7 +18,8 @@
 //   7. records the node and its children; leaves are written to the final
 //      permutation, inner children pushed.
 // Node ids and leaf slots come from ranges reserved per subtree (2m - 2 ids,
-// m leaf slots for m points), so the layout is deterministic.
+// m leaf slots for m points), so the layout is deterministic.  CTAs have 128
+// threads (at most 32 points per thread in the statistics).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -29,7 +30,7 @@
 
 namespace {
 
-constexpr int kB = 256;
+constexpr int kB = 128;  // 4 warps; 4 CTAs per SM hide each other's serial sections
 constexpr int kSubN = RPF_CHUNK;
 constexpr int kStack = 24;
 
@@ -41,13 +42,14 @@ struct SubState {
   float tl, tr, rad, wlo, whi;
   unsigned long long akey, bkey;
   int top, next_id, id_end, next_leaf, leaf_end;
-  int leafL, leafR, err;
+  int leafL, leafR, err, ncand;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct SubLayout {
-  size_t sP, sT, sSide, r64, r32, so, sbase, sS1, sS2, sA, sinv, smn, smx, red, total;
+  size_t sP, sT, sSide, r64, r32, so, sbase, sS1, sS2, sA, sinv, smn, smx, svh, slo, shi, red,
+      total;
 };
 
 __host__ __device__ inline SubLayout sub_layout(int d, int ntry, int TG) {
@@ -79,6 +81,12 @@ __host__ __device__ inline SubLayout sub_layout(int d, int ntry, int TG) {
   o = align16(o + 4 * (size_t)ntry);
   l.smx = o;
   o = align16(o + 4 * (size_t)ntry);
+  l.svh = o;
+  o = align16(o + 8 * (size_t)ntry);
+  l.slo = o;
+  o = align16(o + 4 * (size_t)ntry);
+  l.shi = o;
+  o = align16(o + 4 * (size_t)ntry);
   l.red = o;
   o = align16(o + 4 * (size_t)(8 * TG * 5 + 40));
   l.total = o;
@@ -86,7 +94,7 @@ __host__ __device__ inline SubLayout sub_layout(int d, int ntry, int TG) {
 }
 
 template <int TG>
-__global__ void __launch_bounds__(kB, 2) k_subtree(
+__global__ void __launch_bounds__(kB, 4) k_subtree(
     const int32_t* it_node, const int32_t* it_tree, const int32_t* it_begin, const int32_t* it_len,
     const uint64_t* it_key, const int32_t* it_nbase, const int32_t* it_lbase,
     const float* __restrict__ X, const float* __restrict__ xnorm, int64_t n, int64_t Tn, int d,
@@ -110,6 +118,9 @@ __global__ void __launch_bounds__(kB, 2) k_subtree(
   double* sinv = reinterpret_cast<double*>(smraw + lay.sinv);
   float* smn = reinterpret_cast<float*>(smraw + lay.smn);
   float* smx = reinterpret_cast<float*>(smraw + lay.smx);
+  double* svh = reinterpret_cast<double*>(smraw + lay.svh);
+  float* slo = reinterpret_cast<float*>(smraw + lay.slo);
+  float* shi = reinterpret_cast<float*>(smraw + lay.shi);
   float* red = reinterpret_cast<float*>(smraw + lay.red);
   __shared__ SubState S;
   __shared__ int st_nb[kStack], st_m[kStack], st_id[kStack];
@@ -155,31 +166,31 @@ __global__ void __launch_bounds__(kB, 2) k_subtree(
     const int nb = S.nb, m = S.m, id = S.id;
     const uint64_t key = S.key;
 
-    // 1. candidate directions
+    // 1. candidate directions, all in FP32 (r32), widened copy in r64
     for (int idx = tid; idx < ntry * npairs; idx += kB) {
       const int j = idx / npairs, i = idx - j * npairs;
       float g0, g1;
       rpf_gauss_pair(seed, (uint64_t)t, key, (uint64_t)j, i, &g0, &g1);
-      r64[j * d + 2 * i] = (double)g0;
-      if (2 * i + 1 < d) r64[j * d + 2 * i + 1] = (double)g1;
+      r32[j * d + 2 * i] = g0;
+      if (2 * i + 1 < d) r32[j * d + 2 * i + 1] = g1;
     }
     __syncthreads();
-    for (int j = tid; j < ntry; j += kB) sinv[j] = rpf_inv_norm(r64 + j * d, d);
+    float* sinv32 = reinterpret_cast<float*>(sinv);
+    for (int j = tid; j < ntry; j += kB) sinv32[j] = rpf_inv_norm32(r32 + j * d, d);
     __syncthreads();
     for (int idx = tid; idx < ntry * d; idx += kB) {
       const int j = idx / d, k = idx - j * d;
-      const double inv = sinv[j];
-      const double v = inv == 0.0 ? (k == 0 ? 1.0 : 0.0) : __dmul_rn(r64[idx], inv);
-      r64[idx] = v;
-      r32[idx] = __double2float_rn(v);
+      const float inv = sinv32[j];
+      const float v = inv == 0.0f ? (k == 0 ? 1.0f : 0.0f) : __fmul_rn(r32[idx], inv);
+      r32[idx] = v;
+      r64[idx] = (double)v;
     }
     __syncthreads();
 
-    // 2. centre o and the base projections b_j
+    // 2. centre o = the node's first member
     const int og = sP[nb];
     const float* xo = X + (int64_t)og * d;
     for (int k = tid; k < d; k += kB) so[k] = xo[k];
-    for (int j = tid; j < ntry; j += kB) sbase[j] = rpf_p64(xo, r64 + j * d, d);
     __syncthreads();
     const float on = xnorm[og];
 
@@ -225,8 +236,15 @@ __global__ void __launch_bounds__(kB, 2) k_subtree(
     }
 
     // 4. certify the choice of Algorithm 2
+    if (!exact_only) {
+      const double inv_m = 1.0 / (double)m;
+      for (int j = tid; j < ntry; j += kB)
+        rpf_try_bounds(m, inv_m, sS1[j], sS2[j], sA[j], (double)on, radmax, &svh[j], &slo[j],
+                       &shi[j]);
+      __syncthreads();
+    }
     if (tid == 0) {
-      const int w = exact_only ? -1 : rpf_certify(ntry, (double)m, sS1, sS2, sA, sbase, (double)radmax);
+      const int w = exact_only ? -1 : rpf_certify_select(ntry, svh, slo, shi);
       S.exact = w < 0;
       S.js = w;
       S.rad = radmax;
@@ -285,22 +303,51 @@ __global__ void __launch_bounds__(kB, 2) k_subtree(
       }
       __syncthreads();
     } else {
-      // exact min / max among the candidates the bound leaves
+      // exact min / max among the candidates the bound leaves: compact the
+      // candidates, then one warp evaluates their canonical FP64 projections
+      // (FP64 warp instructions are expensive whatever the active lanes)
       const int w = S.js;
       const float lo = S.wlo, hi = S.whi;
       const float* p = p32 + (int64_t)w * Tn + pbase + nb;
+      if (tid == 0) S.ncand = 0;
+      __syncthreads();
       for (int i = tid; i < m; i += kB) {
         const float v = p[i];
-        const bool ca = v <= lo, cb = v >= hi;
-        if (!ca && !cb) continue;
-        const double q = rpf_p64(X + (int64_t)sP[nb + i] * d, r64 + w * d, d);
-        if (ca) atomicMin(&S.akey, rpf_dkey(q));
-        if (cb) atomicMax(&S.bkey, rpf_dkey(q));
+        const int code = (v <= lo ? 1 : 0) | (v >= hi ? 2 : 0);
+        if (code) {
+          const int slot = atomicAdd(&S.ncand, 1);
+          sT[slot] = (i << 2) | code;
+        }
       }
       __syncthreads();
-      if (tid == 0) {
-        S.a = rpf_dkey_inv(S.akey);
-        S.b = rpf_dkey_inv(S.bkey);
+      const int nc = S.ncand;
+      if (warp == 0) {
+        unsigned long long ak = rpf_dkey(INFINITY), bk = rpf_dkey(-INFINITY);
+        for (int q0 = 0; q0 < nc; q0 += 32) {
+          const int q = q0 + lane;
+          if (q < nc) {
+            const int e = sT[q];
+            const double v = rpf_p64(X + (int64_t)sP[nb + (e >> 2)] * d, r64 + w * d, d);
+            if (e & 1) ak = min(ak, rpf_dkey(v));
+            if (e & 2) bk = max(bk, rpf_dkey(v));
+          }
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+          ak = min(ak, __shfl_xor_sync(RPF_FULL, ak, off));
+          bk = max(bk, __shfl_xor_sync(RPF_FULL, bk, off));
+        }
+        if (lane == 0) {
+          S.a = rpf_dkey_inv(ak);
+          S.b = rpf_dkey_inv(bk);
+        }
+      } else if (warp == 1) {
+        // b_w = r_w . o in FP64 (any order: the radius covers it)
+        double acc = 0.0;
+        for (int k = lane; k < d; k += 32) acc = __fma_rn((double)so[k], r64[w * d + k], acc);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(RPF_FULL, acc, off));
+        if (lane == 0) sbase[w] = acc;
       }
       __syncthreads();
     }
@@ -319,7 +366,7 @@ __global__ void __launch_bounds__(kB, 2) k_subtree(
         S.tr = tr;
       }
       node_jstar[id] = js;
-      node_flag[id] = acc ? 0 : 1;
+      node_flag[id] = (acc ? 0 : 1) | (S.exact ? 2 : 0);
       node_c[id] = c;
     }
     __syncthreads();
@@ -329,22 +376,38 @@ __global__ void __launch_bounds__(kB, 2) k_subtree(
       const int js = S.js, flag = S.flag, exact = S.exact;
       const double c = S.c;
       const float tl = S.tl, tr = S.tr;
-      int cnt = 0;
+      if (tid == 0) S.ncand = 0;
+      __syncthreads();
       for (int i = tid; i < m; i += kB) {
-        bool left;
+        int left;
         if (flag) {
           left = i < (m >> 1);
         } else if (exact) {
           left = p64[(int64_t)js * Tn + pbase + nb + i] < c;
         } else {
           const float v = p32[(int64_t)js * Tn + pbase + nb + i];
-          if (v < tl) left = true;
-          else if (v >= tr) left = false;
-          else left = rpf_p64(X + (int64_t)sP[nb + i] * d, r64 + js * d, d) < c;
+          if (v < tl) {
+            left = 1;
+          } else if (v >= tr) {
+            left = 0;
+          } else {  // undecided by the bound: FP64 below
+            left = 2;
+            sT[atomicAdd(&S.ncand, 1)] = i;
+          }
         }
-        sSide[i] = left ? 1 : 0;
-        cnt += left ? 1 : 0;
+        sSide[i] = (uint8_t)left;
       }
+      __syncthreads();
+      if (warp == 0) {
+        const int na = S.ncand;
+        for (int q = lane; q < na; q += 32) {
+          const int i = sT[q];
+          sSide[i] = rpf_p64(X + (int64_t)sP[nb + i] * d, r64 + js * d, d) < c ? 1 : 0;
+        }
+      }
+      __syncthreads();
+      int cnt = 0;
+      for (int i = tid; i < m; i += kB) cnt += sSide[i];
       for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(RPF_FULL, cnt, off);
       if (lane == 0) wsc[warp] = cnt;
       __syncthreads();

@@ -49,7 +49,7 @@ def compare_trees(g, o, T):
     for i in range(len(nodes["key"])):
         if nodes["left"][i] >= 0:
             gi[(int(nodes["tree"][i]), int(nodes["key"][i]))] = (
-                int(nodes["jstar"][i]), int(nodes["flag"][i]), nodes["c"][i])
+                int(nodes["jstar"][i]), int(nodes["flag"][i]) & 1, nodes["c"][i])
     count = 0
     for t in range(T):
         on = o.nodes(t)
