@@ -98,11 +98,12 @@ int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* s
   cudaGetDevice(&f->device);
   int rc;
   if ((rc = dalloc(f, &f->X, (size_t)n * d)) || (rc = dalloc(f, &f->xnorm, (size_t)n)) ||
-      (rc = dalloc(f, &f->perm, (size_t)n * p->n_trees))) {
+      (rc = dalloc(f, &f->perm, (size_t)n * p->n_trees)) || (rc = dalloc(f, &f->d_err, 1))) {
     free_forest(f);
     return rc;
   }
-  cudaError_t e = cudaMemcpyAsync(f->X, X, sizeof(float) * n * d, cudaMemcpyDefault, s);
+  cudaError_t e = cudaMemsetAsync(f->d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->X, X, sizeof(float) * n * d, cudaMemcpyDefault, s);
   if (e != cudaSuccess) {
     free_forest(f);
     return rpf_cuda_err(e);

@@ -224,6 +224,8 @@ struct rpf_forest {
   int32_t max_leaf = 0;
   std::vector<int64_t> tree_tile_begin;  // T + 1 (host): tiles of tree t
 
+  int* d_err = nullptr;  // device error word (RPF_ETIMEOUT from bounded waits)
+
   // staging for host outputs of rpf_all_knn
   void* stage = nullptr;
   size_t stage_bytes = 0;

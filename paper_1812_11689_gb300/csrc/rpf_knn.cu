@@ -20,14 +20,18 @@
 #include <vector>
 
 #include "rpf_internal.cuh"
+#include "rpf_tma.cuh"
 
 namespace {
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Register-resident sorted top-K (ascending by (d, idx)); KMAX is a compile-
-// time capacity, K <= KMAX the runtime length.
+// Register-resident sorted list of the KMAX smallest (d, idx) offered so far
+// (ascending; empty slots are (+inf, -1)).  Every caller needs the K <= KMAX
+// smallest, which the first K entries are.  The length is a compile-time
+// constant so the list stays in registers (a run-time length makes the
+// compiler place it in local memory); insertion is a branch-free network.
 template <int KMAX>
 struct TopK {
   float kd[KMAX];
@@ -39,111 +43,162 @@ struct TopK {
       ki[q] = -1;
     }
   }
-  __device__ __forceinline__ float worst_d(int K) const {
-    float w = kd[0];
-#pragma unroll
-    for (int q = 0; q < KMAX; ++q)
-      if (q == K - 1) w = kd[q];
-    return w;
+  __device__ __forceinline__ bool better_than_last(float v, int j) const {
+    return rpf_less(v, j, kd[KMAX - 1], ki[KMAX - 1]);
   }
-  __device__ __forceinline__ int worst_i(int K) const {
-    int w = ki[0];
+  // insert (v, j); the caller checked better_than_last
+  __device__ __forceinline__ void insert(float v, int j) {
 #pragma unroll
-    for (int q = 0; q < KMAX; ++q)
-      if (q == K - 1) w = ki[q];
-    return w;
-  }
-  // insert assuming (v, j) < entry K-1
-  __device__ __forceinline__ void insert(int K, float v, int j) {
-    bool done = false;
-#pragma unroll
-    for (int q = KMAX - 1; q >= 0; --q) {
-      if (q < K && !done) {
-        if (q > 0 && rpf_less(v, j, kd[q - 1], ki[q - 1])) {
-          kd[q] = kd[q - 1];
-          ki[q] = ki[q - 1];
-        } else {
-          kd[q] = v;
-          ki[q] = j;
-          done = true;
-        }
-      }
+    for (int q = KMAX - 1; q >= 1; --q) {
+      const bool sh = rpf_less(v, j, kd[q - 1], ki[q - 1]);
+      const bool pl = !sh && rpf_less(v, j, kd[q], ki[q]);
+      kd[q] = sh ? kd[q - 1] : (pl ? v : kd[q]);
+      ki[q] = sh ? ki[q - 1] : (pl ? j : ki[q]);
     }
+    const bool p0 = rpf_less(v, j, kd[0], ki[0]);
+    kd[0] = p0 ? v : kd[0];
+    ki[0] = p0 ? j : ki[0];
   }
-  __device__ __forceinline__ bool contains(int K, int j) const {
+  __device__ __forceinline__ void offer(float v, int j) {
+    if (better_than_last(v, j)) insert(v, j);
+  }
+  __device__ __forceinline__ bool contains(int j) const {
     bool f = false;
 #pragma unroll
-    for (int q = 0; q < KMAX; ++q) f |= (q < K) && (ki[q] == j);
+    for (int q = 0; q < KMAX; ++q) f |= ki[q] == j;
     return f;
   }
-  __device__ __forceinline__ void offer(int K, float v, int j, float& wd, int& wi) {
-    if (rpf_less(v, j, wd, wi)) {
-      insert(K, v, j);
-      wd = worst_d(K);
-      wi = worst_i(K);
-    }
+  // first K entries to out[0..K)
+  __device__ __forceinline__ void store(int K, uint2* out) const {
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q)
+      if (q < K) out[q] = make_uint2(__float_as_uint(kd[q]), (unsigned)ki[q]);
   }
 };
 
 // ---------------------------------------------------------------------------
-// Plain leaf tiles.  Tile = consecutive leaves of one tree (sorted leaf list)
-// with at most blockDim rows.  Rows staged in shared memory when they fit.
+// Plain leaf tiles.  A tile is a run of consecutive leaves of one tree (the
+// leaf list is sorted by begin), so its rows are the permutation positions
+// b0 .. b0 + rows - 1.  Rows are staged in shared memory by bulk copies
+// (TMA engine), padded to dp floats with zeros beyond d.  Work item = one
+// leaf and a block of 32 of its rows, taken by one warp: lane l owns row
+// lb + 32 w + l (its coordinates in registers when d <= 64) and scans every
+// column of the leaf, whose coordinates are broadcast from shared memory.
+// Each distance is the canonical fmaf chain over k in order, so d32 is
+// bit-identical to the oracle's.
 // cand layout: [(g * n + point) * K + k] as (d32 bits, idx).
 // ---------------------------------------------------------------------------
-template <int KMAX, bool SMEM>
-__global__ void __launch_bounds__(1024) k_leaf_plain(const int32_t* tile_first, const int32_t* tile_count,
-                             int64_t tile_base, const int32_t* leaf_tree,
-                             const int32_t* leaf_begin, const int32_t* leaf_len,
-                             const int32_t* perm, const float* X, int64_t n, int d, int K,
-                             int t0, uint2* cand) {
-  extern __shared__ float xs[];
+template <int KMAX, bool REG>
+__global__ void __launch_bounds__(128) k_leaf_plain(const int32_t* tile_first,
+                                                    const int32_t* tile_count, int64_t tile_base,
+                                                    const int32_t* leaf_tree,
+                                                    const int32_t* leaf_begin,
+                                                    const int32_t* leaf_len, const int32_t* perm,
+                                                    const float* __restrict__ X, int64_t n, int d,
+                                                    int dp, int K, int t0, uint2* cand, int* err) {
+  extern __shared__ __align__(16) float xs[];
   __shared__ int leaf_off[1025];
+  __shared__ int item_off[1025];
+  __shared__ __align__(8) uint64_t bar;
   const int64_t tile = tile_base + blockIdx.x;
   const int lf0 = tile_first[tile], nl = tile_count[tile];
   const int t = leaf_tree[lf0];
   const int b0 = leaf_begin[lf0];
-  // leaves of a tile are consecutive in the tree's permutation (sorted by
-  // begin), so row r of the tile is permutation position b0 + r
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int q = threadIdx.x; q < nl; q += blockDim.x) leaf_off[q] = leaf_begin[lf0 + q] - b0;
   if (threadIdx.x == 0) leaf_off[nl] = leaf_begin[lf0 + nl - 1] + leaf_len[lf0 + nl - 1] - b0;
   __syncthreads();
   const int rows = leaf_off[nl];
   const int32_t* prow = perm + (int64_t)t * n + b0;
-  const int dp = d + 1;
-  if (SMEM) {  // coalesced row copies, one warp per row
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int r = w; r < rows; r += nw) {
-      const float* src = X + (int64_t)prow[r] * d;
-      for (int k = l; k < d; k += 32) xs[r * dp + k] = src[k];
+  if (warp == 0) {  // item_off[q] = sum over earlier leaves of ceil(len / 32)
+    int run = 0;
+    for (int q0 = 0; q0 < nl; q0 += 32) {
+      const int q = q0 + lane;
+      const int v = q < nl ? (leaf_off[q + 1] - leaf_off[q] + 31) >> 5 : 0;
+      int x = v;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(RPF_FULL, x, off);
+        if (lane >= off) x += y;
+      }
+      if (q < nl) item_off[q] = run + x - v;
+      run += __shfl_sync(RPF_FULL, x, 31);
+    }
+    if (lane == 0) item_off[nl] = run;
+  }
+  if ((d & 3) == 0) {
+    if (threadIdx.x == 0) {
+      rpf_mbar_init(&bar, 1);
+      rpf_mbar_arrive_expect_tx(&bar, (uint32_t)rows * (uint32_t)d * 4u);
     }
     __syncthreads();
+    for (int r = threadIdx.x; r < rows; r += blockDim.x)
+      rpf_bulk_g2s(xs + r * dp, X + (int64_t)prow[r] * d, (uint32_t)d * 4u, &bar);
+    for (int r = threadIdx.x; r < rows; r += blockDim.x)
+      for (int k = d; k < dp; ++k) xs[r * dp + k] = 0.0f;
+    if (!rpf_mbar_wait(&bar, 0, err)) return;
+  } else {
+    for (int r = warp; r < rows; r += nwarp) {
+      const float* src = X + (int64_t)prow[r] * d;
+      for (int k = lane; k < dp; k += 32) xs[r * dp + k] = k < d ? src[k] : 0.0f;
+    }
   }
-  const int i = threadIdx.x;
-  if (i >= rows) return;
-  int lo = 0, hi = nl - 1;  // leaf of row i: last q with leaf_off[q] <= i
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (leaf_off[mid] <= i) lo = mid;
-    else hi = mid - 1;
-  }
-  const int lb = leaf_off[lo], le = leaf_off[lo + 1];
-  const int gi = prow[i];
-  TopK<KMAX> tk;
-  tk.init();
-  float wd = INFINITY;
-  int wi = -1;
-  const float* xi = SMEM ? xs + i * dp : X + (int64_t)gi * d;
-  for (int jr = lb; jr < le; ++jr) {
-    if (jr == i) continue;
-    const int gj = prow[jr];
-    const float* xj = SMEM ? xs + jr * dp : X + (int64_t)gj * d;
-    const float v = rpf_d32(xi, xj, d);
-    tk.offer(K, v, gj, wd, wi);
-  }
-  uint2* out = cand + ((int64_t)(t - t0) * n + gi) * K;
+  __syncthreads();
+  const int nitems = item_off[nl];
+  const int d4 = (d + 3) & ~3;
+  for (int it = warp; it < nitems; it += nwarp) {
+    int lo = 0, hi = nl - 1;  // leaf of item it: last q with item_off[q] <= it
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (item_off[mid] <= it) lo = mid;
+      else hi = mid - 1;
+    }
+    const int lb = leaf_off[lo], le = leaf_off[lo + 1];
+    const int r = lb + 32 * (it - item_off[lo]) + lane;
+    const bool live = r < le;
+    const int rr = live ? r : lb;
+    TopK<KMAX> tk;
+    tk.init();
+    float xr[REG ? 64 : 1];
+    if (REG) {
 #pragma unroll
-  for (int q = 0; q < KMAX; ++q)
-    if (q < K) out[q] = make_uint2(__float_as_uint(tk.kd[q]), (unsigned)tk.ki[q]);
+      for (int k = 0; k < 64; k += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(xs + rr * dp + k);
+        xr[k] = v.x;
+        xr[k + 1] = v.y;
+        xr[k + 2] = v.z;
+        xr[k + 3] = v.w;
+      }
+    }
+    for (int c = lb; c < le; ++c) {
+      const float* y = xs + c * dp;
+      float acc = 0.0f;
+      if (REG) {
+#pragma unroll
+        for (int k = 0; k < 64; k += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(y + k);
+          float e;
+          e = __fsub_rn(xr[k], v.x); acc = __fmaf_rn(e, e, acc);
+          e = __fsub_rn(xr[k + 1], v.y); acc = __fmaf_rn(e, e, acc);
+          e = __fsub_rn(xr[k + 2], v.z); acc = __fmaf_rn(e, e, acc);
+          e = __fsub_rn(xr[k + 3], v.w); acc = __fmaf_rn(e, e, acc);
+        }
+      } else {
+        const float* x = xs + rr * dp;
+        for (int k = 0; k < d4; k += 4) {
+          const float4 a = *reinterpret_cast<const float4*>(x + k);
+          const float4 v = *reinterpret_cast<const float4*>(y + k);
+          float e;
+          e = __fsub_rn(a.x, v.x); acc = __fmaf_rn(e, e, acc);
+          e = __fsub_rn(a.y, v.y); acc = __fmaf_rn(e, e, acc);
+          e = __fsub_rn(a.z, v.z); acc = __fmaf_rn(e, e, acc);
+          e = __fsub_rn(a.w, v.w); acc = __fmaf_rn(e, e, acc);
+        }
+      }
+      if (c != r) tk.offer(acc, prow[c]);
+    }
+    if (live) tk.store(K, cand + ((int64_t)(t - t0) * n + prow[r]) * K);
+  }
 }
 
 // Merge G per-tree lists (sorted, padded with (inf, -1)) into the running list
@@ -159,13 +214,11 @@ __global__ void k_merge(int64_t n, int K, int G, const uint2* cand, uint2* run, 
 #pragma unroll
     for (int q = 0; q < KMAX; ++q)
       if (q < K) {
-        uint2 e = run[i * K + q];
+        const uint2 e = run[i * K + q];
         tk.kd[q] = __uint_as_float(e.x);
         tk.ki[q] = (int)e.y;
       }
   }
-  float wd = tk.worst_d(K);
-  int wi = tk.worst_i(K);
   for (int g = 0; g < G; ++g) {
     const uint2* c = cand + ((int64_t)g * n + i) * K;
     for (int q = 0; q < K; ++q) {
@@ -173,11 +226,8 @@ __global__ void k_merge(int64_t n, int K, int G, const uint2* cand, uint2* run, 
       const int j = (int)e.y;
       if (j < 0) break;
       const float v = __uint_as_float(e.x);
-      if (!rpf_less(v, j, wd, wi)) break;  // lists are sorted: nothing later fits
-      if (tk.contains(K, j)) continue;
-      tk.insert(K, v, j);
-      wd = tk.worst_d(K);
-      wi = tk.worst_i(K);
+      if (!tk.better_than_last(v, j)) break;  // sorted list: nothing later fits
+      if (!tk.contains(j)) tk.insert(v, j);    // a duplicate has the same key
     }
   }
   if (last) {
@@ -188,9 +238,7 @@ __global__ void k_merge(int64_t n, int K, int G, const uint2* cand, uint2* run, 
         dist[i * K + q] = tk.ki[q] < 0 ? INFINITY : __fsqrt_rn(tk.kd[q]);
       }
   } else {
-#pragma unroll
-    for (int q = 0; q < KMAX; ++q)
-      if (q < K) run[i * K + q] = make_uint2(__float_as_uint(tk.kd[q]), (unsigned)tk.ki[q]);
+    tk.store(K, run + i * K);
   }
 }
 
@@ -233,17 +281,11 @@ __global__ void k_qscan(const float* Q, int64_t m, int d, int T, int K, const in
   const float* x = Q + q * d;
   TopK<KMAX> tk;
   tk.init();
-  float wd = INFINITY;
-  int wi = -1;
   for (int a = 0; a < ln; ++a) {
     const int j = mem[a];
-    const float v = rpf_d32(x, X + (int64_t)j * d, d);
-    tk.offer(K, v, j, wd, wi);
+    tk.offer(rpf_d32(x, X + (int64_t)j * d, d), j);
   }
-  uint2* out = cand + ((int64_t)t * m + q) * K;
-#pragma unroll
-  for (int q2 = 0; q2 < KMAX; ++q2)
-    if (q2 < K) out[q2] = make_uint2(__float_as_uint(tk.kd[q2]), (unsigned)tk.ki[q2]);
+  tk.store(K, cand + ((int64_t)t * m + q) * K);
 }
 
 // Exact kNN by brute force (ground truth for the Sec. 5.1 metrics): one
@@ -259,12 +301,9 @@ __global__ void k_brute(const float* X, int64_t n, int d, const float* Q, int64_
   const int me = (live && self) ? self[q] : -1;
   TopK<KMAX> tk;
   tk.init();
-  float wd = INFINITY;
-  int wi = -1;
   for (int64_t j = 0; j < n; ++j) {
     if ((int)j == me) continue;
-    const float v = rpf_d32(y, x + j * d, d);
-    tk.offer(K, v, (int)j, wd, wi);
+    tk.offer(rpf_d32(y, x + j * d, d), (int)j);
   }
   if (!live) return;
 #pragma unroll
@@ -282,20 +321,24 @@ void launch_brute(const float* X, int64_t n, int d, const float* Q, int64_t m,
 }
 
 template <int KMAX>
-void launch_leaf(const rpf_forest* f, int64_t tb, int64_t nt, int K, int t0, uint2* cand,
+void launch_leaf(const rpf_forest* f, int64_t tb, int64_t nt, int K, int t0, uint2* cand, int* err,
                  cudaStream_t s) {
   const int rows = f->tile_rows;
-  const size_t smem = sizeof(float) * (size_t)rows * (f->d + 1);
-  if (smem <= 200 * 1024) {
+  const int dp = ((f->d + 3) & ~3) + 4;
+  const size_t smem = sizeof(float) * (size_t)rows * dp;
+  // padded rows of exactly 64 floats can live in registers (dp == 68)
+  if (dp == 68) {
     cudaFuncSetAttribute(k_leaf_plain<KMAX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    RPF_LAUNCH("k_leaf_plain", s, k_leaf_plain<KMAX, true><<<(unsigned)nt, rows, smem, s>>>(
+    RPF_LAUNCH("k_leaf_plain", s, k_leaf_plain<KMAX, true><<<(unsigned)nt, 128, smem, s>>>(
         f->tile_first, f->tile_count, tb, f->leaf_tree, f->leaf_begin, f->leaf_len, f->perm, f->X,
-        f->n, f->d, K, t0, cand));
+        f->n, f->d, dp, K, t0, cand, err));
   } else {
-    RPF_LAUNCH("k_leaf_plain", s, k_leaf_plain<KMAX, false><<<(unsigned)nt, rows, 0, s>>>(
+    cudaFuncSetAttribute(k_leaf_plain<KMAX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    RPF_LAUNCH("k_leaf_plain", s, k_leaf_plain<KMAX, false><<<(unsigned)nt, 128, smem, s>>>(
         f->tile_first, f->tile_count, tb, f->leaf_tree, f->leaf_begin, f->leaf_len, f->perm, f->X,
-        f->n, f->d, K, t0, cand));
+        f->n, f->d, dp, K, t0, cand, err));
   }
 }
 
@@ -355,9 +398,12 @@ int rpf_build_tiles(rpf_forest* f, cudaStream_t s) {
     sl[i] = ll[order[i]];
     maxleaf = std::max(maxleaf, sl[i]);
   }
-  int rows = ((maxleaf + 31) / 32) * 32;
-  rows = std::max(rows, 64);
+  // tile rows: the largest leaf rounded up to a warp, at least 128; the
+  // staged rows must fit in shared memory
+  const int dp = ((f->d + 3) & ~3) + 4;
+  int rows = std::max(128, ((maxleaf + 31) / 32) * 32);
   rows = std::min(rows, 1024);
+  if ((size_t)rows * dp * 4 > 200 * 1024) return RPF_EINVAL;
   std::vector<int32_t> tf, tc;
   std::vector<int64_t> ttb(T + 1, 0);
   int64_t i = 0;
@@ -417,11 +463,19 @@ int rpf_all_knn_dev(rpf_forest* f, int K, int32_t* idx, float* dist, void* ws, s
     const int g = std::min(G, T - t0);
     const int64_t tb = f->tree_tile_begin[t0];
     const int64_t nt = f->tree_tile_begin[t0 + g] - tb;
-    if (nt > 0) RPF_KDISPATCH(K, launch_leaf, f, tb, nt, K, t0, cand, s);
+    if (nt > 0) RPF_KDISPATCH(K, launch_leaf, f, tb, nt, K, t0, cand, f->d_err, s);
     const bool first = t0 == 0, last = t0 + g >= T;
     RPF_KDISPATCH(K, launch_merge, n, K, g, cand, run, first, last, idx, dist, s);
   }
   RPF_CU(cudaGetLastError());
+  // a bounded device wait that gave up is reported here
+  int herr = 0;
+  RPF_CU(cudaMemcpyAsync(&herr, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RPF_CU(cudaStreamSynchronize(s));
+  if (herr) {
+    cudaMemsetAsync(f->d_err, 0, sizeof(int), s);
+    return herr;
+  }
   return RPF_OK;
 }
 

@@ -1,0 +1,67 @@
+// rpf_tma.cuh -- bulk asynchronous copies (TMA engine, cp.async.bulk) of
+// point rows into shared memory, completed on an mbarrier.
+//
+// A CTA stages up to blockDim rows at once: thread 0 posts the expected byte
+// count, every thread then issues the bulk copy of its own row (one 16-byte
+// aligned, 16-byte-multiple global span), and all threads wait on the
+// barrier's phase.  Every wait is bounded: after RPF_WAIT_LIMIT polls the
+// thread records RPF_ETIMEOUT in the error word and gives up.
+#pragma once
+
+#include "rpf_internal.cuh"
+
+#define RPF_WAIT_LIMIT (1u << 26)
+
+__device__ __forceinline__ uint32_t rpf_smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void rpf_mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(rpf_smem_addr(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void rpf_mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(rpf_smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool rpf_mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(rpf_smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the given phase parity; returns false (and sets *err) on
+// timeout.
+__device__ __forceinline__ bool rpf_mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  for (uint32_t it = 0; it < RPF_WAIT_LIMIT; ++it)
+    if (rpf_mbar_try_wait(bar, parity)) return true;
+  if (err) atomicExch(err, RPF_ETIMEOUT);
+  return false;
+}
+
+// Order this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void rpf_fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16) from global src (16-byte aligned)
+// to shared dst (16-byte aligned), completing on bar.
+__device__ __forceinline__ void rpf_bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                             uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(rpf_smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(rpf_smem_addr(bar))
+      : "memory");
+}
