@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -23,30 +24,58 @@ bool rpf_is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+int rpf_alloc(void** p, size_t bytes, cudaStream_t s) {
+  static std::mutex mu;
+  static bool tuned[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> g(mu);
+    if (!tuned[dev]) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+      cudaGetLastError();
+      tuned[dev] = true;
+    }
+  }
+  *p = nullptr;
+  if (cudaMallocAsync(p, std::max<size_t>(bytes, 256), s) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return RPF_ENOMEM;
+  }
+  return RPF_OK;
+}
+
+void rpf_release(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
 namespace {
 
 template <typename T>
-int dalloc(rpf_forest* f, T** p, size_t count) {
+int dalloc(rpf_forest* f, T** p, size_t count, cudaStream_t s) {
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count * sizeof(T), 16));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return RPF_ENOMEM;
-  }
+  int rc = rpf_alloc(&q, count * sizeof(T), s);
+  if (rc) return rc;
   f->owned.push_back(q);
   *p = (T*)q;
   return RPF_OK;
 }
 
+// The forest's memory is released in stream order on the legacy stream:
+// callers make sure no work that uses the forest is still in flight.
 void free_forest(rpf_forest* f) {
   if (!f) return;
-  for (void* p : f->owned) cudaFree(p);
+  for (void* p : f->owned) rpf_release(p, 0);
   void* ps[] = {f->node_key,  f->node_tree,  f->node_begin, f->node_len,  f->node_left,
                 f->node_right, f->node_jstar, f->node_flag, f->node_c,    f->node_dir,
-                f->node_dir32, f->leaf_tree,  f->leaf_begin, f->leaf_len, f->tile_first,
-                f->tile_count, f->stage};
-  for (void* p : ps)
-    if (p) cudaFree(p);
+                f->node_dir32, f->leaf_tree,  f->leaf_begin, f->leaf_len, f->tile_cnt,
+                f->tile_off,  f->tile_leaf,  f->stage};
+  for (void* p : ps) rpf_release(p, 0);
   delete f;
 }
 
@@ -97,8 +126,8 @@ int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* s
   if (f->prm.growth == 2 && (size_t)p->n_try * d * 4 + 2048 > 200 * 1024) f->prm.growth = 1;
   cudaGetDevice(&f->device);
   int rc;
-  if ((rc = dalloc(f, &f->X, (size_t)n * d)) || (rc = dalloc(f, &f->xnorm, (size_t)n)) ||
-      (rc = dalloc(f, &f->perm, (size_t)n * p->n_trees)) || (rc = dalloc(f, &f->d_err, 1))) {
+  if ((rc = dalloc(f, &f->X, (size_t)n * d, s)) || (rc = dalloc(f, &f->xnorm, (size_t)n, s)) ||
+      (rc = dalloc(f, &f->perm, (size_t)n * p->n_trees, s)) || (rc = dalloc(f, &f->d_err, 1, s))) {
     free_forest(f);
     return rc;
   }
@@ -140,13 +169,10 @@ int rpf_all_knn(rpf_forest* f, int32_t K, int32_t* idx, float* dist, void* works
   if (!dev_out) {
     const size_t need = (size_t)n * K * 8;
     if (f->stage_bytes < need) {
-      if (f->stage) cudaFree(f->stage);
+      rpf_release(f->stage, s);
       f->stage = nullptr;
       f->stage_bytes = 0;
-      if (cudaMalloc(&f->stage, need) != cudaSuccess) {
-        cudaGetLastError();
-        return RPF_ENOMEM;
-      }
+      if (rpf_alloc(&f->stage, need, s)) return RPF_ENOMEM;
       f->stage_bytes = need;
     }
     di = (int32_t*)f->stage;

@@ -35,6 +35,7 @@
 
 #include "rpf_decide.cuh"
 #include "rpf_proj.cuh"
+#include "rpf_scan.cuh"
 
 namespace {
 
@@ -65,21 +66,16 @@ struct Counts {
 
 template <typename T>
 int grow_buf(T** p, int64_t old_n, int64_t new_n, cudaStream_t s, bool keep) {
-  T* q = nullptr;
-  cudaError_t e = cudaMalloc((void**)&q, sizeof(T) * (size_t)std::max<int64_t>(new_n, 1));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return RPF_ENOMEM;
-  }
+  void* q = nullptr;
+  if (rpf_alloc(&q, sizeof(T) * (size_t)std::max<int64_t>(new_n, 1), s)) return RPF_ENOMEM;
   if (*p) {
     if (keep && old_n > 0) {
-      e = cudaMemcpyAsync(q, *p, sizeof(T) * (size_t)old_n, cudaMemcpyDeviceToDevice, s);
+      cudaError_t e = cudaMemcpyAsync(q, *p, sizeof(T) * (size_t)old_n, cudaMemcpyDeviceToDevice, s);
       if (e != cudaSuccess) return rpf_cuda_err(e);
     }
-    cudaStreamSynchronize(s);
-    cudaFree(*p);
+    rpf_release(*p, s);
   }
-  *p = q;
+  *p = (T*)q;
   return RPF_OK;
 }
 
@@ -722,79 +718,6 @@ __global__ void k_count_exact(int F, const int32_t* fr_exact, unsigned long long
 }
 
 // --- node table compaction: valid slots (tree >= 0) keep their order -------
-__global__ void k_flag_count(const int32_t* node_tree, int64_t N, int32_t* blk_cnt) {
-  __shared__ int ws[32];
-  const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
-  int v = (i < N && node_tree[i] >= 0) ? 1 : 0;
-  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(RPF_FULL, v, off);
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int s = 0;
-    for (int u = 0; u < 32; ++u) s += ws[u];
-    blk_cnt[blockIdx.x] = s;
-  }
-}
-
-__global__ void __launch_bounds__(1024) k_scan_blocks(int32_t* blk, int nb, int32_t* total) {
-  __shared__ int ws[32];
-  __shared__ int run, tile_tot;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x == 0) run = 0;
-  __syncthreads();
-  for (int t0 = 0; t0 < nb; t0 += 1024) {
-    const int i = t0 + threadIdx.x;
-    const int v = i < nb ? blk[i] : 0;
-    int x = v;
-    for (int off = 1; off < 32; off <<= 1) {
-      int y = __shfl_up_sync(RPF_FULL, x, off);
-      if (lane >= off) x += y;
-    }
-    if (lane == 31) ws[w] = x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int r = 0;
-      for (int u = 0; u < 32; ++u) {
-        int a = ws[u];
-        ws[u] = r;
-        r += a;
-      }
-      tile_tot = r;
-    }
-    __syncthreads();
-    if (i < nb) blk[i] = run + x - v + ws[w];
-    __syncthreads();
-    if (threadIdx.x == 0) run += tile_tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *total = run;
-}
-
-__global__ void k_new_ids(const int32_t* node_tree, int64_t N, const int32_t* blk_off,
-                          int32_t* new_id) {
-  __shared__ int ws[32];
-  const int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int v = (i < N && node_tree[i] >= 0) ? 1 : 0;
-  int x = v;
-  for (int off = 1; off < 32; off <<= 1) {
-    int y = __shfl_up_sync(RPF_FULL, x, off);
-    if (lane >= off) x += y;
-  }
-  if (lane == 31) ws[w] = x;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int r = 0;
-    for (int u = 0; u < 32; ++u) {
-      int a = ws[u];
-      ws[u] = r;
-      r += a;
-    }
-  }
-  __syncthreads();
-  if (i < N) new_id[i] = v ? blk_off[blockIdx.x] + x - v + ws[w] : -1;
-}
-
 __global__ void k_compact_nodes(int64_t N, const int32_t* new_id, const uint64_t* key,
                                 const int32_t* tree, const int32_t* begin, const int32_t* len,
                                 const int32_t* left, const int32_t* right, const int32_t* jstar,
@@ -814,6 +737,16 @@ __global__ void k_compact_nodes(int64_t N, const int32_t* new_id, const uint64_t
   ojstar[o] = jstar[i];
   oflag[o] = flag[i];
   oc[o] = c[i];
+}
+
+__global__ void k_compact_leaves(int64_t S, const int32_t* pos, const int32_t* tree,
+                                 const int32_t* begin, const int32_t* len, int32_t* otree,
+                                 int32_t* obegin, int32_t* olen) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S || pos[i] < 0) return;
+  otree[pos[i]] = tree[i];
+  obegin[pos[i]] = begin[i];
+  olen[pos[i]] = len[i];
 }
 
 // r* of every split node (regenerated from its key and chosen try).
@@ -871,11 +804,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
   uint64_t* it_key = nullptr;
   std::vector<void*> tmp;
   auto talloc = [&](void** p, size_t bytes) -> int {
-    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return RPF_ENOMEM;
-    }
+    if (rpf_alloc(p, bytes, s)) return RPF_ENOMEM;
     tmp.push_back(*p);
     return RPF_OK;
   };
@@ -885,23 +814,18 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
                   lv.fr_rad, lv.fr_wlo, lv.fr_whi, lv.fr_akey, lv.fr_bkey, lv.ch_nleft, lv.ch_loff,
                   lv.cp_sum, lv.cp_min, lv.cp_max, lv.cp_s1, lv.cp_s2, lv.cp_a, lv.cp_min32,
                   lv.cp_max32, lv.cp_rad, lv.dir64, lv.dir32};
-    for (void* p : ps)
-      if (p) cudaFree(p);
+    for (void* p : ps) rpf_release(p, s);
     for (int q = 0; q < 2; ++q) {
       void* qs[] = {lv.fr_node[q], lv.fr_tree[q], lv.fr_begin[q], lv.fr_len[q], lv.fr_cb[q],
                     lv.fr_nc[q], lv.fr_key[q], lv.ch_node[q], lv.ch_start[q], lv.ch_len[q]};
-      for (void* p : qs)
-        if (p) cudaFree(p);
+      for (void* p : qs) rpf_release(p, s);
     }
     lv = Level();
   };
   auto cleanup = [&]() {
-    cudaStreamSynchronize(s);
-    for (void* p : tmp) cudaFree(p);
+    for (void* p : tmp) rpf_release(p, s);
     tmp.clear();
     free_level();
-    if (h_cnt) cudaFreeHost(h_cnt);
-    h_cnt = nullptr;
   };
 #define RPF_TRY(x) \
   do {             \
@@ -923,9 +847,15 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
   RPF_TRY(talloc((void**)&ex_count, sizeof(int32_t)));
   RPF_TRYCU(cudaMemsetAsync(d_exact, 0, sizeof(unsigned long long), s));
   RPF_TRYCU(cudaMemsetAsync(d_err, 0, sizeof(int), s));
-  if (cudaMallocHost((void**)&h_cnt, sizeof(Counts)) != cudaSuccess) {
-    cleanup();
-    return RPF_ENOMEM;
+  {  // one pinned counter block per host thread, kept for the process
+    static thread_local Counts* pinned = nullptr;
+    if (!pinned && cudaMallocHost((void**)&pinned, sizeof(Counts)) != cudaSuccess) {
+      cudaGetLastError();
+      pinned = nullptr;
+      cleanup();
+      return RPF_ENOMEM;
+    }
+    h_cnt = pinned;
   }
   RPF_TRY(talloc((void**)&p32, sizeof(float) * Tn * ntry));
   RPF_TRY(talloc((void**)&p64, sizeof(double) * Tn * ntry));
@@ -1231,45 +1161,45 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     leaves_used = lrun;
   }
 
-  // ---- compact the node table, regenerate the chosen directions -----------
+  // ---- compact the node and leaf tables, regenerate chosen directions ----
   {
     const int64_t N = nodes_used;
-    const int nb = (int)((N + 1023) / 1024);
-    int32_t *blk = nullptr, *new_id = nullptr, *d_total = nullptr;
-    RPF_TRY(talloc((void**)&blk, 4 * ((size_t)nb + 1)));
-    RPF_TRY(talloc((void**)&new_id, 4 * (size_t)N));
-    RPF_TRY(talloc((void**)&d_total, 4));
-    RPF_LAUNCH("k_flag_count", s, k_flag_count<<<nb, 1024, 0, s>>>(fo->node_tree, N, blk));
-    RPF_LAUNCH("k_scan_blocks", s, k_scan_blocks<<<1, 1024, 0, s>>>(blk, nb, d_total));
-    RPF_LAUNCH("k_new_ids", s, k_new_ids<<<nb, 1024, 0, s>>>(fo->node_tree, N, blk, new_id));
-    int32_t total = 0;
+    int32_t *blk = nullptr, *new_id = nullptr, *d_tot = nullptr;
+    const int64_t nbmax = (std::max(nodes_used, leaves_used) + 1023) / 1024 + 1;
+    RPF_TRY(talloc((void**)&blk, 4 * (size_t)nbmax));
+    RPF_TRY(talloc((void**)&new_id, 4 * (size_t)std::max<int64_t>(N, 1)));
+    RPF_TRY(talloc((void**)&d_tot, 8));
+    const int32_t* ntree = fo->node_tree;
+    rpf_scan(
+        N, [=] __device__(int64_t i) -> int { return ntree[i] >= 0 ? 1 : 0; },
+        [=] __device__(int64_t i, int p) { new_id[i] = ntree[i] >= 0 ? p : -1; }, blk, d_tot, s);
+    int32_t tot[2] = {0, 0};
     int err_h = 0;
-    RPF_TRYCU(cudaMemcpyAsync(&total, d_total, 4, cudaMemcpyDeviceToHost, s));
+    RPF_TRYCU(cudaMemcpyAsync(&tot[0], d_tot, 4, cudaMemcpyDeviceToHost, s));
     RPF_TRYCU(cudaMemcpyAsync(&err_h, d_err, 4, cudaMemcpyDeviceToHost, s));
     RPF_TRYCU(cudaStreamSynchronize(s));
     if (err_h) {
       cleanup();
       return RPF_EINTERNAL;
     }
+    const int32_t total = tot[0];
     const int64_t M = std::max<int64_t>(total, 1);
     uint64_t* okey = nullptr;
     int32_t *otree = nullptr, *obegin = nullptr, *olen = nullptr, *oleft = nullptr,
             *oright = nullptr, *ojstar = nullptr, *oflag = nullptr;
     double* oc = nullptr;
-    bool ok = cudaMalloc((void**)&okey, 8 * M) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&otree, 4 * M) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&obegin, 4 * M) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&olen, 4 * M) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&oleft, 4 * M) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&oright, 4 * M) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&ojstar, 4 * M) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&oflag, 4 * M) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&oc, 8 * M) == cudaSuccess;
-    if (!ok) {
-      cudaGetLastError();
+    int rc = rpf_alloc((void**)&okey, 8 * M, s);
+    if (!rc) rc = rpf_alloc((void**)&otree, 4 * M, s);
+    if (!rc) rc = rpf_alloc((void**)&obegin, 4 * M, s);
+    if (!rc) rc = rpf_alloc((void**)&olen, 4 * M, s);
+    if (!rc) rc = rpf_alloc((void**)&oleft, 4 * M, s);
+    if (!rc) rc = rpf_alloc((void**)&oright, 4 * M, s);
+    if (!rc) rc = rpf_alloc((void**)&ojstar, 4 * M, s);
+    if (!rc) rc = rpf_alloc((void**)&oflag, 4 * M, s);
+    if (!rc) rc = rpf_alloc((void**)&oc, 8 * M, s);
+    if (rc) {
       void* ps[] = {okey, otree, obegin, olen, oleft, oright, ojstar, oflag, oc};
-      for (void* p : ps)
-        if (p) cudaFree(p);
+      for (void* p : ps) rpf_release(p, s);
       cleanup();
       return RPF_ENOMEM;
     }
@@ -1277,10 +1207,9 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
         N, new_id, fo->node_key, fo->node_tree, fo->node_begin, fo->node_len, fo->node_left,
         fo->node_right, fo->node_jstar, fo->node_flag, fo->node_c, okey, otree, obegin, olen,
         oleft, oright, ojstar, oflag, oc));
-    cudaStreamSynchronize(s);
     void* olds[] = {fo->node_key, fo->node_tree, fo->node_begin, fo->node_len, fo->node_left,
                     fo->node_right, fo->node_jstar, fo->node_flag, fo->node_c};
-    for (void* p : olds) cudaFree(p);
+    for (void* p : olds) rpf_release(p, s);
     fo->node_key = okey;
     fo->node_tree = otree;
     fo->node_begin = obegin;
@@ -1292,17 +1221,45 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     fo->node_c = oc;
     fo->n_nodes = total;
     fo->nodes_cap = total;
-    if (cudaMalloc((void**)&fo->node_dir, sizeof(double) * M * d) != cudaSuccess ||
-        cudaMalloc((void**)&fo->node_dir32, sizeof(float) * M * d) != cudaSuccess) {
-      cudaGetLastError();
+    if (rpf_alloc((void**)&fo->node_dir, sizeof(double) * M * d, s) ||
+        rpf_alloc((void**)&fo->node_dir32, sizeof(float) * M * d, s)) {
       cleanup();
       return RPF_ENOMEM;
     }
     RPF_LAUNCH("k_node_dirs", s, k_node_dirs<<<nblk(total, 64), 64, 0, s>>>(
         total, d, seed, fo->node_key, fo->node_tree, fo->node_left, fo->node_jstar, fo->node_flag,
         fo->node_dir, fo->node_dir32));
+
+    // leaves: keep the used slots (len > 0) in slot order
+    const int64_t S = leaves_used;
+    const int32_t* llen = fo->leaf_len;
+    int32_t* lpos = new_id;  // reuse: S <= N + items is not guaranteed, so size check
+    if (S > N) RPF_TRY(talloc((void**)&lpos, 4 * (size_t)S));
+    rpf_scan(
+        S, [=] __device__(int64_t i) -> int { return llen[i] > 0 ? 1 : 0; },
+        [=] __device__(int64_t i, int p) { lpos[i] = llen[i] > 0 ? p : -1; }, blk, d_tot + 1, s);
+    RPF_TRYCU(cudaMemcpyAsync(&tot[1], d_tot + 1, 4, cudaMemcpyDeviceToHost, s));
+    RPF_TRYCU(cudaStreamSynchronize(s));
+    const int64_t NL = std::max<int32_t>(tot[1], 1);
+    int32_t *lt = nullptr, *lb = nullptr, *ll = nullptr;
+    if (rpf_alloc((void**)&lt, 4 * NL, s) || rpf_alloc((void**)&lb, 4 * NL, s) ||
+        rpf_alloc((void**)&ll, 4 * NL, s)) {
+      rpf_release(lt, s);
+      rpf_release(lb, s);
+      cleanup();
+      return RPF_ENOMEM;
+    }
+    const int32_t *st = fo->leaf_tree, *sb = fo->leaf_begin;
+    RPF_LAUNCH("k_compact_leaves", s, k_compact_leaves<<<nblk(S, 256), 256, 0, s>>>(
+        S, lpos, st, sb, llen, lt, lb, ll));
+    rpf_release(fo->leaf_tree, s);
+    rpf_release(fo->leaf_begin, s);
+    rpf_release(fo->leaf_len, s);
+    fo->leaf_tree = lt;
+    fo->leaf_begin = lb;
+    fo->leaf_len = ll;
+    fo->n_leaves = tot[1];
   }
-  fo->n_leaves = leaves_used;  // slots; empty slots (len 0) are dropped with the tiles
   {
     unsigned long long ex = 0;
     RPF_TRYCU(cudaMemcpyAsync(&ex, d_exact, sizeof(ex), cudaMemcpyDeviceToHost, s));

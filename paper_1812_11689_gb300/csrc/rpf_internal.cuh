@@ -216,13 +216,14 @@ struct rpf_forest {
   int32_t max_depth = 0;
   int64_t n_exact = 0;  // nodes decided by the FP64 fallback
 
-  // all-kNN tiles (built once from the leaf table)
-  int32_t tile_rows = 0;
-  int64_t n_tiles = 0;
-  int32_t* tile_first = nullptr;  // first leaf of tile
-  int32_t* tile_count = nullptr;  // leaves in tile
-  int32_t max_leaf = 0;
-  std::vector<int64_t> tree_tile_begin;  // T + 1 (host): tiles of tree t
+  // all-kNN tiles: tile (t, k) holds the leaves of tree t whose begin lies in
+  // [k R, (k + 1) R); a tile has at most R + L - 1 rows
+  int32_t tile_region = 0;        // R
+  int32_t tile_rows = 0;          // R + L - 1
+  int64_t tiles_per_tree = 0;     // ceil(n / R)
+  int32_t* tile_cnt = nullptr;    // leaves per tile
+  int32_t* tile_off = nullptr;    // first entry of the tile in tile_leaf
+  int32_t* tile_leaf = nullptr;   // leaf indices grouped by tile
 
   int* d_err = nullptr;  // device error word (RPF_ETIMEOUT from bounded waits)
 
@@ -255,6 +256,10 @@ struct rpf_trace_scope {
 
 int rpf_cuda_err(cudaError_t e);
 bool rpf_is_device_ptr(const void* p);
+// Stream-ordered device allocation from the device's default pool, which is
+// set to keep freed memory cached (repeated builds reuse it without syncs).
+int rpf_alloc(void** p, size_t bytes, cudaStream_t s);
+void rpf_release(void* p, cudaStream_t s);
 
 // growth (rpf_grow.cu)
 int rpf_grow(rpf_forest* f, cudaStream_t s);

@@ -21,6 +21,7 @@
 
 #include "rpf_internal.cuh"
 #include "rpf_tma.cuh"
+#include "rpf_scan.cuh"
 
 namespace {
 
@@ -88,9 +89,10 @@ struct TopK {
 // bit-identical to the oracle's.
 // cand layout: [(g * n + point) * K + k] as (d32 bits, idx).
 // ---------------------------------------------------------------------------
-template <int KMAX, bool REG>
-__global__ void __launch_bounds__(128) k_leaf_plain(const int32_t* tile_first,
-                                                    const int32_t* tile_count, int64_t tile_base,
+template <int KMAX, bool REG, bool STAGE>
+__global__ void __launch_bounds__(128, 4) k_leaf_plain(const int32_t* tile_cnt,
+                                                    const int32_t* tile_off,
+                                                    const int32_t* tile_leaf, int64_t tile_base,
                                                     const int32_t* leaf_tree,
                                                     const int32_t* leaf_begin,
                                                     const int32_t* leaf_len, const int32_t* perm,
@@ -99,14 +101,29 @@ __global__ void __launch_bounds__(128) k_leaf_plain(const int32_t* tile_first,
   extern __shared__ __align__(16) float xs[];
   __shared__ int leaf_off[1025];
   __shared__ int item_off[1025];
+  __shared__ int lbeg[1024];
+  __shared__ int b0s;
   __shared__ __align__(8) uint64_t bar;
   const int64_t tile = tile_base + blockIdx.x;
-  const int lf0 = tile_first[tile], nl = tile_count[tile];
-  const int t = leaf_tree[lf0];
-  const int b0 = leaf_begin[lf0];
+  const int nl = tile_cnt[tile];
+  if (nl == 0) return;
+  const int32_t* tl = tile_leaf + tile_off[tile];
+  const int t = leaf_tree[tl[0]];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int q = threadIdx.x; q < nl; q += blockDim.x) leaf_off[q] = leaf_begin[lf0 + q] - b0;
-  if (threadIdx.x == 0) leaf_off[nl] = leaf_begin[lf0 + nl - 1] + leaf_len[lf0 + nl - 1] - b0;
+  // the tile's leaves (at most 1024), ordered by begin: rank sort
+  for (int q = threadIdx.x; q < nl; q += blockDim.x) lbeg[q] = leaf_begin[tl[q]];
+  __syncthreads();
+  for (int q = threadIdx.x; q < nl; q += blockDim.x) {
+    const int b = lbeg[q];
+    int rank = 0;
+    for (int p = 0; p < nl; ++p) rank += lbeg[p] < b;
+    leaf_off[rank] = b;
+    if (rank == nl - 1) leaf_off[nl] = b + leaf_len[tl[q]];
+    if (rank == 0) b0s = b;
+  }
+  __syncthreads();
+  const int b0 = b0s;
+  for (int q = threadIdx.x; q <= nl; q += blockDim.x) leaf_off[q] -= b0;
   __syncthreads();
   const int rows = leaf_off[nl];
   const int32_t* prow = perm + (int64_t)t * n + b0;
@@ -126,7 +143,7 @@ __global__ void __launch_bounds__(128) k_leaf_plain(const int32_t* tile_first,
     }
     if (lane == 0) item_off[nl] = run;
   }
-  if ((d & 3) == 0) {
+  if (STAGE && (d & 3) == 0) {
     if (threadIdx.x == 0) {
       rpf_mbar_init(&bar, 1);
       rpf_mbar_arrive_expect_tx(&bar, (uint32_t)rows * (uint32_t)d * 4u);
@@ -137,7 +154,7 @@ __global__ void __launch_bounds__(128) k_leaf_plain(const int32_t* tile_first,
     for (int r = threadIdx.x; r < rows; r += blockDim.x)
       for (int k = d; k < dp; ++k) xs[r * dp + k] = 0.0f;
     if (!rpf_mbar_wait(&bar, 0, err)) return;
-  } else {
+  } else if (STAGE) {
     for (int r = warp; r < rows; r += nwarp) {
       const float* src = X + (int64_t)prow[r] * d;
       for (int k = lane; k < dp; k += 32) xs[r * dp + k] = k < d ? src[k] : 0.0f;
@@ -170,32 +187,49 @@ __global__ void __launch_bounds__(128) k_leaf_plain(const int32_t* tile_first,
         xr[k + 3] = v.w;
       }
     }
-    for (int c = lb; c < le; ++c) {
-      const float* y = xs + c * dp;
-      float acc = 0.0f;
+    // four columns at a time: four independent canonical chains per lane
+    for (int c0 = lb; c0 < le; c0 += 4) {
+      int cc[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cc[j] = min(c0 + j, le - 1);
+      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       if (REG) {
 #pragma unroll
         for (int k = 0; k < 64; k += 4) {
-          const float4 v = *reinterpret_cast<const float4*>(y + k);
-          float e;
-          e = __fsub_rn(xr[k], v.x); acc = __fmaf_rn(e, e, acc);
-          e = __fsub_rn(xr[k + 1], v.y); acc = __fmaf_rn(e, e, acc);
-          e = __fsub_rn(xr[k + 2], v.z); acc = __fmaf_rn(e, e, acc);
-          e = __fsub_rn(xr[k + 3], v.w); acc = __fmaf_rn(e, e, acc);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 v = *reinterpret_cast<const float4*>(xs + cc[j] * dp + k);
+            float e;
+            e = __fsub_rn(xr[k], v.x); acc[j] = __fmaf_rn(e, e, acc[j]);
+            e = __fsub_rn(xr[k + 1], v.y); acc[j] = __fmaf_rn(e, e, acc[j]);
+            e = __fsub_rn(xr[k + 2], v.z); acc[j] = __fmaf_rn(e, e, acc[j]);
+            e = __fsub_rn(xr[k + 3], v.w); acc[j] = __fmaf_rn(e, e, acc[j]);
+          }
         }
-      } else {
+      } else if (STAGE) {
         const float* x = xs + rr * dp;
         for (int k = 0; k < d4; k += 4) {
           const float4 a = *reinterpret_cast<const float4*>(x + k);
-          const float4 v = *reinterpret_cast<const float4*>(y + k);
-          float e;
-          e = __fsub_rn(a.x, v.x); acc = __fmaf_rn(e, e, acc);
-          e = __fsub_rn(a.y, v.y); acc = __fmaf_rn(e, e, acc);
-          e = __fsub_rn(a.z, v.z); acc = __fmaf_rn(e, e, acc);
-          e = __fsub_rn(a.w, v.w); acc = __fmaf_rn(e, e, acc);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 v = *reinterpret_cast<const float4*>(xs + cc[j] * dp + k);
+            float e;
+            e = __fsub_rn(a.x, v.x); acc[j] = __fmaf_rn(e, e, acc[j]);
+            e = __fsub_rn(a.y, v.y); acc[j] = __fmaf_rn(e, e, acc[j]);
+            e = __fsub_rn(a.z, v.z); acc[j] = __fmaf_rn(e, e, acc[j]);
+            e = __fsub_rn(a.w, v.w); acc[j] = __fmaf_rn(e, e, acc[j]);
+          }
         }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          acc[j] = rpf_d32(X + (int64_t)prow[rr] * d, X + (int64_t)prow[cc[j]] * d, d);
       }
-      if (c != r) tk.offer(acc, prow[c]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = c0 + j;
+        if (c < le && c != r) tk.offer(acc[j], prow[c]);
+      }
     }
     if (live) tk.store(K, cand + ((int64_t)(t - t0) * n + prow[r]) * K);
   }
@@ -326,20 +360,18 @@ void launch_leaf(const rpf_forest* f, int64_t tb, int64_t nt, int K, int t0, uin
   const int rows = f->tile_rows;
   const int dp = ((f->d + 3) & ~3) + 4;
   const size_t smem = sizeof(float) * (size_t)rows * dp;
-  // padded rows of exactly 64 floats can live in registers (dp == 68)
-  if (dp == 68) {
-    cudaFuncSetAttribute(k_leaf_plain<KMAX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    RPF_LAUNCH("k_leaf_plain", s, k_leaf_plain<KMAX, true><<<(unsigned)nt, 128, smem, s>>>(
-        f->tile_first, f->tile_count, tb, f->leaf_tree, f->leaf_begin, f->leaf_len, f->perm, f->X,
-        f->n, f->d, dp, K, t0, cand, err));
-  } else {
-    cudaFuncSetAttribute(k_leaf_plain<KMAX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    RPF_LAUNCH("k_leaf_plain", s, k_leaf_plain<KMAX, false><<<(unsigned)nt, 128, smem, s>>>(
-        f->tile_first, f->tile_count, tb, f->leaf_tree, f->leaf_begin, f->leaf_len, f->perm, f->X,
-        f->n, f->d, dp, K, t0, cand, err));
-  }
+#define RPF_LEAF(REGV, STAGEV, SM)                                                             \
+  do {                                                                                         \
+    cudaFuncSetAttribute(k_leaf_plain<KMAX, REGV, STAGEV>,                                     \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SM));              \
+    RPF_LAUNCH("k_leaf_plain", s, k_leaf_plain<KMAX, REGV, STAGEV><<<(unsigned)nt, 128, SM, s>>>( \
+        f->tile_cnt, f->tile_off, f->tile_leaf, tb, f->leaf_tree, f->leaf_begin, f->leaf_len,  \
+        f->perm, f->X, f->n, f->d, dp, K, t0, cand, err));                                     \
+  } while (0)
+  if (smem > 200 * 1024) RPF_LEAF(false, false, 0);   // rows read from global memory
+  else if (dp == 68) RPF_LEAF(true, true, smem);      // 64-float rows held in registers
+  else RPF_LEAF(false, true, smem);
+#undef RPF_LEAF
 }
 
 template <int KMAX>
@@ -368,77 +400,69 @@ void launch_qscan(const rpf_forest* f, const float* Q, int64_t m, int K, const i
 
 }  // namespace
 
+namespace {
+__global__ void k_tile_count(int64_t nl, const int32_t* leaf_tree, const int32_t* leaf_begin,
+                             int64_t ntile, int R, int32_t* cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nl) return;
+  atomicAdd(&cnt[leaf_tree[i] * ntile + leaf_begin[i] / R], 1);
+}
+__global__ void k_tile_fill(int64_t nl, const int32_t* leaf_tree, const int32_t* leaf_begin,
+                            int64_t ntile, int R, const int32_t* off, int32_t* cur,
+                            int32_t* tile_leaf) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nl) return;
+  const int64_t tile = leaf_tree[i] * ntile + leaf_begin[i] / R;
+  tile_leaf[off[tile] + atomicAdd(&cur[tile], 1)] = (int32_t)i;
+}
+}  // namespace
+
 // ---------------------------------------------------------------------------
-// Work list: leaves sorted by tree (stable), then packed greedily into tiles of
-// at most tile_rows rows.  Built once per forest on the host from the leaf
-// table (a few hundred thousand entries at most).
+// All-kNN work list, on the device: tile (t, k) takes the leaves of tree t
+// whose begin lies in [k R, (k + 1) R).  Leaves of a tree tile its
+// permutation, so a tile's rows are contiguous and number at most R + L - 1;
+// every tree has exactly ceil(n / R) tiles (possibly empty).  R is the
+// largest multiple of 32 up to the leaf bound for which the tile's rows fit in
+// shared memory.
 // ---------------------------------------------------------------------------
 int rpf_build_tiles(rpf_forest* f, cudaStream_t s) {
-  const int64_t nl = f->n_leaves;
-  const int T = f->prm.n_trees;
-  std::vector<int32_t> lt(nl), lb(nl), ll(nl);
-  RPF_CU(cudaMemcpyAsync(lt.data(), f->leaf_tree, 4 * nl, cudaMemcpyDeviceToHost, s));
-  RPF_CU(cudaMemcpyAsync(lb.data(), f->leaf_begin, 4 * nl, cudaMemcpyDeviceToHost, s));
-  RPF_CU(cudaMemcpyAsync(ll.data(), f->leaf_len, 4 * nl, cudaMemcpyDeviceToHost, s));
-  RPF_CU(cudaStreamSynchronize(s));
-  // drop unused slots (len 0), then sort by tree and by begin within a tree
-  std::vector<int64_t> order;
-  order.reserve(nl);
-  for (int64_t i = 0; i < nl; ++i)
-    if (ll[i] > 0) order.push_back(i);
-  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-    return lt[a] != lt[b] ? lt[a] < lt[b] : lb[a] < lb[b];
-  });
-  const int64_t nv = (int64_t)order.size();
-  std::vector<int32_t> st(nv), sb(nv), sl(nv);
-  int32_t maxleaf = 1;
-  for (int64_t i = 0; i < nv; ++i) {
-    st[i] = lt[order[i]];
-    sb[i] = lb[order[i]];
-    sl[i] = ll[order[i]];
-    maxleaf = std::max(maxleaf, sl[i]);
-  }
-  // tile rows: the largest leaf rounded up to a warp, at least 128; the
-  // staged rows must fit in shared memory
+  const int T = f->prm.n_trees, L = f->prm.leaf_max;
   const int dp = ((f->d + 3) & ~3) + 4;
-  int rows = std::max(128, ((maxleaf + 31) / 32) * 32);
-  rows = std::min(rows, 1024);
-  if ((size_t)rows * dp * 4 > 200 * 1024) return RPF_EINVAL;
-  std::vector<int32_t> tf, tc;
-  std::vector<int64_t> ttb(T + 1, 0);
-  int64_t i = 0;
-  for (int t = 0; t < T; ++t) {
-    ttb[t] = (int64_t)tf.size();
-    while (i < nv && st[i] == t) {
-      int r = 0, c = 0;
-      const int64_t first = i;
-      while (i < nv && st[i] == t && r + sl[i] <= rows) {
-        r += sl[i];
-        ++c;
-        ++i;
-      }
-      if (c == 0) return RPF_EINTERNAL;  // a leaf larger than a tile
-      tf.push_back((int32_t)first);
-      tc.push_back(c);
-    }
+  // prefer tiles small enough for four CTAs per SM (<= 56 KB of rows)
+  int R = std::max(32, ((L + 31) / 32) * 32);
+  while (R > 32 && (size_t)(R + L - 1) * dp * 4 > 56 * 1024) R -= 32;
+  R = std::min(R, 1024 - L + 1 > 0 ? std::max(32, ((1024 - L + 1) / 32) * 32) : 32);
+  const int64_t ntile = (f->n + R - 1) / R;
+  const int64_t N = (int64_t)T * ntile;
+  const int64_t nl = f->n_leaves;
+  int32_t *blk = nullptr, *tot = nullptr, *cur = nullptr;
+  if (rpf_alloc((void**)&f->tile_cnt, 4 * (size_t)N, s) ||
+      rpf_alloc((void**)&f->tile_off, 4 * (size_t)(N + 1), s) ||
+      rpf_alloc((void**)&f->tile_leaf, 4 * (size_t)std::max<int64_t>(nl, 1), s) ||
+      rpf_alloc((void**)&cur, 4 * (size_t)N, s) ||
+      rpf_alloc((void**)&blk, 4 * (size_t)((N + 1023) / 1024 + 1), s) ||
+      rpf_alloc((void**)&tot, 4, s)) {
+    rpf_release(cur, s);
+    rpf_release(blk, s);
+    return RPF_ENOMEM;
   }
-  ttb[T] = (int64_t)tf.size();
-  RPF_CU(cudaMemcpyAsync(f->leaf_tree, st.data(), 4 * nv, cudaMemcpyHostToDevice, s));
-  RPF_CU(cudaMemcpyAsync(f->leaf_begin, sb.data(), 4 * nv, cudaMemcpyHostToDevice, s));
-  RPF_CU(cudaMemcpyAsync(f->leaf_len, sl.data(), 4 * nv, cudaMemcpyHostToDevice, s));
-  f->n_leaves = nv;
-  const int64_t ntl = (int64_t)tf.size();
-  if (f->tile_first) cudaFree(f->tile_first);
-  if (f->tile_count) cudaFree(f->tile_count);
-  RPF_CU(cudaMalloc((void**)&f->tile_first, 4 * std::max<int64_t>(ntl, 1)));
-  RPF_CU(cudaMalloc((void**)&f->tile_count, 4 * std::max<int64_t>(ntl, 1)));
-  RPF_CU(cudaMemcpyAsync(f->tile_first, tf.data(), 4 * ntl, cudaMemcpyHostToDevice, s));
-  RPF_CU(cudaMemcpyAsync(f->tile_count, tc.data(), 4 * ntl, cudaMemcpyHostToDevice, s));
-  RPF_CU(cudaStreamSynchronize(s));
-  f->tile_rows = rows;
-  f->n_tiles = ntl;
-  f->max_leaf = maxleaf;
-  f->tree_tile_begin.assign(ttb.begin(), ttb.end());
+  RPF_CU(cudaMemsetAsync(f->tile_cnt, 0, 4 * (size_t)N, s));
+  RPF_CU(cudaMemsetAsync(cur, 0, 4 * (size_t)N, s));
+  RPF_LAUNCH("k_tile_count", s, k_tile_count<<<nblk(nl, 256), 256, 0, s>>>(
+      nl, f->leaf_tree, f->leaf_begin, ntile, R, f->tile_cnt));
+  const int32_t* cnt = f->tile_cnt;
+  int32_t* off = f->tile_off;
+  rpf_scan(N, [=] __device__(int64_t i) -> int { return cnt[i]; },
+           [=] __device__(int64_t i, int p) { off[i] = p; }, blk, tot, s);
+  RPF_LAUNCH("k_tile_fill", s, k_tile_fill<<<nblk(nl, 256), 256, 0, s>>>(
+      nl, f->leaf_tree, f->leaf_begin, ntile, R, f->tile_off, cur, f->tile_leaf));
+  rpf_release(cur, s);
+  rpf_release(blk, s);
+  rpf_release(tot, s);
+  f->tile_region = R;
+  f->tile_rows = R + L - 1;
+  f->tiles_per_tree = ntile;
+  RPF_CU(cudaGetLastError());
   return RPF_OK;
 }
 
@@ -461,8 +485,8 @@ int rpf_all_knn_dev(rpf_forest* f, int K, int32_t* idx, float* dist, void* ws, s
   uint2* cand = (uint2*)((char*)ws + run_b);
   for (int t0 = 0; t0 < T; t0 += G) {
     const int g = std::min(G, T - t0);
-    const int64_t tb = f->tree_tile_begin[t0];
-    const int64_t nt = f->tree_tile_begin[t0 + g] - tb;
+    const int64_t tb = (int64_t)t0 * f->tiles_per_tree;
+    const int64_t nt = (int64_t)g * f->tiles_per_tree;
     if (nt > 0) RPF_KDISPATCH(K, launch_leaf, f, tb, nt, K, t0, cand, f->d_err, s);
     const bool first = t0 == 0, last = t0 + g >= T;
     RPF_KDISPATCH(K, launch_merge, n, K, g, cand, run, first, last, idx, dist, s);
