@@ -154,6 +154,12 @@ int rpf_forest_info(const rpf_forest* f, int64_t* n, int32_t* d, int32_t* n_tree
                     int64_t* n_nodes, int64_t* n_leaves, int32_t* max_depth,
                     int64_t* n_exact_nodes);
 
+/* Counters (host, first n_out of): [0] nodes decided by the FP64 fallback,
+   [1] rows the BF16 form rescanned exactly because its certificate failed
+   (cumulative over rpf_all_knn calls), [2] level-synchronous growth levels,
+   [3] leaf-tile region R. */
+int rpf_forest_counters(const rpf_forest* f, int64_t* out, int32_t n_out);
+
 /* Final permutation of tree t (n int32, host): every leaf is a contiguous
    segment, members in ascending original index. */
 int rpf_forest_perm(const rpf_forest* f, int32_t t, int32_t* perm_host);

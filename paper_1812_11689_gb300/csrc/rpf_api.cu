@@ -127,11 +127,13 @@ int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* s
   cudaGetDevice(&f->device);
   int rc;
   if ((rc = dalloc(f, &f->X, (size_t)n * d, s)) || (rc = dalloc(f, &f->xnorm, (size_t)n, s)) ||
-      (rc = dalloc(f, &f->perm, (size_t)n * p->n_trees, s)) || (rc = dalloc(f, &f->d_err, 1, s))) {
+      (rc = dalloc(f, &f->perm, (size_t)n * p->n_trees, s)) || (rc = dalloc(f, &f->d_err, 1, s)) ||
+      (rc = dalloc(f, &f->d_fallback, 1, s))) {
     free_forest(f);
     return rc;
   }
   cudaError_t e = cudaMemsetAsync(f->d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->d_fallback, 0, sizeof(unsigned long long), s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(f->X, X, sizeof(float) * n * d, cudaMemcpyDefault, s);
   if (e != cudaSuccess) {
     free_forest(f);
@@ -255,6 +257,15 @@ int rpf_forest_info(const rpf_forest* f, int64_t* n, int32_t* d, int32_t* n_tree
   if (n_leaves) *n_leaves = f->n_leaves;
   if (max_depth) *max_depth = f->max_depth;
   if (n_exact_nodes) *n_exact_nodes = f->n_exact;
+  return RPF_OK;
+}
+
+int rpf_forest_counters(const rpf_forest* f, int64_t* out, int32_t n_out) {
+  if (!f || !out || n_out < 0) return RPF_EINVAL;
+  unsigned long long fb = 0;
+  RPF_CU(cudaMemcpy(&fb, f->d_fallback, sizeof(fb), cudaMemcpyDeviceToHost));
+  const int64_t v[4] = {f->n_exact, (int64_t)fb, f->max_depth, f->tile_region};
+  for (int i = 0; i < n_out && i < 4; ++i) out[i] = v[i];
   return RPF_OK;
 }
 

@@ -226,6 +226,7 @@ struct rpf_forest {
   int32_t* tile_leaf = nullptr;   // leaf indices grouped by tile
 
   int* d_err = nullptr;  // device error word (RPF_ETIMEOUT from bounded waits)
+  unsigned long long* d_fallback = nullptr;  // rows the BF16 form rescanned exactly
 
   // staging for host outputs of rpf_all_knn
   void* stage = nullptr;

@@ -120,6 +120,12 @@ class Forest:
         return {"n": n.value, "d": d.value, "n_trees": T.value, "n_nodes": nn.value,
                 "n_leaves": nl.value, "max_depth": md.value, "n_exact_nodes": ne.value}
 
+    def counters(self) -> dict:
+        out = np.zeros(4, np.int64)
+        check(_lib.lib().rpf_forest_counters(self._h, out.ctypes.data, 4), "counters")
+        return {"exact_nodes": int(out[0]), "bf16_fallback_rows": int(out[1]),
+                "phase_a_levels": int(out[2]), "tile_region": int(out[3])}
+
     def perm(self, t: int) -> np.ndarray:
         out = np.empty(self.n, np.int32)
         check(_lib.lib().rpf_forest_perm(self._h, t, out.ctypes.data), "perm")

@@ -281,3 +281,32 @@ def test_trace_counts_and_times_launches():
     assert l1 - l0 == sum(v["launches"] for v in tr.values())
     assert tr["k_leaf_plain"]["launches"] >= 1 and tr["k_merge"]["launches"] >= 1
     assert all(v["ms"] >= 0.0 for v in tr.values())
+
+
+@pytest.mark.parametrize("K", [1, 7, 10, 16, 20])
+def test_chosen_form_equals_plain_and_oracle(K):
+    X = synth.make("aniso20_d64", n=12000)
+    o = oracle.Forest(X, 4, 128, 5, seed=3)
+    oi, od = o.all_knn(K)
+    p = gpu_forest(X, 4, 128, 5, seed=3, form=0)
+    c = gpu_forest(X, 4, 128, 5, seed=3, form=1)
+    pi, pd = p.all_knn(K)
+    ci, cd = c.all_knn(K)
+    assert torch.equal(pi, ci) and torch.equal(pd, cd)
+    check_knn(ci.cpu().numpy(), cd.cpu().numpy(), oi, od, X)
+
+
+def test_chosen_form_certificate_fallback_is_exact():
+    # a scaled simplex with tiny noise: all pairwise squared distances agree
+    # to ~2e-6 relative, below what the split-BF16 Gram resolves, so the
+    # shortlist certificate fails and rows are rescanned exactly -- the lists
+    # must still equal the oracle's
+    rng = np.random.default_rng(0)
+    n = d = 256
+    X = (10.0 * np.eye(n, d) + 1e-5 * rng.standard_normal((n, d))).astype(np.float32)
+    o = oracle.Forest(X, 3, 64, 3, seed=1)
+    oi, od = o.all_knn(10)
+    c = gpu_forest(X, 3, 64, 3, seed=1, form=1)
+    ci, cd = c.all_knn(10)
+    assert np.array_equal(ci.cpu().numpy(), oi) and np.array_equal(cd.cpu().numpy(), od)
+    assert c.counters()["bf16_fallback_rows"] > 0
