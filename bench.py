@@ -141,40 +141,98 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def roofline(trace, w, fo, n, hbm_peak, peak_kind):
-    """Roofline of the kernel with the largest share of the timed steps."""
-    if not trace:
-        return None, None
-    top = max(trace, key=lambda k: trace[k]["ms"])
-    t = trace[top]
-    nodes = fo.nodes()
-    internal = nodes["left"] >= 0
-    active = int(nodes["len"][internal].sum())  # point-levels projected per build
+SUBTREE_MAX = 4096          # nodes of at most this many points grow CTA-locally
+FP32_LANES = 152 * 128      # FP32 lanes of a GB300 (152 SMs x 128)
+SM_MAX_GHZ = 2.07
+
+
+def work_model(fo, w, n):
+    """Algorithmic bytes (and FLOPs) per step of each main kernel.
+
+    Growth: every point of an internal node is projected once per level; its
+    X row (4d B) is the minimum read.  Phase A (nodes > 4096 points) also
+    reads perm and the point norm and writes nTry FP32 projections; phase B
+    reads perm and writes the final permutation once per subtree.  Leaf
+    tiles: every point's row once per tree plus its perm entry and its
+    per-tree top-K list (8K B); FLOPs 2 d m^2 per leaf of m points.  Merge:
+    T per-tree lists in, the final list out.
+    """
+    nd = fo.nodes()
+    ln = nd["len"].astype(np.int64)
+    internal = nd["left"] >= 0
+    A = internal & (ln > SUBTREE_MAX)
+    B = internal & (ln <= SUBTREE_MAX)
+    kids = np.concatenate([nd["left"][A], nd["right"][A]])
+    kids = kids[kids >= 0]
+    rb = int(ln[kids][(ln[kids] <= SUBTREE_MAX) & internal[kids]].sum())
+    if n <= SUBTREE_MAX and n > w.leaf_max:  # every root is a subtree root
+        rb += n * w.n_trees
+    pl_a, pl_b = int(ln[A].sum()), int(ln[B].sum())
+    leaf_len = ln[~internal]
     d, T, K, nt = w.d, w.n_trees, w.k, w.n_try
-    # algorithmic bytes per build / per all-kNN for each kernel
-    per_step = {
-        "k_proj32": active * (4 * d + 4 + 4 + 4 * nt),       # X row, perm, |x|, p32 out
-        "k_proj64": active * (4 * d + 4 + 8 * nt),
-        "k_side_count": active * (4 + 4 + 1),                 # p32*, perm, side
-        "k_scatter": active * (1 + 4 + 4),                    # side, perm in, perm out
-        "k_var32": active * (4 * nt),
-        "k_leaf_plain": n * T * (4 * d + 4 + 8 * K),          # rows, perm, per-tree lists
-        "k_leaf_bf16": n * T * (4 * d + 4 + 8 * K),
-        "k_merge": n * (T * 8 * K + 8 * K),                   # per-tree lists, outputs
+    return {
+        "k_subtree": {"bytes": pl_b * (4 * d + 4) + rb * 8},
+        "k_proj_a": {"bytes": pl_a * (4 * d + 4 + 4 + 4 * nt)},
+        "k_side_count": {"bytes": pl_a * (4 + 4 + 1)},
+        "k_scatter": {"bytes": pl_a * (1 + 4 + 4)},
+        "k_leaf_plain": {"bytes": n * T * (4 * d + 4 + 8 * K),
+                         "flops": 2 * d * int((leaf_len ** 2).sum())},
+        "k_leaf_bf16": {"bytes": n * T * (4 * d + 4 + 8 * K),
+                        "flops": 2 * d * int((leaf_len ** 2).sum())},
+        "k_merge": {"bytes": n * (T * 8 * K + 8 * K)},
+        "_point_levels": {"phase_a": pl_a, "phase_b": pl_b,
+                          "leaf_m2_per_point_per_tree": float((leaf_len ** 2).sum()) / (n * T)},
     }
-    steps = t.get("steps", 1)
-    bytes_total = per_step.get(top)
-    if bytes_total is None:
-        return top, None
-    bytes_per_launch = bytes_total * steps / t["launches"]
-    ms_per_launch = t["ms"] / t["launches"]
-    ach = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9
-    return top, {"kernel": top, "bound": "hbm", "achieved": round(ach, 1),
-                 "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
-                 "peak_source": peak_kind, "traffic": None,
-                 "algorithmic_bytes_per_launch": int(bytes_per_launch),
-                 "ms_per_launch": round(ms_per_launch, 5), "launches": t["launches"],
-                 "share": None}
+
+
+def traffic_record(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of the kernel (the summary states the source digest)."""
+    import hashlib
+    import re
+    p = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", txt)
+    src = re.search(r"source_sha256:\s*([0-9a-f]+)\s+files:\s*(.+)", txt)
+    if not m or not src:
+        return None
+    h = hashlib.sha256()
+    for f in src.group(2).split():
+        f = os.path.join(ROOT, f)
+        if not os.path.exists(f):
+            return None
+        h.update(open(f, "rb").read())
+    if h.hexdigest() != src.group(1):
+        return None
+    return int(m.group(1))
+
+
+def rooflines(trace, work, hbm_peak, peak_kind, steps, workload):
+    """Per-kernel roofline fractions; the kernel with the largest share first."""
+    tot = sum(v["ms"] for v in trace.values()) or 1.0
+    fp32_peak = 2 * FP32_LANES * SM_MAX_GHZ * 1e9 / 1e12  # TFLOP/s, FMA = 2
+    out = []
+    for k, t in sorted(trace.items(), key=lambda kv: -kv[1]["ms"]):
+        if k not in work or t["launches"] == 0:
+            continue
+        ms_launch = t["ms"] / t["launches"]
+        per_launch = work[k]["bytes"] * steps / t["launches"]
+        ach = per_launch / (ms_launch * 1e-3) / 1e9
+        r = {"kernel": k, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
+             "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+             "peak_source": peak_kind, "traffic": traffic_record(k, workload),
+             "algorithmic_bytes_per_launch": int(per_launch),
+             "ms_per_launch": round(ms_launch, 5), "launches_per_step": t["launches"] // steps,
+             "share": round(t["ms"] / tot, 4)}
+        if "flops" in work[k]:
+            fl = work[k]["flops"] * steps / t["launches"] / (ms_launch * 1e-3) / 1e12
+            r["fp32_alu"] = {"achieved": round(fl, 2), "peak": round(fp32_peak, 1),
+                             "unit": "TFLOP/s", "frac": round(fl / fp32_peak, 4),
+                             "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+        out.append(r)
+    return out
 
 
 def run_gb300(args, rank, world, local_rank):
@@ -199,16 +257,16 @@ def run_gb300(args, rank, world, local_rank):
         out = f.all_knn(w.k, workspace=ws[form])
         return f, out
 
-    def timed(form, K, trace=False):
+    def timed(form, K, trace=False, kwt=None, wst=None):
         times, b_ms, a_ms = [], [], []
         for _ in range(K):
             flush.fill_(1)
             torch.cuda.synchronize()
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
-            f = forest.Forest(Xd, form=form, **kw)
+            f = forest.Forest(Xd, form=form, **(kwt or kw))
             e1.record(stream)
-            f.all_knn(w.k, workspace=ws[form])
+            f.all_knn(w.k, workspace=ws[form] if wst is None else wst)
             e2.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e2))
@@ -247,7 +305,11 @@ def run_gb300(args, rank, world, local_rank):
     value = world * n / (ms_step * 1e-3)
 
     # plain FP32 form on the same workload
+    forest.Trace.read()
+    forest.Trace.enable(True)
     p_times, p_b, p_a = timed(plain, args.steps)
+    forest.Trace.enable(False)
+    trace_p = forest.Trace.read()
     p_ms = sum(p_times) / len(p_times)
 
     # end to end through the C ABI with host buffers
@@ -276,17 +338,59 @@ def run_gb300(args, rank, world, local_rank):
     bi, bd = forest.brute_knn(Xd, Xd[rows.long()].contiguous(), w.k, self_idx=rows)
     ci_s, cd_s = ci[rows.long()].cpu().numpy(), cd[rows.long()].cpu().numpy()
     bi, bd = bi.cpu().numpy(), bd.cpu().numpy()
-    miss = sum(len(set(bi[r]) - set(ci_s[r])) for r in range(len(bi))) / float(bi.size)
-    disc = float((cd_s[:, -1].mean() - bd[:, -1].mean()) / bd[:, -1].mean())
+
+    def missing(found):
+        return sum(len(set(bi[r]) - set(found[r])) for r in range(len(bi))) / float(bi.size)
+
+    def discrepancy(found_d):
+        mt = bd[:, -1].astype(np.float64).mean()
+        return float((found_d[:, -1].astype(np.float64).mean() - mt) / mt)
+
+    miss, disc = missing(ci_s), discrepancy(cd_s)
+    # The first T' trees of a forest are the T'-tree forest (node keys and
+    # draws depend on the tree index only), so growing the ensemble finds the
+    # smallest T with a missing rate <= 1 %; that T is then timed like the
+    # configured one.
+    at1 = None
+    if miss > 0.01:
+        sweep = []
+        for Tn in (64, 96, 128, 192, 256, 384, 512):
+            kwt = dict(kw, n_trees=Tn)
+            f2 = forest.Forest(Xd, form=chosen, **kwt)
+            wst = torch.empty(f2.workspace_bytes(w.k), dtype=torch.uint8, device=dev)
+            i2, d2 = f2.all_knn(w.k, workspace=wst)
+            m2 = missing(i2[rows.long()].cpu().numpy())
+            sweep.append({"n_trees": Tn, "missing_rate": round(m2, 5)})
+            f2.close()
+            if m2 <= 0.01:
+                t2, b2, a2 = timed(chosen, args.steps, kwt=kwt, wst=wst)
+                ms2 = sum(t2) / len(t2)
+                pt2, _, pa2 = timed(plain, args.steps, kwt=kwt, wst=wst)
+                at1 = {"n_trees": Tn, "missing_rate": round(m2, 5),
+                       "knn_distance_discrepancy": round(discrepancy(d2[rows.long()].cpu().numpy()), 6),
+                       "value": round(world * n / (ms2 * 1e-3), 1), "ms_per_step": round(ms2, 3),
+                       "stage_ms": {"build": round(sum(b2) / len(b2), 3),
+                                    "all_knn": round(sum(a2) / len(a2), 3)},
+                       "plain": {"value": round(world * n / (sum(pt2) / len(pt2) * 1e-3), 1),
+                                 "all_knn_ms": round(sum(pa2) / len(pa2), 3)}}
+                break
+            del wst
+        if at1 is None:
+            at1 = {"not_reached_by_n_trees": 512}
+        at1["sweep"] = sweep
     info = fc.info()
 
     hbm_peak, peak_kind = peaks()
-    for k in trace:
-        trace[k]["steps"] = args.steps
-    top, roof = roofline(trace, w, fc, n, hbm_peak, peak_kind)
-    if roof is not None:
-        tot = sum(v["ms"] for v in trace.values())
-        roof["share"] = round(trace[top]["ms"] / tot, 4) if tot else None
+    work = work_model(fc, w, n)
+    roofs = rooflines(trace, work, hbm_peak, peak_kind, args.steps, args.workload)
+    roofs_p = rooflines(trace_p, work, hbm_peak, peak_kind, args.steps, args.workload)
+    roof = None
+    if roofs:
+        top = roofs[0]
+        roof = {k: top[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+        roof.update({"kernel": top["kernel"], "share": top["share"], "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": top["algorithmic_bytes_per_launch"],
+                     "ms_per_launch": top["ms_per_launch"]})
     fc.close()
     fp.close()
 
@@ -315,6 +419,7 @@ def run_gb300(args, rank, world, local_rank):
         "chosen_equals_plain": same,
         "missing_rate": round(miss, 5),
         "knn_distance_discrepancy": round(disc, 6),
+        "at_missing_rate_le_1pct": at1,
         "accuracy_sample": "2000 points vs exact brute force (rpf_brute_knn)",
         "forest": info,
         "e2e": {"value": round(world * n / e2e_s, 1), "unit": "queries/s",
@@ -322,6 +427,9 @@ def run_gb300(args, rank, world, local_rank):
         "gpu_launches": int((l1 - l0) / args.steps),
         "gpu_launches_per_step": True,
         "roofline": roof,
+        "kernel_rooflines": roofs,
+        "plain_leaf_roofline": [r for r in roofs_p if r["kernel"] == "k_leaf_plain"],
+        "work_model": work["_point_levels"],
         "kernels_ms_per_step": {k: round(v["ms"] / args.steps, 4) for k, v in
                                 sorted(trace.items(), key=lambda kv: -kv[1]["ms"])},
         "clocks": clk,

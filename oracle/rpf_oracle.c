@@ -15,7 +15,7 @@
  *
  * Readings of points where the paper is silent (each restated where used):
  *   leaf rule   : a node with more than L points is split, so no leaf holds
- *                 more than L points (the "leaf capacity" of Sec. 5.2; the
+ *                 more than L points (the leaf size bound of Sec. 5.2; the
  *                 n_s of Algorithm 1 is L + 1).
  *   randomness  : every random draw is a pure function of (seed, tree, node
  *                 key, ...) through a SplitMix64 chain, so the order in which
@@ -153,8 +153,8 @@ void orc_sincos2pif(float u, float* c_out, float* s_out) {
 }
 
 /* ------------------------------------------------------------------------- */
-/* Random direction for (tree t, node key, try j): Sec. 2, "generate a random */
-/* direction" of Algorithms 1 and 2, all in FP32: g_{2i}, g_{2i+1} by         */
+/* Random direction for (tree t, node key, try j): the direction draw of    */
+/* Algorithms 1 and 2 (Sec. 2), all in FP32: g_{2i}, g_{2i+1} by             */
 /* Box-Muller from the top 24 bits of words c = 2i and c = 2i+1; then         */
 /* s = sequential fmaf sum of g_k^2, inv = 1 / sqrtf(s), r_k = g_k * inv.     */
 /* r is returned as doubles (exactly the FP32 values).                        */
@@ -186,7 +186,7 @@ void orc_direction(uint64_t seed, uint64_t t, uint64_t key, uint64_t j, int d,
   free(g);
 }
 
-/* Projection coefficient r . x (Sec. 2, "projection coefficient"). */
+/* Projection of x on the direction r (Sec. 2, Algorithms 1-2). */
 double orc_proj(const float* x, const double* r, int d) {
   double p = 0.0;
   for (int k = 0; k < d; ++k) p = fma((double)x[k], r[k], p);

@@ -24,8 +24,8 @@
 #define RPF_FULL 0xffffffffu
 
 // ---------------------------------------------------------------------------
-// Counter-based random numbers (Sec. 2 "generate a random direction" and
-// "c ~ runif[a, b]").  mix64 is the SplitMix64 output function (Steele, Lea &
+// Counter-based random numbers for the direction draws and the uniform split
+// point of Algorithms 1-2 (Sec. 2).  mix64 is the SplitMix64 output function (Steele, Lea &
 // Flood 2014); word() absorbs (tag, tree, node key, try/attempt, counter) into
 // the seed one field at a time.  Root key 1; child key = mix64(key ^ (1 +
 // side) * GAMMA), side 0 = left, 1 = right.
