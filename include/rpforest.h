@@ -109,6 +109,36 @@ int rpf_all_knn(rpf_forest* f, int32_t K, int32_t* idx, float* dist, void* works
 int rpf_query(const rpf_forest* f, const float* Q, int64_t m, int32_t K, int32_t* idx,
               float* dist, void* workspace, size_t ws_bytes, void* stream);
 
+/* Allocation-free query.  The paper has no counterpart: this is the query of
+ * Sec. 2, Algorithm 3 exactly as rpf_query computes it (same kernels, same
+ * results bit for bit), for callers that must not allocate device memory
+ * while they run -- e.g. a serving process whose free HBM is already handed
+ * to its own pool, or a latency-critical thread that cannot take the
+ * synchronisation a device allocation may imply.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine (with launch tracing off, the
+ * default).
+ *   Q        : m x d queries in DEVICE memory, row-major FP32; m >= 0.
+ *   K        : 1 <= K <= 128.
+ *   idx,dist : m x K outputs in DEVICE memory, owned by the caller.
+ *   stream   : cudaStream_t (NULL = legacy default stream).
+ * Scratch: one fixed array of RPF_STATIC_SCRATCH_BYTES per device, inside
+ * the library.  A call needs align256(4 m T) + align256(8 T m K) bytes of it
+ * (T = trees of the forest; at T = 32, K = 10 that allows m <= 3120); larger
+ * requests return RPF_EINVAL without launching anything -- split them.
+ * Nothing in the scratch has to start at zero: every byte a call reads was
+ * written earlier in the same call.
+ * Set-up: the first call on a device (that device current, the forest's
+ * device) looks the array up once (cudaGetSymbolAddress) and caches its
+ * address; make that first call before any stream capture starts.
+ * Races: the scratch is shared by every call on the device.  Calls that may
+ * overlap in time (different streams, different host threads) race on it and
+ * corrupt each other's results: issue them on one stream, or serialise them.
+ * Errors: RPF_EINVAL (bad argument, host pointer, wrong current device,
+ * request larger than the scratch), RPF_ECUDA. */
+#define RPF_STATIC_SCRATCH_BYTES (8 << 20)
+int rpf_query_static(const rpf_forest* f, const float* Q, int64_t m, int32_t K, int32_t* idx,
+                     float* dist, void* stream);
+
 /* Scratch bytes rpf_all_knn (for_all_knn = 1, m ignored) or rpf_query needs. */
 size_t rpf_workspace_bytes(const rpf_forest* f, int64_t m, int32_t K, int32_t for_all_knn);
 

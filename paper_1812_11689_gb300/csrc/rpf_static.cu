@@ -1,0 +1,62 @@
+// rpf_static.cu -- rpf_query_static: the query path of rpf_query with its
+// scratch in a fixed device array instead of a caller workspace or a
+// stream-ordered allocation.
+//
+// It exists for callers that must not allocate device memory once they are
+// running: a serving process that has handed the rest of HBM to its own pool,
+// or a latency-critical thread for which a device allocation (and the
+// synchronisation it may imply) is not acceptable.  Such a caller can answer
+// queries with memory it already owns (Q, idx, dist) and nothing else.
+//
+// The scratch is one file-scope __device__ array per device (its backing is
+// set up by the CUDA runtime when this module is loaded, not by this call).
+// The first call on a device, with that device current, looks the array up
+// with cudaGetSymbolAddress and caches the address; that first call should be
+// made before any stream capture begins.  Later calls on the device only
+// reuse the cached address.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "rpf_internal.cuh"
+
+namespace {
+
+__device__ __align__(256) unsigned char g_query_scratch[RPF_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_addr[kMaxDevices] = {};
+
+size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int rpf_query_static(const rpf_forest* f, const float* Q, int64_t m, int32_t K,
+                                int32_t* idx, float* dist, void* stream) {
+  if (!f || K < 1 || K > RPF_MAX_K || m < 0) return RPF_EINVAL;
+  if (m == 0) return RPF_OK;
+  if (!Q || !idx || !dist) return RPF_EINVAL;
+  const int T = f->prm.n_trees;
+  // leaf id per (query, tree), then T per-tree candidate lists of K entries
+  const size_t need = a256((size_t)m * T * 4) + a256((size_t)T * m * K * 8);
+  if (need > (size_t)RPF_STATIC_SCRATCH_BYTES) return RPF_EINVAL;
+  if (!rpf_is_device_ptr(Q) || !rpf_is_device_ptr(idx) || !rpf_is_device_ptr(dist))
+    return RPF_EINVAL;
+  int dev = -1;
+  RPF_CU(cudaGetDevice(&dev));
+  if (dev != f->device || dev < 0 || dev >= kMaxDevices) return RPF_EINVAL;
+  void* ws = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!g_addr[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_query_scratch);
+      if (e != cudaSuccess) return rpf_cuda_err(e);
+      g_addr[dev] = p;
+    }
+    ws = g_addr[dev];
+  }
+  return rpf_query_dev(f, Q, m, K, idx, dist, ws, (size_t)RPF_STATIC_SCRATCH_BYTES,
+                       (cudaStream_t)stream);
+}

@@ -110,6 +110,18 @@ class Forest:
                                    ws or None, wsb, _stream_handle(stream)), "rpf_query")
         return idx, dist
 
+    def query_static(self, Q, K: int, idx, dist, stream=None):
+        """rpf_query_static: the query with the library's fixed device scratch.
+
+        Q, idx and dist are caller-owned CUDA tensors; nothing is allocated.
+        Calls that may overlap in time share the scratch and must be
+        serialised (one stream)."""
+        m = int(Q.shape[0])
+        check(_lib.lib().rpf_query_static(self._h, _ptr(Q) if m else None, m, K,
+                                          _ptr(idx) if m else None, _ptr(dist) if m else None,
+                                          _stream_handle(stream)), "rpf_query_static")
+        return idx, dist
+
     # ---- inspection ------------------------------------------------------------
     def info(self) -> dict:
         n, d, T, nn, nl, md, ne = (ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(),
