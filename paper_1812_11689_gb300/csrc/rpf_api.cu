@@ -74,7 +74,7 @@ void free_forest(rpf_forest* f) {
   void* ps[] = {f->node_key,  f->node_tree,  f->node_begin, f->node_len,  f->node_left,
                 f->node_right, f->node_jstar, f->node_flag, f->node_c,    f->node_dir,
                 f->node_dir32, f->leaf_tree,  f->leaf_begin, f->leaf_len, f->tile_cnt,
-                f->tile_off,  f->tile_leaf,  f->stage};
+                f->tile_off,  f->tile_leaf,  f->stage,      f->pk_tiles, f->pk_bits};
   for (void* p : ps) rpf_release(p, 0);
   delete f;
 }
@@ -139,7 +139,8 @@ int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* s
     free_forest(f);
     return rpf_cuda_err(e);
   }
-  if ((rc = rpf_grow(f, s)) || (rc = rpf_build_tiles(f, s))) {
+  if ((rc = rpf_grow(f, s)) || (rc = rpf_build_tiles(f, s)) ||
+      (f->prm.form == 1 && (rc = rpf_build_packs(f, s)))) {
     free_forest(f);
     return rc;
   }

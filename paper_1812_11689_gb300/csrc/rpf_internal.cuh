@@ -225,6 +225,12 @@ struct rpf_forest {
   int32_t* tile_off = nullptr;    // first entry of the tile in tile_leaf
   int32_t* tile_leaf = nullptr;   // leaf indices grouped by tile
 
+  // chosen-form tiles: runs of consecutive leaves of one tree, <= 128 rows
+  int4* pk_tiles = nullptr;          // (tree, first position, rows, 0), tree-major
+  uint32_t* pk_bits = nullptr;       // T x pk_nwords: bit p set iff a leaf begins at p
+  int64_t pk_nwords = 0;
+  std::vector<int64_t> pk_tree_off;  // first tile of every tree (T + 1 entries)
+
   int* d_err = nullptr;  // device error word (RPF_ETIMEOUT from bounded waits)
   unsigned long long* d_fallback = nullptr;  // rows the BF16 form rescanned exactly
 
@@ -266,6 +272,10 @@ void rpf_release(void* p, cudaStream_t s);
 int rpf_grow(rpf_forest* f, cudaStream_t s);
 // leaf tiles + merge + query (rpf_knn.cu)
 int rpf_build_tiles(rpf_forest* f, cudaStream_t s);
+// chosen-form leaf tiles (rpf_leaf_tc.cu)
+int rpf_build_packs(rpf_forest* f, cudaStream_t s);
+bool rpf_tc_supported(const rpf_forest* f, int K);
+int rpf_leaf_tc(const rpf_forest* f, int t0, int g, int K, uint2* cand, cudaStream_t s);
 int rpf_all_knn_dev(rpf_forest* f, int K, int32_t* idx, float* dist, void* ws, size_t ws_bytes,
                     cudaStream_t s);
 int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t* idx, float* dist,

@@ -22,7 +22,6 @@
 #include "rpf_internal.cuh"
 #include "rpf_tma.cuh"
 #include "rpf_scan.cuh"
-#include "rpf_umma.cuh"
 
 namespace {
 
@@ -267,317 +266,6 @@ __device__ __forceinline__ void rpf_row_exact(const float* xs, int dp, int d4, i
   }
 }
 
-// Unsorted buffer of the SB smallest (value, index) offered, with the
-// smallest value it has rejected or evicted (theta): every index outside the
-// buffer had a value >= theta.  Replacement evicts the current maximum.
-template <int SB>
-struct ShortList {
-  float v[SB];
-  int i[SB];
-  float vmax, theta;
-  int imax;
-  __device__ __forceinline__ void init() {
-#pragma unroll
-    for (int q = 0; q < SB; ++q) {
-      v[q] = INFINITY;
-      i[q] = -1;
-    }
-    vmax = INFINITY;
-    imax = 0;
-    theta = INFINITY;
-  }
-  __device__ __forceinline__ void offer(float x, int j) {
-    if (!(x < vmax)) {
-      theta = fminf(theta, x);
-      return;
-    }
-    theta = fminf(theta, vmax);
-#pragma unroll
-    for (int q = 0; q < SB; ++q) {
-      const bool hit = q == imax;
-      v[q] = hit ? x : v[q];
-      i[q] = hit ? j : i[q];
-    }
-    vmax = v[0];
-    imax = 0;
-#pragma unroll
-    for (int q = 1; q < SB; ++q) {
-      const bool gt = v[q] > vmax;
-      vmax = gt ? v[q] : vmax;
-      imax = gt ? q : imax;
-    }
-  }
-};
-
-// ---------------------------------------------------------------------------
-// Chosen form: BF16 tensor-core Gram + exact re-rank of a shortlist.
-//
-// Per leaf of more than 48 points (at most 128): rows are centred on the
-// leaf's FP32 mean (y = x - c) and split into BF16 pairs y ~ hi + lo; three
-// tcgen05.mma chains (hi hi^T + hi lo^T + lo hi^T, M = 128, N = 16-padded
-// leaf size, FP32 accumulation in TMEM) give the Gram matrix G.  Row r reads
-// its Gram row from TMEM and keeps the SB smallest approximate squared
-// distances D~_rj = n_r + n_j - 2 G_rj (n = FP32 squared norm of y) in an
-// unsorted buffer, re-ranks them with the canonical FP32 d32 and certifies:
-// every j outside the buffer has D~_rj >= theta, and
-//   | D~_rj - |y_r - y_j|^2 | <= eps_r = ce (|y_r|^2 + max |y|^2)
-//     ce = 2^-13 + (d + 8) 2^-23 + 3 (d16 + 4) 2^-21
-//   (2^-13 covers the split-BF16 residual 2^-16 |y_k| per element and the
-//   dropped lo lo^T term, 3 2^-16 |y_r||y_j| in all, doubled in D~, with
-//   room for underflow in the products; (d + 8) 2^-23 the FP32 norms and the
-//   combination; 3 (d16 + 4) 2^-21 the accumulation of 3 d16 products in the
-//   tensor core's FP32 accumulator, taken at 2^-22 per addition so that
-//   truncating internal adds are covered, doubled in D~).  The tensor path
-//   is taken only when 2^-90 <= max |y|^2 <= 2^120, so every D~ is finite and
-//   BF16 subnormals are negligible.
-//   | |y_r - y_j| - |x_r - x_j| | <= eta_r = 2^-23 (|y_r| + max |y|)
-//   sqrt(d32_rj) >= (1 - (d + 3) 2^-23) |x_r - x_j|
-// so if sqrt(d32) of the K-th exact entry is below
-//   (1 - (d + 3) 2^-23) (sqrt(theta - eps_r) - eta_r)
-// no point outside the buffer can enter the top-K: the list equals the plain
-// form's bit for bit.  Otherwise the row is rescanned exactly (counted in
-// *fallbacks).  Leaves of at most 48 points are scanned exactly.
-// ---------------------------------------------------------------------------
-template <int KMAX, int SB>
-__global__ void __launch_bounds__(128, 3) k_leaf_bf16(
-    const int32_t* tile_cnt, const int32_t* tile_off, const int32_t* tile_leaf, int64_t tile_base,
-    const int32_t* leaf_tree, const int32_t* leaf_begin, const int32_t* leaf_len,
-    const int32_t* perm, const float* __restrict__ X, int64_t n, int d, int dp, int d16,
-    int rows_max, int K, int t0, uint2* cand, int* err, unsigned long long* fallbacks) {
-  extern __shared__ __align__(1024) unsigned char smraw[];
-  float* xs = reinterpret_cast<float*>(smraw);
-  const size_t a_off = (((size_t)rows_max * dp * 4) + 1023) & ~(size_t)1023;
-  __nv_bfloat16* Ahi = reinterpret_cast<__nv_bfloat16*>(smraw + a_off);
-  const int KC = d16 < 128 ? d16 : 128;  // Gram columns per tensor-core chunk
-  __nv_bfloat16* Alo = Ahi + 128 * KC;
-  float* nrm = reinterpret_cast<float*>(Alo + 128 * KC);
-  float* ynm = nrm + 128;
-  float* cen = ynm + 128;
-  int* slots = reinterpret_cast<int*>(cen + ((d + 3) & ~3));  // 128 threads x SB
-  __shared__ int leaf_off[257];
-  __shared__ int lbeg[256];
-  __shared__ int b0s;
-  __shared__ float red[8];
-  __shared__ __align__(8) uint64_t bar_tma, bar_mma;
-  __shared__ uint32_t tmem_base;
-  const int64_t tile = tile_base + blockIdx.x;
-  const int nl = tile_cnt[tile];
-  if (nl == 0) return;
-  const int32_t* tl = tile_leaf + tile_off[tile];
-  const int t = leaf_tree[tl[0]];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int q = tid; q < nl; q += blockDim.x) lbeg[q] = leaf_begin[tl[q]];
-  __syncthreads();
-  for (int q = tid; q < nl; q += blockDim.x) {
-    const int b = lbeg[q];
-    int rank = 0;
-    for (int p = 0; p < nl; ++p) rank += lbeg[p] < b;
-    leaf_off[rank] = b;
-    if (rank == nl - 1) leaf_off[nl] = b + leaf_len[tl[q]];
-    if (rank == 0) b0s = b;
-  }
-  __syncthreads();
-  const int b0 = b0s;
-  for (int q = tid; q <= nl; q += blockDim.x) leaf_off[q] -= b0;
-  __syncthreads();
-  const int rows = leaf_off[nl];
-  const int32_t* prow = perm + (int64_t)t * n + b0;
-  if (tid == 0) {
-    rpf_mbar_init(&bar_tma, 1);
-    rpf_mbar_init(&bar_mma, 1);
-    rpf_mbar_arrive_expect_tx(&bar_tma, (uint32_t)rows * (uint32_t)d * 4u);
-  }
-  if (warp == 0) rpf_tmem_alloc(&tmem_base, 128);
-  rpf_tc_fence_before();
-  __syncthreads();
-  rpf_tc_fence_after();
-  const uint32_t tbase = tmem_base;
-  for (int r = tid; r < rows; r += blockDim.x)
-    rpf_bulk_g2s(xs + r * dp, X + (int64_t)prow[r] * d, (uint32_t)d * 4u, &bar_tma);
-  for (int r = tid; r < rows; r += blockDim.x)
-    for (int k = d; k < dp; ++k) xs[r * dp + k] = 0.0f;
-  const bool ok_tma = rpf_mbar_wait(&bar_tma, 0, err);
-  bool ok = __syncthreads_and(ok_tma) != 0;  // block-uniform from here on
-  const int d4 = (d + 3) & ~3;
-  uint32_t mma_phase = 0;
-  bool mma_pending = false;
-  const float ce = 0x1p-13f + (float)(d + 8) * 0x1p-23f + 3.0f * (float)(d16 + 4) * 0x1p-21f;
-  for (int q = 0; q < nl && ok; ++q) {
-    const int lb = leaf_off[q], le = leaf_off[q + 1], m = le - lb;
-    if (m <= 48 || m > 128) {  // exact scan
-      for (int r = lb + tid; r < le; r += blockDim.x) {
-        TopK<KMAX> tk;
-        tk.init();
-        rpf_row_exact<KMAX>(xs, dp, d4, r, lb, le, prow, tk);
-        tk.store(K, cand + ((int64_t)(t - t0) * n + prow[r]) * K);
-      }
-      continue;
-    }
-    // (a) leaf mean
-    for (int k = tid; k < d; k += blockDim.x) {
-      float sacc = 0.0f;
-      for (int r = lb; r < le; ++r) sacc = __fadd_rn(sacc, xs[r * dp + k]);
-      cen[k] = __fdiv_rn(sacc, (float)m);
-    }
-    __syncthreads();
-    const int npad = (m + 15) & ~15;
-    const uint32_t idesc = rpf_umma_idesc_bf16(128, npad);
-    // (b, c) centred split-BF16 tiles of KC columns at a time and the FP32
-    // squared norms; G += hi hi^T + hi lo^T + lo hi^T on the tensor core
-    float yy = 0.0f;
-    for (int k0 = 0; k0 < d16 && ok; k0 += KC) {
-      if (k0 > 0) {  // the previous chunk's MMAs must be done reading the tiles
-        const bool w = rpf_mbar_wait(&bar_mma, mma_phase, err);
-        mma_phase ^= 1u;
-        mma_pending = false;
-        ok = __syncthreads_and(w) != 0;
-        if (!ok) break;
-      }
-      const int r = tid;
-      for (int k = 0; k < KC; ++k) {
-        const int kk = k0 + k;
-        float y = 0.0f;
-        if (r < m && kk < d) y = __fsub_rn(xs[(lb + r) * dp + kk], cen[kk]);
-        const __nv_bfloat16 h = __float2bfloat16_rn(y);
-        const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(y, __bfloat162float(h)));
-        const int idx = rpf_umma_index(r, k, 16);
-        Ahi[idx] = h;
-        Alo[idx] = l;
-        yy = __fmaf_rn(y, y, yy);
-      }
-      rpf_fence_proxy_async();  // BF16 tiles -> visible to the tensor core
-      rpf_tc_fence_before();
-      __syncthreads();
-      if (tid == 0) {
-        rpf_tc_fence_after();
-        const uint32_t hb = rpf_saddr(Ahi), lbs = rpf_saddr(Alo);
-        for (int s2 = 0; s2 < KC / 16; ++s2) {
-          const uint32_t off = (uint32_t)s2 * 2u * 16u * 128u;
-          const uint64_t dh = rpf_umma_desc(hb + off, 16u * 128u, 128u);
-          const uint64_t dl = rpf_umma_desc(lbs + off, 16u * 128u, 128u);
-          rpf_umma_bf16(tbase, dh, dh, idesc, (k0 > 0 || s2 > 0) ? 1u : 0u);
-          rpf_umma_bf16(tbase, dh, dl, idesc, 1u);
-          rpf_umma_bf16(tbase, dl, dh, idesc, 1u);
-        }
-        rpf_umma_commit(&bar_mma);
-      }
-      mma_pending = true;
-    }
-    if (!ok) break;
-    float nmax = 0.0f;
-    {
-      const int r = tid;
-      nrm[r] = yy;
-      const float yup = __fmul_ru(yy, 1.0f + (float)(d + 4) * 0x1p-23f);
-      ynm[r] = __fsqrt_ru(yup);
-      if (r < m) nmax = yup;
-    }
-    for (int off = 16; off >= 1; off >>= 1) nmax = fmaxf(nmax, __shfl_xor_sync(RPF_FULL, nmax, off));
-    if (lane == 0) red[warp] = nmax;
-    {
-      const bool w = rpf_mbar_wait(&bar_mma, mma_phase, err);
-      mma_phase ^= 1u;
-      mma_pending = false;
-      ok = __syncthreads_and(w) != 0;
-      if (!ok) break;
-    }
-    rpf_tc_fence_after();
-    const float Nmax = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
-    const float Ymax = __fsqrt_ru(Nmax);
-    if (!(Nmax >= 0x1p-90f && Nmax <= 0x1p120f)) {  // out of the certified range: exact scan
-      for (int r = lb + tid; r < le; r += blockDim.x) {
-        TopK<KMAX> tk;
-        tk.init();
-        rpf_row_exact<KMAX>(xs, dp, d4, r, lb, le, prow, tk);
-        tk.store(K, cand + ((int64_t)(t - t0) * n + prow[r]) * K);
-      }
-      __syncthreads();
-      continue;
-    }
-    // (d) shortlist, exact re-rank, certificate
-    if (ok && 32 * warp < m) {
-      const int r = tid;
-      const bool live = r < m;
-      ShortList<SB> sl;
-      sl.init();
-      const float nr = nrm[r];
-#pragma unroll 1
-      for (int c0 = 0; c0 < npad; c0 += 8) {
-        float g[8];
-        rpf_tmem_ld8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, g);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int c = c0 + j;
-          if (live && c < m && c != r)
-            sl.offer(__fsub_rn(__fadd_rn(nr, nrm[c]), __fmul_rn(2.0f, g[j])), c);
-        }
-      }
-      if (live) {
-        TopK<KMAX> ex;
-        ex.init();
-        const float* x = xs + (lb + r) * dp;
-        int* my = slots + tid * SB;  // shortlist indices, read back with a rolled loop
-        int ns = 0;
-#pragma unroll
-        for (int q2 = 0; q2 < SB; ++q2)
-          if (sl.i[q2] >= 0) my[ns++] = sl.i[q2];
-#pragma unroll 1
-        for (int e0 = 0; e0 < ns; e0 += 4) {
-          int cc[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) cc[j] = lb + my[e0 + j < ns ? e0 + j : e0];
-          float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-          for (int k = 0; k < d4; k += 4) {
-            const float4 a = *reinterpret_cast<const float4*>(x + k);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const float4 v = *reinterpret_cast<const float4*>(xs + cc[j] * dp + k);
-              float e;
-              e = __fsub_rn(a.x, v.x); acc[j] = __fmaf_rn(e, e, acc[j]);
-              e = __fsub_rn(a.y, v.y); acc[j] = __fmaf_rn(e, e, acc[j]);
-              e = __fsub_rn(a.z, v.z); acc[j] = __fmaf_rn(e, e, acc[j]);
-              e = __fsub_rn(a.w, v.w); acc[j] = __fmaf_rn(e, e, acc[j]);
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (e0 + j < ns) ex.offer(acc[j], prow[cc[j]]);
-        }
-        bool cert = sl.theta == INFINITY;  // nothing was left out
-        if (!cert && ns >= K) {
-          float rhok = 0.0f;
-#pragma unroll
-          for (int q2 = 0; q2 < KMAX; ++q2)
-            if (q2 == K - 1) rhok = ex.kd[q2];
-          const float eps = __fmul_ru(ce, __fadd_ru(nr, Nmax));
-          const float eta = __fmul_ru(0x1p-23f, __fadd_ru(ynm[r], Ymax));
-          const float base = __fsub_rd(__fsqrt_rd(fmaxf(__fsub_rd(sl.theta, eps), 0.0f)), eta);
-          const float lower = __fmul_rd(1.0f - (float)(d + 3) * 0x1p-23f, base);
-          cert = __fsqrt_ru(rhok) < lower;
-        }
-        if (!cert) {
-          ex.init();
-          rpf_row_exact<KMAX>(xs, dp, d4, lb + r, lb, le, prow, ex);
-          atomicAdd(fallbacks, 1ULL);
-        }
-        ex.store(K, cand + ((int64_t)(t - t0) * n + prow[lb + r]) * K);
-      }
-    }
-    rpf_tc_fence_before();
-    __syncthreads();
-  }
-  // after a timed-out wait: give copies and MMAs still in flight one more
-  // bounded wait before the shared memory and TMEM are given up
-  if (!ok_tma) rpf_mbar_wait(&bar_tma, 0, nullptr);
-  if (mma_pending) rpf_mbar_wait(&bar_mma, mma_phase, nullptr);
-  rpf_tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    rpf_tc_fence_after();
-    rpf_tmem_dealloc(tbase, 128);
-  }
-}
-
 // Merge G per-tree lists (sorted, padded with (inf, -1)) into the running list
 // of each point.  first: no running list yet; last: write the final outputs.
 template <int KMAX>
@@ -717,34 +405,6 @@ void launch_leaf(const rpf_forest* f, int64_t tb, int64_t nt, int K, int t0, uin
 #undef RPF_LEAF
 }
 
-template <int KMAX, int SB>
-void launch_leaf_bf16(const rpf_forest* f, int64_t tb, int64_t nt, int K, int t0, uint2* cand,
-                      int* err, cudaStream_t s) {
-  const int dp = ((f->d + 3) & ~3) + 4;
-  const int d16 = (f->d + 15) & ~15;
-  const size_t a_off = (((size_t)f->tile_rows * dp * 4) + 1023) & ~(size_t)1023;
-  const int KC = std::min(d16, 128);
-  const size_t need =
-      a_off + (size_t)2 * 128 * KC * 2 + 4 * (256 + ((f->d + 3) & ~3)) + 4 * 128 * SB;
-  // at least 60 KB so that at most three CTAs (3 x 128 TMEM columns) share an SM
-  const size_t smem = std::max<size_t>(need, 60 * 1024);
-  cudaFuncSetAttribute(k_leaf_bf16<KMAX, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
-  RPF_LAUNCH("k_leaf_bf16", s, k_leaf_bf16<KMAX, SB><<<(unsigned)nt, 128, smem, s>>>(
-      f->tile_cnt, f->tile_off, f->tile_leaf, tb, f->leaf_tree, f->leaf_begin, f->leaf_len, f->perm,
-      f->X, f->n, f->d, dp, d16, f->tile_rows, K, t0, cand, err, f->d_fallback));
-}
-
-bool rpf_bf16_supported(const rpf_forest* f, int K) {
-  const int dp = ((f->d + 3) & ~3) + 4;
-  const int d16 = (f->d + 15) & ~15;
-  const size_t a_off = (((size_t)f->tile_rows * dp * 4) + 1023) & ~(size_t)1023;
-  const int KC = std::min(d16, 128);
-  const size_t smem = a_off + (size_t)2 * 128 * KC * 2 + 4 * (256 + ((f->d + 3) & ~3)) + 4 * 128 * 32;
-  return f->prm.leaf_max <= 128 && K <= 26 && (f->d % 4) == 0 && f->tile_region <= 256 &&
-         smem <= 200 * 1024;
-}
-
 template <int KMAX>
 void launch_merge(int64_t n, int K, int G, const uint2* cand, uint2* run, bool first, bool last,
                   int32_t* idx, float* dist, cudaStream_t s) {
@@ -860,12 +520,9 @@ int rpf_all_knn_dev(rpf_forest* f, int K, int32_t* idx, float* dist, void* ws, s
     const int64_t tb = (int64_t)t0 * f->tiles_per_tree;
     const int64_t nt = (int64_t)g * f->tiles_per_tree;
     if (nt > 0) {
-      if (f->prm.form == 1 && rpf_bf16_supported(f, K)) {
-        // shortlist of SB >= K + 6 entries
-        if (K <= 8) launch_leaf_bf16<8, 16>(f, tb, nt, K, t0, cand, f->d_err, s);
-        else if (K <= 10) launch_leaf_bf16<16, 16>(f, tb, nt, K, t0, cand, f->d_err, s);
-        else if (K <= 16) launch_leaf_bf16<16, 32>(f, tb, nt, K, t0, cand, f->d_err, s);
-        else launch_leaf_bf16<32, 32>(f, tb, nt, K, t0, cand, f->d_err, s);
+      if (f->prm.form == 1 && rpf_tc_supported(f, K)) {
+        const int rc = rpf_leaf_tc(f, t0, g, K, cand, s);
+        if (rc) return rc;
       } else {
         RPF_KDISPATCH(K, launch_leaf, f, tb, nt, K, t0, cand, f->d_err, s);
       }

@@ -1,0 +1,641 @@
+// rpf_leaf_tc.cu -- chosen form of the leaf distances of Algorithm 3 (Sec. 2):
+// the K nearest points of every point inside each of its leaves, with the
+// inner products on the 5th-generation tensor cores and a certified exact
+// FP32 re-rank, so that every list is bit-identical to the plain form's.
+//
+// Work layout.  The leaves of one tree are contiguous segments of the tree's
+// permutation.  k_pack_tiles packs runs of consecutive leaves greedily into
+// tiles of at most 128 rows (a leaf never straddles two tiles); k_leaf_tc is a
+// persistent kernel whose CTAs take tiles in turn.  Per tile (128 threads,
+// thread r = row r):
+//   1. rows are staged in shared memory by bulk copies (TMA engine, mbarrier);
+//      leaf boundaries come from a per-tree bitmask of leaf starts.
+//   2. Leaves of at most TC_SLOTS + 1 points ("small") need no arithmetic
+//      shortcut: every row offers all of its leaf to the exact re-rank.
+//   3. Rows of larger leaves are centred on their leaf's FP32 mean (y = x - c)
+//      and split into BF16 pairs y ~ hi + lo; G = hi hi^T + hi lo^T + lo hi^T
+//      is accumulated by tcgen05.mma (kind::f16, M = 128, N = rows padded to
+//      16, FP32 in TMEM) over chunks of at most 128 coordinates.
+//   4. Row r reads its Gram row from TMEM (tcgen05.ld) twice: first to find
+//      tau, the K-th smallest approximate squared distance
+//      D~_rj = n_r + n_j - 2 G_rj (n = FP32 squared norm of y) with a
+//      branch-free min/max network; then to collect every j with
+//      D~_rj <= tau', a certified margin above tau.
+//   5. The collected candidates are re-ranked with the canonical FP32 d32
+//      (the plain form's exact key) into a sorted list of 64-bit keys
+//      (d32 bits << 32 | index), which orders exactly like (d32, index).
+//   6. Certificate.  Every j that was not collected has D~_rj > tau', and
+//        | D~_rj - |y_r - y_j|^2 | <= eps_r = ce (n_r + N_leaf)
+//        | |y_r - y_j| - |x_r - x_j| | <= eta_r = 2^-23 (|y_r| + Y_leaf)
+//        sqrt(d32_rj) >= (1 - (d + 3) 2^-23) |x_r - x_j|
+//      (ce: 2^-13 for the split-BF16 residual, 2^-16 |y_k| per element, and
+//      the dropped lo lo^T term, doubled in D~, with room for underflow;
+//      (d + 8) 2^-23 for the FP32 norms and combination; 3 (d16 + 4) 2^-21
+//      for the tensor core's FP32 accumulation of 3 d16 products, taken at
+//      2^-22 per addition so that truncating internal adds are covered,
+//      doubled in D~).  So no excluded j can enter the top-K if
+//        sqrt_ru(d32 of the K-th collected) < (1 - (d + 3) 2^-23)
+//                                             (sqrt_rd(tau' - eps_r) - eta_r).
+//      tau' = eps_r + (sqrt(tau + eps_r)(1 + 4 (d + 3) 2^-23) + 2 eta_r)^2
+//      makes this hold whenever the bounds are not loose.  A row that fails
+//      the certificate, or collects more than TC_SLOTS candidates, is
+//      rescanned exactly (counted in *fallbacks).  The tensor path is used
+//      only when 2^-90 <= max |y|^2 <= 2^120 in the leaf (every D~ finite,
+//      BF16 subnormals negligible); other leaves are scanned exactly.
+// Every device wait is bounded; on a timeout the kernel records RPF_ETIMEOUT,
+// waits once more (bounded) for copies and MMAs in flight, frees its TMEM and
+// returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rpf_internal.cuh"
+#include "rpf_scan.cuh"
+#include "rpf_tma.cuh"
+#include "rpf_umma.cuh"
+
+#define TC_ROWS 128
+#define TC_SLOTS 32       // exact re-rank candidates per row
+#define TC_SEG 4096       // packing segment (positions) per thread
+#define TC_SEG_TILES 72   // >= 2 (TC_SEG + 128) / 128 + 1 tiles per segment
+#define TC_MAX_BIG 8      // leaves of > TC_SLOTS + 1 points in one tile (<= 3)
+
+namespace {
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// Sorted list of the KK smallest 64-bit keys offered (ascending; empty slots
+// are all-ones).  Insertion is a branch-free min/max network.
+template <int KK>
+struct Top64 {
+  unsigned long long k[KK];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int q = 0; q < KK; ++q) k[q] = ~0ull;
+  }
+  __device__ __forceinline__ void insert(unsigned long long x) {
+#pragma unroll
+    for (int q = KK - 1; q >= 1; --q) k[q] = max(k[q - 1], min(k[q], x));
+    k[0] = min(k[0], x);
+  }
+  // d32 of the K-th entry: the list is sorted, so it is the smallest key at
+  // or after position K - 1 (a reduction keeps the list in registers)
+  __device__ __forceinline__ float kth_d32(int K) const {
+    unsigned long long m = ~0ull;
+#pragma unroll
+    for (int q = 0; q < KK; ++q) m = min(m, q >= K - 1 ? k[q] : ~0ull);
+    return __uint_as_float((unsigned)(m >> 32));
+  }
+  // first K entries as (d32 bits, index); empty slots as (+inf, -1)
+  __device__ __forceinline__ void store(int K, uint2* out) const {
+#pragma unroll
+    for (int q = 0; q < KK; ++q)
+      if (q < K) {
+        const bool e = k[q] == ~0ull;
+        out[q] = e ? make_uint2(0x7f800000u, 0xffffffffu)
+                   : make_uint2((unsigned)(k[q] >> 32), (unsigned)k[q]);
+      }
+  }
+};
+
+__device__ __forceinline__ unsigned long long key64(float d32, int idx) {
+  return ((unsigned long long)__float_as_uint(d32) << 32) | (unsigned)idx;
+}
+
+// Sorted list of the KK smallest floats offered (branch-free network).
+template <int KK>
+struct TopF {
+  float v[KK];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int q = 0; q < KK; ++q) v[q] = INFINITY;
+  }
+  __device__ __forceinline__ void insert(float x) {
+#pragma unroll
+    for (int q = KK - 1; q >= 1; --q) v[q] = fmaxf(v[q - 1], fminf(v[q], x));
+    v[0] = fminf(v[0], x);
+  }
+  __device__ __forceinline__ float kth(int K) const {  // sorted: min over q >= K - 1
+    float r = INFINITY;
+#pragma unroll
+    for (int q = 0; q < KK; ++q) r = fminf(r, q >= K - 1 ? v[q] : INFINITY);
+    return r;
+  }
+};
+
+// Exact d32 of tile row r against up to four tile rows c[0..3] (canonical
+// chains over k in order; rows padded with zeros to d4).
+__device__ __forceinline__ void d32x4(const float* xs, int dp, int d4, int r, const int (&c)[4],
+                                      float (&acc)[4]) {
+  const float* x = xs + r * dp;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) acc[j] = 0.0f;
+  for (int k = 0; k < d4; k += 4) {
+    const float4 a = *reinterpret_cast<const float4*>(x + k);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4 v = *reinterpret_cast<const float4*>(xs + c[j] * dp + k);
+      float e;
+      e = __fsub_rn(a.x, v.x); acc[j] = __fmaf_rn(e, e, acc[j]);
+      e = __fsub_rn(a.y, v.y); acc[j] = __fmaf_rn(e, e, acc[j]);
+      e = __fsub_rn(a.z, v.z); acc[j] = __fmaf_rn(e, e, acc[j]);
+      e = __fsub_rn(a.w, v.w); acc[j] = __fmaf_rn(e, e, acc[j]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Packing
+// ---------------------------------------------------------------------------
+__global__ void k_leaf_bits(int64_t nl, const int32_t* leaf_tree, const int32_t* leaf_begin,
+                            int64_t nwords, uint32_t* bits) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nl) return;
+  const int b = leaf_begin[i];
+  atomicOr(bits + (int64_t)leaf_tree[i] * nwords + (b >> 5), 1u << (b & 31));
+}
+
+// smallest leaf start >= p in one tree's bitmask, or n
+__device__ int64_t next_start(const uint32_t* b, int64_t n, int64_t p) {
+  if (p >= n) return n;
+  int64_t w = p >> 5;
+  uint32_t x = b[w] & (0xffffffffu << (p & 31));
+  const int64_t nw = (n + 31) >> 5;
+  while (x == 0) {
+    if (++w >= nw) return n;
+    x = b[w];
+  }
+  const int64_t s = (w << 5) + __ffs(x) - 1;
+  return s < n ? s : n;
+}
+
+// largest leaf start in (p, lim], or -1 (lim < n)
+__device__ int64_t last_start_le(const uint32_t* b, int64_t p, int64_t lim) {
+  int64_t w = lim >> 5;
+  uint32_t x = b[w] & (0xffffffffu >> (31 - (lim & 31)));
+  const int64_t w0 = (p + 1) >> 5;
+  while (true) {
+    if (w == w0) x &= 0xffffffffu << ((p + 1) & 31);
+    if (x) break;
+    if (--w < w0) return -1;
+    x = b[w];
+  }
+  return (w << 5) + 31 - __clz(x);
+}
+
+// One thread per (tree, segment of TC_SEG positions): the leaves that begin
+// in the segment, packed greedily in order into tiles of <= TC_ROWS rows.
+__global__ void k_pack_tiles(int T, int64_t n, int64_t nseg, int64_t nwords, const uint32_t* bits,
+                             int2* slot, int32_t* cnt) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (int64_t)T * nseg) return;
+  const int t = (int)(g / nseg);
+  const int64_t sg = g % nseg;
+  const uint32_t* b = bits + (int64_t)t * nwords;
+  const int64_t s0 = sg * TC_SEG, s1 = std::min<int64_t>(n, s0 + TC_SEG);
+  int64_t p = next_start(b, n, s0);
+  int c = 0;
+  if (p < s1) {
+    const int64_t E = next_start(b, n, s1);  // end of the segment's last leaf
+    while (p < E) {
+      const int64_t lim = std::min<int64_t>(p + TC_ROWS, E);
+      int64_t e = lim == n ? n : -1;
+      if (e < 0) {
+        e = last_start_le(b, p, lim);
+        if (e < 0) e = lim;  // cannot happen: the leaf at p ends by p + L
+      }
+      if (c < TC_SEG_TILES) slot[g * TC_SEG_TILES + c] = make_int2((int)p, (int)(e - p));
+      ++c;
+      p = e;
+    }
+  }
+  cnt[g] = c;
+}
+
+__global__ void k_pack_fill(int64_t G, int64_t nseg, const int2* slot, const int32_t* cnt,
+                            const int32_t* off, int4* tiles) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int t = (int)(g / nseg);
+  const int c = min(cnt[g], TC_SEG_TILES);
+  for (int j = 0; j < c; ++j) {
+    const int2 s = slot[g * TC_SEG_TILES + j];
+    tiles[off[g] + j] = make_int4(t, s.x, s.y, 0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The persistent chosen-form kernel
+// ---------------------------------------------------------------------------
+template <int KK>
+__global__ void __launch_bounds__(TC_ROWS, 3) k_leaf_tc(
+    const int4* __restrict__ tiles, int64_t tlo, int64_t thi, const uint32_t* __restrict__ bits,
+    int64_t nwords, const int32_t* __restrict__ perm, const float* __restrict__ X, int64_t n,
+    int d, int dp, int d16, int K, int t0, uint2* cand, int* err,
+    unsigned long long* fallbacks) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  const int KC = d16 < 128 ? d16 : 128;  // Gram coordinates per tensor-core chunk
+  const int d4 = (d + 3) & ~3;
+  float* xs = reinterpret_cast<float*>(smraw);
+  const size_t a_off = (((size_t)TC_ROWS * dp * 4) + 1023) & ~(size_t)1023;
+  __nv_bfloat16* Ahi = reinterpret_cast<__nv_bfloat16*>(smraw + a_off);
+  __nv_bfloat16* Alo = Ahi + TC_ROWS * KC;
+  float* cen = reinterpret_cast<float*>(Alo + TC_ROWS * KC);  // TC_MAX_BIG x d4
+  unsigned char* slots = reinterpret_cast<unsigned char*>(cen + TC_MAX_BIG * d4);
+  __shared__ float nrm[TC_ROWS], ynm[TC_ROWS];
+  __shared__ int prow_s[TC_ROWS], big_of_start[TC_ROWS];
+  __shared__ uint32_t wmask[4];
+  __shared__ unsigned nmax_bits[TC_MAX_BIG];
+  __shared__ int big_lb[TC_MAX_BIG], big_le[TC_MAX_BIG], nbig;
+  __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    rpf_mbar_init(&bar_tma, 1);
+    rpf_mbar_init(&bar_mma, 1);
+  }
+  if (warp == 0) rpf_tmem_alloc(&tmem_base, 128);
+  rpf_tc_fence_before();
+  __syncthreads();
+  rpf_tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  const uint32_t tlane = tbase + ((uint32_t)(32 * warp) << 16);
+  const float ce = 0x1p-13f + (float)(d + 8) * 0x1p-23f + 3.0f * (float)(d16 + 4) * 0x1p-21f;
+  const float gam = (float)(d + 3) * 0x1p-23f;
+  uint32_t tma_phase = 0, mma_phase = 0;
+  bool ok = true, tma_pending = false, mma_pending = false;
+  const int r = tid;
+
+  for (int64_t tile = tlo + blockIdx.x; tile < thi && ok; tile += gridDim.x) {
+    const int4 tl = tiles[tile];
+    const int t = tl.x, p0 = tl.y, rows = tl.z;
+    const int32_t* pt = perm + (int64_t)t * n + p0;
+    const uint32_t* bt = bits + (int64_t)t * nwords;
+    // (1) rows, leaf starts, staging
+    bool start = false;
+    if (r < rows) {
+      prow_s[r] = pt[r];
+      const int64_t p = (int64_t)p0 + r;
+      start = (bt[p >> 5] >> (p & 31)) & 1u;
+    }
+    const uint32_t bal = __ballot_sync(RPF_FULL, start);
+    if (lane == 0) wmask[warp] = bal;
+    if (tid == 0) {
+      nbig = 0;
+      rpf_mbar_arrive_expect_tx(&bar_tma, (uint32_t)rows * (uint32_t)d * 4u);
+    }
+    if (tid < TC_MAX_BIG) nmax_bits[tid] = 0u;
+    __syncthreads();
+    for (int q = tid; q < rows; q += TC_ROWS)
+      rpf_bulk_g2s(xs + q * dp, X + (int64_t)prow_s[q] * d, (uint32_t)d * 4u, &bar_tma);
+    tma_pending = true;
+    for (int k = d; k < dp; ++k) xs[r * dp + k] = 0.0f;
+    // leaf [lb, le) of row r (tile-relative)
+    int lb = 0, le = rows;
+    if (r < rows) {
+      const int w = r >> 5, b = r & 31;
+      uint32_t x = wmask[w] & (0xffffffffu >> (31 - b));
+      int ww = w;
+      while (x == 0 && ww > 0) x = wmask[--ww];
+      lb = x ? (ww << 5) + 31 - __clz(x) : 0;
+      x = b == 31 ? 0u : (wmask[w] & (0xffffffffu << (b + 1)));
+      ww = w;
+      while (x == 0 && ww < 3) x = wmask[++ww];
+      le = x ? min((ww << 5) + __ffs(x) - 1, rows) : rows;
+    }
+    const int m = le - lb;
+    const bool live = r < rows;
+    const bool big = live && m - 1 > TC_SLOTS;
+    if (big && r == lb) {
+      const int sidx = atomicAdd(&nbig, 1);  // at most 3 leaves of > 33 rows in 128
+      big_of_start[r] = sidx;
+      big_lb[sidx] = lb;
+      big_le[sidx] = le;
+    }
+    {
+      const bool w = rpf_mbar_wait(&bar_tma, tma_phase, err);
+      tma_phase ^= 1u;
+      tma_pending = false;
+      ok = __syncthreads_and(w) != 0;
+      if (!ok) break;
+    }
+    const int nb = nbig;
+    const int bslot = big ? big_of_start[lb] : -1;
+    bool cert_ok = true;  // the leaf is in the tensor path's certified range
+    if (nb > 0) {
+      // (2) FP32 mean of every large leaf
+      for (int j = 0; j < nb; ++j) {
+        const int b0 = big_lb[j], b1 = big_le[j];
+        for (int k = tid; k < d; k += TC_ROWS) {
+          float s = 0.0f;
+          for (int q = b0; q < b1; ++q) s = __fadd_rn(s, xs[q * dp + k]);
+          cen[j * d4 + k] = __fdiv_rn(s, (float)(b1 - b0));
+        }
+      }
+      __syncthreads();
+      // (3) centred split-BF16 tiles, FP32 squared norms, Gram on the tensor core
+      const int npad = (rows + 15) & ~15;
+      const uint32_t idesc = rpf_umma_idesc_bf16(TC_ROWS, npad);
+      float yy = 0.0f;
+      for (int k0 = 0; k0 < d16 && ok; k0 += KC) {
+        if (k0 > 0) {  // the previous chunk's MMAs must be done reading the tiles
+          const bool w = rpf_mbar_wait(&bar_mma, mma_phase, err);
+          mma_phase ^= 1u;
+          mma_pending = false;
+          ok = __syncthreads_and(w) != 0;
+          if (!ok) break;
+        }
+        for (int kk = 0; kk < KC; kk += 8) {
+          uint32_t hp[4], lp[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            float y2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int k = k0 + kk + 2 * u + h;
+              float y = 0.0f;
+              if (bslot >= 0 && k < d) y = __fsub_rn(xs[r * dp + k], cen[bslot * d4 + k]);
+              yy = __fmaf_rn(y, y, yy);
+              y2[h] = y;
+            }
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(y2[0]), h1 = __float2bfloat16_rn(y2[1]);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(__fsub_rn(y2[0], __bfloat162float(h0)));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(__fsub_rn(y2[1], __bfloat162float(h1)));
+            hp[u] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            lp[u] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+          }
+          const int idx = rpf_umma_index(r, kk, 16);  // 8 consecutive k: 16 bytes
+          *reinterpret_cast<uint4*>(Ahi + idx) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+          *reinterpret_cast<uint4*>(Alo + idx) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
+        }
+        rpf_fence_proxy_async();  // BF16 tiles -> visible to the tensor core
+        rpf_tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+          rpf_tc_fence_after();
+          const uint32_t hb = rpf_saddr(Ahi), lbs = rpf_saddr(Alo);
+          for (int s2 = 0; s2 < KC / 16; ++s2) {
+            const uint32_t off = (uint32_t)s2 * 2u * 16u * 128u;
+            const uint64_t dh = rpf_umma_desc(hb + off, 16u * 128u, 128u);
+            const uint64_t dl = rpf_umma_desc(lbs + off, 16u * 128u, 128u);
+            rpf_umma_bf16(tbase, dh, dh, idesc, (k0 > 0 || s2 > 0) ? 1u : 0u);
+            rpf_umma_bf16(tbase, dh, dl, idesc, 1u);
+            rpf_umma_bf16(tbase, dl, dh, idesc, 1u);
+          }
+          rpf_umma_commit(&bar_mma);
+        }
+        mma_pending = true;
+      }
+      if (!ok) break;
+      nrm[r] = yy;
+      const float yup = __fmul_ru(yy, 1.0f + (float)(d + 4) * 0x1p-23f);
+      ynm[r] = __fsqrt_ru(yup);
+      if (bslot >= 0) atomicMax(&nmax_bits[bslot], __float_as_uint(yup));
+      {
+        const bool w = rpf_mbar_wait(&bar_mma, mma_phase, err);
+        mma_phase ^= 1u;
+        mma_pending = false;
+        ok = __syncthreads_and(w) != 0;
+        if (!ok) break;
+      }
+      rpf_tc_fence_after();
+      if (bslot >= 0) {
+        const float Nm = __uint_as_float(nmax_bits[bslot]);
+        cert_ok = Nm >= 0x1p-90f && Nm <= 0x1p120f;
+      }
+    }
+    // (4) per-row candidates: small leaves offer everything; large leaves
+    // offer the certified margin around tau
+    unsigned char* my = slots + r * TC_SLOTS;
+    int ns = 0;
+    float tau2 = 0.0f, eps = 0.0f, eta = 0.0f;
+    const bool tc_row = big && cert_ok;
+    if (__any_sync(RPF_FULL, tc_row)) {
+      int lo = tc_row ? lb : TC_ROWS, hi = tc_row ? le : 0;
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        lo = min(lo, __shfl_xor_sync(RPF_FULL, lo, off));
+        hi = max(hi, __shfl_xor_sync(RPF_FULL, hi, off));
+      }
+      lo &= ~7;
+      const float nr = nrm[r];
+      TopF<KK> th;
+      th.init();
+#pragma unroll 1
+      for (int c0 = lo; c0 < hi; c0 += 8) {
+        float g[8];
+        rpf_tmem_ld8(tlane + (uint32_t)c0, g);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int c = c0 + j;
+          const float D = __fmaf_rn(-2.0f, g[j], __fadd_rn(nr, nrm[c < TC_ROWS ? c : 0]));
+          const bool use = tc_row && c >= lb && c < le && c != r;
+          th.insert(use ? D : INFINITY);
+        }
+      }
+      if (tc_row) {
+        const float tau = th.kth(K);
+        const float Nm = __uint_as_float(nmax_bits[bslot]);
+        eps = __fmul_ru(ce, __fadd_ru(nr, Nm));
+        eta = __fmul_ru(0x1p-23f, __fadd_ru(ynm[r], __fsqrt_ru(Nm)));
+        const float s = __fadd_ru(__fmul_ru(__fsqrt_ru(__fadd_ru(tau, eps)), 1.0f + 4.0f * gam),
+                                  2.0f * eta);
+        tau2 = __fadd_ru(eps, __fmul_ru(s, s));
+      }
+#pragma unroll 1
+      for (int c0 = lo; c0 < hi; c0 += 8) {
+        float g[8];
+        rpf_tmem_ld8(tlane + (uint32_t)c0, g);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int c = c0 + j;
+          const float D = __fmaf_rn(-2.0f, g[j], __fadd_rn(nr, nrm[c < TC_ROWS ? c : 0]));
+          if (tc_row && c >= lb && c < le && c != r && D <= tau2) {
+            if (ns < TC_SLOTS) my[ns] = (unsigned char)c;
+            ++ns;
+          }
+        }
+      }
+    }
+    const bool exact_row = live && (!big || !cert_ok);
+    if (live && !big) {  // small leaf: everything is a candidate
+      for (int c = lb; c < le; ++c)
+        if (c != r) my[ns++] = (unsigned char)c;
+    }
+    // (5) exact re-rank of the candidates
+    Top64<KK> ex;
+    ex.init();
+    bool redo = false;
+    if (live && (!big || tc_row)) {
+      const int nc = min(ns, TC_SLOTS);
+#pragma unroll 1
+      for (int e0 = 0; e0 < nc; e0 += 4) {
+        int cc[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cc[j] = my[e0 + j < nc ? e0 + j : e0];
+        float acc[4];
+        d32x4(xs, dp, d4, r, cc, acc);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (e0 + j < nc) ex.insert(key64(acc[j], prow_s[cc[j]]));
+      }
+      if (tc_row) {
+        // (6) certificate
+        if (ns > TC_SLOTS) {
+          redo = true;
+        } else {
+          const float rk = ex.kth_d32(K);
+          const float base = __fsub_rd(__fsqrt_rd(fmaxf(__fsub_rd(tau2, eps), 0.0f)), eta);
+          const float lower = __fmul_rd(1.0f - gam, base);
+          redo = !(__fsqrt_ru(rk) < lower);
+        }
+      }
+    }
+    if (redo || exact_row) {  // exact scan of the whole leaf
+      ex.init();
+#pragma unroll 1
+      for (int c0 = lb; c0 < le; c0 += 4) {
+        int cc[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cc[j] = min(c0 + j, le - 1);
+        float acc[4];
+        d32x4(xs, dp, d4, r, cc, acc);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (c0 + j < le && c0 + j != r) ex.insert(key64(acc[j], prow_s[c0 + j]));
+      }
+      if (redo) atomicAdd(fallbacks, 1ULL);
+    }
+    if (live) ex.store(K, cand + ((int64_t)(t - t0) * n + prow_s[r]) * K);
+    // (7) the tile's shared memory and TMEM are reused by the next tile
+    rpf_fence_proxy_async();
+    rpf_tc_fence_before();
+    __syncthreads();
+  }
+  // after a timed-out wait: one more bounded wait for work in flight
+  if (tma_pending) rpf_mbar_wait(&bar_tma, tma_phase, nullptr);
+  if (mma_pending) rpf_mbar_wait(&bar_mma, mma_phase, nullptr);
+  rpf_tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    rpf_tc_fence_after();
+    rpf_tmem_dealloc(tbase, 128);
+  }
+}
+
+size_t tc_smem(int d, int dp) {
+  const int d16 = (d + 15) & ~15, KC = std::min(d16, 128), d4 = (d + 3) & ~3;
+  const size_t a_off = (((size_t)TC_ROWS * dp * 4) + 1023) & ~(size_t)1023;
+  const size_t need = a_off + (size_t)2 * TC_ROWS * KC * 2 + (size_t)TC_MAX_BIG * d4 * 4 +
+                      (size_t)TC_ROWS * TC_SLOTS;
+  // at least 60 KB so that at most three CTAs (3 x 128 TMEM columns) share an SM
+  return std::max<size_t>(need, 60 * 1024);
+}
+
+template <int KK>
+int launch_tc(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint2* cand,
+              cudaStream_t s) {
+  if (thi <= tlo) return RPF_OK;
+  const int d = f->d, dp = ((d + 3) & ~3) + 4, d16 = (d + 15) & ~15;
+  const size_t smem = tc_smem(d, dp);
+  RPF_CU(cudaFuncSetAttribute(k_leaf_tc<KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem));
+  int dev = 0, sms = 0, occ = 0;
+  RPF_CU(cudaGetDevice(&dev));
+  RPF_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  RPF_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_leaf_tc<KK>, TC_ROWS, smem));
+  occ = std::max(1, std::min(occ, 3));
+  const int64_t grid = std::min<int64_t>(thi - tlo, (int64_t)sms * occ);
+  RPF_LAUNCH("k_leaf_tc", s, k_leaf_tc<KK><<<(unsigned)grid, TC_ROWS, smem, s>>>(
+      f->pk_tiles, tlo, thi, f->pk_bits, f->pk_nwords, f->perm, f->X, f->n, d, dp, d16, K, t0,
+      cand, f->d_err, f->d_fallback));
+  return RPF_OK;
+}
+
+}  // namespace
+
+bool rpf_tc_supported(const rpf_forest* f, int K) {
+  const int d = f->d, dp = ((d + 3) & ~3) + 4;
+  // dynamic shared memory up to 220 KB (the opt-in limit is 227 KB per CTA)
+  return f->pk_tiles != nullptr && f->prm.leaf_max <= TC_ROWS && K <= 32 && (d % 4) == 0 &&
+         tc_smem(d, dp) <= 220 * 1024;
+}
+
+int rpf_build_packs(rpf_forest* f, cudaStream_t s) {
+  const int T = f->prm.n_trees;
+  const int64_t n = f->n, nl = f->n_leaves;
+  const int64_t nwords = (n + 31) >> 5, nseg = (n + TC_SEG - 1) / TC_SEG;
+  const int64_t G = (int64_t)T * nseg;
+  int2* slot = nullptr;
+  int32_t *cnt = nullptr, *off = nullptr, *blk = nullptr, *tot = nullptr;
+  if (rpf_alloc((void**)&f->pk_bits, 4 * (size_t)(T * nwords), s) ||
+      rpf_alloc((void**)&slot, 8 * (size_t)G * TC_SEG_TILES, s) ||
+      rpf_alloc((void**)&cnt, 4 * (size_t)G, s) || rpf_alloc((void**)&off, 4 * (size_t)G, s) ||
+      rpf_alloc((void**)&blk, 4 * (size_t)((G + 1023) / 1024 + 1), s) ||
+      rpf_alloc((void**)&tot, 4, s)) {
+    rpf_release(slot, s);
+    rpf_release(cnt, s);
+    rpf_release(off, s);
+    rpf_release(blk, s);
+    return RPF_ENOMEM;
+  }
+  f->pk_nwords = nwords;
+  RPF_CU(cudaMemsetAsync(f->pk_bits, 0, 4 * (size_t)(T * nwords), s));
+  RPF_LAUNCH("k_leaf_bits", s, k_leaf_bits<<<nblk(nl, 256), 256, 0, s>>>(
+      nl, f->leaf_tree, f->leaf_begin, nwords, f->pk_bits));
+  RPF_LAUNCH("k_pack_tiles", s, k_pack_tiles<<<nblk(G, 128), 128, 0, s>>>(
+      T, n, nseg, nwords, f->pk_bits, slot, cnt));
+  const int32_t* cn = cnt;
+  int32_t* of = off;
+  rpf_scan(G, [=] __device__(int64_t i) -> int { return min(cn[i], TC_SEG_TILES); },
+           [=] __device__(int64_t i, int p) { of[i] = p; }, blk, tot, s);
+  // per-tree tile offsets (segments are tree-major) and the tile count
+  std::vector<int32_t> h_off(G), h_cnt(G);
+  int32_t h_tot = 0;
+  RPF_CU(cudaMemcpyAsync(h_off.data(), off, 4 * (size_t)G, cudaMemcpyDeviceToHost, s));
+  RPF_CU(cudaMemcpyAsync(h_cnt.data(), cnt, 4 * (size_t)G, cudaMemcpyDeviceToHost, s));
+  RPF_CU(cudaMemcpyAsync(&h_tot, tot, 4, cudaMemcpyDeviceToHost, s));
+  RPF_CU(cudaStreamSynchronize(s));
+  bool over = false;
+  for (int64_t g = 0; g < G; ++g) over |= h_cnt[g] > TC_SEG_TILES;
+  if (over) {  // cannot happen: a segment packs into at most TC_SEG_TILES tiles
+    rpf_release(slot, s);
+    rpf_release(cnt, s);
+    rpf_release(off, s);
+    rpf_release(blk, s);
+    rpf_release(tot, s);
+    return RPF_EINTERNAL;
+  }
+  f->pk_tree_off.assign(T + 1, 0);
+  for (int t = 0; t < T; ++t) f->pk_tree_off[t] = h_off[(int64_t)t * nseg];
+  f->pk_tree_off[T] = h_tot;
+  if (rpf_alloc((void**)&f->pk_tiles, 16 * (size_t)std::max(h_tot, 1), s)) {
+    rpf_release(slot, s);
+    rpf_release(cnt, s);
+    rpf_release(off, s);
+    rpf_release(blk, s);
+    rpf_release(tot, s);
+    return RPF_ENOMEM;
+  }
+  RPF_LAUNCH("k_pack_fill", s, k_pack_fill<<<nblk(G, 128), 128, 0, s>>>(G, nseg, slot, cnt, off,
+                                                                       f->pk_tiles));
+  rpf_release(slot, s);
+  rpf_release(cnt, s);
+  rpf_release(off, s);
+  rpf_release(blk, s);
+  rpf_release(tot, s);
+  RPF_CU(cudaGetLastError());
+  return RPF_OK;
+}
+
+int rpf_leaf_tc(const rpf_forest* f, int t0, int g, int K, uint2* cand, cudaStream_t s) {
+  const int64_t tlo = f->pk_tree_off[t0], thi = f->pk_tree_off[t0 + g];
+  if (K <= 4) return launch_tc<4>(f, tlo, thi, K, t0, cand, s);
+  if (K <= 8) return launch_tc<8>(f, tlo, thi, K, t0, cand, s);
+  if (K <= 12) return launch_tc<12>(f, tlo, thi, K, t0, cand, s);
+  if (K <= 16) return launch_tc<16>(f, tlo, thi, K, t0, cand, s);
+  if (K <= 24) return launch_tc<24>(f, tlo, thi, K, t0, cand, s);
+  return launch_tc<32>(f, tlo, thi, K, t0, cand, s);
+}

@@ -296,17 +296,25 @@ def test_chosen_form_equals_plain_and_oracle(K):
     check_knn(ci.cpu().numpy(), cd.cpu().numpy(), oi, od, X)
 
 
-def test_chosen_form_certificate_fallback_is_exact():
-    # a scaled simplex with tiny noise: all pairwise squared distances agree
-    # to ~2e-6 relative, below what the split-BF16 Gram resolves, so the
-    # shortlist certificate fails and rows are rescanned exactly -- the lists
-    # must still equal the oracle's
+@pytest.mark.parametrize("shape", ["simplex_d256", "cross_polytope_d64"])
+def test_chosen_form_certificate_fallback_is_exact(shape):
+    # near-equidistant points: all pairwise squared distances agree to ~1e-6
+    # relative, below what the split-BF16 Gram resolves, so the certificate
+    # fails and rows are rescanned exactly -- the lists must still equal the
+    # oracle's.  d = 256 runs the Gram in two 128-coordinate chunks.
     rng = np.random.default_rng(0)
-    n = d = 256
-    X = (10.0 * np.eye(n, d) + 1e-5 * rng.standard_normal((n, d))).astype(np.float32)
-    o = oracle.Forest(X, 3, 64, 3, seed=1)
+    if shape == "simplex_d256":
+        n = d = 256
+        X = 10.0 * np.eye(n, d)
+        T, L, ntry = 3, 64, 3
+    else:
+        d = 64
+        X = np.concatenate([10.0 * np.eye(d), -10.0 * np.eye(d)])
+        T, L, ntry = 3, 128, 3
+    X = (X + 1e-5 * rng.standard_normal(X.shape)).astype(np.float32)
+    o = oracle.Forest(X, T, L, ntry, seed=1)
     oi, od = o.all_knn(10)
-    c = gpu_forest(X, 3, 64, 3, seed=1, form=1)
+    c = gpu_forest(X, T, L, ntry, seed=1, form=1)
     ci, cd = c.all_knn(10)
     assert np.array_equal(ci.cpu().numpy(), oi) and np.array_equal(cd.cpu().numpy(), od)
     assert c.counters()["bf16_fallback_rows"] > 0
