@@ -285,17 +285,20 @@ def run_gb300(args, rank, world, local_rank):
         torch.distributed.barrier()
     clocks = Clocks(local_rank)
     clocks.start()
-    forest.Trace.read()
-    forest.Trace.enable(True)
     l0 = forest.Trace.launch_count()
-    times, b_ms, a_ms = timed(chosen, args.steps, trace=True)
+    times, b_ms, a_ms = timed(chosen, args.steps)
     l1 = forest.Trace.launch_count()
-    forest.Trace.enable(False)
-    trace = forest.Trace.read()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
+    # per-kernel CUDA-event times: the same steps again, traced (event pairs
+    # around every launch), outside the timed region above
+    forest.Trace.read()
+    forest.Trace.enable(True)
+    timed(chosen, args.steps)
+    forest.Trace.enable(False)
+    trace = forest.Trace.read()
     total_ms = sum(times)
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -305,9 +308,10 @@ def run_gb300(args, rank, world, local_rank):
     value = world * n / (ms_step * 1e-3)
 
     # plain FP32 form on the same workload
+    p_times, p_b, p_a = timed(plain, args.steps)
     forest.Trace.read()
     forest.Trace.enable(True)
-    p_times, p_b, p_a = timed(plain, args.steps)
+    timed(plain, args.steps)
     forest.Trace.enable(False)
     trace_p = forest.Trace.read()
     p_ms = sum(p_times) / len(p_times)

@@ -542,11 +542,18 @@ int launch_tc(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint
   const size_t smem = tc_smem(d, dp);
   RPF_CU(cudaFuncSetAttribute(k_leaf_tc<KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem));
-  int dev = 0, sms = 0, occ = 0;
+  int dev = 0, sms = 0, smem_sm = 0;
   RPF_CU(cudaGetDevice(&dev));
   RPF_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  RPF_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_leaf_tc<KK>, TC_ROWS, smem));
-  occ = std::max(1, std::min(occ, 3));
+  RPF_CU(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  RPF_CU(cudaFuncSetAttribute(k_leaf_tc<KK>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              100));
+  cudaFuncAttributes fa;
+  RPF_CU(cudaFuncGetAttributes(&fa, k_leaf_tc<KK>));
+  // CTAs per SM that shared memory allows (1 KB per CTA is reserved by the
+  // system); at most three, so that their TMEM (3 x 128 columns) fits
+  const size_t per_cta = smem + fa.sharedSizeBytes + 1024;
+  const int occ = std::max(1, std::min(3, (int)((size_t)smem_sm / per_cta)));
   const int64_t grid = std::min<int64_t>(thi - tlo, (int64_t)sms * occ);
   RPF_LAUNCH("k_leaf_tc", s, k_leaf_tc<KK><<<(unsigned)grid, TC_ROWS, smem, s>>>(
       f->pk_tiles, tlo, thi, f->pk_bits, f->pk_nwords, f->perm, f->X, f->n, d, dp, d16, K, t0,
