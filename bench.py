@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="aniso20_d64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the serving measurement (resident 2M-point forest)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--profile-step", action="store_true",
                     help="one warm-up step and one step of the chosen form, nothing else "
@@ -438,9 +440,61 @@ def run_gb300(args, rank, world, local_rank):
                                 sorted(trace.items(), key=lambda kv: -kv[1]["ms"])},
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_serve:
+        line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(X, w, os.cpu_count() or 1)
     return line
+
+
+def run_serving(args, dev, n_requests=300):
+    """Serving on the resident-forest workload: saturation throughput (all
+    requests at once), then Poisson arrivals at 0.5 / 0.8 / 0.95 of it, for
+    each K; p50 / p99 from arrival to results ready on the host."""
+    import torch
+    from paper_1812_11689_gb300 import forest, serve, synth
+    w = synth.WORKLOADS["mix50_d96"]
+    X = torch.from_numpy(synth.make("mix50_d96", seed=args.seed)).to(dev)
+    t0 = time.perf_counter()
+    f = forest.Forest(X, n_trees=w.n_trees, leaf_max=w.leaf_max, n_try=w.n_try, seed=args.seed,
+                      form=forest.FORM_CHOSEN)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    sizes = synth.request_sizes(n_requests, seed=args.seed, max_size=w.extra["max_request"])
+    out = {"workload": "mix50_d96", "n": w.n, "d": w.d, "n_trees": w.n_trees,
+           "leaf_max": w.leaf_max, "requests_per_run": n_requests,
+           "request_sizes": "floor(exp(U(0, ln 4097))) clamped to [1, 4096]",
+           "build_s": round(build_s, 3), "slots": 4, "max_batch": 8192, "runs": {}}
+
+    def make_reqs(K, stream0):
+        return [serve.Request(i, synth.queries("mix50_d96", int(m), seed=args.seed,
+                                               stream=stream0 + i), K, 0.0)
+                for i, m in enumerate(sizes)]
+
+    for K in w.extra["k_set"]:
+        serve.Server(f, slots=4).run(make_reqs(K, 1000)[:20])  # warm-up
+        srv = serve.Server(f, slots=4, max_batch=8192)
+        sat = serve.latency_summary(srv.run(make_reqs(K, 2000)))
+        runs = {"saturation": sat}
+        mean_m = float(np.mean(sizes))
+        for load in (0.5, 0.8, 0.95):
+            rate = load * sat["queries_per_s"] / mean_m
+            arr = synth.poisson_arrivals(n_requests, rate_per_s=rate, seed=args.seed + 1)
+            srv = serve.Server(f, slots=4, max_batch=8192)
+            res = serve.latency_summary(srv.run(make_reqs(K, 3000), arr))
+            res["offered_requests_per_s"] = round(rate, 1)
+            res["batches"] = srv.n_batches
+            runs["load_%.2f" % load] = res
+        # accuracy of the served answers on a sample, against exact brute force
+        Qs = torch.from_numpy(synth.queries("mix50_d96", 500, seed=args.seed, stream=9999)).to(dev)
+        qi, _ = f.query(Qs, K)
+        bi, _ = forest.brute_knn(X, Qs, K)
+        qi, bi = qi.cpu().numpy(), bi.cpu().numpy()
+        runs["missing_rate_sample_500"] = round(
+            sum(len(set(bi[r]) - set(qi[r])) for r in range(len(bi))) / float(bi.size), 5)
+        out["runs"]["K=%d" % K] = runs
+    f.close()
+    return out
 
 
 def run_profile_step(args):

@@ -10,8 +10,12 @@
 //   k_merge        per point, merge the per-tree lists of a group of trees
 //                  into the running top-K (duplicates have identical keys
 //                  because d32 is symmetric and deterministic)
-//   k_route        drop each query through each tree (FP64 r* . q < c)
-//   k_qscan        per (query, tree): top-K of the leaf the query fell into
+//   k_route_w      drop each query through each tree (FP64 r* . q < c,
+//                  certified from FP32 and recomputed in FP64 when undecided)
+//   k_qscan_cta    per (query, tree): top-K of the leaf the query fell into
+//                  (leaf rows TMA-staged, bitonic sort of 64-bit keys);
+//                  k_qscan is the one-thread-per-pair form for leaves > 128
+// The chosen form of the all-kNN leaf tiles is in rpf_leaf_tc.cu.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -307,30 +311,6 @@ __global__ void k_merge(int64_t n, int K, int G, const uint2* cand, uint2* run, 
   }
 }
 
-// Drop query q through tree t: at a split node go left iff r* . q < c (FP64
-// canonical fma chain), at a rank-split node go left.  Output: leaf node id.
-__global__ void k_route(const float* Q, int64_t m, int d, int T, const int32_t* node_left,
-                        const int32_t* node_right, const int32_t* node_flag, const double* node_c,
-                        const double* node_dir, int32_t* qleaf) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= m * T) return;
-  const int64_t q = g / T;
-  const int t = (int)(g % T);
-  const float* x = Q + q * d;
-  int node = t;
-  while (node_left[node] >= 0) {
-    if (node_flag[node] & 1) {  // rank split: every query goes left
-      node = node_left[node];
-      continue;
-    }
-    const double* r = node_dir + (int64_t)node * d;
-    double p = 0.0;
-    for (int k = 0; k < d; ++k) p = __fma_rn((double)__ldg(x + k), r[k], p);
-    node = (p < node_c[node]) ? node_left[node] : node_right[node];
-  }
-  qleaf[g] = node;
-}
-
 template <int KMAX>
 __global__ void k_qscan(const float* Q, int64_t m, int d, int T, int K, const int32_t* qleaf,
                         const int32_t* node_tree, const int32_t* node_begin,
@@ -351,6 +331,234 @@ __global__ void k_qscan(const float* Q, int64_t m, int d, int T, int K, const in
     tk.offer(rpf_d32(x, X + (int64_t)j * d, d), j);
   }
   tk.store(K, cand + ((int64_t)t * m + q) * K);
+}
+
+// Routing, one warp per (query q, tree t) (Sec. 2, Algorithm 3).  At a split
+// node the decision is r* . q < c with the canonical FP64 chain p64 (fold of
+// fma((double)q_k, r_k, p) over k in order).  The directions are FP32 values
+// widened to double, so the warp first forms s = r* . q in FP32 (lane-strided
+// fmaf, then a butterfly) with A = sum |q_k r_k|; p64 lies within
+//   e = (ceil(d / 32) + 7) 2^-24 A_up
+// of s (FP32 error of s: (ceil(d/32) + 5) u A; FP64 error of p64: d 2^-53 A;
+// A_up bounds A despite its own rounding).  Only when c falls inside
+// [s - e, s + e] does lane 0 evaluate p64 itself.  Rank-split nodes send
+// every query left.
+__global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, int64_t m, int d,
+                                                 int T, const int32_t* __restrict__ node_left,
+                                                 const int32_t* __restrict__ node_right,
+                                                 const int32_t* __restrict__ node_flag,
+                                                 const double* __restrict__ node_c,
+                                                 const double* __restrict__ node_dir,
+                                                 const float* __restrict__ node_dir32,
+                                                 int32_t* qleaf) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= m * T) return;  // whole warp
+  const int64_t q = g / T;
+  const int t = (int)(g % T);
+  const float* x = Q + q * d;
+  const int per = (d + 31) >> 5;
+  const float kerr = (float)(per + 7) * 0x1p-24f;
+  const float kA = 1.0f + (float)(per + 6) * 0x1p-23f;
+  int node = t;
+  int left = node_left[node];
+  while (left >= 0) {
+    // every field of the node is requested at once (one round trip per level)
+    const int flag = node_flag[node];
+    const int right = node_right[node];
+    const double c = node_c[node];
+    const float* r32 = node_dir32 + (int64_t)node * d;
+    float sacc = 0.0f, aacc = 0.0f;
+    for (int k = lane; k < d; k += 32) {
+      const float xv = __ldg(x + k), rv = __ldg(r32 + k);
+      sacc = __fmaf_rn(xv, rv, sacc);
+      aacc = __fmaf_rn(fabsf(xv), fabsf(rv), aacc);
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      sacc = __fadd_rn(sacc, __shfl_xor_sync(RPF_FULL, sacc, off));
+      aacc = __fadd_rn(aacc, __shfl_xor_sync(RPF_FULL, aacc, off));
+    }
+    int go_left;
+    if (flag & 1) {  // rank split: every query goes left
+      go_left = 1;
+    } else {
+      const double e = (double)__fmul_ru(kerr, __fmul_ru(aacc, kA));
+      const double lo = __dsub_rd((double)sacc, e), hi = __dadd_ru((double)sacc, e);
+      if (hi < c) {
+        go_left = 1;
+      } else if (lo >= c) {
+        go_left = 0;
+      } else {  // undecided by the bound: the canonical FP64 chain
+        int v = 0;
+        if (lane == 0) {
+          const double* r = node_dir + (int64_t)node * d;
+          double p = 0.0;
+          for (int k = 0; k < d; ++k) p = __fma_rn((double)__ldg(x + k), r[k], p);
+          v = p < c;
+        }
+        go_left = __shfl_sync(RPF_FULL, v, 0);
+      }
+    }
+    node = go_left ? left : right;
+    left = node_left[node];
+  }
+  if (lane == 0) qleaf[g] = node;
+}
+
+// Leaf scan for queries, one CTA of QS_T threads per (query q, tree t): the
+// leaf's rows are staged in shared memory by bulk copies, thread j computes
+// the canonical d32 of q and leaf point j, and a bitonic sort of the 64-bit
+// keys (d32 bits << 32 | index, ordered exactly like (d32, index)) gives the
+// leaf's top-K.  Leaves of at most QS_T points.
+#define QS_T 128
+__global__ void __launch_bounds__(QS_T) k_qscan_cta(const float* __restrict__ Q, int64_t m, int d,
+                                                    int dp, int T, int K, const int32_t* qleaf,
+                                                    const int32_t* node_tree,
+                                                    const int32_t* node_begin,
+                                                    const int32_t* node_len,
+                                                    const int32_t* __restrict__ perm,
+                                                    const float* __restrict__ X, int64_t n,
+                                                    uint2* cand, int* err) {
+  extern __shared__ __align__(16) float qs_rows[];  // QS_T x dp, then the query (dp)
+  __shared__ unsigned long long keys[QS_T];
+  __shared__ int pid[QS_T];
+  __shared__ __align__(8) uint64_t bar;
+  const int64_t g = blockIdx.x;
+  const int64_t q = g / T;
+  const int t = (int)(g % T);
+  const int tid = threadIdx.x;
+  const int leaf = qleaf[g];
+  const int len = node_len[leaf];
+  const int32_t* mem = perm + (int64_t)node_tree[leaf] * n + node_begin[leaf];
+  float* qv = qs_rows + QS_T * dp;
+  if (tid < len) pid[tid] = mem[tid];
+  for (int k = tid; k < dp; k += QS_T) qv[k] = k < d ? Q[q * d + k] : 0.0f;
+  if (tid == 0) {
+    rpf_mbar_init(&bar, 1);
+    rpf_mbar_arrive_expect_tx(&bar, (uint32_t)len * (uint32_t)d * 4u);
+  }
+  __syncthreads();
+  if (tid < len) {
+    rpf_bulk_g2s(qs_rows + tid * dp, X + (int64_t)pid[tid] * d, (uint32_t)d * 4u, &bar);
+    for (int k = d; k < dp; ++k) qs_rows[tid * dp + k] = 0.0f;
+  }
+  const bool ok = __syncthreads_and(rpf_mbar_wait(&bar, 0, err)) != 0;
+  if (!ok) {  // one more bounded wait for copies in flight, then give up
+    rpf_mbar_wait(&bar, 0, nullptr);
+    return;
+  }
+  unsigned long long key = ~0ull;
+  if (tid < len) {
+    const float* y = qs_rows + tid * dp;
+    float acc = 0.0f;
+    for (int k = 0; k < d; k += 4) {
+      const float4 a = *reinterpret_cast<const float4*>(qv + k);
+      const float4 b = *reinterpret_cast<const float4*>(y + k);
+      float e;
+      e = __fsub_rn(a.x, b.x); acc = __fmaf_rn(e, e, acc);
+      e = __fsub_rn(a.y, b.y); acc = __fmaf_rn(e, e, acc);
+      e = __fsub_rn(a.z, b.z); acc = __fmaf_rn(e, e, acc);
+      e = __fsub_rn(a.w, b.w); acc = __fmaf_rn(e, e, acc);
+    }
+    key = ((unsigned long long)__float_as_uint(acc) << 32) | (unsigned)pid[tid];
+  }
+  keys[tid] = key;
+  __syncthreads();
+  for (int kk = 2; kk <= QS_T; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      const int p = tid ^ j;
+      if (p > tid) {
+        const unsigned long long a = keys[tid], b = keys[p];
+        const bool up = (tid & kk) == 0;
+        if ((a > b) == up) {
+          keys[tid] = b;
+          keys[p] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (tid < K) {
+    const unsigned long long v = keys[tid];
+    cand[((int64_t)t * m + q) * K + tid] =
+        v == ~0ull ? make_uint2(0x7f800000u, 0xffffffffu)
+                   : make_uint2((unsigned)(v >> 32), (unsigned)v);
+  }
+}
+
+// Final merge for a batch of queries, one CTA per query: its T per-tree
+// lists (T K entries) are sorted together as 64-bit keys (bitonic sort in
+// shared memory), duplicates -- the same point found in several trees, with
+// identical keys -- are dropped, and the first K distinct keys are the answer
+// (the same list the running merge k_merge produces).  T K <= QM_MAX.
+#define QM_T 256
+#define QM_MAX 4096
+__global__ void __launch_bounds__(QM_T) k_qmerge_cta(int64_t m, int K, int T, int N,
+                                                     const uint2* __restrict__ cand,
+                                                     int32_t* idx, float* dist) {
+  extern __shared__ unsigned long long mk[];  // N keys, N a power of two
+  __shared__ int wsum[QM_T / 32];
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int TK = T * K;
+  for (int i = tid; i < N; i += QM_T) {
+    unsigned long long key = ~0ull;
+    if (i < TK) {
+      const int t = i / K, j = i - t * K;
+      const uint2 e = cand[((int64_t)t * m + q) * K + j];
+      if (e.y != 0xffffffffu) key = ((unsigned long long)e.x << 32) | e.y;
+    }
+    mk[i] = key;
+  }
+  __syncthreads();
+  for (int kk = 2; kk <= N; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < N; i += QM_T) {
+        const int p = i ^ j;
+        if (p > i) {
+          const unsigned long long a = mk[i], b = mk[p];
+          if ((a > b) == ((i & kk) == 0)) {
+            mk[i] = b;
+            mk[p] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // rank of every distinct key: each thread takes a contiguous segment
+  const int S = (N + QM_T - 1) / QM_T;
+  const int s0 = min(tid * S, N), s1 = min(s0 + S, N);
+  int cnt = 0;
+  for (int i = s0; i < s1; ++i)
+    cnt += mk[i] != ~0ull && (i == 0 || mk[i] != mk[i - 1]);
+  int x = cnt;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(RPF_FULL, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  int base = 0, total = 0;
+  for (int w = 0; w < QM_T / 32; ++w) {
+    if (w < warp) base += wsum[w];
+    total += wsum[w];
+  }
+  int r = base + x - cnt;
+  for (int i = s0; i < s1 && r < K; ++i) {
+    const unsigned long long v = mk[i];
+    if (v != ~0ull && (i == 0 || v != mk[i - 1])) {
+      idx[q * K + r] = (int)(unsigned)v;
+      dist[q * K + r] = __fsqrt_rn(__uint_as_float((unsigned)(v >> 32)));
+      ++r;
+    }
+  }
+  for (int rr = total + tid; rr < K; rr += QM_T) {
+    idx[q * K + rr] = -1;
+    dist[q * K + rr] = INFINITY;
+  }
 }
 
 // Exact kNN by brute force (ground truth for the Sec. 5.1 metrics): one
@@ -555,10 +763,27 @@ int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t
   if (ws_bytes < align256((size_t)m * T * 4) + align256((size_t)T * m * K * 8)) return RPF_EINVAL;
   int32_t* qleaf = (int32_t*)ws;
   uint2* cand = (uint2*)((char*)ws + align256((size_t)m * T * 4));
-  RPF_LAUNCH("k_route", s, k_route<<<nblk(m * T, 128), 128, 0, s>>>(Q, m, f->d, T, f->node_left, f->node_right,
-                                           f->node_flag, f->node_c, f->node_dir, qleaf));
-  RPF_KDISPATCH(K, launch_qscan, f, Q, m, K, qleaf, cand, s);
-  RPF_KDISPATCH(K, launch_merge, m, K, T, cand, nullptr, true, true, idx, dist, s);
+  RPF_LAUNCH("k_route_w", s, k_route_w<<<nblk(m * T * 32, 256), 256, 0, s>>>(
+      Q, m, f->d, T, f->node_left, f->node_right, f->node_flag, f->node_c, f->node_dir,
+      f->node_dir32, qleaf));
+  const int dp = ((f->d + 3) & ~3) + 4;
+  const size_t qsm = (size_t)(QS_T + 1) * dp * 4;
+  if (f->prm.leaf_max <= QS_T && (f->d % 4) == 0 && qsm <= 200 * 1024) {
+    cudaFuncSetAttribute(k_qscan_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
+    RPF_LAUNCH("k_qscan_cta", s, k_qscan_cta<<<(unsigned)(m * T), QS_T, qsm, s>>>(
+        Q, m, f->d, dp, T, K, qleaf, f->node_tree, f->node_begin, f->node_len, f->perm, f->X,
+        f->n, cand, f->d_err));
+  } else {
+    RPF_KDISPATCH(K, launch_qscan, f, Q, m, K, qleaf, cand, s);
+  }
+  if ((int64_t)T * K <= QM_MAX) {
+    int N = 1;
+    while (N < T * K) N <<= 1;
+    RPF_LAUNCH("k_qmerge_cta", s, k_qmerge_cta<<<(unsigned)m, QM_T, (size_t)N * 8, s>>>(
+        m, K, T, N, cand, idx, dist));
+  } else {
+    RPF_KDISPATCH(K, launch_merge, m, K, T, cand, nullptr, true, true, idx, dist, s);
+  }
   RPF_CU(cudaGetLastError());
   return RPF_OK;
 }
