@@ -24,6 +24,9 @@ __device__ __forceinline__ void rpf_proj4(const float* __restrict__ X, int d, co
     for (int q = 0; q < TG; ++q) acc[p][q] = 0.0f;
   }
   if ((d & 3) == 0) {
+    // unrolled so that the next coordinates' row loads are issued while the
+    // current ones are multiplied (each chain still runs over k in order)
+#pragma unroll 2
     for (int k = 0; k < d; k += 4) {
       const float4 o4 = *reinterpret_cast<const float4*>(so + k);
       float4 r4[TG];
