@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="aniso20_d64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the ensemble sweep (128 nested trees, heavy-tailed data)")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the serving measurement (resident 2M-point forest)")
     ap.add_argument("--seed", type=int, default=0)
@@ -146,6 +148,19 @@ class Clocks:
 SUBTREE_MAX = 4096          # nodes of at most this many points grow CTA-locally
 FP32_LANES = 152 * 128      # FP32 lanes of a GB300 (152 SMs x 128)
 SM_MAX_GHZ = 2.07
+
+
+def discrepancy_full(found_d, true_d):
+    """kNN-distance discrepancy of Sec. 5.1 at k = K: relative gap of the mean
+    K-th distance found to the mean true K-th distance, over the points whose
+    found and true lists are both full; also returns how many were not."""
+    fk = found_d[:, -1].astype(np.float64)
+    tk = true_d[:, -1].astype(np.float64)
+    ok = np.isfinite(fk) & np.isfinite(tk)
+    if not ok.any():
+        return None, int((~ok).sum())
+    mt = tk[ok].mean()
+    return round(float((fk[ok].mean() - mt) / mt), 6), int((~ok).sum())
 
 
 def work_model(fo, w, n):
@@ -349,8 +364,7 @@ def run_gb300(args, rank, world, local_rank):
         return sum(len(set(bi[r]) - set(found[r])) for r in range(len(bi))) / float(bi.size)
 
     def discrepancy(found_d):
-        mt = bd[:, -1].astype(np.float64).mean()
-        return float((found_d[:, -1].astype(np.float64).mean() - mt) / mt)
+        return discrepancy_full(found_d, bd)[0]
 
     miss, disc = missing(ci_s), discrepancy(cd_s)
     # The first T' trees of a forest are the T'-tree forest (node keys and
@@ -440,6 +454,8 @@ def run_gb300(args, rank, world, local_rank):
                                 sorted(trace.items(), key=lambda kv: -kv[1]["ms"])},
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_sweep:
+        line["ensemble_sweep"] = run_sweep(args, dev)
     if rank == 0 and world == 1 and not args.no_serve:
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -494,6 +510,66 @@ def run_serving(args, dev, n_requests=300):
             sum(len(set(bi[r]) - set(qi[r])) for r in range(len(bi))) / float(bi.size), 5)
         out["runs"]["K=%d" % K] = runs
     f.close()
+    return out
+
+
+def run_sweep(args, dev, rows=2000):
+    """Ensemble sweep (Sec. 5.2 accuracy experiments on synthetic data): one
+    forest of 128 trees over the heavy-tailed workload answers all-kNN over
+    its first T trees for every T of the sweep (nested ensembles), for
+    nTry = 1 and 5, both forms; missing rate and kNN-distance discrepancy on
+    a sample of points against exact brute force."""
+    import torch
+    from paper_1812_11689_gb300 import forest, synth
+    w = synth.WORKLOADS["student3_d32"]
+    Xh = synth.make("student3_d32", seed=args.seed)
+    X = torch.from_numpy(Xh).to(dev)
+    n = w.n
+    r = torch.from_numpy(np.sort(np.random.default_rng(2).choice(n, rows, replace=False))
+                         .astype(np.int32)).to(dev)
+    bi, bd = forest.brute_knn(X, X[r.long()].contiguous(), w.k, self_idx=r)
+    bi, bd = bi.cpu().numpy(), bd.cpu().numpy()
+    out = {"workload": "student3_d32", "n": n, "d": w.d, "leaf_max": w.leaf_max, "k": w.k,
+           "sample": "%d points vs exact brute force" % rows, "n_try": {}}
+    for ntry in (1, 5):
+        f = {}
+        for form in (forest.FORM_PLAIN, forest.FORM_CHOSEN):
+            t0 = time.perf_counter()
+            f[form] = forest.Forest(X, n_trees=max(w.extra["t_sweep"]), leaf_max=w.leaf_max,
+                                    n_try=ntry, seed=args.seed, form=form)
+            torch.cuda.synchronize()
+            build_s = time.perf_counter() - t0
+        rows_out, prev = [], None
+        monotone = True
+        for T in w.extra["t_sweep"]:
+            res = {"n_trees": T}
+            lists = {}
+            for form, nm in ((forest.FORM_PLAIN, "plain"), (forest.FORM_CHOSEN, "chosen")):
+                f[form].all_knn(w.k, n_trees=T)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                i, d = f[form].all_knn(w.k, n_trees=T)
+                e1.record()
+                torch.cuda.synchronize()
+                res[nm + "_all_knn_ms"] = round(e0.elapsed_time(e1), 3)
+                lists[nm] = (i, d)
+            res["chosen_equals_plain"] = bool(torch.equal(lists["plain"][0], lists["chosen"][0])
+                                              and torch.equal(lists["plain"][1], lists["chosen"][1]))
+            ci = lists["chosen"][0][r.long()].cpu().numpy()
+            cd = lists["chosen"][1][r.long()].cpu().numpy()
+            miss = np.array([len(set(bi[q]) - set(ci[q])) for q in range(rows)])
+            if prev is not None and np.any(miss > prev):
+                monotone = False
+            prev = miss
+            res["missing_rate"] = round(float(miss.sum()) / bi.size, 5)
+            res["knn_distance_discrepancy"], res["points_with_short_lists"] = \
+                discrepancy_full(cd, bd)
+            rows_out.append(res)
+        out["n_try"][str(ntry)] = {"build_s_128_trees_chosen": round(build_s, 3), "by_T": rows_out,
+                                   "missing_per_point_non_increasing_in_T": monotone}
+        for v in f.values():
+            v.close()
     return out
 
 

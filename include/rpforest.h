@@ -95,9 +95,20 @@ int rpf_all_knn(rpf_forest* f, int32_t K, int32_t* idx, float* dist, void* works
                 size_t ws_bytes, void* stream);
 
 /*
+ * rpf_all_knn_trees -- rpf_all_knn over the first n_trees trees only.  Every
+ * random draw is keyed by the tree index, so the first T' trees of a forest
+ * are exactly the forest that rpf_build grows with T' trees (a nested
+ * ensemble): one forest answers the whole sweep over T of the accuracy
+ * experiments (Sec. 5.2).  1 <= n_trees <= the forest's trees; the other
+ * arguments, the outputs and the errors are those of rpf_all_knn.
+ */
+int rpf_all_knn_trees(rpf_forest* f, int32_t n_trees, int32_t K, int32_t* idx, float* dist,
+                      void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * rpf_query -- K nearest neighbours of m new points Q among the data, found
- * in the union of the leaves each query falls into (Algorithm 3: "let q fall
- * through tree t_i").  Nothing is excluded.  Safe to call concurrently on one
+ * in the union of the leaves each query falls into (Algorithm 3: each query is
+ * dropped through every tree).  Nothing is excluded.  Safe to call concurrently on one
  * forest from several host threads with different streams and workspaces.
  *   Q        : m x d queries (device or host); m >= 0 (m = 0 is a no-op).
  *   K        : 1 <= K <= 128.

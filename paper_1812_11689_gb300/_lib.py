@@ -52,6 +52,8 @@ def lib() -> ctypes.CDLL:
             L.rpf_build.restype = ctypes.c_int
             L.rpf_all_knn.argtypes = [_vp, _i32, _vp, _vp, _vp, _sz, _vp]
             L.rpf_all_knn.restype = ctypes.c_int
+            L.rpf_all_knn_trees.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp, _sz, _vp]
+            L.rpf_all_knn_trees.restype = ctypes.c_int
             L.rpf_query.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _sz, _vp]
             L.rpf_query.restype = ctypes.c_int
             L.rpf_query_static.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp]
@@ -97,7 +99,8 @@ def check(code: int, what: str) -> None:
 
 
 # names of every symbol include/rpforest.h declares (checked by the CPU tests)
-EXPORTED = ("rpf_default_params", "rpf_build", "rpf_all_knn", "rpf_query", "rpf_query_static",
+EXPORTED = ("rpf_default_params", "rpf_build", "rpf_all_knn", "rpf_all_knn_trees", "rpf_query",
+            "rpf_query_static",
             "rpf_workspace_bytes", "rpf_free", "rpf_error_string", "rpf_forest_info",
             "rpf_forest_perm", "rpf_forest_leaves", "rpf_forest_nodes", "rpf_directions",
             "rpf_brute_knn", "rpf_trace_enable", "rpf_launch_count", "rpf_trace_read",

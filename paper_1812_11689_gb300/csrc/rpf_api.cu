@@ -163,7 +163,14 @@ size_t rpf_workspace_bytes(const rpf_forest* f, int64_t m, int32_t K, int32_t fo
 
 int rpf_all_knn(rpf_forest* f, int32_t K, int32_t* idx, float* dist, void* workspace,
                 size_t ws_bytes, void* stream) {
+  if (!f) return RPF_EINVAL;
+  return rpf_all_knn_trees(f, f->prm.n_trees, K, idx, dist, workspace, ws_bytes, stream);
+}
+
+int rpf_all_knn_trees(rpf_forest* f, int32_t n_trees, int32_t K, int32_t* idx, float* dist,
+                      void* workspace, size_t ws_bytes, void* stream) {
   if (!f || !idx || !dist || K < 1 || K > RPF_MAX_K) return RPF_EINVAL;
+  if (n_trees < 1 || n_trees > f->prm.n_trees) return RPF_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = f->n;
   const bool dev_out = rpf_is_device_ptr(idx) && rpf_is_device_ptr(dist);
@@ -192,7 +199,7 @@ int rpf_all_knn(rpf_forest* f, int32_t K, int32_t* idx, float* dist, void* works
     }
     own_ws = true;
   }
-  int rc = rpf_all_knn_dev(f, K, di, dd, ws, wsb, s);
+  int rc = rpf_all_knn_dev(f, n_trees, K, di, dd, ws, wsb, s);
   if (own_ws) cudaFreeAsync(ws, s);
   if (rc) return rc;
   if (!dev_out) {

@@ -712,10 +712,9 @@ size_t rpf_all_knn_ws(const rpf_forest* f, int K) {
   return align256((size_t)T * n * K * 8) + align256((size_t)n * K * 8);
 }
 
-int rpf_all_knn_dev(rpf_forest* f, int K, int32_t* idx, float* dist, void* ws, size_t ws_bytes,
-                    cudaStream_t s) {
+int rpf_all_knn_dev(rpf_forest* f, int T, int K, int32_t* idx, float* dist, void* ws,
+                    size_t ws_bytes, cudaStream_t s) {
   const int64_t n = f->n;
-  const int T = f->prm.n_trees;
   const size_t run_b = align256((size_t)n * K * 8);
   const size_t per_tree = (size_t)n * K * 8;
   if (ws_bytes < run_b + align256(per_tree)) return RPF_EINVAL;

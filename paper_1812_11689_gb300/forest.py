@@ -81,7 +81,8 @@ class Forest:
     def workspace_bytes(self, K: int, m: int = 0, all_knn: bool = True) -> int:
         return int(_lib.lib().rpf_workspace_bytes(self._h, m, K, 1 if all_knn else 0))
 
-    def all_knn(self, K: int, idx=None, dist=None, workspace=None, stream=None):
+    def all_knn(self, K: int, idx=None, dist=None, workspace=None, stream=None, n_trees=None):
+        """rpf_all_knn; with n_trees, rpf_all_knn_trees over the first n_trees trees."""
         dev = torch.device("cuda", torch.cuda.current_device())
         if idx is None:
             idx = torch.empty((self.n, K), dtype=torch.int32, device=dev)
@@ -89,8 +90,13 @@ class Forest:
             dist = torch.empty((self.n, K), dtype=torch.float32, device=dev)
         ws, wsb = (0, 0) if workspace is None else (_ptr(workspace), workspace.numel()
                                                      * workspace.element_size())
-        check(_lib.lib().rpf_all_knn(self._h, K, _ptr(idx), _ptr(dist), ws or None, wsb,
-                                     _stream_handle(stream)), "rpf_all_knn")
+        if n_trees is None:
+            check(_lib.lib().rpf_all_knn(self._h, K, _ptr(idx), _ptr(dist), ws or None, wsb,
+                                         _stream_handle(stream)), "rpf_all_knn")
+        else:
+            check(_lib.lib().rpf_all_knn_trees(self._h, int(n_trees), K, _ptr(idx), _ptr(dist),
+                                               ws or None, wsb, _stream_handle(stream)),
+                  "rpf_all_knn_trees")
         return idx, dist
 
     def query(self, Q, K: int, idx=None, dist=None, workspace=None, stream=None):

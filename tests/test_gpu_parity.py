@@ -318,3 +318,16 @@ def test_chosen_form_certificate_fallback_is_exact(shape):
     ci, cd = c.all_knn(10)
     assert np.array_equal(ci.cpu().numpy(), oi) and np.array_equal(cd.cpu().numpy(), od)
     assert c.counters()["bf16_fallback_rows"] > 0
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_all_knn_over_tree_prefixes_equals_the_smaller_forests(form):
+    # nested ensembles: the first T' trees of a forest are the T'-tree forest
+    X = synth.make("student3_d32", n=15000)
+    g = gpu_forest(X, 8, 64, 5, seed=6, form=form)
+    for Tp in (1, 3, 8):
+        gi, gd = g.all_knn(10, n_trees=Tp)
+        oi, od = oracle.Forest(X, Tp, 64, 5, seed=6).all_knn(10)
+        check_knn(gi.cpu().numpy(), gd.cpu().numpy(), oi, od, X)
+    with pytest.raises(RuntimeError):
+        g.all_knn(10, n_trees=9)
