@@ -150,6 +150,20 @@ FP32_LANES = 152 * 128      # FP32 lanes of a GB300 (152 SMs x 128)
 SM_MAX_GHZ = 2.07
 
 
+def replica_value(total_ms, n, steps, world, device):
+    """Whole-job throughput of `world` independent replicas (weak scaling):
+    each rank answered n points per step; the job's time is the slowest
+    rank's (max over ranks).  Returns (ms per step, points per second)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / steps
+    return ms_step, world * n / (ms_step * 1e-3)
+
+
 def discrepancy_full(found_d, true_d):
     """kNN-distance discrepancy of Sec. 5.1 at k = K: relative gap of the mean
     K-th distance found to the mean true K-th distance, over the points whose
@@ -316,13 +330,7 @@ def run_gb300(args, rank, world, local_rank):
     timed(chosen, args.steps)
     forest.Trace.enable(False)
     trace = forest.Trace.read()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_step = total_ms / args.steps
-    value = world * n / (ms_step * 1e-3)
+    ms_step, value = replica_value(sum(times), n, args.steps, world, dev)
 
     # plain FP32 form on the same workload
     p_times, p_b, p_a = timed(plain, args.steps)
