@@ -229,6 +229,7 @@ struct rpf_forest {
   int4* pk_tiles = nullptr;          // (tree, first position, rows, 0), tree-major
   uint32_t* pk_bits = nullptr;       // T x pk_nwords: bit p set iff a leaf begins at p
   int64_t pk_nwords = 0;
+  int32_t pk_rows = 128;             // tile row capacity: 128, or 256 when L > 128
   std::vector<int64_t> pk_tree_off;  // first tile of every tree (T + 1 entries)
 
   int* d_err = nullptr;  // device error word (RPF_ETIMEOUT from bounded waits)

@@ -56,7 +56,6 @@
 #include "rpf_tma.cuh"
 #include "rpf_umma.cuh"
 
-#define TC_ROWS 128
 #define TC_SLOTS 32       // exact re-rank candidates per row
 #define TC_SEG 4096       // packing segment (positions) per thread
 #define TC_SEG_TILES 72   // >= 2 (TC_SEG + 128) / 128 + 1 tiles per segment
@@ -186,9 +185,9 @@ __device__ int64_t last_start_le(const uint32_t* b, int64_t p, int64_t lim) {
 }
 
 // One thread per (tree, segment of TC_SEG positions): the leaves that begin
-// in the segment, packed greedily in order into tiles of <= TC_ROWS rows.
+// in the segment, packed greedily in order into tiles of <= cap rows.
 __global__ void k_pack_tiles(int T, int64_t n, int64_t nseg, int64_t nwords, const uint32_t* bits,
-                             int2* slot, int32_t* cnt) {
+                             int cap, int2* slot, int32_t* cnt) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (int64_t)T * nseg) return;
   const int t = (int)(g / nseg);
@@ -200,7 +199,7 @@ __global__ void k_pack_tiles(int T, int64_t n, int64_t nseg, int64_t nwords, con
   if (p < s1) {
     const int64_t E = next_start(b, n, s1);  // end of the segment's last leaf
     while (p < E) {
-      const int64_t lim = std::min<int64_t>(p + TC_ROWS, E);
+      const int64_t lim = std::min<int64_t>(p + cap, E);
       int64_t e = lim == n ? n : -1;
       if (e < 0) {
         e = last_start_le(b, p, lim);
@@ -229,24 +228,30 @@ __global__ void k_pack_fill(int64_t G, int64_t nseg, const int2* slot, const int
 // ---------------------------------------------------------------------------
 // The persistent chosen-form kernel
 // ---------------------------------------------------------------------------
-template <int KK>
-__global__ void __launch_bounds__(TC_ROWS, 3) k_leaf_tc(
+// ROWS = 128: one M = 128 accumulator of N <= 128 columns (128 TMEM columns,
+// up to three CTAs per SM).  ROWS = 256 (leaves of up to 256 points): two
+// M = 128 blocks (rows 0-127 and 128-255) against all N <= 256 rows, the
+// block-b accumulator at TMEM column 256 b (512 columns, one CTA per SM);
+// warp w reads lane quarter w % 4 of block w / 4.
+template <int KK, int ROWS>
+__global__ void __launch_bounds__(ROWS, ROWS == 128 ? 3 : 1) k_leaf_tc(
     const int4* __restrict__ tiles, int64_t tlo, int64_t thi, const uint32_t* __restrict__ bits,
     int64_t nwords, const int32_t* __restrict__ perm, const float* __restrict__ X, int64_t n,
-    int d, int dp, int d16, int K, int t0, uint2* cand, int* err,
+    int d, int dp, int d16, int KC, int K, int t0, uint2* cand, int* err,
     unsigned long long* fallbacks) {
   extern __shared__ __align__(1024) unsigned char smraw[];
-  const int KC = d16 < 128 ? d16 : 128;  // Gram coordinates per tensor-core chunk
+  constexpr int RG = ROWS / 8;                  // 8-row groups of the BF16 tiles
+  constexpr uint32_t TCOLS = ROWS == 128 ? 128u : 512u;
   const int d4 = (d + 3) & ~3;
   float* xs = reinterpret_cast<float*>(smraw);
-  const size_t a_off = (((size_t)TC_ROWS * dp * 4) + 1023) & ~(size_t)1023;
+  const size_t a_off = (((size_t)ROWS * dp * 4) + 1023) & ~(size_t)1023;
   __nv_bfloat16* Ahi = reinterpret_cast<__nv_bfloat16*>(smraw + a_off);
-  __nv_bfloat16* Alo = Ahi + TC_ROWS * KC;
-  float* cen = reinterpret_cast<float*>(Alo + TC_ROWS * KC);  // TC_MAX_BIG x d4
+  __nv_bfloat16* Alo = Ahi + ROWS * KC;
+  float* cen = reinterpret_cast<float*>(Alo + ROWS * KC);  // TC_MAX_BIG x d4
   unsigned char* slots = reinterpret_cast<unsigned char*>(cen + TC_MAX_BIG * d4);
-  __shared__ float nrm[TC_ROWS], ynm[TC_ROWS];
-  __shared__ int prow_s[TC_ROWS], big_of_start[TC_ROWS];
-  __shared__ uint32_t wmask[4];
+  __shared__ float nrm[ROWS], ynm[ROWS];
+  __shared__ int prow_s[ROWS], big_of_start[ROWS];
+  __shared__ uint32_t wmask[ROWS / 32];
   __shared__ unsigned nmax_bits[TC_MAX_BIG];
   __shared__ int big_lb[TC_MAX_BIG], big_le[TC_MAX_BIG], nbig;
   __shared__ __align__(8) uint64_t bar_tma, bar_mma;
@@ -256,12 +261,13 @@ __global__ void __launch_bounds__(TC_ROWS, 3) k_leaf_tc(
     rpf_mbar_init(&bar_tma, 1);
     rpf_mbar_init(&bar_mma, 1);
   }
-  if (warp == 0) rpf_tmem_alloc(&tmem_base, 128);
+  if (warp == 0) rpf_tmem_alloc(&tmem_base, TCOLS);
   rpf_tc_fence_before();
   __syncthreads();
   rpf_tc_fence_after();
   const uint32_t tbase = tmem_base;
-  const uint32_t tlane = tbase + ((uint32_t)(32 * warp) << 16);
+  const uint32_t tlane =
+      tbase + (uint32_t)(256 * (warp >> 2)) + ((uint32_t)(32 * (warp & 3)) << 16);
   const float ce = 0x1p-13f + (float)(d + 8) * 0x1p-23f + 3.0f * (float)(d16 + 4) * 0x1p-21f;
   const float gam = (float)(d + 3) * 0x1p-23f;
   uint32_t tma_phase = 0, mma_phase = 0;
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(TC_ROWS, 3) k_leaf_tc(
     }
     if (tid < TC_MAX_BIG) nmax_bits[tid] = 0u;
     __syncthreads();
-    for (int q = tid; q < rows; q += TC_ROWS)
+    for (int q = tid; q < rows; q += ROWS)
       rpf_bulk_g2s(xs + q * dp, X + (int64_t)prow_s[q] * d, (uint32_t)d * 4u, &bar_tma);
     tma_pending = true;
     for (int k = d; k < dp; ++k) xs[r * dp + k] = 0.0f;
@@ -302,14 +308,14 @@ __global__ void __launch_bounds__(TC_ROWS, 3) k_leaf_tc(
       lb = x ? (ww << 5) + 31 - __clz(x) : 0;
       x = b == 31 ? 0u : (wmask[w] & (0xffffffffu << (b + 1)));
       ww = w;
-      while (x == 0 && ww < 3) x = wmask[++ww];
+      while (x == 0 && ww < ROWS / 32 - 1) x = wmask[++ww];
       le = x ? min((ww << 5) + __ffs(x) - 1, rows) : rows;
     }
     const int m = le - lb;
     const bool live = r < rows;
     const bool big = live && m - 1 > TC_SLOTS;
     if (big && r == lb) {
-      const int sidx = atomicAdd(&nbig, 1);  // at most 3 leaves of > 33 rows in 128
+      const int sidx = atomicAdd(&nbig, 1);  // at most ROWS / 34 leaves of > 33 rows
       big_of_start[r] = sidx;
       big_lb[sidx] = lb;
       big_le[sidx] = le;
@@ -328,7 +334,7 @@ __global__ void __launch_bounds__(TC_ROWS, 3) k_leaf_tc(
       // (2) FP32 mean of every large leaf
       for (int j = 0; j < nb; ++j) {
         const int b0 = big_lb[j], b1 = big_le[j];
-        for (int k = tid; k < d; k += TC_ROWS) {
+        for (int k = tid; k < d; k += ROWS) {
           float s = 0.0f;
           for (int q = b0; q < b1; ++q) s = __fadd_rn(s, xs[q * dp + k]);
           cen[j * d4 + k] = __fdiv_rn(s, (float)(b1 - b0));
@@ -337,7 +343,7 @@ __global__ void __launch_bounds__(TC_ROWS, 3) k_leaf_tc(
       __syncthreads();
       // (3) centred split-BF16 tiles, FP32 squared norms, Gram on the tensor core
       const int npad = (rows + 15) & ~15;
-      const uint32_t idesc = rpf_umma_idesc_bf16(TC_ROWS, npad);
+      const uint32_t idesc = rpf_umma_idesc_bf16(128, npad);
       float yy = 0.0f;
       for (int k0 = 0; k0 < d16 && ok; k0 += KC) {
         if (k0 > 0) {  // the previous chunk's MMAs must be done reading the tiles
@@ -366,7 +372,7 @@ __global__ void __launch_bounds__(TC_ROWS, 3) k_leaf_tc(
             hp[u] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
             lp[u] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
           }
-          const int idx = rpf_umma_index(r, kk, 16);  // 8 consecutive k: 16 bytes
+          const int idx = rpf_umma_index(r, kk, RG);  // 8 consecutive k: 16 bytes
           *reinterpret_cast<uint4*>(Ahi + idx) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
           *reinterpret_cast<uint4*>(Alo + idx) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
         }
@@ -376,13 +382,21 @@ __global__ void __launch_bounds__(TC_ROWS, 3) k_leaf_tc(
         if (tid == 0) {
           rpf_tc_fence_after();
           const uint32_t hb = rpf_saddr(Ahi), lbs = rpf_saddr(Alo);
-          for (int s2 = 0; s2 < KC / 16; ++s2) {
-            const uint32_t off = (uint32_t)s2 * 2u * 16u * 128u;
-            const uint64_t dh = rpf_umma_desc(hb + off, 16u * 128u, 128u);
-            const uint64_t dl = rpf_umma_desc(lbs + off, 16u * 128u, 128u);
-            rpf_umma_bf16(tbase, dh, dh, idesc, (k0 > 0 || s2 > 0) ? 1u : 0u);
-            rpf_umma_bf16(tbase, dh, dl, idesc, 1u);
-            rpf_umma_bf16(tbase, dl, dh, idesc, 1u);
+          const uint32_t lbo = (uint32_t)RG * 128u;  // next 8-column group along K
+          for (int blk = 0; blk < ROWS / 128; ++blk) {
+            if (blk * 128 >= rows) break;
+            const uint32_t dcol = tbase + (uint32_t)(256 * blk);
+            const uint32_t aoff = (uint32_t)blk * 16u * 128u;  // rows 128 blk ...
+            for (int s2 = 0; s2 < KC / 16; ++s2) {
+              const uint32_t off = (uint32_t)s2 * 2u * lbo;
+              const uint64_t ah = rpf_umma_desc(hb + off + aoff, lbo, 128u);
+              const uint64_t al = rpf_umma_desc(lbs + off + aoff, lbo, 128u);
+              const uint64_t bh = rpf_umma_desc(hb + off, lbo, 128u);
+              const uint64_t bl = rpf_umma_desc(lbs + off, lbo, 128u);
+              rpf_umma_bf16(dcol, ah, bh, idesc, (k0 > 0 || s2 > 0) ? 1u : 0u);
+              rpf_umma_bf16(dcol, ah, bl, idesc, 1u);
+              rpf_umma_bf16(dcol, al, bh, idesc, 1u);
+            }
           }
           rpf_umma_commit(&bar_mma);
         }
@@ -413,7 +427,7 @@ __global__ void __launch_bounds__(TC_ROWS, 3) k_leaf_tc(
     float tau2 = 0.0f, eps = 0.0f, eta = 0.0f;
     const bool tc_row = big && cert_ok;
     if (__any_sync(RPF_FULL, tc_row)) {
-      int lo = tc_row ? lb : TC_ROWS, hi = tc_row ? le : 0;
+      int lo = tc_row ? lb : ROWS, hi = tc_row ? le : 0;
 #pragma unroll
       for (int off = 16; off >= 1; off >>= 1) {
         lo = min(lo, __shfl_xor_sync(RPF_FULL, lo, off));
@@ -430,7 +444,7 @@ __global__ void __launch_bounds__(TC_ROWS, 3) k_leaf_tc(
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int c = c0 + j;
-          const float D = __fmaf_rn(-2.0f, g[j], __fadd_rn(nr, nrm[c < TC_ROWS ? c : 0]));
+          const float D = __fmaf_rn(-2.0f, g[j], __fadd_rn(nr, nrm[c < ROWS ? c : 0]));
           const bool use = tc_row && c >= lb && c < le && c != r;
           th.insert(use ? D : INFINITY);
         }
@@ -451,7 +465,7 @@ __global__ void __launch_bounds__(TC_ROWS, 3) k_leaf_tc(
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int c = c0 + j;
-          const float D = __fmaf_rn(-2.0f, g[j], __fadd_rn(nr, nrm[c < TC_ROWS ? c : 0]));
+          const float D = __fmaf_rn(-2.0f, g[j], __fadd_rn(nr, nrm[c < ROWS ? c : 0]));
           if (tc_row && c >= lb && c < le && c != r && D <= tau2) {
             if (ns < TC_SLOTS) my[ns] = (unsigned char)c;
             ++ns;
@@ -521,53 +535,71 @@ __global__ void __launch_bounds__(TC_ROWS, 3) k_leaf_tc(
   __syncthreads();
   if (warp == 0) {
     rpf_tc_fence_after();
-    rpf_tmem_dealloc(tbase, 128);
+    rpf_tmem_dealloc(tbase, TCOLS);  // exactly the columns allocated
   }
 }
 
-size_t tc_smem(int d, int dp) {
-  const int d16 = (d + 15) & ~15, KC = std::min(d16, 128), d4 = (d + 3) & ~3;
-  const size_t a_off = (((size_t)TC_ROWS * dp * 4) + 1023) & ~(size_t)1023;
-  const size_t need = a_off + (size_t)2 * TC_ROWS * KC * 2 + (size_t)TC_MAX_BIG * d4 * 4 +
-                      (size_t)TC_ROWS * TC_SLOTS;
-  // at least 60 KB so that at most three CTAs (3 x 128 TMEM columns) share an SM
-  return std::max<size_t>(need, 60 * 1024);
+size_t tc_smem(int d, int dp, int rows, int KC) {
+  const int d4 = (d + 3) & ~3;
+  const size_t a_off = (((size_t)rows * dp * 4) + 1023) & ~(size_t)1023;
+  const size_t need = a_off + (size_t)2 * rows * KC * 2 + (size_t)TC_MAX_BIG * d4 * 4 +
+                      (size_t)rows * TC_SLOTS;
+  // with 128-row tiles at least 60 KB, so that at most three CTAs (3 x 128
+  // TMEM columns) share an SM; 256-row tiles hold all 512 columns
+  return rows == 128 ? std::max<size_t>(need, 60 * 1024) : std::max<size_t>(need, 120 * 1024);
 }
 
-template <int KK>
+// Gram coordinates per chunk: the largest multiple of 16 (<= 128) for which
+// the CTA's shared memory fits 220 KB (the opt-in limit is 227 KB); 0 if none
+int tc_chunk(int d, int rows) {
+  const int d16 = (d + 15) & ~15, dp = ((d + 3) & ~3) + 4;
+  for (int kc = std::min(d16, 128); kc >= 16; kc -= 16)
+    if (tc_smem(d, dp, rows, kc) <= 220 * 1024) return kc;
+  return 0;
+}
+
+template <int KK, int ROWS>
 int launch_tc(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint2* cand,
               cudaStream_t s) {
   if (thi <= tlo) return RPF_OK;
   const int d = f->d, dp = ((d + 3) & ~3) + 4, d16 = (d + 15) & ~15;
-  const size_t smem = tc_smem(d, dp);
-  RPF_CU(cudaFuncSetAttribute(k_leaf_tc<KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const int KC = tc_chunk(d, ROWS);
+  const size_t smem = tc_smem(d, dp, ROWS, KC);
+  RPF_CU(cudaFuncSetAttribute(k_leaf_tc<KK, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem));
   int dev = 0, sms = 0, smem_sm = 0;
   RPF_CU(cudaGetDevice(&dev));
   RPF_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   RPF_CU(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-  RPF_CU(cudaFuncSetAttribute(k_leaf_tc<KK>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  RPF_CU(cudaFuncSetAttribute(k_leaf_tc<KK, ROWS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                               100));
   cudaFuncAttributes fa;
-  RPF_CU(cudaFuncGetAttributes(&fa, k_leaf_tc<KK>));
+  RPF_CU(cudaFuncGetAttributes(&fa, k_leaf_tc<KK, ROWS>));
   // CTAs per SM that shared memory allows (1 KB per CTA is reserved by the
-  // system); at most three, so that their TMEM (3 x 128 columns) fits
+  // system), and that TMEM allows: three of 128 columns or one of 512
   const size_t per_cta = smem + fa.sharedSizeBytes + 1024;
-  const int occ = std::max(1, std::min(3, (int)((size_t)smem_sm / per_cta)));
+  const int tmem_cap = ROWS == 128 ? 3 : 1;
+  const int occ = std::max(1, std::min(tmem_cap, (int)((size_t)smem_sm / per_cta)));
   const int64_t grid = std::min<int64_t>(thi - tlo, (int64_t)sms * occ);
-  RPF_LAUNCH("k_leaf_tc", s, k_leaf_tc<KK><<<(unsigned)grid, TC_ROWS, smem, s>>>(
-      f->pk_tiles, tlo, thi, f->pk_bits, f->pk_nwords, f->perm, f->X, f->n, d, dp, d16, K, t0,
-      cand, f->d_err, f->d_fallback));
+  RPF_LAUNCH("k_leaf_tc", s, k_leaf_tc<KK, ROWS><<<(unsigned)grid, ROWS, smem, s>>>(
+      f->pk_tiles, tlo, thi, f->pk_bits, f->pk_nwords, f->perm, f->X, f->n, d, dp, d16, KC, K,
+      t0, cand, f->d_err, f->d_fallback));
   return RPF_OK;
+}
+
+template <int KK>
+int launch_tc_rows(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint2* cand,
+                   cudaStream_t s) {
+  return f->pk_rows == 128 ? launch_tc<KK, 128>(f, tlo, thi, K, t0, cand, s)
+                           : launch_tc<KK, 256>(f, tlo, thi, K, t0, cand, s);
 }
 
 }  // namespace
 
 bool rpf_tc_supported(const rpf_forest* f, int K) {
-  const int d = f->d, dp = ((d + 3) & ~3) + 4;
-  // dynamic shared memory up to 220 KB (the opt-in limit is 227 KB per CTA)
-  return f->pk_tiles != nullptr && f->prm.leaf_max <= TC_ROWS && K <= 32 && (d % 4) == 0 &&
-         tc_smem(d, dp) <= 220 * 1024;
+  const int rows = f->prm.leaf_max <= 128 ? 128 : 256;
+  return f->pk_tiles != nullptr && f->prm.leaf_max <= 256 && K <= 32 && (f->d % 4) == 0 &&
+         tc_chunk(f->d, rows) > 0;
 }
 
 int rpf_build_packs(rpf_forest* f, cudaStream_t s) {
@@ -592,8 +624,9 @@ int rpf_build_packs(rpf_forest* f, cudaStream_t s) {
   RPF_CU(cudaMemsetAsync(f->pk_bits, 0, 4 * (size_t)(T * nwords), s));
   RPF_LAUNCH("k_leaf_bits", s, k_leaf_bits<<<nblk(nl, 256), 256, 0, s>>>(
       nl, f->leaf_tree, f->leaf_begin, nwords, f->pk_bits));
+  f->pk_rows = f->prm.leaf_max <= 128 ? 128 : 256;
   RPF_LAUNCH("k_pack_tiles", s, k_pack_tiles<<<nblk(G, 128), 128, 0, s>>>(
-      T, n, nseg, nwords, f->pk_bits, slot, cnt));
+      T, n, nseg, nwords, f->pk_bits, f->pk_rows, slot, cnt));
   const int32_t* cn = cnt;
   int32_t* of = off;
   rpf_scan(G, [=] __device__(int64_t i) -> int { return min(cn[i], TC_SEG_TILES); },
@@ -639,10 +672,10 @@ int rpf_build_packs(rpf_forest* f, cudaStream_t s) {
 
 int rpf_leaf_tc(const rpf_forest* f, int t0, int g, int K, uint2* cand, cudaStream_t s) {
   const int64_t tlo = f->pk_tree_off[t0], thi = f->pk_tree_off[t0 + g];
-  if (K <= 4) return launch_tc<4>(f, tlo, thi, K, t0, cand, s);
-  if (K <= 8) return launch_tc<8>(f, tlo, thi, K, t0, cand, s);
-  if (K <= 12) return launch_tc<12>(f, tlo, thi, K, t0, cand, s);
-  if (K <= 16) return launch_tc<16>(f, tlo, thi, K, t0, cand, s);
-  if (K <= 24) return launch_tc<24>(f, tlo, thi, K, t0, cand, s);
-  return launch_tc<32>(f, tlo, thi, K, t0, cand, s);
+  if (K <= 4) return launch_tc_rows<4>(f, tlo, thi, K, t0, cand, s);
+  if (K <= 8) return launch_tc_rows<8>(f, tlo, thi, K, t0, cand, s);
+  if (K <= 12) return launch_tc_rows<12>(f, tlo, thi, K, t0, cand, s);
+  if (K <= 16) return launch_tc_rows<16>(f, tlo, thi, K, t0, cand, s);
+  if (K <= 24) return launch_tc_rows<24>(f, tlo, thi, K, t0, cand, s);
+  return launch_tc_rows<32>(f, tlo, thi, K, t0, cand, s);
 }

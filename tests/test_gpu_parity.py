@@ -331,3 +331,19 @@ def test_all_knn_over_tree_prefixes_equals_the_smaller_forests(form):
         check_knn(gi.cpu().numpy(), gd.cpu().numpy(), oi, od, X)
     with pytest.raises(RuntimeError):
         g.all_knn(10, n_trees=9)
+
+
+@pytest.mark.parametrize("name,n,d_ok", [("subspace16_d128", 9000, 128), ("aniso20_d64", 9000, 64)])
+def test_chosen_form_leaves_up_to_256_points(name, n, d_ok):
+    # leaf bound 256: 256-row tiles, two M = 128 tensor-core blocks against all
+    # rows; d = 128 also runs the Gram in two 64-coordinate chunks
+    X = synth.make(name, n=n)
+    assert X.shape[1] == d_ok
+    o = oracle.Forest(X, 3, 256, 3, seed=8)
+    oi, od = o.all_knn(20)
+    c = gpu_forest(X, 3, 256, 3, seed=8, form=1)
+    p = gpu_forest(X, 3, 256, 3, seed=8, form=0)
+    ci, cd = c.all_knn(20)
+    pi, pd = p.all_knn(20)
+    assert torch.equal(ci, pi) and torch.equal(cd, pd)
+    check_knn(ci.cpu().numpy(), cd.cpu().numpy(), oi, od, X)
