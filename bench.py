@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="aniso20_d64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large batched workload (1M points, d = 128, T = 64)")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the ensemble sweep (128 nested trees, heavy-tailed data)")
     ap.add_argument("--no-serve", action="store_true",
@@ -56,6 +58,19 @@ def dist_env():
     w = int(os.environ.get("WORLD_SIZE", "1"))
     lr = int(os.environ.get("LOCAL_RANK", "0"))
     return r, w, lr
+
+
+def bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            j = json.load(open(p))
+            for k in ("bf16_tflops", "bf16_TFLOPs"):
+                if k in j:
+                    return float(j[k]), "measured"
+        except Exception:
+            pass
+    return BF16_TFLOPS
 
 
 def peaks():
@@ -147,6 +162,7 @@ class Clocks:
 
 SUBTREE_MAX = 4096          # nodes of at most this many points grow CTA-locally
 FP32_LANES = 152 * 128      # FP32 lanes of a GB300 (152 SMs x 128)
+BF16_TFLOPS = (1900.0, "fallback (dense BF16, one earlier GB300 measurement)")
 SM_MAX_GHZ = 2.07
 
 
@@ -208,8 +224,10 @@ def work_model(fo, w, n):
         "k_scatter": {"bytes": pl_a * (1 + 4 + 4)},
         "k_leaf_plain": {"bytes": n * T * (4 * d + 4 + 8 * K),
                          "flops": 2 * d * int((leaf_len ** 2).sum())},
-        "k_leaf_bf16": {"bytes": n * T * (4 * d + 4 + 8 * K),
-                        "flops": 2 * d * int((leaf_len ** 2).sum())},
+        "k_leaf_tc": {"bytes": n * T * (4 * d + 4 + 8 * K),
+                      "flops": 2 * d * int((leaf_len ** 2).sum()),
+                      "tensor_flops": 3 * 2 * ((d + 15) // 16 * 16)
+                      * int((leaf_len[leaf_len > 33] ** 2).sum())},
         "k_merge": {"bytes": n * (T * 8 * K + 8 * K)},
         "_point_levels": {"phase_a": pl_a, "phase_b": pl_b,
                           "leaf_m2_per_point_per_tree": float((leaf_len ** 2).sum()) / (n * T)},
@@ -257,6 +275,14 @@ def rooflines(trace, work, hbm_peak, peak_kind, steps, workload):
              "algorithmic_bytes_per_launch": int(per_launch),
              "ms_per_launch": round(ms_launch, 5), "launches_per_step": t["launches"] // steps,
              "share": round(t["ms"] / tot, 4)}
+        if "tensor_flops" in work[k]:
+            tf = work[k]["tensor_flops"] * steps / t["launches"] / (ms_launch * 1e-3) / 1e12
+            bp, bsrc = bf16_peak()
+            r["tensor_bf16"] = {"achieved": round(tf, 2), "peak": bp,
+                                "unit": "TFLOP/s", "frac": round(tf / bp, 5),
+                                "peak_source": bsrc,
+                                "flops": "3 BF16 products (split hi/lo) x 2 d16 m^2 per "
+                                         "leaf of more than 33 points"}
         if "flops" in work[k]:
             fl = work[k]["flops"] * steps / t["launches"] / (ms_launch * 1e-3) / 1e12
             r["fp32_alu"] = {"achieved": round(fl, 2), "peak": round(fp32_peak, 1),
@@ -462,6 +488,8 @@ def run_gb300(args, rank, world, local_rank):
                                 sorted(trace.items(), key=lambda kv: -kv[1]["ms"])},
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_large:
+        line["large_batched"] = run_large(args, dev)
     if rank == 0 and world == 1 and not args.no_sweep:
         line["ensemble_sweep"] = run_sweep(args, dev)
     if rank == 0 and world == 1 and not args.no_serve:
@@ -578,6 +606,50 @@ def run_sweep(args, dev, rows=2000):
                                    "missing_per_point_non_increasing_in_T": monotone}
         for v in f.values():
             v.close()
+    return out
+
+
+def run_large(args, dev, rows=1000):
+    """All-kNN on the large batched workload (points near a 16-dimensional
+    subspace, n = 1,000,000, d = 128, T = 64, leaf bound 256, K = 20): the
+    chosen form's persistent tensor-core launch over every (tree, leaf) tile,
+    against the plain form on the same forest shape."""
+    import torch
+    from paper_1812_11689_gb300 import forest, synth
+    w = synth.WORKLOADS["subspace16_d128"]
+    X = torch.from_numpy(synth.make("subspace16_d128", seed=args.seed)).to(dev)
+    out = {"workload": "subspace16_d128", "n": w.n, "d": w.d, "n_trees": w.n_trees,
+           "leaf_max": w.leaf_max, "k": w.k, "n_try": w.n_try}
+    res = {}
+    for form, nm in ((forest.FORM_CHOSEN, "chosen"), (forest.FORM_PLAIN, "plain")):
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        f = forest.Forest(X, n_trees=w.n_trees, leaf_max=w.leaf_max, n_try=w.n_try,
+                          seed=args.seed, form=form)
+        e1.record()
+        i, d = f.all_knn(w.k)
+        e2.record()
+        torch.cuda.synchronize()
+        res[nm] = (i, d, e0.elapsed_time(e1), e1.elapsed_time(e2), f.counters())
+        f.close()
+    ci, cd, bc, ac, cnt = res["chosen"]
+    pi, pd, bp, ap, _ = res["plain"]
+    r = torch.from_numpy(np.sort(np.random.default_rng(3).choice(w.n, rows, replace=False))
+                         .astype(np.int32)).to(dev)
+    bi, _ = forest.brute_knn(X, X[r.long()].contiguous(), w.k, self_idx=r)
+    bi, cis = bi.cpu().numpy(), ci[r.long()].cpu().numpy()
+    out.update({
+        "chosen": {"build_ms": round(bc, 2), "all_knn_ms": round(ac, 2),
+                   "queries_per_s": round(w.n / ((bc + ac) * 1e-3), 1),
+                   "certificate_fallback_rows": cnt.get("bf16_fallback_rows")},
+        "plain": {"build_ms": round(bp, 2), "all_knn_ms": round(ap, 2),
+                  "queries_per_s": round(w.n / ((bp + ap) * 1e-3), 1)},
+        "chosen_equals_plain": bool(torch.equal(ci, pi) and torch.equal(cd, pd)),
+        "missing_rate_sample": round(sum(len(set(bi[q]) - set(cis[q])) for q in range(rows))
+                                     / float(bi.size), 5),
+        "sample": "%d points vs exact brute force" % rows,
+        "timing": "one cold step per form (build + all-kNN), CUDA events"})
     return out
 
 
