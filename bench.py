@@ -492,6 +492,7 @@ def run_gb300(args, rank, world, local_rank):
         line["large_batched"] = run_large(args, dev)
     if rank == 0 and world == 1 and not args.no_sweep:
         line["ensemble_sweep"] = run_sweep(args, dev)
+        line["n_try_ablation"] = run_ntry_ablation(args, dev)
     if rank == 0 and world == 1 and not args.no_serve:
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -650,6 +651,48 @@ def run_large(args, dev, rows=1000):
                                      / float(bi.size), 5),
         "sample": "%d points vs exact brute force" % rows,
         "timing": "one cold step per form (build + all-kNN), CUDA events"})
+    return out
+
+
+def run_ntry_ablation(args, dev, rows=2000):
+    """nTry ablation (Sec. 5.2 varies the projections tried per split): on the
+    anisotropic workload (T = 40) and the heavy-tailed one (T = 32), the
+    missing rate, discrepancy, build time and the share of split nodes the
+    certified FP32 path had to settle in FP64, for nTry in {1, 3, 5, 10, 20}."""
+    import torch
+    from paper_1812_11689_gb300 import forest, synth
+    out = {}
+    for name, T in (("aniso20_d64", 40), ("student3_d32", 32)):
+        w = synth.WORKLOADS[name]
+        X = torch.from_numpy(synth.make(name, seed=args.seed)).to(dev)
+        r = torch.from_numpy(np.sort(np.random.default_rng(4).choice(w.n, rows, replace=False))
+                             .astype(np.int32)).to(dev)
+        bi, bd = forest.brute_knn(X, X[r.long()].contiguous(), w.k, self_idx=r)
+        bi, bd = bi.cpu().numpy(), bd.cpu().numpy()
+        res = []
+        for ntry in (1, 3, 5, 10, 20):
+            kw = dict(n_trees=T, leaf_max=w.leaf_max, n_try=ntry, seed=args.seed,
+                      form=forest.FORM_CHOSEN)
+            forest.Forest(X, **kw).close()  # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f = forest.Forest(X, **kw)
+            e1.record()
+            i, d = f.all_knn(w.k)
+            torch.cuda.synchronize()
+            info = f.info()
+            ci, cd = i[r.long()].cpu().numpy(), d[r.long()].cpu().numpy()
+            internal = (info["n_nodes"] - info["n_leaves"])
+            res.append({"n_try": ntry, "build_ms": round(e0.elapsed_time(e1), 2),
+                        "missing_rate": round(sum(len(set(bi[q]) - set(ci[q]))
+                                                  for q in range(rows)) / float(bi.size), 5),
+                        "knn_distance_discrepancy": discrepancy_full(cd, bd)[0],
+                        "fp64_settled_split_share": round(info["n_exact_nodes"] / max(internal, 1), 5),
+                        "max_depth": info["max_depth"]})
+            f.close()
+        out[name] = {"n_trees": T, "leaf_max": w.leaf_max, "k": w.k, "by_n_try": res,
+                     "sample": "%d points vs exact brute force" % rows}
     return out
 
 

@@ -84,7 +84,9 @@ def test_trees_bit_exact_mix5(growth):
 @pytest.mark.parametrize("name,n,L,ntry", [("aniso20_d64", 20000, 128, 5),
                                            ("student3_d32", 20000, 64, 5),
                                            ("subspace16_d128", 8000, 256, 3),
-                                           ("mix50_d96", 9000, 128, 1)])
+                                           ("mix50_d96", 9000, 128, 1),
+                                           ("student3_d32", 6000, 64, 10),
+                                           ("aniso20_d64", 6000, 128, 20)])
 def test_trees_bit_exact_workload_shapes(name, n, L, ntry):
     X = synth.make(name, n=n)
     o = oracle.Forest(X, 4, L, ntry, seed=5)
