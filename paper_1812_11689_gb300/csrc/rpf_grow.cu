@@ -99,21 +99,43 @@ __global__ void k_xnorm(const float* X, int64_t n, int d, float* out) {
 }
 
 // Directions of the frontier nodes and the base projections b_j = p64(o, r_j)
-// of each node's first member o.
-__global__ void k_dirs_a(int F, int ntry, int d, uint64_t seed, int64_t n, const int32_t* fr_tree,
-                         const int32_t* fr_begin, const uint64_t* fr_key, const int32_t* perm_cur,
-                         const float* X, double* dir64, float* dir32, double* fr_base,
-                         int32_t* fr_ogid) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (int64_t)F * ntry) return;
+// of each node's first member o; one warp per (node, try).  The lanes draw
+// the Box-Muller pairs; the normalisation's sum and b_j keep their sequential
+// order (one lane), so r and b_j equal rpf_gen_direction / rpf_p64 bit for bit.
+__global__ void __launch_bounds__(128) k_dirs_a(int F, int ntry, int d, uint64_t seed, int64_t n,
+                                                const int32_t* fr_tree, const int32_t* fr_begin,
+                                                const uint64_t* fr_key, const int32_t* perm_cur,
+                                                const float* X, double* dir64, float* dir32,
+                                                double* fr_base, int32_t* fr_ogid) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= (int64_t)F * ntry) return;  // whole warp
   const int f = (int)(g / ntry), j = (int)(g % ntry);
+  const uint64_t t = (uint64_t)fr_tree[f], key = fr_key[f];
   double* r = dir64 + g * d;
   float* r32 = dir32 + g * d;
-  rpf_gen_direction(seed, (uint64_t)fr_tree[f], fr_key[f], (uint64_t)j, d, r32, r);
-  for (int k = 0; k < d; ++k) r32[k] = (float)r[k];
-  const int32_t og = perm_cur[(int64_t)fr_tree[f] * n + fr_begin[f]];
-  fr_base[g] = rpf_p64(X + (int64_t)og * d, r, d);
-  if (j == 0) fr_ogid[f] = og;
+  for (int i = lane; 2 * i < d; i += 32) {
+    float g0, g1;
+    rpf_gauss_pair(seed, t, key, (uint64_t)j, i, &g0, &g1);
+    r32[2 * i] = g0;
+    if (2 * i + 1 < d) r32[2 * i + 1] = g1;
+  }
+  __syncwarp();
+  float inv = 0.0f;
+  if (lane == 0) inv = rpf_inv_norm32(r32, d);
+  inv = __shfl_sync(RPF_FULL, inv, 0);
+  __syncwarp();
+  for (int k = lane; k < d; k += 32) {
+    const float v = inv == 0.0f ? (k == 0 ? 1.0f : 0.0f) : __fmul_rn(r32[k], inv);
+    r32[k] = v;
+    r[k] = (double)v;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    const int32_t og = perm_cur[(int64_t)t * n + fr_begin[f]];
+    fr_base[g] = rpf_p64(X + (int64_t)og * d, r, d);
+    if (j == 0) fr_ogid[f] = og;
+  }
 }
 
 // Directions for explicit keys (inspection entry point).
@@ -188,50 +210,66 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
   if (threadIdx.x == 0) cp_rad[c] = radmax;
 }
 
-// Per node: merge the chunk statistics, certify Algorithm 2's choice.
-__global__ void k_certify_a(int F, int ntry, int exact_only, const int32_t* fr_cb,
-                            const int32_t* fr_nc, const int32_t* fr_len, const double* cp_s1,
-                            const double* cp_s2, const double* cp_a, const float* cp_min,
-                            const float* cp_max, const float* cp_rad, const double* fr_base,
-                            int32_t* fr_exact, int32_t* fr_jstar, float* fr_rad, float* fr_wlo,
-                            float* fr_whi, unsigned long long* fr_akey,
-                            unsigned long long* fr_bkey) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= F) return;
+// Per node: merge the chunk statistics, certify Algorithm 2's choice.  One
+// warp per node: lane j merges try j's chunk partials (in chunk order) and
+// bounds its dispersion; the radius and the winner's extremes are lane-
+// strided min / max reductions; lane 0 selects.
+__global__ void __launch_bounds__(128) k_certify_a(
+    int F, int ntry, int exact_only, const int32_t* fr_cb, const int32_t* fr_nc,
+    const int32_t* fr_len, const double* cp_s1, const double* cp_s2, const double* cp_a,
+    const float* cp_min, const float* cp_max, const float* cp_rad, const double* fr_base,
+    int32_t* fr_exact, int32_t* fr_jstar, float* fr_rad, float* fr_wlo, float* fr_whi,
+    unsigned long long* fr_akey, unsigned long long* fr_bkey) {
+  __shared__ double s_vh[4][RPF_MAX_TRY];
+  __shared__ float s_lo[4][RPF_MAX_TRY], s_hi[4][RPF_MAX_TRY];
+  const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if (f >= F) return;  // whole warp
   const int cb = fr_cb[f], nc = fr_nc[f];
   float rad = 0.0f;
-  for (int c = cb; c < cb + nc; ++c) rad = fmaxf(rad, cp_rad[c]);
-  fr_rad[f] = rad;
-  double vh[RPF_MAX_TRY];
-  float lo_[RPF_MAX_TRY], hi_[RPF_MAX_TRY];
+  for (int c = cb + lane; c < cb + nc; c += 32) rad = fmaxf(rad, cp_rad[c]);
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) rad = fmaxf(rad, __shfl_xor_sync(RPF_FULL, rad, off));
+  if (lane == 0) fr_rad[f] = rad;
   const int m = fr_len[f];
   const double inv_m = 1.0 / (double)m;
-  for (int j = 0; j < ntry; ++j) {
+  for (int j = lane; j < ntry; j += 32) {
     double a = 0.0, b = 0.0, e = 0.0;
     for (int c = cb; c < cb + nc; ++c) {
       a = __dadd_rn(a, cp_s1[(int64_t)c * ntry + j]);
       b = __dadd_rn(b, cp_s2[(int64_t)c * ntry + j]);
       e = __dadd_rn(e, cp_a[(int64_t)c * ntry + j]);
     }
-    rpf_try_bounds(m, inv_m, a, b, e, fr_base[(int64_t)f * ntry + j], rad, &vh[j], &lo_[j], &hi_[j]);
+    rpf_try_bounds(m, inv_m, a, b, e, fr_base[(int64_t)f * ntry + j], rad, &s_vh[wib][j],
+                   &s_lo[wib][j], &s_hi[wib][j]);
   }
-  const int w = exact_only ? -1 : rpf_certify_select(ntry, vh, lo_, hi_);
+  __syncwarp();
+  int w = -1;
+  if (lane == 0) w = exact_only ? -1 : rpf_certify_select(ntry, s_vh[wib], s_lo[wib], s_hi[wib]);
+  w = __shfl_sync(RPF_FULL, w, 0);
   if (w < 0) {
-    fr_exact[f] = 1;
+    if (lane == 0) fr_exact[f] = 1;
     return;
   }
   float lo = INFINITY, hi = -INFINITY;
-  for (int c = cb; c < cb + nc; ++c) {
+  for (int c = cb + lane; c < cb + nc; c += 32) {
     lo = fminf(lo, cp_min[(int64_t)c * ntry + w]);
     hi = fmaxf(hi, cp_max[(int64_t)c * ntry + w]);
   }
-  const float r2 = __fmul_ru(2.0f, rad);
-  fr_exact[f] = 0;
-  fr_jstar[f] = w;
-  fr_wlo[f] = __fadd_ru(lo, r2);  // min candidates: q' <= wlo
-  fr_whi[f] = __fsub_rd(hi, r2);  // max candidates: q' >= whi
-  fr_akey[f] = rpf_dkey(INFINITY);
-  fr_bkey[f] = rpf_dkey(-INFINITY);
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(RPF_FULL, lo, off));
+    hi = fmaxf(hi, __shfl_xor_sync(RPF_FULL, hi, off));
+  }
+  if (lane == 0) {
+    const float r2 = __fmul_ru(2.0f, rad);
+    fr_exact[f] = 0;
+    fr_jstar[f] = w;
+    fr_wlo[f] = __fadd_ru(lo, r2);  // min candidates: q' <= wlo
+    fr_whi[f] = __fsub_rd(hi, r2);  // max candidates: q' >= whi
+    fr_akey[f] = rpf_dkey(INFINITY);
+    fr_bkey[f] = rpf_dkey(-INFINITY);
+  }
 }
 
 // Exact FP64 projections of the min / max candidates of certified nodes.
@@ -749,23 +787,42 @@ __global__ void k_compact_leaves(int64_t S, const int32_t* pos, const int32_t* t
   olen[pos[i]] = len[i];
 }
 
-// r* of every split node (regenerated from its key and chosen try).
-__global__ void k_node_dirs(int64_t N, int d, uint64_t seed, const uint64_t* key,
-                            const int32_t* tree, const int32_t* left, const int32_t* jstar,
-                            const int32_t* flag, double* dir, float* dir32) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+// r* of every split node (regenerated from its key and chosen try), one warp
+// per node: lanes draw the Box-Muller pairs, lane 0 forms the sequential
+// FP32 norm, so r equals rpf_gen_direction's bit for bit.
+__global__ void __launch_bounds__(128) k_node_dirs(int64_t N, int d, uint64_t seed,
+                                                   const uint64_t* key, const int32_t* tree,
+                                                   const int32_t* left, const int32_t* jstar,
+                                                   const int32_t* flag, double* dir, float* dir32) {
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= N) return;  // whole warp
   double* r = dir + i * d;
   float* r32 = dir32 + i * d;
   if (left[i] < 0 || (flag[i] & 1) || jstar[i] < 0) {
-    for (int k = 0; k < d; ++k) {
+    for (int k = lane; k < d; k += 32) {
       r[k] = 0.0;
       r32[k] = 0.0f;
     }
     return;
   }
-  rpf_gen_direction(seed, (uint64_t)tree[i], key[i], (uint64_t)jstar[i], d, r32, r);
-  for (int k = 0; k < d; ++k) r32[k] = (float)r[k];
+  const uint64_t t = (uint64_t)tree[i], kk = key[i], j = (uint64_t)jstar[i];
+  for (int p = lane; 2 * p < d; p += 32) {
+    float g0, g1;
+    rpf_gauss_pair(seed, t, kk, j, p, &g0, &g1);
+    r32[2 * p] = g0;
+    if (2 * p + 1 < d) r32[2 * p + 1] = g1;
+  }
+  __syncwarp();
+  float inv = 0.0f;
+  if (lane == 0) inv = rpf_inv_norm32(r32, d);
+  inv = __shfl_sync(RPF_FULL, inv, 0);
+  __syncwarp();
+  for (int k = lane; k < d; k += 32) {
+    const float v = inv == 0.0f ? (k == 0 ? 1.0f : 0.0f) : __fmul_rn(r32[k], inv);
+    r32[k] = v;
+    r[k] = (double)v;
+  }
 }
 
 }  // namespace
@@ -1047,7 +1104,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     uint64_t* fr_key = lv.fr_key[cur];
     int32_t *ch_node = lv.ch_node[cur], *ch_start = lv.ch_start[cur], *ch_len = lv.ch_len[cur];
 
-    RPF_LAUNCH("k_dirs_a", s, k_dirs_a<<<nblk(F * ntry, 64), 64, 0, s>>>(
+    RPF_LAUNCH("k_dirs_a", s, k_dirs_a<<<nblk(F * ntry * 32, 128), 128, 0, s>>>(
         Fi, ntry, d, seed, n, fr_tree, fr_begin, fr_key, perm_cur, fo->X, lv.dir64, lv.dir32,
         lv.fr_base, lv.fr_ogid));
 #define RPF_PROJ_A(TGV)                                                                          \
@@ -1069,7 +1126,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
       default: RPF_PROJ_A(8); break;
     }
 #undef RPF_PROJ_A
-    RPF_LAUNCH("k_certify_a", s, k_certify_a<<<nblk(F, 64), 64, 0, s>>>(
+    RPF_LAUNCH("k_certify_a", s, k_certify_a<<<nblk(F * 32, 128), 128, 0, s>>>(
         Fi, ntry, exact_only, fr_cb, fr_nc, fr_len, lv.cp_s1, lv.cp_s2, lv.cp_a, lv.cp_min32,
         lv.cp_max32, lv.cp_rad, lv.fr_base, lv.fr_exact, lv.fr_jstar, lv.fr_rad, lv.fr_wlo,
         lv.fr_whi, lv.fr_akey, lv.fr_bkey));
@@ -1226,7 +1283,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
       cleanup();
       return RPF_ENOMEM;
     }
-    RPF_LAUNCH("k_node_dirs", s, k_node_dirs<<<nblk(total, 64), 64, 0, s>>>(
+    RPF_LAUNCH("k_node_dirs", s, k_node_dirs<<<nblk((int64_t)total * 32, 128), 128, 0, s>>>(
         total, d, seed, fo->node_key, fo->node_tree, fo->node_left, fo->node_jstar, fo->node_flag,
         fo->node_dir, fo->node_dir32));
 
