@@ -333,16 +333,20 @@ __global__ void k_qscan(const float* Q, int64_t m, int d, int T, int K, const in
   tk.store(K, cand + ((int64_t)t * m + q) * K);
 }
 
-// Routing, one warp per (query q, tree t) (Sec. 2, Algorithm 3).  At a split
-// node the decision is r* . q < c with the canonical FP64 chain p64 (fold of
+// Routing, one group of RW = 8 lanes per (query q, tree t) (Sec. 2,
+// Algorithm 3); a warp walks four (query, tree) paths at once, so four
+// chains of dependent node loads are in flight.  At a split node the decision
+// is r* . q < c with the canonical FP64 chain p64 (fold of
 // fma((double)q_k, r_k, p) over k in order).  The directions are FP32 values
-// widened to double, so the warp first forms s = r* . q in FP32 (lane-strided
-// fmaf, then a butterfly) with A = sum |q_k r_k|; p64 lies within
-//   e = (ceil(d / 32) + 7) 2^-24 A_up
-// of s (FP32 error of s: (ceil(d/32) + 5) u A; FP64 error of p64: d 2^-53 A;
+// widened to double, so the group first forms s = r* . q in FP32 (lane-
+// strided fmaf over at most ceil(d / 8) terms, then a 3-level butterfly) with
+// A = sum |q_k r_k|; p64 lies within
+//   e = (ceil(d / 8) + 7) 2^-24 A_up
+// of s (FP32 error of s: (ceil(d/8) + 3) u A; FP64 error of p64: d 2^-53 A;
 // A_up bounds A despite its own rounding).  Only when c falls inside
-// [s - e, s + e] does lane 0 evaluate p64 itself.  Rank-split nodes send
-// every query left.
+// [s - e, s + e] does the group's first lane evaluate p64 itself.  Rank-split
+// nodes send every query left.
+#define RW 8
 __global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, int64_t m, int d,
                                                  int T, const int32_t* __restrict__ node_left,
                                                  const int32_t* __restrict__ node_right,
@@ -351,13 +355,14 @@ __global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, in
                                                  const double* __restrict__ node_dir,
                                                  const float* __restrict__ node_dir32,
                                                  int32_t* qleaf) {
-  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (g >= m * T) return;  // whole warp
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / RW;
+  const int lane = threadIdx.x & 31, sub = lane & (RW - 1);
+  const unsigned gmask = ((1u << RW) - 1u) << (lane & ~(RW - 1));
+  if (g >= m * T) return;  // whole group
   const int64_t q = g / T;
   const int t = (int)(g % T);
   const float* x = Q + q * d;
-  const int per = (d + 31) >> 5;
+  const int per = (d + RW - 1) / RW;
   const float kerr = (float)(per + 7) * 0x1p-24f;
   const float kA = 1.0f + (float)(per + 6) * 0x1p-23f;
   int node = t;
@@ -369,15 +374,15 @@ __global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, in
     const double c = node_c[node];
     const float* r32 = node_dir32 + (int64_t)node * d;
     float sacc = 0.0f, aacc = 0.0f;
-    for (int k = lane; k < d; k += 32) {
+    for (int k = sub; k < d; k += RW) {
       const float xv = __ldg(x + k), rv = __ldg(r32 + k);
       sacc = __fmaf_rn(xv, rv, sacc);
       aacc = __fmaf_rn(fabsf(xv), fabsf(rv), aacc);
     }
 #pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-      sacc = __fadd_rn(sacc, __shfl_xor_sync(RPF_FULL, sacc, off));
-      aacc = __fadd_rn(aacc, __shfl_xor_sync(RPF_FULL, aacc, off));
+    for (int off = RW / 2; off >= 1; off >>= 1) {
+      sacc = __fadd_rn(sacc, __shfl_xor_sync(gmask, sacc, off, RW));
+      aacc = __fadd_rn(aacc, __shfl_xor_sync(gmask, aacc, off, RW));
     }
     int go_left;
     if (flag & 1) {  // rank split: every query goes left
@@ -391,19 +396,19 @@ __global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, in
         go_left = 0;
       } else {  // undecided by the bound: the canonical FP64 chain
         int v = 0;
-        if (lane == 0) {
+        if (sub == 0) {
           const double* r = node_dir + (int64_t)node * d;
           double p = 0.0;
           for (int k = 0; k < d; ++k) p = __fma_rn((double)__ldg(x + k), r[k], p);
           v = p < c;
         }
-        go_left = __shfl_sync(RPF_FULL, v, 0);
+        go_left = __shfl_sync(gmask, v, 0, RW);
       }
     }
     node = go_left ? left : right;
     left = node_left[node];
   }
-  if (lane == 0) qleaf[g] = node;
+  if (sub == 0) qleaf[g] = node;
 }
 
 // Leaf scan for queries, one CTA of QS_T threads per (query q, tree t): the
@@ -762,7 +767,7 @@ int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t
   if (ws_bytes < align256((size_t)m * T * 4) + align256((size_t)T * m * K * 8)) return RPF_EINVAL;
   int32_t* qleaf = (int32_t*)ws;
   uint2* cand = (uint2*)((char*)ws + align256((size_t)m * T * 4));
-  RPF_LAUNCH("k_route_w", s, k_route_w<<<nblk(m * T * 32, 256), 256, 0, s>>>(
+  RPF_LAUNCH("k_route_w", s, k_route_w<<<nblk(m * T * RW, 256), 256, 0, s>>>(
       Q, m, f->d, T, f->node_left, f->node_right, f->node_flag, f->node_c, f->node_dir,
       f->node_dir32, qleaf));
   const int dp = ((f->d + 3) & ~3) + 4;
