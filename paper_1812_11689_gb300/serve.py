@@ -51,6 +51,7 @@ class _Slot:
     reqs: list = field(default_factory=list)
     rows: int = 0
     K: int = 0
+    host_q: torch.Tensor = None      # pinned staging, allocated once per slot
     host_idx: torch.Tensor = None
     host_dist: torch.Tensor = None
     keep: list = field(default_factory=list)   # device buffers alive until done
@@ -104,11 +105,29 @@ class Server:
             rows += m
         return batch, rows, head.K
 
+    def _pinned(self, slot: _Slot, rows: int, K: int) -> None:
+        """Pinned host staging of the slot, grown (rarely) to the batch's size:
+        page-locking memory is slow, so it is not done per batch."""
+        d = self.forest.d
+        if slot.host_q is None or slot.host_q.shape[0] < rows:
+            cap = max(rows, self.max_batch)
+            slot.host_q = torch.empty((cap, d), dtype=torch.float32).pin_memory()
+        if slot.host_idx is None or slot.host_idx.numel() < rows * K:
+            cap = max(rows * K, self.max_batch * K)
+            slot.host_idx = torch.empty(cap, dtype=torch.int32).pin_memory()
+            slot.host_dist = torch.empty(cap, dtype=torch.float32).pin_memory()
+
     def _launch(self, slot: _Slot, batch, rows: int, K: int) -> None:
         d = self.forest.d
-        Qh = torch.from_numpy(np.concatenate([r.Q for r in batch])).pin_memory()
-        slot.host_idx = torch.empty((rows, K), dtype=torch.int32).pin_memory()
-        slot.host_dist = torch.empty((rows, K), dtype=torch.float32).pin_memory()
+        self._pinned(slot, rows, K)
+        Qh = slot.host_q[:rows]
+        o = 0
+        for r in batch:
+            m = r.Q.shape[0]
+            Qh[o:o + m].numpy()[...] = r.Q
+            o += m
+        hidx = slot.host_idx[:rows * K].view(rows, K)
+        hdist = slot.host_dist[:rows * K].view(rows, K)
         with torch.cuda.stream(slot.stream):
             Qd = torch.empty((rows, d), dtype=torch.float32, device=self.device)
             idx = torch.empty((rows, K), dtype=torch.int32, device=self.device)
@@ -117,11 +136,11 @@ class Server:
                              dtype=torch.uint8, device=self.device)
             Qd.copy_(Qh, non_blocking=True)
             self.forest.query(Qd, K, idx=idx, dist=dist, workspace=ws, stream=slot.stream)
-            slot.host_idx.copy_(idx, non_blocking=True)
-            slot.host_dist.copy_(dist, non_blocking=True)
+            hidx.copy_(idx, non_blocking=True)
+            hdist.copy_(dist, non_blocking=True)
             slot.event = torch.cuda.Event()
             slot.event.record(slot.stream)
-        slot.keep = [Qh, Qd, idx, dist, ws]
+        slot.keep = [Qd, idx, dist, ws, hidx, hdist]
         slot.reqs, slot.rows, slot.K = batch, rows, K
         for r in batch:
             r.batch = self.n_batches
@@ -149,11 +168,12 @@ class Server:
             if not slot.reqs or not slot.event.query():
                 continue
             t = self.now()
+            hidx, hdist = slot.keep[4], slot.keep[5]
             o = 0
             for r in slot.reqs:
                 m = r.Q.shape[0]
-                r.idx = slot.host_idx[o:o + m].numpy().copy()
-                r.dist = slot.host_dist[o:o + m].numpy().copy()
+                r.idx = hidx[o:o + m].numpy().copy()
+                r.dist = hdist[o:o + m].numpy().copy()
                 r.done = t
                 o += m
                 self.finished.append(r)
