@@ -20,9 +20,12 @@
 
 #include "rpf_internal.cuh"
 
-namespace {
+// The scratch itself: file scope, one copy per device that loads the library,
+// held until the process exits.  In host code this name is only a stand-in;
+// kernels get the device address from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_query_scratch[RPF_STATIC_SCRATCH_BYTES];
 
-__device__ __align__(256) unsigned char g_query_scratch[RPF_STATIC_SCRATCH_BYTES];
+namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;

@@ -349,3 +349,30 @@ def test_chosen_form_leaves_up_to_256_points(name, n, d_ok):
     pi, pd = p.all_knn(20)
     assert torch.equal(ci, pi) and torch.equal(cd, pd)
     check_knn(ci.cpu().numpy(), cd.cpu().numpy(), oi, od, X)
+
+
+@pytest.mark.parametrize("case", ["identical", "duplicates", "huge", "tiny", "small", "few"])
+def test_chosen_form_degenerate_and_extreme_scales(case):
+    # d = 8 so that the tensor-core form runs; leaves of all-equal points
+    # (spread 0) and coordinates near 3e18 or 1e-25 fall outside the range
+    # the certificate covers and are scanned exactly; 1e-10 stays inside it
+    rng = np.random.default_rng(11)
+    n, d = 3000, 8
+    if case == "identical":
+        X = np.full((600, d), 2.5, np.float32)
+    elif case == "duplicates":
+        X = rng.standard_normal((n, d)).astype(np.float32)
+        X[200:900] = X[5]
+    elif case == "huge":
+        X = (3e18 * rng.standard_normal((n, d))).astype(np.float32)
+    elif case == "tiny":
+        X = (1e-25 * rng.standard_normal((n, d))).astype(np.float32)
+    elif case == "small":
+        X = (1e-10 * rng.standard_normal((n, d))).astype(np.float32)
+    else:
+        X = rng.standard_normal((40, d)).astype(np.float32)
+    o = oracle.Forest(X, 3, 64, 3, seed=2)
+    oi, od = o.all_knn(10)
+    c = gpu_forest(X, 3, 64, 3, seed=2, form=1)
+    ci, cd = c.all_knn(10)
+    assert np.array_equal(ci.cpu().numpy(), oi) and np.array_equal(cd.cpu().numpy(), od)
