@@ -82,7 +82,8 @@ def lib():
             L.orc_d32.argtypes = [_f32p, _f32p, ctypes.c_int]
             L.orc_build.restype = ctypes.c_void_p
             L.orc_build.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
-                                    ctypes.c_int32, ctypes.c_int32, _u64, ctypes.c_int32]
+                                    ctypes.c_int32, ctypes.c_int32, _u64, ctypes.c_int32,
+                                    ctypes.c_int32]
             L.orc_free.restype = None
             L.orc_free.argtypes = [ctypes.c_void_p]
             L.orc_n_nodes.restype = ctypes.c_int64
@@ -181,16 +182,21 @@ NODE_FIELDS = ("key", "begin", "len", "depth", "leaf", "jstar", "flag", "attempt
 
 
 class Forest:
-    """T rpTrees grown on X (Algorithm 3, first loop)."""
+    """T rpTrees grown on X (Algorithm 3, first loop).
+
+    split_rule 0: c drawn uniformly on [a, b] (Algorithm 1); 1: the median of
+    the projections (Sec. 2's other usual split point), ties by point index.
+    """
 
     def __init__(self, X: np.ndarray, n_trees: int, leaf_max: int, n_try: int,
-                 seed: int = 0, threads: int | None = None):
+                 seed: int = 0, threads: int | None = None, split_rule: int = 0):
         self.X = np.ascontiguousarray(X, np.float32)
         self.n, self.d = self.X.shape
         self.T, self.L, self.n_try, self.seed = n_trees, leaf_max, n_try, seed
+        self.split_rule = split_rule
         self.threads = threads or default_threads()
         h = lib().orc_build(_p(self.X, _f32p), self.n, self.d, n_trees, leaf_max, n_try,
-                            seed, self.threads)
+                            seed, self.threads, split_rule)
         if not h:
             raise ValueError("orc_build rejected its arguments")
         self._h = ctypes.c_void_p(h)

@@ -28,6 +28,9 @@
  *                 S the canonical-order sum of p (argmax of V == argmax SD).
  *   split point : c = fma(u, b - a, a), u uniform in [0,1); accepted iff
  *                 a < c <= b, else redrawn (8 attempts), else a rank split.
+ *                 Median rule: the floor(m/2) points smallest in
+ *                 (projection, point index) order go left; c = the
+ *                 projection of the first point that goes right.
  *   distance    : d32 = fold_k fmaf(x_k - y_k, x_k - y_k, s) in FP32, ties
  *                 broken by the smaller index; reported distance sqrtf(d32).
  *
@@ -264,6 +267,7 @@ typedef struct {
 typedef struct {
   int64_t n;
   int32_t d, T, L, ntry;
+  int32_t split_rule; /* 0: c ~ U[a, b]; 1: median of the projections */
   uint64_t seed;
   orc_tree* trees;
   const float* X; /* borrowed: valid only during orc_build */
@@ -285,6 +289,29 @@ static int64_t orc_push_dir(orc_tree* tr, const double* r, int d) {
   }
   memcpy(tr->dirs + (size_t)d * (size_t)tr->n_dirs, r, sizeof(double) * (size_t)d);
   return tr->n_dirs++;
+}
+
+/* (p[i], id[i]) < (p[j], id[j]) in the order the median rule uses: by
+   projection, ties by the point's index. */
+static int orc_key_less(const double* p, const int32_t* id, int64_t i, int64_t j) {
+  return p[i] < p[j] || (p[i] == p[j] && id[i] < id[j]);
+}
+
+/* ord[0..m) = 0..m-1 sorted by (p, id): plain bottom-up merge sort. */
+static void orc_sort_by_key(const double* p, const int32_t* id, int64_t m, int64_t* ord) {
+  int64_t* buf = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+  for (int64_t i = 0; i < m; ++i) ord[i] = i;
+  for (int64_t w = 1; w < m; w *= 2) {
+    for (int64_t lo = 0; lo < m; lo += 2 * w) {
+      int64_t mid = lo + w < m ? lo + w : m, hi = lo + 2 * w < m ? lo + 2 * w : m;
+      int64_t a = lo, b = mid, k = lo;
+      while (a < mid && b < hi) buf[k++] = orc_key_less(p, id, ord[b], ord[a]) ? ord[b++] : ord[a++];
+      while (a < mid) buf[k++] = ord[a++];
+      while (b < hi) buf[k++] = ord[b++];
+    }
+    memcpy(ord, buf, sizeof(int64_t) * (size_t)m);
+  }
+  free(buf);
 }
 
 /* Split one node (Algorithm 1 body with Algorithm 2 for the direction). */
@@ -329,7 +356,7 @@ static void orc_split(const orc_forest* F, orc_tree* tr, int64_t t, int64_t ni,
       if (p[i] < a) a = p[i];
       if (p[i] > b) b = p[i];
     }
-    for (int att = 0; att < ORC_SPLIT_ATTEMPTS; ++att) {
+    for (int att = 0; F->split_rule == 0 && att < ORC_SPLIT_ATTEMPTS; ++att) {
       double u = orc_u53(orc_word(F->seed, ORC_TAG_SPLIT, (uint64_t)t, nd->key, (uint64_t)att, 0));
       double cc = fma(u, b - a, a);
       if (cc > a && cc <= b) {
@@ -343,9 +370,32 @@ static void orc_split(const orc_forest* F, orc_tree* tr, int64_t t, int64_t ni,
   nd->a = a;
   nd->b = b;
 
-  /* W_L = {p < c}, W_R = {p >= c}; stable, so node order stays ascending. */
+  /* Median rule (Sec. 2, the other usual split point): the floor(m/2) points
+     smallest in (projection, index) order go left, node order kept on each
+     side; c is the projection of the first point that goes right, so a
+     query goes left iff its projection is below the median. */
   int64_t nl = 0;
-  if (accepted) {
+  if (F->split_rule == 1 && jstar >= 0) {
+    int64_t* ord = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+    uint8_t* left = (uint8_t*)calloc((size_t)m, 1);
+    orc_sort_by_key(p, mem, m, ord);
+    const int64_t h = m / 2;
+    for (int64_t k = 0; k < h; ++k) left[ord[k]] = 1;
+    c = p[ord[h]];
+    int64_t w = 0;
+    for (int64_t i = 0; i < m; ++i)
+      if (left[i]) tmp[w++] = mem[i];
+    nl = w;
+    for (int64_t i = 0; i < m; ++i)
+      if (!left[i]) tmp[w++] = mem[i];
+    free(ord);
+    free(left);
+    nd->c = c;
+    nd->flag = 0;
+    nd->attempt = -1;
+    nd->dir = orc_push_dir(tr, rbuf + (size_t)jstar * d, d);
+    nd = &tr->nodes[ni];
+  } else if (accepted) {
     int64_t w = 0;
     for (int64_t i = 0; i < m; ++i)
       if (p[i] < c) tmp[w++] = mem[i];
@@ -435,9 +485,11 @@ static void orc_grow_tree(const orc_forest* F, int64_t t) {
 /* Build T trees (Algorithm 3, first loop).  Trees are independent, so with
    OpenMP they are grown one per thread -- the multicore scheme of Sec. 5.3. */
 orc_forest* orc_build(const float* X, int64_t n, int32_t d, int32_t T, int32_t L,
-                      int32_t ntry, uint64_t seed, int32_t threads) {
+                      int32_t ntry, uint64_t seed, int32_t threads, int32_t split_rule) {
   if (!X || n < 1 || d < 1 || T < 1 || L < 1 || ntry < 1) return NULL;
+  if (split_rule < 0 || split_rule > 1) return NULL;
   orc_forest* F = (orc_forest*)calloc(1, sizeof(orc_forest));
+  F->split_rule = split_rule;
   F->n = n;
   F->d = d;
   F->T = T;

@@ -301,3 +301,57 @@ def test_metric_definitions_on_hand_examples():
     fd = np.array([[1.0, 2.0, 5.0], [1.0, 1.0, 2.0]])
     assert oracle.knn_distance_discrepancy(fd, td) == pytest.approx((3.5 - 3.0) / 3.0)
     assert oracle.knn_distance_discrepancy(td, td) == 0.0
+
+
+def _median_checks(F, X, exact_line=False):
+    depth_bound = 0
+    while -(-F.n // 2 ** depth_bound) > F.L:  # ceil(n / 2^k) > L
+        depth_bound += 1
+    for t in range(F.T):
+        perm = F.perm(t)
+        assert np.array_equal(np.sort(perm), np.arange(F.n))
+        nd = F.nodes(t)
+        assert nd["depth"][nd["leaf"] == 1].max() <= depth_bound
+        for i in np.where(nd["leaf"] == 0)[0]:
+            b, m = nd["begin"][i], nd["len"][i]
+            nl = nd["len"][nd["left"][i]]
+            assert nl == m // 2  # halving, rank splits included
+            if nd["flag"][i]:
+                continue
+            r = F.node_dir(t, i)
+            mem = perm[b:b + m]
+            p = X[mem].astype(np.float64) @ r
+            c = nd["c"][i]
+            if exact_line:  # d = 1: the products are exact, so is the order
+                order = np.lexsort((mem, p))
+                assert set(mem[order[:nl]]) == set(mem[:nl])
+                assert c == p[order[nl]]
+            else:
+                tol = 4 * X.shape[1] * 2.0 ** -53 * np.abs(X[mem]).astype(np.float64).sum(1).max()
+                assert p[:nl].max() <= c + tol and p[nl:].min() >= c - tol
+                assert abs(p[nl:].min() - c) <= tol  # c is the first right point's
+
+
+def test_median_rule_halves_every_split_at_the_median():
+    X = synth.make("aniso20_d64", n=3000)
+    F = oracle.Forest(X, 3, 40, 4, seed=1, split_rule=1)
+    _median_checks(F, X)
+    # the uniform rule on the same data is generally deeper than the halving bound
+    assert oracle.Forest(X, 3, 40, 4, seed=1).nodes(0)["depth"].max() >= \
+        F.nodes(0)["depth"].max()
+
+
+def test_median_rule_on_a_line_with_many_ties():
+    rng = np.random.default_rng(5)
+    X = rng.integers(0, 40, size=(2000, 1)).astype(np.float32)
+    F = oracle.Forest(X, 3, 30, 2, seed=2, split_rule=1)
+    _median_checks(F, X, exact_line=True)
+
+
+def test_median_rule_identical_points_take_rank_splits():
+    X = np.full((500, 3), 1.5, np.float32)
+    F = oracle.Forest(X, 2, 20, 3, seed=0, split_rule=1)
+    for t in range(2):
+        nd = F.nodes(t)
+        assert np.all(nd["flag"][nd["leaf"] == 0] == 1)
+    _median_checks(F, X)
