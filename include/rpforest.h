@@ -51,7 +51,11 @@ typedef struct {
   int32_t n_try;      /* nTry in [1, 64]: candidate directions per node; the one  */
                       /* with the largest projected dispersion wins (Algorithm 2). */
                       /* 1 = the basic rpTree.                                    */
-  int32_t split_rule; /* 0 = c uniform on [min, max] of the projections (Sec. 2). */
+  int32_t split_rule; /* 0 = c uniform on [min, max] of the projections (Sec. 2);
+                         1 = the median (Sec. 2's other usual split point): the
+                         floor(m/2) points smallest in (projection, point index)
+                         order go left, c = the first right point's projection,
+                         so queries go left iff their projection is below c. */
   int32_t form;       /* leaf distance tiles: 0 = plain FP32 SIMT; 1 = BF16       */
                       /* tensor-core Gram + exact FP32 re-rank of a shortlist.    */
                       /* Both return identical lists.                             */

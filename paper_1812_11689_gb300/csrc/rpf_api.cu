@@ -112,7 +112,7 @@ int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* s
   *out = nullptr;
   if (!X || !p || n < 1 || d < 1 || d > RPF_MAX_D) return RPF_EINVAL;
   if (p->n_trees < 1 || p->leaf_max < 1 || p->leaf_max > RPF_MAX_LEAF || p->n_try < 1 || p->n_try > RPF_MAX_TRY) return RPF_EINVAL;
-  if (p->split_rule != 0 || p->form < 0 || p->form > 1 || p->growth < 0 || p->growth > 2)
+  if (p->split_rule < 0 || p->split_rule > 1 || p->form < 0 || p->form > 1 || p->growth < 0 || p->growth > 2)
     return RPF_EINVAL;
   if (n * (int64_t)p->n_trees >= ((int64_t)1 << 31)) return RPF_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;

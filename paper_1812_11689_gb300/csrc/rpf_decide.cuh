@@ -156,3 +156,25 @@ __device__ __forceinline__ void rpf_side_thresholds(double c, double base, doubl
   *tl = __double2float_rd(__dsub_rd(__dsub_rd(c, base), rad));
   *tr = __double2float_ru(__dadd_ru(__dsub_ru(c, base), rad));
 }
+
+// Median rule: order-preserving key of p64 (+0.0 for -0.0, so that equal
+// projections get equal keys)
+__device__ __forceinline__ unsigned long long rpf_mkey(double p) {
+  return rpf_dkey(__dadd_rn(p, 0.0));
+}
+
+// Median rule: digit of radix pass `pass` (8 passes over the 64-bit order-
+// preserving key of p64, then 4 over the point index among equal keys) and
+// whether the point matches the prefix selected so far.
+__device__ __forceinline__ bool rpf_med_digit(int pass, unsigned long long key, uint32_t id,
+                                              unsigned long long pk, uint32_t pid, int* dig) {
+  if (pass < 8) {
+    const int sh = 56 - 8 * pass;
+    *dig = (int)((key >> sh) & 255ull);
+    return pass == 0 || ((key ^ pk) >> (sh + 8)) == 0ull;
+  }
+  const int sh = 24 - 8 * (pass - 8);
+  *dig = (int)((id >> sh) & 255u);
+  return key == pk && (pass == 8 || ((id ^ pid) >> (sh + 8)) == 0u);
+}
+

@@ -51,6 +51,11 @@ struct Level {
   double *fr_mu{}, *fr_min{}, *fr_max{};
   float *fr_tl{}, *fr_tr{}, *fr_rad{}, *fr_wlo{}, *fr_whi{};
   unsigned long long *fr_akey{}, *fr_bkey{};
+  // median rule: selected key, point index and remaining rank per node, and
+  // a 256-bin histogram per node for the radix passes
+  unsigned long long* md_key{};
+  uint32_t* md_id{};
+  int32_t *md_rank{}, *md_hist{};
   int32_t *ch_node[2]{}, *ch_start[2]{}, *ch_len[2]{};
   int32_t *ch_nleft{}, *ch_loff{};
   double *cp_sum{}, *cp_min{}, *cp_max{};
@@ -443,21 +448,127 @@ __global__ void k_csum_nodes(int pass, int F, int ntry, const int32_t* fr_cb, co
 }
 
 // Split point (Algorithm 1) and node record; certified side thresholds.
-__global__ void k_split_a(int F, int ntry, uint64_t seed, const int32_t* fr_node,
+// ---------------------------------------------------------------------------
+// Median rule (split_rule 1, Sec. 2's other usual split point): the floor(m/2)
+// points smallest in (p64 of the winning try, point index) order go left and
+// c is the p64 of the first point that goes right.  The rank-floor(m/2)
+// element is found by radix selection over the order-preserving 64-bit key of
+// p64 (8 passes of 8 bits) and then over the point index among equal keys
+// (4 passes): per pass every chunk adds its shared-memory histogram of the
+// keys that match the node's prefix so far into the node's 256 bins, and one
+// warp per node picks the digit that holds the remaining rank.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_med_p64(
+    const int32_t* ch_node, const int32_t* ch_start, const int32_t* ch_len, const int32_t* fr_tree,
+    const int32_t* fr_begin, const int32_t* fr_exact, const int32_t* fr_jstar, const float* X,
+    const int32_t* perm_cur, int64_t n, int64_t Tn, int d, int ntry, const double* dir64,
+    double* p64) {
+  const int c = blockIdx.x;
+  const int f = ch_node[c];
+  const int js = fr_jstar[f];
+  if (js < 0 || fr_exact[f]) return;  // exact nodes hold every try's p64 already
+  const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
+  const double* r = dir64 + ((int64_t)f * ntry + js) * d;
+  for (int i = threadIdx.x; i < ch_len[c]; i += blockDim.x)
+    p64[(int64_t)js * Tn + base + i] = rpf_p64(X + (int64_t)perm_cur[base + i] * d, r, d);
+}
+
+__global__ void k_med_init(int F, const int32_t* fr_len, unsigned long long* md_key,
+                           uint32_t* md_id, int32_t* md_rank) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  md_key[f] = 0ull;
+  md_id[f] = 0u;
+  md_rank[f] = fr_len[f] >> 1;
+}
+
+__global__ void __launch_bounds__(kBlock) k_med_hist(
+    int pass, const int32_t* ch_node, const int32_t* ch_start, const int32_t* ch_len,
+    const int32_t* fr_tree, const int32_t* fr_begin, const int32_t* fr_jstar,
+    const int32_t* perm_cur, int64_t n, int64_t Tn, const double* p64,
+    const unsigned long long* md_key, const uint32_t* md_id, int32_t* md_hist) {
+  __shared__ int h[256];
+  const int c = blockIdx.x;
+  const int f = ch_node[c];
+  const int js = fr_jstar[f];
+  if (js < 0) return;  // rank split: no median
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
+  const unsigned long long pk = md_key[f];
+  const uint32_t pid = md_id[f];
+  for (int i = threadIdx.x; i < ch_len[c]; i += blockDim.x) {
+    int dig;
+    const unsigned long long key = rpf_mkey(p64[(int64_t)js * Tn + base + i]);
+    if (rpf_med_digit(pass, key, (uint32_t)perm_cur[base + i], pk, pid, &dig))
+      atomicAdd(&h[dig], 1);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < 256; b += blockDim.x)
+    if (h[b]) atomicAdd(&md_hist[(int64_t)f * 256 + b], h[b]);
+}
+
+// one warp per node: the digit whose bin holds the remaining rank; the bins
+// are cleared for the next pass
+__global__ void __launch_bounds__(128) k_med_select(int pass, int F, const int32_t* fr_jstar,
+                                                    unsigned long long* md_key, uint32_t* md_id,
+                                                    int32_t* md_rank, int32_t* md_hist) {
+  const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (f >= F || fr_jstar[f] < 0) return;  // whole warp
+  int32_t* hb = md_hist + (int64_t)f * 256 + 8 * lane;
+  int v[8], sum = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    v[q] = hb[q];
+    sum += v[q];
+  }
+  int x = sum;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(RPF_FULL, x, off);
+    if (lane >= off) x += y;
+  }
+  const int pre = x - sum;
+  const int rank = md_rank[f];
+  if (rank >= pre && rank < pre + sum) {  // exactly one lane holds the rank
+    int cum = pre, dig = -1;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (dig < 0) {
+        if (rank < cum + v[q]) dig = 8 * lane + q;
+        else cum += v[q];
+      }
+    }
+    md_rank[f] = rank - cum;
+    if (pass < 8) md_key[f] |= (unsigned long long)dig << (56 - 8 * pass);
+    else md_id[f] |= (uint32_t)dig << (24 - 8 * (pass - 8));
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) hb[q] = 0;
+}
+
+__global__ void k_split_a(int F, int ntry, uint64_t seed, int median, const int32_t* fr_node,
                           const int32_t* fr_tree, const uint64_t* fr_key, const int32_t* fr_exact,
                           const int32_t* fr_jstar, const double* fr_a, const double* fr_b,
-                          const double* fr_base, const float* fr_rad, double* fr_c,
-                          int32_t* fr_flag, float* fr_tl, float* fr_tr, int32_t* node_jstar,
-                          int32_t* node_flag, double* node_c) {
+                          const double* fr_base, const float* fr_rad,
+                          const unsigned long long* md_key, double* fr_c, int32_t* fr_flag,
+                          float* fr_tl, float* fr_tr, int32_t* node_jstar, int32_t* node_flag,
+                          double* node_c) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= F) return;
   const int js = fr_jstar[f];
   double c = NAN;
-  const int acc =
-      js >= 0 ? rpf_split_point(seed, (uint64_t)fr_tree[f], fr_key[f], fr_a[f], fr_b[f], &c) : 0;
+  int acc = 0;
+  if (js >= 0 && median) {  // c = the p64 of the first point that goes right
+    c = rpf_dkey_inv(md_key[f]);
+    acc = 1;
+  } else if (js >= 0) {
+    acc = rpf_split_point(seed, (uint64_t)fr_tree[f], fr_key[f], fr_a[f], fr_b[f], &c);
+  }
   fr_c[f] = c;
   fr_flag[f] = acc ? 0 : 1;
-  if (acc && !fr_exact[f]) {
+  if (acc && !median && !fr_exact[f]) {
     float tl, tr;
     rpf_side_thresholds(c, fr_base[(int64_t)f * ntry + js], (double)fr_rad[f], &tl, &tr);
     fr_tl[f] = tl;
@@ -474,8 +585,8 @@ __global__ void __launch_bounds__(kBlock) k_side_count(
     const int32_t* fr_begin, const int32_t* fr_len, const int32_t* fr_exact,
     const int32_t* fr_jstar, const int32_t* fr_flag, const double* fr_c, const float* fr_tl,
     const float* fr_tr, const float* X, const int32_t* perm_cur, int64_t n, int64_t Tn, int d,
-    int ntry, const float* p32, const double* p64, const double* dir64, uint8_t* side,
-    int32_t* ch_nleft) {
+    int ntry, const float* p32, const double* p64, const double* dir64, int median,
+    const unsigned long long* md_key, const uint32_t* md_id, uint8_t* side, int32_t* ch_nleft) {
   const int c = blockIdx.x;
   const int f = ch_node[c];
   const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
@@ -491,6 +602,10 @@ __global__ void __launch_bounds__(kBlock) k_side_count(
     bool left;
     if (flag) {
       left = (ch_start[c] + i) < (m >> 1);
+    } else if (median) {  // (key, index) below the median element's
+      const unsigned long long key = rpf_mkey(p64[(int64_t)js * Tn + base + i]);
+      left = key < md_key[f] ||
+             (key == md_key[f] && (uint32_t)perm_cur[base + i] < md_id[f]);
     } else if (exact) {
       left = p64[(int64_t)js * Tn + base + i] < cc;
     } else {
@@ -841,6 +956,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
   const int d = fo->d;
   const int T = fo->prm.n_trees, L = fo->prm.leaf_max, ntry = fo->prm.n_try;
   const int exact_only = fo->prm.growth == 1 ? 1 : 0;
+  const int median = fo->prm.split_rule == 1 ? 1 : 0;  // split at the median (Sec. 2)
   const uint64_t seed = fo->prm.seed;
   const int64_t Tn = (int64_t)T * n;
   // nodes of at most `sub` points grow inside one CTA (phase B); when its
@@ -870,7 +986,8 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
                   lv.fr_c, lv.fr_base, lv.fr_mu, lv.fr_min, lv.fr_max, lv.fr_tl, lv.fr_tr,
                   lv.fr_rad, lv.fr_wlo, lv.fr_whi, lv.fr_akey, lv.fr_bkey, lv.ch_nleft, lv.ch_loff,
                   lv.cp_sum, lv.cp_min, lv.cp_max, lv.cp_s1, lv.cp_s2, lv.cp_a, lv.cp_min32,
-                  lv.cp_max32, lv.cp_rad, lv.dir64, lv.dir32};
+                  lv.cp_max32, lv.cp_rad, lv.dir64, lv.dir32, lv.md_key, lv.md_id, lv.md_rank,
+                  lv.md_hist};
     for (void* p : ps) rpf_release(p, s);
     for (int q = 0; q < 2; ++q) {
       void* qs[] = {lv.fr_node[q], lv.fr_tree[q], lv.fr_begin[q], lv.fr_len[q], lv.fr_cb[q],
@@ -1027,6 +1144,10 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
         if ((r = grow_buf(pp, 0, nf, s, false))) return r;
       if ((r = grow_buf(&lv.fr_akey, 0, nf, s, false))) return r;
       if ((r = grow_buf(&lv.fr_bkey, 0, nf, s, false))) return r;
+      if ((r = grow_buf(&lv.md_key, 0, nf, s, false))) return r;
+      if ((r = grow_buf(&lv.md_id, 0, nf, s, false))) return r;
+      if ((r = grow_buf(&lv.md_rank, 0, nf, s, false))) return r;
+      if ((r = grow_buf(&lv.md_hist, 0, nf * 256, s, false))) return r;
       lv.cap_f = nf;
     }
     if (F * ntry > lv.cap_dir) {
@@ -1152,14 +1273,29 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     }
     RPF_LAUNCH("k_count_exact", s,
                k_count_exact<<<nblk(F, 256), 256, 0, s>>>(Fi, lv.fr_exact, d_exact));
+    if (median) {
+      RPF_LAUNCH("k_med_p64", s, k_med_p64<<<Ci, kBlock, 0, s>>>(
+          ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, lv.fr_jstar, fo->X, perm_cur,
+          n, Tn, d, ntry, lv.dir64, p64));
+      RPF_LAUNCH("k_med_init", s, k_med_init<<<nblk(F, 128), 128, 0, s>>>(
+          Fi, fr_len, lv.md_key, lv.md_id, lv.md_rank));
+      RPF_TRYCU(cudaMemsetAsync(lv.md_hist, 0, sizeof(int32_t) * 256 * (size_t)F, s));
+      for (int pass = 0; pass < 12; ++pass) {
+        RPF_LAUNCH("k_med_hist", s, k_med_hist<<<Ci, kBlock, 0, s>>>(
+            pass, ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_jstar, perm_cur, n, Tn, p64,
+            lv.md_key, lv.md_id, lv.md_hist));
+        RPF_LAUNCH("k_med_select", s, k_med_select<<<nblk(F * 32, 128), 128, 0, s>>>(
+            pass, Fi, lv.fr_jstar, lv.md_key, lv.md_id, lv.md_rank, lv.md_hist));
+      }
+    }
     RPF_LAUNCH("k_split_a", s, k_split_a<<<nblk(F, 128), 128, 0, s>>>(
-        Fi, ntry, seed, fr_node, fr_tree, fr_key, lv.fr_exact, lv.fr_jstar, lv.fr_a, lv.fr_b,
-        lv.fr_base, lv.fr_rad, lv.fr_c, lv.fr_flag, lv.fr_tl, lv.fr_tr, fo->node_jstar,
-        fo->node_flag, fo->node_c));
+        Fi, ntry, seed, median, fr_node, fr_tree, fr_key, lv.fr_exact, lv.fr_jstar, lv.fr_a,
+        lv.fr_b, lv.fr_base, lv.fr_rad, lv.md_key, lv.fr_c, lv.fr_flag, lv.fr_tl, lv.fr_tr,
+        fo->node_jstar, fo->node_flag, fo->node_c));
     RPF_LAUNCH("k_side_count", s, k_side_count<<<Ci, kBlock, 0, s>>>(
         ch_node, ch_start, ch_len, fr_tree, fr_begin, fr_len, lv.fr_exact, lv.fr_jstar,
         lv.fr_flag, lv.fr_c, lv.fr_tl, lv.fr_tr, fo->X, perm_cur, n, Tn, d, ntry, p32, p64,
-        lv.dir64, side, lv.ch_nleft));
+        lv.dir64, median, lv.md_key, lv.md_id, side, lv.ch_nleft));
     RPF_LAUNCH("k_node_scan", s, k_node_scan<<<nblk(F, 128), 128, 0, s>>>(
         Fi, n_nodes, fr_node, fr_tree, fr_begin, fr_len, fr_key, fr_cb, fr_nc, lv.ch_nleft,
         lv.ch_loff, lv.fr_nl, fo->node_key, fo->node_tree, fo->node_begin, fo->node_len,

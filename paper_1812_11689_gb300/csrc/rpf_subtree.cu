@@ -43,6 +43,9 @@ struct SubState {
   unsigned long long akey, bkey;
   int top, next_id, id_end, next_leaf, leaf_end;
   int leafL, leafR, err, ncand;
+  unsigned long long mkey;  // median rule: key, point index and rank being selected
+  uint32_t mid;
+  int mrank;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -98,7 +101,8 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     const int32_t* it_node, const int32_t* it_tree, const int32_t* it_begin, const int32_t* it_len,
     const uint64_t* it_key, const int32_t* it_nbase, const int32_t* it_lbase,
     const float* __restrict__ X, const float* __restrict__ xnorm, int64_t n, int64_t Tn, int d,
-    int ntry, int L, uint64_t seed, int exact_only, int32_t* perm_final, float* p32, double* p64,
+    int ntry, int L, uint64_t seed, int exact_only, int median, int32_t* perm_final, float* p32,
+    double* p64,
     uint64_t* node_key, int32_t* node_tree, int32_t* node_begin, int32_t* node_len,
     int32_t* node_left, int32_t* node_right, int32_t* node_jstar, int32_t* node_flag,
     double* node_c, int32_t* leaf_tree, int32_t* leaf_begin, int32_t* leaf_len,
@@ -126,6 +130,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
   __shared__ int st_nb[kStack], st_m[kStack], st_id[kStack];
   __shared__ uint64_t st_key[kStack];
   __shared__ int wsc[kB / 32];
+  __shared__ int mhist[256];  // median rule: radix histogram
   __shared__ int tile_tot;
 
   const int it = blockIdx.x;
@@ -302,7 +307,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
         }
       }
       __syncthreads();
-    } else {
+    } else if (!median) {
       // exact min / max among the candidates the bound leaves: compact the
       // candidates, then one warp evaluates their canonical FP64 projections
       // (FP64 warp instructions are expensive whatever the active lanes)
@@ -352,14 +357,79 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
       __syncthreads();
     }
 
+    // 5m. median rule (Sec. 2's other usual split point): the floor(m/2)
+    // points smallest in (p64 of the winner, point index) order go left.  The
+    // rank-floor(m/2) element is found by radix selection in shared memory:
+    // 8 passes over the order-preserving key of p64, 4 over the point index
+    // among equal keys; warp 0 picks the digit that holds the remaining rank.
+    if (median && S.js >= 0) {
+      const int js = S.js;
+      double* pj = p64 + (int64_t)js * Tn + pbase + nb;
+      if (!S.exact)
+        for (int i = tid; i < m; i += kB) pj[i] = rpf_p64(X + (int64_t)sP[nb + i] * d, r64 + js * d, d);
+      if (tid == 0) {
+        S.mkey = 0ull;
+        S.mid = 0u;
+        S.mrank = m >> 1;
+      }
+      __syncthreads();
+      for (int pass = 0; pass < 12; ++pass) {
+        for (int b = tid; b < 256; b += kB) mhist[b] = 0;
+        __syncthreads();
+        const unsigned long long pk = S.mkey;
+        const uint32_t pid = S.mid;
+        for (int i = tid; i < m; i += kB) {
+          int dig;
+          if (rpf_med_digit(pass, rpf_mkey(pj[i]), (uint32_t)sP[nb + i], pk, pid, &dig))
+            atomicAdd(&mhist[dig], 1);
+        }
+        __syncthreads();
+        if (warp == 0) {
+          int v[8], sum = 0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            v[q] = mhist[8 * lane + q];
+            sum += v[q];
+          }
+          int x = sum;
+#pragma unroll
+          for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(RPF_FULL, x, off);
+            if (lane >= off) x += y;
+          }
+          const int pre = x - sum, rank = S.mrank;
+          if (rank >= pre && rank < pre + sum) {
+            int cum = pre, dig = -1;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              if (dig < 0) {
+                if (rank < cum + v[q]) dig = 8 * lane + q;
+                else cum += v[q];
+              }
+            }
+            S.mrank = rank - cum;
+            if (pass < 8) S.mkey = pk | ((unsigned long long)dig << (56 - 8 * pass));
+            else S.mid = pid | ((uint32_t)dig << (24 - 8 * (pass - 8)));
+          }
+        }
+        __syncthreads();
+      }
+    }
+
     // 5. split point and node record
     if (tid == 0) {
       const int js = S.js;
       double c = NAN;
-      const int acc = js >= 0 ? rpf_split_point(seed, (uint64_t)t, key, S.a, S.b, &c) : 0;
+      int acc = 0;
+      if (js >= 0 && median) {  // c = the p64 of the first point that goes right
+        c = rpf_dkey_inv(S.mkey);
+        acc = 1;
+      } else if (js >= 0) {
+        acc = rpf_split_point(seed, (uint64_t)t, key, S.a, S.b, &c);
+      }
       S.c = c;
       S.flag = acc ? 0 : 1;
-      if (acc && !S.exact) {
+      if (acc && !median && !S.exact) {
         float tl, tr;
         rpf_side_thresholds(c, sbase[js], (double)S.rad, &tl, &tr);
         S.tl = tl;
@@ -382,6 +452,9 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
         int left;
         if (flag) {
           left = i < (m >> 1);
+        } else if (median) {  // (key, index) below the median element's
+          const unsigned long long k = rpf_mkey(p64[(int64_t)js * Tn + pbase + nb + i]);
+          left = k < S.mkey || (k == S.mkey && (uint32_t)sP[nb + i] < S.mid);
         } else if (exact) {
           left = p64[(int64_t)js * Tn + pbase + nb + i] < c;
         } else {
@@ -537,6 +610,7 @@ int rpf_grow_subtrees(rpf_forest* fo, int64_t n_items, const int32_t* it_node,
   const int d = fo->d, ntry = fo->prm.n_try, L = fo->prm.leaf_max;
   const int64_t n = fo->n, Tn = n * fo->prm.n_trees;
   const int exact_only = fo->prm.growth == 1 ? 1 : 0;
+  const int median = fo->prm.split_rule == 1 ? 1 : 0;
   const int TG = ntry <= 5 ? ntry : 8;
   const size_t smem = sub_layout(d, ntry, TG).total;
   if (smem > 200 * 1024) return RPF_EINVAL;
@@ -545,7 +619,8 @@ int rpf_grow_subtrees(rpf_forest* fo, int64_t n_items, const int32_t* it_node,
     cudaFuncSetAttribute(k_subtree<TGV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     RPF_LAUNCH("k_subtree", s, k_subtree<TGV><<<(unsigned)n_items, kB, smem, s>>>(                \
         it_node, it_tree, it_begin, it_len, it_key, it_nbase, it_lbase, fo->X, fo->xnorm, n, Tn,  \
-        d, ntry, L, fo->prm.seed, exact_only, fo->perm, p32, p64, fo->node_key, fo->node_tree,    \
+        d, ntry, L, fo->prm.seed, exact_only, median, fo->perm, p32, p64, fo->node_key,          \
+        fo->node_tree,                                                                            \
         fo->node_begin, fo->node_len, fo->node_left, fo->node_right, fo->node_jstar,              \
         fo->node_flag, fo->node_c, fo->leaf_tree, fo->leaf_begin, fo->leaf_len, d_exact, d_err)); \
   } while (0)

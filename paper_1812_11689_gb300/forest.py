@@ -16,6 +16,7 @@ from ._lib import check, rpf_params
 
 FORM_PLAIN, FORM_CHOSEN = 0, 1
 GROWTH_DEFAULT, GROWTH_FP64, GROWTH_CERTIFIED = 0, 1, 2
+SPLIT_UNIFORM, SPLIT_MEDIAN = 0, 1
 
 
 def _stream_handle(stream) -> int:
@@ -52,10 +53,10 @@ class Forest:
 
     def __init__(self, X, n_trees: int = 10, leaf_max: int = 50, n_try: int = 5,
                  form: int = FORM_PLAIN, growth: int = GROWTH_DEFAULT, seed: int = 0,
-                 stream=None):
+                 stream=None, split_rule: int = SPLIT_UNIFORM):
         X = _as_points(X)
         self.n, self.d = int(X.shape[0]), int(X.shape[1])
-        self.params = rpf_params(n_trees, leaf_max, n_try, 0, form, growth, seed)
+        self.params = rpf_params(n_trees, leaf_max, n_try, split_rule, form, growth, seed)
         h = ctypes.c_void_p()
         check(_lib.lib().rpf_build(_ptr(X), self.n, self.d, ctypes.byref(self.params),
                                    _stream_handle(stream), ctypes.byref(h)), "rpf_build")

@@ -53,7 +53,7 @@ def test_build_rejects_bad_arguments_before_touching_the_gpu(L):
     assert L.rpf_build(buf, 10, 0, ctypes.byref(p), None, ctypes.byref(out)) == -1
     assert L.rpf_build(buf, 10, 2, ctypes.byref(p), None, None) == -1
     for bad in (dict(n_trees=0), dict(leaf_max=0), dict(leaf_max=1025), dict(n_try=0), dict(n_try=65),
-                dict(form=2), dict(growth=3), dict(split_rule=1)):
+                dict(form=2), dict(growth=3), dict(split_rule=2), dict(split_rule=-1)):
         q = _lib.rpf_params(10, 50, 5, 0, 0, 0, 0)
         for k, v in bad.items():
             setattr(q, k, v)

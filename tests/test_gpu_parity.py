@@ -376,3 +376,45 @@ def test_chosen_form_degenerate_and_extreme_scales(case):
     c = gpu_forest(X, 3, 64, 3, seed=2, form=1)
     ci, cd = c.all_knn(10)
     assert np.array_equal(ci.cpu().numpy(), oi) and np.array_equal(cd.cpu().numpy(), od)
+
+
+def _median_forest(X, T, L, ntry, seed=0, growth=0, form=0):
+    from paper_1812_11689_gb300 import forest
+    return F(torch.from_numpy(np.ascontiguousarray(X)).cuda(), n_trees=T, leaf_max=L, n_try=ntry,
+             seed=seed, growth=growth, form=form, split_rule=forest.SPLIT_MEDIAN)
+
+
+@pytest.mark.parametrize("name,n,L,ntry", [("mix5_d10", 2000, 50, 5),
+                                           ("aniso20_d64", 30000, 128, 5),
+                                           ("student3_d32", 20000, 64, 3)])
+def test_median_rule_trees_and_all_knn_bit_exact(name, n, L, ntry):
+    # the level-synchronous phase (nodes > 4096 points) and the CTA subtrees
+    # both select the median by radix passes; both growth modes
+    X = synth.make(name, n=n)
+    o = oracle.Forest(X, 4, L, ntry, seed=7, split_rule=1)
+    for growth in (1, 2):
+        g = _median_forest(X, 4, L, ntry, seed=7, growth=growth)
+        compare_trees(g, o, 4)
+    oi, od = o.all_knn(10)
+    for form in (0, 1):
+        g = _median_forest(X, 4, L, ntry, seed=7, form=form)
+        gi, gd = g.all_knn(10)
+        check_knn(gi.cpu().numpy(), gd.cpu().numpy(), oi, od, X)
+
+
+def test_median_rule_ties_and_queries():
+    # integer coordinates on a line and a duplicate block: ties at the median
+    # are split by point index; queries route on the median value
+    rng = np.random.default_rng(9)
+    X1 = rng.integers(0, 40, size=(12000, 1)).astype(np.float32)
+    o = oracle.Forest(X1, 3, 30, 2, seed=2, split_rule=1)
+    compare_trees(_median_forest(X1, 3, 30, 2, seed=2), o, 3)
+    X = synth.make("mix50_d96", n=9000)
+    X[100:700] = X[3]
+    o = oracle.Forest(X, 3, 64, 3, seed=4, split_rule=1)
+    g = _median_forest(X, 3, 64, 3, seed=4)
+    compare_trees(g, o, 3)
+    Q = synth.queries("mix50_d96", 300, stream=31)
+    qi, qd = g.query(torch.from_numpy(Q).cuda(), 10)
+    oi, od = o.query(Q, 10)
+    assert np.array_equal(qi.cpu().numpy(), oi) and np.array_equal(qd.cpu().numpy(), od)
