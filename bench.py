@@ -493,6 +493,7 @@ def run_gb300(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_sweep:
         line["ensemble_sweep"] = run_sweep(args, dev)
         line["n_try_ablation"] = run_ntry_ablation(args, dev)
+        line["split_rules"] = run_split_rules(args, dev)
     if rank == 0 and world == 1 and not args.no_serve:
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -692,6 +693,49 @@ def run_ntry_ablation(args, dev, rows=2000):
                         "max_depth": info["max_depth"]})
             f.close()
         out[name] = {"n_trees": T, "leaf_max": w.leaf_max, "k": w.k, "by_n_try": res,
+                     "sample": "%d points vs exact brute force" % rows}
+    return out
+
+
+def run_split_rules(args, dev, rows=2000):
+    """Split rules (Sec. 2): c uniform on [min, max] of the projections
+    against the median, on the anisotropic (T = 40) and heavy-tailed (T = 32)
+    workloads -- build time, depth, all-kNN time, missing rate."""
+    import torch
+    from paper_1812_11689_gb300 import forest, synth
+    out = {}
+    for name, T in (("aniso20_d64", 40), ("student3_d32", 32)):
+        w = synth.WORKLOADS[name]
+        X = torch.from_numpy(synth.make(name, seed=args.seed)).to(dev)
+        r = torch.from_numpy(np.sort(np.random.default_rng(5).choice(w.n, rows, replace=False))
+                             .astype(np.int32)).to(dev)
+        bi, bd = forest.brute_knn(X, X[r.long()].contiguous(), w.k, self_idx=r)
+        bi, bd = bi.cpu().numpy(), bd.cpu().numpy()
+        res = {}
+        for rule, nm in ((forest.SPLIT_UNIFORM, "uniform"), (forest.SPLIT_MEDIAN, "median")):
+            kw = dict(n_trees=T, leaf_max=w.leaf_max, n_try=w.n_try, seed=args.seed,
+                      form=forest.FORM_CHOSEN, split_rule=rule)
+            forest.Forest(X, **kw).close()  # warm-up
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            f = forest.Forest(X, **kw)
+            e1.record()
+            i, d = f.all_knn(w.k)
+            e2.record()
+            torch.cuda.synchronize()
+            info, cnt = f.info(), f.counters()
+            ci, cd = i[r.long()].cpu().numpy(), d[r.long()].cpu().numpy()
+            res[nm] = {"build_ms": round(e0.elapsed_time(e1), 2),
+                       "all_knn_ms": round(e1.elapsed_time(e2), 2),
+                       "queries_per_s": round(w.n / (e0.elapsed_time(e2) * 1e-3), 1),
+                       "max_depth": info["max_depth"],
+                       "phase_a_levels": cnt.get("phase_a_levels"),
+                       "missing_rate": round(sum(len(set(bi[q]) - set(ci[q]))
+                                                 for q in range(rows)) / float(bi.size), 5),
+                       "knn_distance_discrepancy": discrepancy_full(cd, bd)[0]}
+            f.close()
+        out[name] = {"n_trees": T, "leaf_max": w.leaf_max, "k": w.k, "by_rule": res,
                      "sample": "%d points vs exact brute force" % rows}
     return out
 
