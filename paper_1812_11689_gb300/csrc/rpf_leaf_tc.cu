@@ -229,12 +229,12 @@ __global__ void k_pack_fill(int64_t G, int64_t nseg, const int2* slot, const int
 // The persistent chosen-form kernel
 // ---------------------------------------------------------------------------
 // ROWS = 128: one M = 128 accumulator of N <= 128 columns (128 TMEM columns,
-// up to three CTAs per SM).  ROWS = 256 (leaves of up to 256 points): two
+// up to four CTAs per SM).  ROWS = 256 (leaves of up to 256 points): two
 // M = 128 blocks (rows 0-127 and 128-255) against all N <= 256 rows, the
 // block-b accumulator at TMEM column 256 b (512 columns, one CTA per SM);
 // warp w reads lane quarter w % 4 of block w / 4.
 template <int KK, int ROWS>
-__global__ void __launch_bounds__(ROWS, ROWS == 128 ? 3 : 1) k_leaf_tc(
+__global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
     const int4* __restrict__ tiles, int64_t tlo, int64_t thi, const uint32_t* __restrict__ bits,
     int64_t nwords, const int32_t* __restrict__ perm, const float* __restrict__ X, int64_t n,
     int d, int dp, int d16, int KC, int K, int t0, uint2* cand, int* err,
@@ -539,20 +539,30 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 3 : 1) k_leaf_tc(
   }
 }
 
-size_t tc_smem(int d, int dp, int rows, int KC) {
+size_t tc_need(int d, int dp, int rows, int KC) {
   const int d4 = (d + 3) & ~3;
   const size_t a_off = (((size_t)rows * dp * 4) + 1023) & ~(size_t)1023;
-  const size_t need = a_off + (size_t)2 * rows * KC * 2 + (size_t)TC_MAX_BIG * d4 * 4 +
-                      (size_t)rows * TC_SLOTS;
-  // with 128-row tiles at least 60 KB, so that at most three CTAs (3 x 128
-  // TMEM columns) share an SM; 256-row tiles hold all 512 columns
-  return rows == 128 ? std::max<size_t>(need, 60 * 1024) : std::max<size_t>(need, 120 * 1024);
+  return a_off + (size_t)2 * rows * KC * 2 + (size_t)TC_MAX_BIG * d4 * 4 +
+         (size_t)rows * TC_SLOTS;
 }
 
-// Gram coordinates per chunk: the largest multiple of 16 (<= 128) for which
-// the CTA's shared memory fits 220 KB (the opt-in limit is 227 KB); 0 if none
+// Dynamic shared memory of a CTA.  128-row tiles: if the tile fits 52 KB,
+// at least 46 KB (four CTAs per SM, 4 x 128 TMEM columns), else at least
+// 60 KB (three CTAs); 256-row tiles hold all 512 TMEM columns (one CTA).
+size_t tc_smem(int d, int dp, int rows, int KC) {
+  const size_t need = tc_need(d, dp, rows, KC);
+  if (rows == 256) return std::max<size_t>(need, 120 * 1024);
+  return need <= 52 * 1024 ? std::max<size_t>(need, 46 * 1024) : std::max<size_t>(need, 60 * 1024);
+}
+
+// Gram coordinates per chunk (a multiple of 16, <= 128): with 128-row tiles
+// the largest that lets four CTAs share an SM, if any; otherwise the largest
+// for which the CTA fits 220 KB (the opt-in limit is 227 KB); 0 if none.
 int tc_chunk(int d, int rows) {
   const int d16 = (d + 15) & ~15, dp = ((d + 3) & ~3) + 4;
+  if (rows == 128)
+    for (int kc = std::min(d16, 128); kc >= 16; kc -= 16)
+      if (tc_need(d, dp, rows, kc) <= 52 * 1024) return kc;
   for (int kc = std::min(d16, 128); kc >= 16; kc -= 16)
     if (tc_smem(d, dp, rows, kc) <= 220 * 1024) return kc;
   return 0;
@@ -576,9 +586,9 @@ int launch_tc(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint
   cudaFuncAttributes fa;
   RPF_CU(cudaFuncGetAttributes(&fa, k_leaf_tc<KK, ROWS>));
   // CTAs per SM that shared memory allows (1 KB per CTA is reserved by the
-  // system), and that TMEM allows: three of 128 columns or one of 512
+  // system), and that TMEM allows: four of 128 columns or one of 512
   const size_t per_cta = smem + fa.sharedSizeBytes + 1024;
-  const int tmem_cap = ROWS == 128 ? 3 : 1;
+  const int tmem_cap = ROWS == 128 ? 4 : 1;
   const int occ = std::max(1, std::min(tmem_cap, (int)((size_t)smem_sm / per_cta)));
   const int64_t grid = std::min<int64_t>(thi - tlo, (int64_t)sms * occ);
   RPF_LAUNCH("k_leaf_tc", s, k_leaf_tc<KK, ROWS><<<(unsigned)grid, ROWS, smem, s>>>(
