@@ -157,6 +157,19 @@ int rpf_query_static(const rpf_forest* f, const float* Q, int64_t m, int32_t K, 
 /* Scratch bytes rpf_all_knn (for_all_knn = 1, m ignored) or rpf_query needs. */
 size_t rpf_workspace_bytes(const rpf_forest* f, int64_t m, int32_t K, int32_t for_all_knn);
 
+/*
+ * rpf_add_trees -- grow n_new more trees onto a built forest (an incremental
+ * ensemble: Sec. 5.2 studies accuracy as trees are added).  Every random
+ * draw is keyed by the tree's index, so the result is exactly the forest
+ * rpf_build would grow with T + n_new trees: trees 0..T-1 are untouched and
+ * trees T..T+n_new-1 are the ones that build would grow.  The forest's
+ * tables are reallocated (stream-ordered on `stream`); no other call may use
+ * the forest meanwhile.  Synchronises `stream` before returning.
+ * Errors: RPF_EINVAL (n_new < 1, or (T + n_new) n >= 2^31), RPF_ENOMEM,
+ * RPF_ECUDA; on an error the forest keeps its first T trees.
+ */
+int rpf_add_trees(rpf_forest* f, int32_t n_new, void* stream);
+
 /* Release the forest and its device memory.  NULL is a no-op. */
 void rpf_free(rpf_forest* f);
 

@@ -79,6 +79,46 @@ void free_forest(rpf_forest* f) {
   delete f;
 }
 
+// Node table of a forest grown in two parts (rpf_add_trees): part A (T trees,
+// Na nodes, roots at ids 0..T-1) and part B (dT trees, roots at ids
+// 0..dT-1).  Routing starts tree t at node t, so the merged table puts the
+// roots first: A's roots, B's roots, then A's other nodes, then B's.
+__device__ __forceinline__ int64_t merged_id(int64_t i, bool is_b, int T, int dT, int64_t Na) {
+  if (!is_b) return i < T ? i : i + dT;
+  return i < dT ? T + i : Na + i;
+}
+
+__global__ void k_merge_nodes(int64_t N, int is_b, int T, int dT, int64_t Na, int d,
+                              const uint64_t* key, const int32_t* tree, const int32_t* begin,
+                              const int32_t* len, const int32_t* left, const int32_t* right,
+                              const int32_t* jstar, const int32_t* flag, const double* c,
+                              const double* dir, const float* dir32, uint64_t* okey,
+                              int32_t* otree, int32_t* obegin, int32_t* olen, int32_t* oleft,
+                              int32_t* oright, int32_t* ojstar, int32_t* oflag, double* oc,
+                              double* odir, float* odir32) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t o = merged_id(i, is_b != 0, T, dT, Na);
+  okey[o] = key[i];
+  otree[o] = tree[i] + (is_b ? T : 0);
+  obegin[o] = begin[i];
+  olen[o] = len[i];
+  oleft[o] = left[i] >= 0 ? (int32_t)merged_id(left[i], is_b != 0, T, dT, Na) : -1;
+  oright[o] = right[i] >= 0 ? (int32_t)merged_id(right[i], is_b != 0, T, dT, Na) : -1;
+  ojstar[o] = jstar[i];
+  oflag[o] = flag[i];
+  oc[o] = c[i];
+  for (int k = 0; k < d; ++k) {
+    odir[o * d + k] = dir[i * d + k];
+    odir32[o * d + k] = dir32[i * d + k];
+  }
+}
+
+__global__ void k_shift_tree(int64_t N, int add, const int32_t* in, int32_t* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) out[i] = in[i] + add;
+}
+
 }  // namespace
 
 extern "C" {
@@ -155,6 +195,132 @@ int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* s
 }
 
 void rpf_free(rpf_forest* f) { free_forest(f); }
+
+int rpf_add_trees(rpf_forest* f, int32_t n_new, void* stream) {
+  if (!f || n_new < 1) return RPF_EINVAL;
+  const int T = f->prm.n_trees;
+  const int64_t n = f->n;
+  const int d = f->d;
+  if ((int64_t)(T + n_new) * n >= ((int64_t)1 << 31) || T + n_new > (1 << 20)) return RPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the new trees grow in a temporary forest over the same points (X and
+  // the norms borrowed, not owned), their draws keyed by T + t
+  rpf_forest* g = new rpf_forest();
+  g->n = n;
+  g->d = d;
+  g->prm = f->prm;
+  g->prm.n_trees = n_new;
+  g->device = f->device;
+  g->t_base = f->t_base + T;
+  g->X = f->X;
+  g->xnorm = f->xnorm;
+  g->d_err = f->d_err;
+  g->d_fallback = f->d_fallback;
+  int rc = dalloc(g, &g->perm, (size_t)n * n_new, s);
+  if (!rc) rc = rpf_grow(g, s);
+  if (rc) {
+    g->X = nullptr;
+    free_forest(g);
+    return rc;
+  }
+  // merged permutation and node / leaf tables
+  const int64_t Na = f->n_nodes, Nb = g->n_nodes, N = Na + Nb;
+  const int64_t La = f->n_leaves, Lb = g->n_leaves;
+  int32_t* perm = nullptr;
+  uint64_t* key = nullptr;
+  int32_t *tree = nullptr, *begin = nullptr, *len = nullptr, *left = nullptr, *right = nullptr,
+          *jstar = nullptr, *flag = nullptr, *ltree = nullptr, *lbegin = nullptr, *llen = nullptr;
+  double *c = nullptr, *dir = nullptr;
+  float* dir32 = nullptr;
+  void** bufs[] = {(void**)&perm, (void**)&key, (void**)&tree, (void**)&begin, (void**)&len,
+                   (void**)&left, (void**)&right, (void**)&jstar, (void**)&flag, (void**)&c,
+                   (void**)&dir, (void**)&dir32, (void**)&ltree, (void**)&lbegin,
+                   (void**)&llen};
+  const size_t sizes[] = {4 * (size_t)(T + n_new) * n, 8 * (size_t)N, 4 * (size_t)N,
+                          4 * (size_t)N, 4 * (size_t)N, 4 * (size_t)N, 4 * (size_t)N,
+                          4 * (size_t)N, 4 * (size_t)N, 8 * (size_t)N, 8 * (size_t)N * d,
+                          4 * (size_t)N * d, 4 * (size_t)(La + Lb), 4 * (size_t)(La + Lb),
+                          4 * (size_t)(La + Lb)};
+  for (int i = 0; i < 15 && !rc; ++i) rc = rpf_alloc(bufs[i], sizes[i], s);
+  if (rc) {
+    for (auto b : bufs) rpf_release(*b, s);
+    g->X = nullptr;
+    free_forest(g);
+    return RPF_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(perm, f->perm, 4 * (size_t)T * n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(perm + (size_t)T * n, g->perm, 4 * (size_t)n_new * n,
+                        cudaMemcpyDeviceToDevice, s);
+  const rpf_forest* parts[2] = {f, g};
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    const rpf_forest* q = parts[b];
+    const int64_t Nq = q->n_nodes;
+    if (Nq > 0) {
+      k_merge_nodes<<<(unsigned)((Nq + 127) / 128), 128, 0, s>>>(
+          Nq, b, T, n_new, Na, d, q->node_key, q->node_tree, q->node_begin, q->node_len,
+          q->node_left, q->node_right, q->node_jstar, q->node_flag, q->node_c, q->node_dir,
+          q->node_dir32, key, tree, begin, len, left, right, jstar, flag, c, dir, dir32);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess && La > 0)
+    e = cudaMemcpyAsync(ltree, f->leaf_tree, 4 * (size_t)La, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && Lb > 0) {
+    k_shift_tree<<<(unsigned)((Lb + 255) / 256), 256, 0, s>>>(Lb, T, g->leaf_tree, ltree + La);
+    e = cudaGetLastError();
+  }
+  const int32_t* lsrc[2][2] = {{f->leaf_begin, f->leaf_len}, {g->leaf_begin, g->leaf_len}};
+  if (e == cudaSuccess && La > 0) e = cudaMemcpyAsync(lbegin, lsrc[0][0], 4 * (size_t)La, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && La > 0) e = cudaMemcpyAsync(llen, lsrc[0][1], 4 * (size_t)La, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && Lb > 0) e = cudaMemcpyAsync(lbegin + La, lsrc[1][0], 4 * (size_t)Lb, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && Lb > 0) e = cudaMemcpyAsync(llen + La, lsrc[1][1], 4 * (size_t)Lb, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) {
+    for (auto b : bufs) rpf_release(*b, s);
+    g->X = nullptr;
+    free_forest(g);
+    return rpf_cuda_err(e);
+  }
+  // install: the old tables go back to the pool, the tile layouts are rebuilt
+  for (auto& o : f->owned)
+    if (o == f->perm) o = perm;
+  void* olds[] = {f->perm, f->node_key, f->node_tree, f->node_begin, f->node_len, f->node_left,
+                  f->node_right, f->node_jstar, f->node_flag, f->node_c, f->node_dir,
+                  f->node_dir32, f->leaf_tree, f->leaf_begin, f->leaf_len, f->tile_cnt,
+                  f->tile_off, f->tile_leaf, f->pk_tiles, f->pk_bits};
+  for (void* o : olds) rpf_release(o, s);
+  f->perm = perm;
+  f->node_key = key;
+  f->node_tree = tree;
+  f->node_begin = begin;
+  f->node_len = len;
+  f->node_left = left;
+  f->node_right = right;
+  f->node_jstar = jstar;
+  f->node_flag = flag;
+  f->node_c = c;
+  f->node_dir = dir;
+  f->node_dir32 = dir32;
+  f->leaf_tree = ltree;
+  f->leaf_begin = lbegin;
+  f->leaf_len = llen;
+  f->tile_cnt = f->tile_off = f->tile_leaf = nullptr;
+  f->pk_tiles = nullptr;
+  f->pk_bits = nullptr;
+  f->n_nodes = f->nodes_cap = N;
+  f->n_leaves = La + Lb;
+  f->n_exact += g->n_exact;
+  f->max_depth = std::max(f->max_depth, g->max_depth);
+  f->prm.n_trees = T + n_new;
+  g->X = nullptr;
+  g->xnorm = nullptr;
+  free_forest(g);  // its own tables only (X, norms and error words are f's)
+  if ((rc = rpf_build_tiles(f, s)) || (f->prm.form == 1 && (rc = rpf_build_packs(f, s))))
+    return rc;
+  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e == cudaSuccess ? RPF_OK : rpf_cuda_err(e);
+}
 
 size_t rpf_workspace_bytes(const rpf_forest* f, int64_t m, int32_t K, int32_t for_all_knn) {
   if (!f || K < 1 || K > RPF_MAX_K || m < 0) return 0;

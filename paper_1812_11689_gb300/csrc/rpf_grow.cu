@@ -107,7 +107,8 @@ __global__ void k_xnorm(const float* X, int64_t n, int d, float* out) {
 // of each node's first member o; one warp per (node, try).  The lanes draw
 // the Box-Muller pairs; the normalisation's sum and b_j keep their sequential
 // order (one lane), so r and b_j equal rpf_gen_direction / rpf_p64 bit for bit.
-__global__ void __launch_bounds__(128) k_dirs_a(int F, int ntry, int d, uint64_t seed, int64_t n,
+__global__ void __launch_bounds__(128) k_dirs_a(int F, int ntry, int d, uint64_t seed, int t_base,
+                                                int64_t n,
                                                 const int32_t* fr_tree, const int32_t* fr_begin,
                                                 const uint64_t* fr_key, const int32_t* perm_cur,
                                                 const float* X, double* dir64, float* dir32,
@@ -116,7 +117,8 @@ __global__ void __launch_bounds__(128) k_dirs_a(int F, int ntry, int d, uint64_t
   const int lane = threadIdx.x & 31;
   if (g >= (int64_t)F * ntry) return;  // whole warp
   const int f = (int)(g / ntry), j = (int)(g % ntry);
-  const uint64_t t = (uint64_t)fr_tree[f], key = fr_key[f];
+  const int tl = fr_tree[f];
+  const uint64_t t = (uint64_t)(tl + t_base), key = fr_key[f];
   double* r = dir64 + g * d;
   float* r32 = dir32 + g * d;
   for (int i = lane; 2 * i < d; i += 32) {
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(128) k_dirs_a(int F, int ntry, int d, uint64_t
   }
   __syncwarp();
   if (lane == 0) {
-    const int32_t og = perm_cur[(int64_t)t * n + fr_begin[f]];
+    const int32_t og = perm_cur[(int64_t)tl * n + fr_begin[f]];
     fr_base[g] = rpf_p64(X + (int64_t)og * d, r, d);
     if (j == 0) fr_ogid[f] = og;
   }
@@ -548,7 +550,8 @@ __global__ void __launch_bounds__(128) k_med_select(int pass, int F, const int32
   for (int q = 0; q < 8; ++q) hb[q] = 0;
 }
 
-__global__ void k_split_a(int F, int ntry, uint64_t seed, int median, const int32_t* fr_node,
+__global__ void k_split_a(int F, int ntry, uint64_t seed, int t_base, int median,
+                          const int32_t* fr_node,
                           const int32_t* fr_tree, const uint64_t* fr_key, const int32_t* fr_exact,
                           const int32_t* fr_jstar, const double* fr_a, const double* fr_b,
                           const double* fr_base, const float* fr_rad,
@@ -564,7 +567,7 @@ __global__ void k_split_a(int F, int ntry, uint64_t seed, int median, const int3
     c = rpf_dkey_inv(md_key[f]);
     acc = 1;
   } else if (js >= 0) {
-    acc = rpf_split_point(seed, (uint64_t)fr_tree[f], fr_key[f], fr_a[f], fr_b[f], &c);
+    acc = rpf_split_point(seed, (uint64_t)(fr_tree[f] + t_base), fr_key[f], fr_a[f], fr_b[f], &c);
   }
   fr_c[f] = c;
   fr_flag[f] = acc ? 0 : 1;
@@ -905,7 +908,7 @@ __global__ void k_compact_leaves(int64_t S, const int32_t* pos, const int32_t* t
 // r* of every split node (regenerated from its key and chosen try), one warp
 // per node: lanes draw the Box-Muller pairs, lane 0 forms the sequential
 // FP32 norm, so r equals rpf_gen_direction's bit for bit.
-__global__ void __launch_bounds__(128) k_node_dirs(int64_t N, int d, uint64_t seed,
+__global__ void __launch_bounds__(128) k_node_dirs(int64_t N, int d, uint64_t seed, int t_base,
                                                    const uint64_t* key, const int32_t* tree,
                                                    const int32_t* left, const int32_t* jstar,
                                                    const int32_t* flag, double* dir, float* dir32) {
@@ -921,7 +924,7 @@ __global__ void __launch_bounds__(128) k_node_dirs(int64_t N, int d, uint64_t se
     }
     return;
   }
-  const uint64_t t = (uint64_t)tree[i], kk = key[i], j = (uint64_t)jstar[i];
+  const uint64_t t = (uint64_t)(tree[i] + t_base), kk = key[i], j = (uint64_t)jstar[i];
   for (int p = lane; 2 * p < d; p += 32) {
     float g0, g1;
     rpf_gauss_pair(seed, t, kk, j, p, &g0, &g1);
@@ -1226,7 +1229,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     int32_t *ch_node = lv.ch_node[cur], *ch_start = lv.ch_start[cur], *ch_len = lv.ch_len[cur];
 
     RPF_LAUNCH("k_dirs_a", s, k_dirs_a<<<nblk(F * ntry * 32, 128), 128, 0, s>>>(
-        Fi, ntry, d, seed, n, fr_tree, fr_begin, fr_key, perm_cur, fo->X, lv.dir64, lv.dir32,
+        Fi, ntry, d, seed, fo->t_base, n, fr_tree, fr_begin, fr_key, perm_cur, fo->X, lv.dir64, lv.dir32,
         lv.fr_base, lv.fr_ogid));
 #define RPF_PROJ_A(TGV)                                                                          \
   do {                                                                                           \
@@ -1289,7 +1292,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
       }
     }
     RPF_LAUNCH("k_split_a", s, k_split_a<<<nblk(F, 128), 128, 0, s>>>(
-        Fi, ntry, seed, median, fr_node, fr_tree, fr_key, lv.fr_exact, lv.fr_jstar, lv.fr_a,
+        Fi, ntry, seed, fo->t_base, median, fr_node, fr_tree, fr_key, lv.fr_exact, lv.fr_jstar, lv.fr_a,
         lv.fr_b, lv.fr_base, lv.fr_rad, lv.md_key, lv.fr_c, lv.fr_flag, lv.fr_tl, lv.fr_tr,
         fo->node_jstar, fo->node_flag, fo->node_c));
     RPF_LAUNCH("k_side_count", s, k_side_count<<<Ci, kBlock, 0, s>>>(
@@ -1420,7 +1423,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
       return RPF_ENOMEM;
     }
     RPF_LAUNCH("k_node_dirs", s, k_node_dirs<<<nblk((int64_t)total * 32, 128), 128, 0, s>>>(
-        total, d, seed, fo->node_key, fo->node_tree, fo->node_left, fo->node_jstar, fo->node_flag,
+        total, d, seed, fo->t_base, fo->node_key, fo->node_tree, fo->node_left, fo->node_jstar, fo->node_flag,
         fo->node_dir, fo->node_dir32));
 
     // leaves: keep the used slots (len > 0) in slot order

@@ -188,6 +188,10 @@ struct rpf_forest {
   int64_t n = 0;
   int32_t d = 0;
   rpf_params prm{};
+  // global index of the forest's first tree: the random draws of tree t use
+  // t_base + t (0 for a build; the current tree count while rpf_add_trees
+  // grows new trees into a temporary forest)
+  int32_t t_base = 0;
   int device = 0;
 
   float* X = nullptr;         // n x d

@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     const int32_t* it_node, const int32_t* it_tree, const int32_t* it_begin, const int32_t* it_len,
     const uint64_t* it_key, const int32_t* it_nbase, const int32_t* it_lbase,
     const float* __restrict__ X, const float* __restrict__ xnorm, int64_t n, int64_t Tn, int d,
-    int ntry, int L, uint64_t seed, int exact_only, int median, int32_t* perm_final, float* p32,
+    int ntry, int L, uint64_t seed, int t_base, int exact_only, int median, int32_t* perm_final,
+    float* p32,
     double* p64,
     uint64_t* node_key, int32_t* node_tree, int32_t* node_begin, int32_t* node_len,
     int32_t* node_left, int32_t* node_right, int32_t* node_jstar, int32_t* node_flag,
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     for (int idx = tid; idx < ntry * npairs; idx += kB) {
       const int j = idx / npairs, i = idx - j * npairs;
       float g0, g1;
-      rpf_gauss_pair(seed, (uint64_t)t, key, (uint64_t)j, i, &g0, &g1);
+      rpf_gauss_pair(seed, (uint64_t)(t + t_base), key, (uint64_t)j, i, &g0, &g1);
       r32[j * d + 2 * i] = g0;
       if (2 * i + 1 < d) r32[j * d + 2 * i + 1] = g1;
     }
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
         c = rpf_dkey_inv(S.mkey);
         acc = 1;
       } else if (js >= 0) {
-        acc = rpf_split_point(seed, (uint64_t)t, key, S.a, S.b, &c);
+        acc = rpf_split_point(seed, (uint64_t)(t + t_base), key, S.a, S.b, &c);
       }
       S.c = c;
       S.flag = acc ? 0 : 1;
@@ -619,7 +620,8 @@ int rpf_grow_subtrees(rpf_forest* fo, int64_t n_items, const int32_t* it_node,
     cudaFuncSetAttribute(k_subtree<TGV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     RPF_LAUNCH("k_subtree", s, k_subtree<TGV><<<(unsigned)n_items, kB, smem, s>>>(                \
         it_node, it_tree, it_begin, it_len, it_key, it_nbase, it_lbase, fo->X, fo->xnorm, n, Tn,  \
-        d, ntry, L, fo->prm.seed, exact_only, median, fo->perm, p32, p64, fo->node_key,          \
+        d, ntry, L, fo->prm.seed, fo->t_base, exact_only, median, fo->perm, p32, p64,            \
+        fo->node_key,                                                                             \
         fo->node_tree,                                                                            \
         fo->node_begin, fo->node_len, fo->node_left, fo->node_right, fo->node_jstar,              \
         fo->node_flag, fo->node_c, fo->leaf_tree, fo->leaf_begin, fo->leaf_len, d_exact, d_err)); \

@@ -100,6 +100,13 @@ class Forest:
                   "rpf_all_knn_trees")
         return idx, dist
 
+    def add_trees(self, n_new: int, stream=None) -> None:
+        """rpf_add_trees: grow n_new more trees (the same forest that a build
+        with n_trees + n_new trees gives)."""
+        check(_lib.lib().rpf_add_trees(self._h, int(n_new), _stream_handle(stream)),
+              "rpf_add_trees")
+        self.params.n_trees += int(n_new)
+
     def query(self, Q, K: int, idx=None, dist=None, workspace=None, stream=None):
         Q = _as_points(Q)
         m = int(Q.shape[0])

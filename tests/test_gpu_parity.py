@@ -418,3 +418,27 @@ def test_median_rule_ties_and_queries():
     qi, qd = g.query(torch.from_numpy(Q).cuda(), 10)
     oi, od = o.query(Q, 10)
     assert np.array_equal(qi.cpu().numpy(), oi) and np.array_equal(qd.cpu().numpy(), od)
+
+
+@pytest.mark.parametrize("form,split_rule", [(0, 0), (1, 0), (1, 1)])
+def test_add_trees_equals_the_larger_build(form, split_rule):
+    # 3 trees, then 2 and 1 more: the forest a 6-tree build grows
+    from paper_1812_11689_gb300 import forest
+    X = synth.make("aniso20_d64", n=15000)
+    kw = dict(leaf_max=128, n_try=5, seed=12, form=form, split_rule=split_rule)
+    Xd = torch.from_numpy(X).cuda()
+    g = forest.Forest(Xd, n_trees=3, **kw)
+    g.add_trees(2)
+    g.add_trees(1)
+    assert g.info()["n_trees"] == 6
+    o = oracle.Forest(X, 6, 128, 5, seed=12, split_rule=split_rule)
+    compare_trees(g, o, 6)
+    oi, od = o.all_knn(10)
+    gi, gd = g.all_knn(10)
+    check_knn(gi.cpu().numpy(), gd.cpu().numpy(), oi, od, X)
+    Q = synth.queries("aniso20_d64", 200, stream=41)
+    qi, qd = g.query(torch.from_numpy(Q).cuda(), 10)
+    ri, rd = o.query(Q, 10)
+    assert np.array_equal(qi.cpu().numpy(), ri) and np.array_equal(qd.cpu().numpy(), rd)
+    with pytest.raises(RuntimeError):
+        g.add_trees(0)
