@@ -333,9 +333,12 @@ def run_gb300(args, rank, world, local_rank):
         return times, b_ms, a_ms
 
     chosen, plain = forest.FORM_CHOSEN, forest.FORM_PLAIN
+    tuned = None
     for _ in range(args.warmup):
         for form in (chosen, plain):
             f, _ = step(form)
+            if form == chosen and tuned is None:  # once: later forests reuse the choice
+                tuned = f.autotune(w.k)
             f.close()
     torch.cuda.synchronize()
     if world > 1:
@@ -471,6 +474,7 @@ def run_gb300(args, rank, world, local_rank):
                   "stage_ms": {"build": round(sum(p_b) / len(p_b), 3),
                                "all_knn": round(sum(p_a) / len(p_a), 3)}},
         "chosen_equals_plain": same,
+        "autotune": tuned,
         "missing_rate": round(miss, 5),
         "knn_distance_discrepancy": disc,
         "at_missing_rate_le_1pct": at1,

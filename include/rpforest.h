@@ -158,6 +158,21 @@ int rpf_query_static(const rpf_forest* f, const float* Q, int64_t m, int32_t K, 
 size_t rpf_workspace_bytes(const rpf_forest* f, int64_t m, int32_t K, int32_t for_all_knn);
 
 /*
+ * rpf_autotune -- pick the tile launch configuration of the chosen form's
+ * leaf kernel (Gram coordinates per tensor-core chunk, CTAs per SM) by
+ * timing every candidate on this forest's own tiles (its first trees) with
+ * K neighbours.  All candidates give identical lists; the fastest is kept for
+ * the rest of the process for forests with the same dimension, tile rows and
+ * K bucket, so later rpf_all_knn calls (of this forest or of new ones of the
+ * same shape) use it.  A forest of the plain form, or one the tensor-core
+ * kernel does not cover, has nothing to tune (chosen = {0, 0}).
+ *   chosen : NULL or int32[2] receiving {Gram chunk, CTAs per SM}.
+ * Allocates a scratch list for the first trees; synchronises `stream`.
+ * Errors: RPF_EINVAL, RPF_ENOMEM, RPF_ECUDA.
+ */
+int rpf_autotune(rpf_forest* f, int32_t K, void* stream, int32_t* chosen);
+
+/*
  * rpf_add_trees -- grow n_new more trees onto a built forest (an incremental
  * ensemble: Sec. 5.2 studies accuracy as trees are added).  Every random
  * draw is keyed by the tree's index, so the result is exactly the forest

@@ -60,6 +60,8 @@ def lib() -> ctypes.CDLL:
             L.rpf_query_static.restype = ctypes.c_int
             L.rpf_workspace_bytes.argtypes = [_vp, _i64, _i32, _i32]
             L.rpf_workspace_bytes.restype = _sz
+            L.rpf_autotune.argtypes = [_vp, _i32, _vp, _vp]
+            L.rpf_autotune.restype = ctypes.c_int
             L.rpf_add_trees.argtypes = [_vp, _i32, _vp]
             L.rpf_add_trees.restype = ctypes.c_int
             L.rpf_free.argtypes = [_vp]
@@ -102,7 +104,7 @@ def check(code: int, what: str) -> None:
 
 # names of every symbol include/rpforest.h declares (checked by the CPU tests)
 EXPORTED = ("rpf_default_params", "rpf_build", "rpf_all_knn", "rpf_all_knn_trees", "rpf_query",
-            "rpf_query_static", "rpf_add_trees",
+            "rpf_query_static", "rpf_add_trees", "rpf_autotune",
             "rpf_workspace_bytes", "rpf_free", "rpf_error_string", "rpf_forest_info",
             "rpf_forest_perm", "rpf_forest_leaves", "rpf_forest_nodes", "rpf_directions",
             "rpf_brute_knn", "rpf_trace_enable", "rpf_launch_count", "rpf_trace_read",

@@ -196,6 +196,11 @@ int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* s
 
 void rpf_free(rpf_forest* f) { free_forest(f); }
 
+int rpf_autotune(rpf_forest* f, int32_t K, void* stream, int32_t* chosen) {
+  if (!f || K < 1 || K > RPF_MAX_K) return RPF_EINVAL;
+  return rpf_tc_autotune(f, K, (cudaStream_t)stream, chosen);
+}
+
 int rpf_add_trees(rpf_forest* f, int32_t n_new, void* stream) {
   if (!f || n_new < 1) return RPF_EINVAL;
   const int T = f->prm.n_trees;

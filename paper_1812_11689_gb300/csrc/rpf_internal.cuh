@@ -281,6 +281,9 @@ int rpf_build_tiles(rpf_forest* f, cudaStream_t s);
 int rpf_build_packs(rpf_forest* f, cudaStream_t s);
 bool rpf_tc_supported(const rpf_forest* f, int K);
 int rpf_leaf_tc(const rpf_forest* f, int t0, int g, int K, uint2* cand, cudaStream_t s);
+// times the chosen-form launch configurations on f's tiles, keeps the fastest
+// for its (d, tile rows, K) for the rest of the process; chosen = {chunk, CTAs}
+int rpf_tc_autotune(const rpf_forest* f, int K, cudaStream_t s, int32_t* chosen);
 // all-kNN over the first T trees (T <= n_trees: nested ensembles)
 int rpf_all_knn_dev(rpf_forest* f, int T, int K, int32_t* idx, float* dist, void* ws,
                     size_t ws_bytes, cudaStream_t s);

@@ -49,6 +49,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "rpf_internal.cuh"
@@ -568,13 +571,33 @@ int tc_chunk(int d, int rows) {
   return 0;
 }
 
+// Launch configuration of the chosen-form kernel: Gram coordinates per
+// chunk and CTAs per SM of the persistent grid.  rpf_tc_autotune times the
+// candidates on a forest's own tiles and keeps the fastest per (d, tile rows,
+// K bucket) for the rest of the process; without a tuned entry the
+// heuristic (largest chunk that fits four CTAs, else three) is used.
+struct TcConf {
+  int kc = 0, occ = 0;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, TcConf> g_tune;
+
 template <int KK, int ROWS>
 int launch_tc(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint2* cand,
-              cudaStream_t s) {
+              cudaStream_t s, const TcConf* force = nullptr) {
   if (thi <= tlo) return RPF_OK;
   const int d = f->d, dp = ((d + 3) & ~3) + 4, d16 = (d + 15) & ~15;
-  const int KC = tc_chunk(d, ROWS);
+  TcConf conf;
+  if (force) {
+    conf = *force;
+  } else {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(d, ROWS, KK));
+    if (it != g_tune.end()) conf = it->second;
+  }
+  const int KC = conf.kc > 0 ? conf.kc : tc_chunk(d, ROWS);
   const size_t smem = tc_smem(d, dp, ROWS, KC);
+  if (smem > 220 * 1024) return RPF_EINVAL;
   RPF_CU(cudaFuncSetAttribute(k_leaf_tc<KK, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem));
   int dev = 0, sms = 0, smem_sm = 0;
@@ -589,7 +612,8 @@ int launch_tc(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint
   // system), and that TMEM allows: four of 128 columns or one of 512
   const size_t per_cta = smem + fa.sharedSizeBytes + 1024;
   const int tmem_cap = ROWS == 128 ? 4 : 1;
-  const int occ = std::max(1, std::min(tmem_cap, (int)((size_t)smem_sm / per_cta)));
+  int occ = std::max(1, std::min(tmem_cap, (int)((size_t)smem_sm / per_cta)));
+  if (conf.occ > 0) occ = std::min(occ, conf.occ);
   const int64_t grid = std::min<int64_t>(thi - tlo, (int64_t)sms * occ);
   RPF_LAUNCH("k_leaf_tc", s, k_leaf_tc<KK, ROWS><<<(unsigned)grid, ROWS, smem, s>>>(
       f->pk_tiles, tlo, thi, f->pk_bits, f->pk_nwords, f->perm, f->X, f->n, d, dp, d16, KC, K,
@@ -599,9 +623,25 @@ int launch_tc(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint
 
 template <int KK>
 int launch_tc_rows(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint2* cand,
-                   cudaStream_t s) {
-  return f->pk_rows == 128 ? launch_tc<KK, 128>(f, tlo, thi, K, t0, cand, s)
-                           : launch_tc<KK, 256>(f, tlo, thi, K, t0, cand, s);
+                   cudaStream_t s, const TcConf* force = nullptr) {
+  return f->pk_rows == 128 ? launch_tc<KK, 128>(f, tlo, thi, K, t0, cand, s, force)
+                           : launch_tc<KK, 256>(f, tlo, thi, K, t0, cand, s, force);
+}
+
+int kk_of(int K) {
+  return K <= 4 ? 4 : K <= 8 ? 8 : K <= 12 ? 12 : K <= 16 ? 16 : K <= 24 ? 24 : 32;
+}
+
+int launch_tc_k(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint2* cand,
+                cudaStream_t s, const TcConf* force = nullptr) {
+  switch (kk_of(K)) {
+    case 4: return launch_tc_rows<4>(f, tlo, thi, K, t0, cand, s, force);
+    case 8: return launch_tc_rows<8>(f, tlo, thi, K, t0, cand, s, force);
+    case 12: return launch_tc_rows<12>(f, tlo, thi, K, t0, cand, s, force);
+    case 16: return launch_tc_rows<16>(f, tlo, thi, K, t0, cand, s, force);
+    case 24: return launch_tc_rows<24>(f, tlo, thi, K, t0, cand, s, force);
+    default: return launch_tc_rows<32>(f, tlo, thi, K, t0, cand, s, force);
+  }
 }
 
 }  // namespace
@@ -681,11 +721,54 @@ int rpf_build_packs(rpf_forest* f, cudaStream_t s) {
 }
 
 int rpf_leaf_tc(const rpf_forest* f, int t0, int g, int K, uint2* cand, cudaStream_t s) {
-  const int64_t tlo = f->pk_tree_off[t0], thi = f->pk_tree_off[t0 + g];
-  if (K <= 4) return launch_tc_rows<4>(f, tlo, thi, K, t0, cand, s);
-  if (K <= 8) return launch_tc_rows<8>(f, tlo, thi, K, t0, cand, s);
-  if (K <= 12) return launch_tc_rows<12>(f, tlo, thi, K, t0, cand, s);
-  if (K <= 16) return launch_tc_rows<16>(f, tlo, thi, K, t0, cand, s);
-  if (K <= 24) return launch_tc_rows<24>(f, tlo, thi, K, t0, cand, s);
-  return launch_tc_rows<32>(f, tlo, thi, K, t0, cand, s);
+  return launch_tc_k(f, f->pk_tree_off[t0], f->pk_tree_off[t0 + g], K, t0, cand, s);
+}
+
+int rpf_tc_autotune(const rpf_forest* f, int K, cudaStream_t s, int32_t* chosen) {
+  if (chosen) chosen[0] = chosen[1] = 0;
+  if (!rpf_tc_supported(f, K)) return RPF_OK;  // the plain form runs: nothing to tune
+  const int d = f->d, dp = ((d + 3) & ~3) + 4, d16 = (d + 15) & ~15, rows = f->pk_rows;
+  const int g = std::min(f->prm.n_trees, 4);  // the tiles of the first trees
+  uint2* cand = nullptr;
+  if (rpf_alloc((void**)&cand, (size_t)g * f->n * K * 8, s)) return RPF_ENOMEM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  TcConf best;
+  float best_ms = INFINITY;
+  int rc = RPF_OK;
+  const int max_occ = rows == 128 ? 4 : 1;
+  for (int kc = 16; kc <= std::min(d16, 128) && !rc; kc += 16) {
+    if (tc_smem(d, dp, rows, kc) > 220 * 1024) continue;
+    for (int occ = 1; occ <= max_occ && !rc; ++occ) {
+      const TcConf c{kc, occ};
+      float ms = INFINITY;
+      for (int rep = 0; rep < 3 && !rc; ++rep) {  // the first run warms caches
+        cudaEventRecord(e0, s);
+        rc = launch_tc_k(f, f->pk_tree_off[0], f->pk_tree_off[g], K, 0, cand, s, &c);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = RPF_ECUDA;
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0) ms = std::min(ms, t);
+      }
+      if (!rc && ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  rpf_release(cand, s);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[std::make_tuple(d, rows, kk_of(K))] = best;
+  }
+  if (chosen) {
+    chosen[0] = best.kc;
+    chosen[1] = best.occ;
+  }
+  return RPF_OK;
 }

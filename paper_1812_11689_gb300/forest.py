@@ -100,6 +100,14 @@ class Forest:
                   "rpf_all_knn_trees")
         return idx, dist
 
+    def autotune(self, K: int, stream=None) -> dict:
+        """rpf_autotune: time the chosen form's tile launch configurations on
+        this forest and keep the fastest for forests of this shape."""
+        chosen = (ctypes.c_int32 * 2)()
+        check(_lib.lib().rpf_autotune(self._h, K, _stream_handle(stream), chosen),
+              "rpf_autotune")
+        return {"gram_chunk": chosen[0], "ctas_per_sm": chosen[1]}
+
     def add_trees(self, n_new: int, stream=None) -> None:
         """rpf_add_trees: grow n_new more trees (the same forest that a build
         with n_trees + n_new trees gives)."""

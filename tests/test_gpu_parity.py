@@ -442,3 +442,15 @@ def test_add_trees_equals_the_larger_build(form, split_rule):
     assert np.array_equal(qi.cpu().numpy(), ri) and np.array_equal(qd.cpu().numpy(), rd)
     with pytest.raises(RuntimeError):
         g.add_trees(0)
+
+
+def test_autotune_picks_a_configuration_and_keeps_the_lists():
+    X = synth.make("aniso20_d64", n=20000)
+    c = gpu_forest(X, 4, 128, 5, seed=3, form=1)
+    ci0, cd0 = c.all_knn(10)
+    ch = c.autotune(10)
+    assert ch["gram_chunk"] in (16, 32, 48, 64) and 1 <= ch["ctas_per_sm"] <= 4
+    ci1, cd1 = c.all_knn(10)
+    assert torch.equal(ci0, ci1) and torch.equal(cd0, cd1)
+    p = gpu_forest(X, 4, 128, 5, seed=3, form=0)
+    assert p.autotune(10) == {"gram_chunk": 0, "ctas_per_sm": 0}
