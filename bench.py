@@ -408,11 +408,15 @@ def run_gb300(args, rank, world, local_rank):
     # draws depend on the tree index only), so growing the ensemble finds the
     # smallest T with a missing rate <= 1 %; that T is then timed like the
     # configured one.
-    at1 = None
-    if miss > 0.01:
-        sweep = []
-        for Tn in (64, 96, 128, 192, 256, 384, 512):
-            kwt = dict(kw, n_trees=Tn)
+    def at_one_percent(rule):
+        """Smallest nested T (first T' trees of a forest = the T'-tree forest)
+        whose missing rate is <= 1 %, with that step timed like the
+        configured one; for one split rule."""
+        res, sweep = None, []
+        for Tn in (w.n_trees, 48, 64, 80, 96, 128, 160, 192, 256, 384, 512):
+            if Tn < w.n_trees or (Tn == w.n_trees and sweep):
+                continue
+            kwt = dict(kw, n_trees=Tn, split_rule=rule)
             f2 = forest.Forest(Xd, form=chosen, **kwt)
             wst = torch.empty(f2.workspace_bytes(w.k), dtype=torch.uint8, device=dev)
             i2, d2 = f2.all_knn(w.k, workspace=wst)
@@ -423,7 +427,7 @@ def run_gb300(args, rank, world, local_rank):
                 t2, b2, a2 = timed(chosen, args.steps, kwt=kwt, wst=wst)
                 ms2 = sum(t2) / len(t2)
                 pt2, _, pa2 = timed(plain, args.steps, kwt=kwt, wst=wst)
-                at1 = {"n_trees": Tn, "missing_rate": round(m2, 5),
+                res = {"n_trees": Tn, "missing_rate": round(m2, 5),
                        "knn_distance_discrepancy": discrepancy(d2[rows.long()].cpu().numpy()),
                        "value": round(world * n / (ms2 * 1e-3), 1), "ms_per_step": round(ms2, 3),
                        "stage_ms": {"build": round(sum(b2) / len(b2), 3),
@@ -432,9 +436,17 @@ def run_gb300(args, rank, world, local_rank):
                                  "all_knn_ms": round(sum(pa2) / len(pa2), 3)}}
                 break
             del wst
-        if at1 is None:
-            at1 = {"not_reached_by_n_trees": 512}
-        at1["sweep"] = sweep
+        if res is None:
+            res = {"not_reached_by_n_trees": 512}
+        res["sweep"] = sweep
+        return res
+
+    at1 = None
+    if miss > 0.01:
+        at1 = {"uniform": at_one_percent(forest.SPLIT_UNIFORM),
+               "median": at_one_percent(forest.SPLIT_MEDIAN)}
+        vals = {k: v.get("value", 0.0) for k, v in at1.items()}
+        at1["best_split_rule"] = max(vals, key=vals.get)
     info = fc.info()
 
     hbm_peak, peak_kind = peaks()

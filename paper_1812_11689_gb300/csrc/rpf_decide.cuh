@@ -178,3 +178,50 @@ __device__ __forceinline__ bool rpf_med_digit(int pass, unsigned long long key, 
   return key == pk && (pass == 8 || ((id ^ pid) >> (sh + 8)) == 0u);
 }
 
+// Median rule, FP32 stage: order-preserving key of a float, its inverse,
+// and the band around the FP32 median (directed roundings).
+__device__ __forceinline__ uint32_t rpf_fkey(float v) {  // order-preserving float key
+  const uint32_t b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float rpf_fkey_inv(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+// the band of a certified node around v32 (directed roundings)
+__device__ __forceinline__ void rpf_med_band(uint32_t fk, float rad, float* lo, float* hi) {
+  const float v = rpf_fkey_inv(fk), r2 = __fmul_ru(2.0f, rad);
+  *lo = __fsub_rd(v, r2);
+  *hi = __fadd_ru(v, r2);
+}
+
+// Warp-collective: the digit of a 256-bin histogram that holds `rank` (lane l
+// looks at bins 8 l .. 8 l + 7); the lane that finds it returns true with the
+// digit and the rank left inside its bin.
+__device__ __forceinline__ bool rpf_pick_digit(const int* hist, int lane, int rank, int* dig_out,
+                                               int* rest_out) {
+  int v[8], sum = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    v[q] = hist[8 * lane + q];
+    sum += v[q];
+  }
+  int x = sum;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(RPF_FULL, x, off);
+    if (lane >= off) x += y;
+  }
+  const int pre = x - sum;
+  if (!(rank >= pre && rank < pre + sum)) return false;
+  int cum = pre, dig = -1;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (dig < 0) {
+      if (rank < cum + v[q]) dig = 8 * lane + q;
+      else cum += v[q];
+    }
+  }
+  *dig_out = dig;
+  *rest_out = rank - cum;
+  return true;
+}

@@ -54,8 +54,9 @@ struct Level {
   // median rule: selected key, point index and remaining rank per node, and
   // a 256-bin histogram per node for the radix passes
   unsigned long long* md_key{};
-  uint32_t* md_id{};
-  int32_t *md_rank{}, *md_hist{};
+  uint32_t *md_id{}, *md_fk{};
+  int32_t *md_rank{}, *md_hist{}, *md_l0{};
+  float *md_lo{}, *md_hi{};
   int32_t *ch_node[2]{}, *ch_start[2]{}, *ch_len[2]{};
   int32_t *ch_nleft{}, *ch_loff{};
   double *cp_sum{}, *cp_min{}, *cp_max{};
@@ -453,57 +454,69 @@ __global__ void k_csum_nodes(int pass, int F, int ntry, const int32_t* fr_cb, co
 // ---------------------------------------------------------------------------
 // Median rule (split_rule 1, Sec. 2's other usual split point): the floor(m/2)
 // points smallest in (p64 of the winning try, point index) order go left and
-// c is the p64 of the first point that goes right.  The rank-floor(m/2)
-// element is found by radix selection over the order-preserving 64-bit key of
-// p64 (8 passes of 8 bits) and then over the point index among equal keys
-// (4 passes): per pass every chunk adds its shared-memory histogram of the
-// keys that match the node's prefix so far into the node's 256 bins, and one
-// warp per node picks the digit that holds the remaining rank.
+// c is the p64 of the first point that goes right.
+//
+// Radix selection in 16 passes of 8 bits; per pass every chunk adds its
+// shared-memory histogram of the keys that match the node's prefix so far
+// into the node's 256 bins, and one warp per node picks the digit that holds
+// the remaining rank.
+//   passes 0-3  (certified nodes): v32 = the rank-floor(m/2) FP32 projection
+//               q' of the winner.  With R the node's certified radius
+//               (|q' - (p64 - b)| <= R), the median's p64 - b lies within
+//               v32 +- R, so points with q' < v32 - 2R are certainly left,
+//               points with q' > v32 + 2R certainly right, and only the band
+//               between gets its p64 computed (k_med_band);
+//   passes 4-11: the order-preserving 64-bit key of p64 (band points, or
+//               every point of an exact node), rank floor(m/2) minus the
+//               certainly-left count;
+//   passes 12-15: the point index among equal keys.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_med_p64(
-    const int32_t* ch_node, const int32_t* ch_start, const int32_t* ch_len, const int32_t* fr_tree,
-    const int32_t* fr_begin, const int32_t* fr_exact, const int32_t* fr_jstar, const float* X,
-    const int32_t* perm_cur, int64_t n, int64_t Tn, int d, int ntry, const double* dir64,
-    double* p64) {
-  const int c = blockIdx.x;
-  const int f = ch_node[c];
-  const int js = fr_jstar[f];
-  if (js < 0 || fr_exact[f]) return;  // exact nodes hold every try's p64 already
-  const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
-  const double* r = dir64 + ((int64_t)f * ntry + js) * d;
-  for (int i = threadIdx.x; i < ch_len[c]; i += blockDim.x)
-    p64[(int64_t)js * Tn + base + i] = rpf_p64(X + (int64_t)perm_cur[base + i] * d, r, d);
-}
-
-__global__ void k_med_init(int F, const int32_t* fr_len, unsigned long long* md_key,
-                           uint32_t* md_id, int32_t* md_rank) {
+__global__ void k_med_init(int F, const int32_t* fr_len, uint32_t* md_fk,
+                           unsigned long long* md_key, uint32_t* md_id, int32_t* md_rank,
+                           int32_t* md_l0) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= F) return;
+  md_fk[f] = 0u;
   md_key[f] = 0ull;
   md_id[f] = 0u;
   md_rank[f] = fr_len[f] >> 1;
+  md_l0[f] = 0;
 }
 
 __global__ void __launch_bounds__(kBlock) k_med_hist(
     int pass, const int32_t* ch_node, const int32_t* ch_start, const int32_t* ch_len,
-    const int32_t* fr_tree, const int32_t* fr_begin, const int32_t* fr_jstar,
-    const int32_t* perm_cur, int64_t n, int64_t Tn, const double* p64,
-    const unsigned long long* md_key, const uint32_t* md_id, int32_t* md_hist) {
+    const int32_t* fr_tree, const int32_t* fr_begin, const int32_t* fr_exact,
+    const int32_t* fr_jstar, const int32_t* perm_cur, int64_t n, int64_t Tn, const float* p32,
+    const double* p64, const uint32_t* md_fk, const unsigned long long* md_key,
+    const uint32_t* md_id, const float* md_lo, const float* md_hi, int32_t* md_hist) {
   __shared__ int h[256];
   const int c = blockIdx.x;
   const int f = ch_node[c];
   const int js = fr_jstar[f];
-  if (js < 0) return;  // rank split: no median
+  const int exact = fr_exact[f];
+  if (js < 0 || (pass < 4 && exact)) return;  // no median / no FP32 stage
   for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
   __syncthreads();
   const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
+  const float* q = p32 + (int64_t)js * Tn + base;
+  const double* p = p64 + (int64_t)js * Tn + base;
+  const uint32_t pf = md_fk[f];
   const unsigned long long pk = md_key[f];
   const uint32_t pid = md_id[f];
+  const float lo = md_lo[f], hi = md_hi[f];
   for (int i = threadIdx.x; i < ch_len[c]; i += blockDim.x) {
     int dig;
-    const unsigned long long key = rpf_mkey(p64[(int64_t)js * Tn + base + i]);
-    if (rpf_med_digit(pass, key, (uint32_t)perm_cur[base + i], pk, pid, &dig))
-      atomicAdd(&h[dig], 1);
+    bool match;
+    if (pass < 4) {
+      const int sh = 24 - 8 * pass;
+      const uint32_t k = rpf_fkey(q[i]);
+      dig = (int)((k >> sh) & 255u);
+      match = pass == 0 || ((k ^ pf) >> (sh + 8)) == 0u;
+    } else {
+      if (!exact && !(q[i] >= lo && q[i] <= hi)) continue;  // decided without p64
+      match = rpf_med_digit(pass - 4, rpf_mkey(p[i]), (uint32_t)perm_cur[base + i], pk, pid, &dig);
+    }
+    if (match) atomicAdd(&h[dig], 1);
   }
   __syncthreads();
   for (int b = threadIdx.x; b < 256; b += blockDim.x)
@@ -512,12 +525,13 @@ __global__ void __launch_bounds__(kBlock) k_med_hist(
 
 // one warp per node: the digit whose bin holds the remaining rank; the bins
 // are cleared for the next pass
-__global__ void __launch_bounds__(128) k_med_select(int pass, int F, const int32_t* fr_jstar,
+__global__ void __launch_bounds__(128) k_med_select(int pass, int F, const int32_t* fr_exact,
+                                                    const int32_t* fr_jstar, uint32_t* md_fk,
                                                     unsigned long long* md_key, uint32_t* md_id,
                                                     int32_t* md_rank, int32_t* md_hist) {
   const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (f >= F || fr_jstar[f] < 0) return;  // whole warp
+  if (f >= F || fr_jstar[f] < 0 || (pass < 4 && fr_exact[f])) return;  // whole warp
   int32_t* hb = md_hist + (int64_t)f * 256 + 8 * lane;
   int v[8], sum = 0;
 #pragma unroll
@@ -543,11 +557,68 @@ __global__ void __launch_bounds__(128) k_med_select(int pass, int F, const int32
       }
     }
     md_rank[f] = rank - cum;
-    if (pass < 8) md_key[f] |= (unsigned long long)dig << (56 - 8 * pass);
-    else md_id[f] |= (uint32_t)dig << (24 - 8 * (pass - 8));
+    if (pass < 4) md_fk[f] |= (uint32_t)dig << (24 - 8 * pass);
+    else if (pass < 12) md_key[f] |= (unsigned long long)dig << (56 - 8 * (pass - 4));
+    else md_id[f] |= (uint32_t)dig << (24 - 8 * (pass - 12));
   }
 #pragma unroll
   for (int q = 0; q < 8; ++q) hb[q] = 0;
+}
+
+// Certified nodes: the band around v32; p64 of the winner for the points in
+// it; the count of points certainly left of the band.
+__global__ void __launch_bounds__(kBlock) k_med_band(
+    const int32_t* ch_node, const int32_t* ch_start, const int32_t* ch_len, const int32_t* fr_tree,
+    const int32_t* fr_begin, const int32_t* fr_exact, const int32_t* fr_jstar,
+    const float* fr_rad, const float* X, const int32_t* perm_cur, int64_t n, int64_t Tn, int d,
+    int ntry, const double* dir64, const float* p32, const uint32_t* md_fk, double* p64,
+    int32_t* md_l0) {
+  __shared__ int wc[kBlock / 32];
+  const int c = blockIdx.x;
+  const int f = ch_node[c];
+  const int js = fr_jstar[f];
+  if (js < 0 || fr_exact[f]) return;  // exact nodes hold every p64 already
+  float lo, hi;
+  rpf_med_band(md_fk[f], fr_rad[f], &lo, &hi);
+  const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
+  const double* r = dir64 + ((int64_t)f * ntry + js) * d;
+  const float* q = p32 + (int64_t)js * Tn + base;
+  int cnt = 0;
+  for (int i = threadIdx.x; i < ch_len[c]; i += blockDim.x) {
+    const float v = q[i];
+    if (v < lo) {
+      ++cnt;
+    } else if (v <= hi) {
+      p64[(int64_t)js * Tn + base + i] = rpf_p64(X + (int64_t)perm_cur[base + i] * d, r, d);
+    }
+  }
+  for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(RPF_FULL, cnt, off);
+  if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int u = 0; u < kBlock / 32; ++u) t += wc[u];
+    if (t) atomicAdd(&md_l0[f], t);
+  }
+}
+
+// Certified nodes: the exact stage selects rank floor(m/2) - (certainly left)
+// among the band; the band is kept for the sides.
+__global__ void k_med_rank(int F, const int32_t* fr_len, const int32_t* fr_exact,
+                           const int32_t* fr_jstar, const float* fr_rad, const uint32_t* md_fk,
+                           const int32_t* md_l0, int32_t* md_rank, float* md_lo, float* md_hi) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F || fr_jstar[f] < 0) return;
+  if (fr_exact[f]) {
+    md_lo[f] = -INFINITY;
+    md_hi[f] = INFINITY;
+    return;
+  }
+  float lo, hi;
+  rpf_med_band(md_fk[f], fr_rad[f], &lo, &hi);
+  md_lo[f] = lo;
+  md_hi[f] = hi;
+  md_rank[f] = (fr_len[f] >> 1) - md_l0[f];
 }
 
 __global__ void k_split_a(int F, int ntry, uint64_t seed, int t_base, int median,
@@ -589,7 +660,8 @@ __global__ void __launch_bounds__(kBlock) k_side_count(
     const int32_t* fr_jstar, const int32_t* fr_flag, const double* fr_c, const float* fr_tl,
     const float* fr_tr, const float* X, const int32_t* perm_cur, int64_t n, int64_t Tn, int d,
     int ntry, const float* p32, const double* p64, const double* dir64, int median,
-    const unsigned long long* md_key, const uint32_t* md_id, uint8_t* side, int32_t* ch_nleft) {
+    const unsigned long long* md_key, const uint32_t* md_id, const float* md_lo,
+    const float* md_hi, uint8_t* side, int32_t* ch_nleft) {
   const int c = blockIdx.x;
   const int f = ch_node[c];
   const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
@@ -605,10 +677,17 @@ __global__ void __launch_bounds__(kBlock) k_side_count(
     bool left;
     if (flag) {
       left = (ch_start[c] + i) < (m >> 1);
-    } else if (median) {  // (key, index) below the median element's
-      const unsigned long long key = rpf_mkey(p64[(int64_t)js * Tn + base + i]);
-      left = key < md_key[f] ||
-             (key == md_key[f] && (uint32_t)perm_cur[base + i] < md_id[f]);
+    } else if (median) {  // certainly below / above the band, else (key, index) order
+      const float q = p32[(int64_t)js * Tn + base + i];
+      if (!exact && q < md_lo[f]) {
+        left = true;
+      } else if (!exact && q > md_hi[f]) {
+        left = false;
+      } else {
+        const unsigned long long key = rpf_mkey(p64[(int64_t)js * Tn + base + i]);
+        left = key < md_key[f] ||
+               (key == md_key[f] && (uint32_t)perm_cur[base + i] < md_id[f]);
+      }
     } else if (exact) {
       left = p64[(int64_t)js * Tn + base + i] < cc;
     } else {
@@ -990,7 +1069,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
                   lv.fr_rad, lv.fr_wlo, lv.fr_whi, lv.fr_akey, lv.fr_bkey, lv.ch_nleft, lv.ch_loff,
                   lv.cp_sum, lv.cp_min, lv.cp_max, lv.cp_s1, lv.cp_s2, lv.cp_a, lv.cp_min32,
                   lv.cp_max32, lv.cp_rad, lv.dir64, lv.dir32, lv.md_key, lv.md_id, lv.md_rank,
-                  lv.md_hist};
+                  lv.md_hist, lv.md_fk, lv.md_l0, lv.md_lo, lv.md_hi};
     for (void* p : ps) rpf_release(p, s);
     for (int q = 0; q < 2; ++q) {
       void* qs[] = {lv.fr_node[q], lv.fr_tree[q], lv.fr_begin[q], lv.fr_len[q], lv.fr_cb[q],
@@ -1151,6 +1230,10 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
       if ((r = grow_buf(&lv.md_id, 0, nf, s, false))) return r;
       if ((r = grow_buf(&lv.md_rank, 0, nf, s, false))) return r;
       if ((r = grow_buf(&lv.md_hist, 0, nf * 256, s, false))) return r;
+      if ((r = grow_buf(&lv.md_fk, 0, nf, s, false))) return r;
+      if ((r = grow_buf(&lv.md_l0, 0, nf, s, false))) return r;
+      if ((r = grow_buf(&lv.md_lo, 0, nf, s, false))) return r;
+      if ((r = grow_buf(&lv.md_hi, 0, nf, s, false))) return r;
       lv.cap_f = nf;
     }
     if (F * ntry > lv.cap_dir) {
@@ -1277,18 +1360,24 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     RPF_LAUNCH("k_count_exact", s,
                k_count_exact<<<nblk(F, 256), 256, 0, s>>>(Fi, lv.fr_exact, d_exact));
     if (median) {
-      RPF_LAUNCH("k_med_p64", s, k_med_p64<<<Ci, kBlock, 0, s>>>(
-          ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, lv.fr_jstar, fo->X, perm_cur,
-          n, Tn, d, ntry, lv.dir64, p64));
       RPF_LAUNCH("k_med_init", s, k_med_init<<<nblk(F, 128), 128, 0, s>>>(
-          Fi, fr_len, lv.md_key, lv.md_id, lv.md_rank));
+          Fi, fr_len, lv.md_fk, lv.md_key, lv.md_id, lv.md_rank, lv.md_l0));
       RPF_TRYCU(cudaMemsetAsync(lv.md_hist, 0, sizeof(int32_t) * 256 * (size_t)F, s));
-      for (int pass = 0; pass < 12; ++pass) {
+      for (int pass = 0; pass < 16; ++pass) {
+        if (pass == 4) {  // the band around the FP32 median; exact keys only inside it
+          RPF_LAUNCH("k_med_band", s, k_med_band<<<Ci, kBlock, 0, s>>>(
+              ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, lv.fr_jstar, lv.fr_rad,
+              fo->X, perm_cur, n, Tn, d, ntry, lv.dir64, p32, lv.md_fk, p64, lv.md_l0));
+          RPF_LAUNCH("k_med_rank", s, k_med_rank<<<nblk(F, 128), 128, 0, s>>>(
+              Fi, fr_len, lv.fr_exact, lv.fr_jstar, lv.fr_rad, lv.md_fk, lv.md_l0, lv.md_rank,
+              lv.md_lo, lv.md_hi));
+        }
         RPF_LAUNCH("k_med_hist", s, k_med_hist<<<Ci, kBlock, 0, s>>>(
-            pass, ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_jstar, perm_cur, n, Tn, p64,
-            lv.md_key, lv.md_id, lv.md_hist));
+            pass, ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, lv.fr_jstar, perm_cur,
+            n, Tn, p32, p64, lv.md_fk, lv.md_key, lv.md_id, lv.md_lo, lv.md_hi, lv.md_hist));
         RPF_LAUNCH("k_med_select", s, k_med_select<<<nblk(F * 32, 128), 128, 0, s>>>(
-            pass, Fi, lv.fr_jstar, lv.md_key, lv.md_id, lv.md_rank, lv.md_hist));
+            pass, Fi, lv.fr_exact, lv.fr_jstar, lv.md_fk, lv.md_key, lv.md_id, lv.md_rank,
+            lv.md_hist));
       }
     }
     RPF_LAUNCH("k_split_a", s, k_split_a<<<nblk(F, 128), 128, 0, s>>>(
@@ -1298,7 +1387,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     RPF_LAUNCH("k_side_count", s, k_side_count<<<Ci, kBlock, 0, s>>>(
         ch_node, ch_start, ch_len, fr_tree, fr_begin, fr_len, lv.fr_exact, lv.fr_jstar,
         lv.fr_flag, lv.fr_c, lv.fr_tl, lv.fr_tr, fo->X, perm_cur, n, Tn, d, ntry, p32, p64,
-        lv.dir64, median, lv.md_key, lv.md_id, side, lv.ch_nleft));
+        lv.dir64, median, lv.md_key, lv.md_id, lv.md_lo, lv.md_hi, side, lv.ch_nleft));
     RPF_LAUNCH("k_node_scan", s, k_node_scan<<<nblk(F, 128), 128, 0, s>>>(
         Fi, n_nodes, fr_node, fr_tree, fr_begin, fr_len, fr_key, fr_cb, fr_nc, lv.ch_nleft,
         lv.ch_loff, lv.fr_nl, fo->node_key, fo->node_tree, fo->node_begin, fo->node_len,

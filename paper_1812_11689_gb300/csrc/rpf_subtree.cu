@@ -44,8 +44,9 @@ struct SubState {
   int top, next_id, id_end, next_leaf, leaf_end;
   int leafL, leafR, err, ncand;
   unsigned long long mkey;  // median rule: key, point index and rank being selected
-  uint32_t mid;
+  uint32_t mid, mfk;        // ... and the FP32 key of the band's centre
   int mrank;
+  float mlo, mhi;           // band of q' outside which the side is certain
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -359,58 +360,79 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     }
 
     // 5m. median rule (Sec. 2's other usual split point): the floor(m/2)
-    // points smallest in (p64 of the winner, point index) order go left.  The
-    // rank-floor(m/2) element is found by radix selection in shared memory:
-    // 8 passes over the order-preserving key of p64, 4 over the point index
-    // among equal keys; warp 0 picks the digit that holds the remaining rank.
+    // points smallest in (p64 of the winner, point index) order go left.
+    // Radix selection in shared memory, warp 0 picking each digit:
+    //   certified nodes: 4 passes find v32, the rank-floor(m/2) FP32
+    //   projection; with R the certified radius, points with q' < v32 - 2R
+    //   are certainly left and q' > v32 + 2R certainly right, so only the
+    //   band between gets its p64 computed;
+    //   then 8 passes over the order-preserving key of p64 and 4 over the
+    //   point index, over the band (every point of an exact node), at rank
+    //   floor(m/2) minus the certainly-left count.
     if (median && S.js >= 0) {
       const int js = S.js;
       double* pj = p64 + (int64_t)js * Tn + pbase + nb;
-      if (!S.exact)
-        for (int i = tid; i < m; i += kB) pj[i] = rpf_p64(X + (int64_t)sP[nb + i] * d, r64 + js * d, d);
+      const float* qj = p32 + (int64_t)js * Tn + pbase + nb;
+      const bool exact = S.exact;
       if (tid == 0) {
         S.mkey = 0ull;
         S.mid = 0u;
+        S.mfk = 0u;
         S.mrank = m >> 1;
+        S.mlo = -INFINITY;
+        S.mhi = INFINITY;
       }
       __syncthreads();
-      for (int pass = 0; pass < 12; ++pass) {
+      for (int pass = exact ? 4 : 0; pass < 16; ++pass) {
+        if (pass == 4 && !exact) {  // the band; p64 inside it; certainly-left count
+          float lo, hi;
+          rpf_med_band(S.mfk, S.rad, &lo, &hi);
+          int cnt = 0;
+          for (int i = tid; i < m; i += kB) {
+            const float v = qj[i];
+            if (v < lo) ++cnt;
+            else if (v <= hi) pj[i] = rpf_p64(X + (int64_t)sP[nb + i] * d, r64 + js * d, d);
+          }
+          for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(RPF_FULL, cnt, off);
+          if (lane == 0) wsc[warp] = cnt;
+          __syncthreads();
+          if (tid == 0) {
+            int t = 0;
+            for (int u = 0; u < kB / 32; ++u) t += wsc[u];
+            S.mrank = (m >> 1) - t;
+            S.mlo = lo;
+            S.mhi = hi;
+          }
+          __syncthreads();
+        }
         for (int b = tid; b < 256; b += kB) mhist[b] = 0;
         __syncthreads();
+        const uint32_t pf = S.mfk;
         const unsigned long long pk = S.mkey;
         const uint32_t pid = S.mid;
+        const float lo = S.mlo, hi = S.mhi;
         for (int i = tid; i < m; i += kB) {
           int dig;
-          if (rpf_med_digit(pass, rpf_mkey(pj[i]), (uint32_t)sP[nb + i], pk, pid, &dig))
-            atomicAdd(&mhist[dig], 1);
+          bool match;
+          if (pass < 4) {
+            const int sh = 24 - 8 * pass;
+            const uint32_t k = rpf_fkey(qj[i]);
+            dig = (int)((k >> sh) & 255u);
+            match = pass == 0 || ((k ^ pf) >> (sh + 8)) == 0u;
+          } else {
+            if (!exact && !(qj[i] >= lo && qj[i] <= hi)) continue;
+            match = rpf_med_digit(pass - 4, rpf_mkey(pj[i]), (uint32_t)sP[nb + i], pk, pid, &dig);
+          }
+          if (match) atomicAdd(&mhist[dig], 1);
         }
         __syncthreads();
         if (warp == 0) {
-          int v[8], sum = 0;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            v[q] = mhist[8 * lane + q];
-            sum += v[q];
-          }
-          int x = sum;
-#pragma unroll
-          for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(RPF_FULL, x, off);
-            if (lane >= off) x += y;
-          }
-          const int pre = x - sum, rank = S.mrank;
-          if (rank >= pre && rank < pre + sum) {
-            int cum = pre, dig = -1;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              if (dig < 0) {
-                if (rank < cum + v[q]) dig = 8 * lane + q;
-                else cum += v[q];
-              }
-            }
-            S.mrank = rank - cum;
-            if (pass < 8) S.mkey = pk | ((unsigned long long)dig << (56 - 8 * pass));
-            else S.mid = pid | ((uint32_t)dig << (24 - 8 * (pass - 8)));
+          int dig, rest;
+          if (rpf_pick_digit(mhist, lane, S.mrank, &dig, &rest)) {
+            S.mrank = rest;
+            if (pass < 4) S.mfk = pf | ((uint32_t)dig << (24 - 8 * pass));
+            else if (pass < 12) S.mkey = pk | ((unsigned long long)dig << (56 - 8 * (pass - 4)));
+            else S.mid = pid | ((uint32_t)dig << (24 - 8 * (pass - 12)));
           }
         }
         __syncthreads();
@@ -453,9 +475,16 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
         int left;
         if (flag) {
           left = i < (m >> 1);
-        } else if (median) {  // (key, index) below the median element's
-          const unsigned long long k = rpf_mkey(p64[(int64_t)js * Tn + pbase + nb + i]);
-          left = k < S.mkey || (k == S.mkey && (uint32_t)sP[nb + i] < S.mid);
+        } else if (median) {  // certainly below / above the band, else (key, index)
+          const float q = p32[(int64_t)js * Tn + pbase + nb + i];
+          if (q < S.mlo) {
+            left = 1;
+          } else if (q > S.mhi) {
+            left = 0;
+          } else {
+            const unsigned long long k = rpf_mkey(p64[(int64_t)js * Tn + pbase + nb + i]);
+            left = k < S.mkey || (k == S.mkey && (uint32_t)sP[nb + i] < S.mid);
+          }
         } else if (exact) {
           left = p64[(int64_t)js * Tn + pbase + nb + i] < c;
         } else {
