@@ -69,6 +69,34 @@ __device__ __forceinline__ double rpf_p64(const float* x, const double* r, int d
   return p;
 }
 
+// Warp-collective canonical FP64 projections of two rows x0, x1 on r; lane 0
+// returns p64(x0, r), lane 1 p64(x1, r).  With x_k and r_k FP32 values the
+// product x_k r_k has at most 48 significant bits and is exact in FP64, so
+// each step fma(x_k, r_k, p) equals p + (x_k r_k) rounded once: the warp forms
+// the products 32 coordinates at a time (coalesced loads) and lanes 0 / 1 add
+// them in order, taking each from the lane that holds it.  The chain then waits
+// only for its additions, not for loads.
+__device__ __forceinline__ double rpf_p64_pair(const float* x0, const float* x1, const double* r,
+                                               int d, int lane) {
+  double p = 0.0;
+  for (int k0 = 0; k0 < d; k0 += 32) {
+    const int k = k0 + lane;
+    double t0 = 0.0, t1 = 0.0;
+    if (k < d) {
+      const double rk = r[k];
+      t0 = __dmul_rn((double)__ldg(x0 + k), rk);
+      t1 = __dmul_rn((double)__ldg(x1 + k), rk);
+    }
+    const int kn = min(32, d - k0);
+    for (int u = 0; u < kn; ++u) {
+      const double v0 = __shfl_sync(RPF_FULL, t0, u);
+      const double v1 = __shfl_sync(RPF_FULL, t1, u);
+      p = __dadd_rn(p, lane == 0 ? v0 : v1);
+    }
+  }
+  return p;
+}
+
 __device__ __forceinline__ float rpf_kappa(int d) { return (float)(d + 4) * 0x1p-24f * 1.0625f; }
 
 // error radius of one point (FP32, rounded up); nn = computed sum of squares

@@ -40,7 +40,8 @@
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kSub = RPF_CHUNK;  // nodes of at most this many points grow in one CTA
+constexpr int kSub = RPF_CHUNK;
+constexpr int kCandList = 256;  // min / max candidates listed per chunk for the warp pass  // nodes of at most this many points grow in one CTA
 
 struct Level {
   int64_t cap_f = 0, cap_c = 0, cap_dir = 0;
@@ -296,13 +297,39 @@ __global__ void __launch_bounds__(kBlock) k_cand(
   const float lo = fr_wlo[f], hi = fr_whi[f];
   const float* p = p32 + (int64_t)js * Tn + base;
   const double* r = dir64 + ((int64_t)f * ntry + js) * d;
+  // candidates are few: list them, then one warp evaluates them two at a
+  // time (rpf_p64_pair); beyond the list's room a thread evaluates its own
+  __shared__ int s_n;
+  __shared__ int s_e[kCandList];
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
   for (int i = threadIdx.x; i < len; i += blockDim.x) {
     const float v = p[i];
     const bool a = v <= lo, b = v >= hi;
     if (!a && !b) continue;
+    const int slot = atomicAdd(&s_n, 1);
+    if (slot < kCandList) {
+      s_e[slot] = (i << 2) | (a ? 1 : 0) | (b ? 2 : 0);
+      continue;
+    }
     const double q = rpf_p64(X + (int64_t)perm_cur[base + i] * d, r, d);
     if (a) atomicMin(&fr_akey[f], rpf_dkey(q));
     if (b) atomicMax(&fr_bkey[f], rpf_dkey(q));
+  }
+  __syncthreads();
+  const int nc = min(s_n, kCandList);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int q0 = 0; q0 < nc; q0 += 2) {
+      const int e0 = s_e[q0], e1 = q0 + 1 < nc ? s_e[q0 + 1] : e0;
+      const double q = rpf_p64_pair(X + (int64_t)perm_cur[base + (e0 >> 2)] * d,
+                                    X + (int64_t)perm_cur[base + (e1 >> 2)] * d, r, d, lane);
+      if (lane < 2) {
+        const int e = lane == 0 ? e0 : e1;
+        if (e & 1) atomicMin(&fr_akey[f], rpf_dkey(q));
+        if (e & 2) atomicMax(&fr_bkey[f], rpf_dkey(q));
+      }
+    }
   }
 }
 

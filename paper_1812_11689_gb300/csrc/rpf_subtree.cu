@@ -33,6 +33,7 @@ namespace {
 constexpr int kB = 128;  // 4 warps; 4 CTAs per SM hide each other's serial sections
 constexpr int kSubN = RPF_CHUNK;
 constexpr int kStack = 24;
+constexpr int kBandSel = 256;  // median rule: bands up to this size are selected by counting
 
 struct SubState {
   uint64_t key;
@@ -133,6 +134,8 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
   __shared__ uint64_t st_key[kStack];
   __shared__ int wsc[kB / 32];
   __shared__ int mhist[256];  // median rule: radix histogram
+  __shared__ unsigned long long bnd_key[kBandSel];  // ... and a small band's keys
+  __shared__ uint32_t bnd_id[kBandSel];
   __shared__ int tile_tot;
 
   const int it = blockIdx.x;
@@ -330,11 +333,12 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
       const int nc = S.ncand;
       if (warp == 0) {
         unsigned long long ak = rpf_dkey(INFINITY), bk = rpf_dkey(-INFINITY);
-        for (int q0 = 0; q0 < nc; q0 += 32) {
-          const int q = q0 + lane;
-          if (q < nc) {
-            const int e = sT[q];
-            const double v = rpf_p64(X + (int64_t)sP[nb + (e >> 2)] * d, r64 + w * d, d);
+        for (int q0 = 0; q0 < nc; q0 += 2) {  // two candidates per pass (lanes 0, 1)
+          const int e0 = sT[q0], e1 = q0 + 1 < nc ? sT[q0 + 1] : e0;
+          const double v = rpf_p64_pair(X + (int64_t)sP[nb + (e0 >> 2)] * d,
+                                        X + (int64_t)sP[nb + (e1 >> 2)] * d, r64 + w * d, d, lane);
+          if (lane < 2) {
+            const int e = lane == 0 ? e0 : e1;
             if (e & 1) ak = min(ak, rpf_dkey(v));
             if (e & 2) bk = max(bk, rpf_dkey(v));
           }
@@ -366,9 +370,11 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     //   projection; with R the certified radius, points with q' < v32 - 2R
     //   are certainly left and q' > v32 + 2R certainly right, so only the
     //   band between gets its p64 computed;
-    //   then 8 passes over the order-preserving key of p64 and 4 over the
-    //   point index, over the band (every point of an exact node), at rank
-    //   floor(m/2) minus the certainly-left count.
+    //   then, at rank floor(m/2) minus the certainly-left count, a band of
+    //   at most 256 points is searched directly (the point with exactly
+    //   that many smaller (key, index) pairs in the band); a larger band,
+    //   and every point of an exact node, takes 8 radix passes over the
+    //   order-preserving key of p64 and 4 over the point index.
     if (median && S.js >= 0) {
       const int js = S.js;
       double* pj = p64 + (int64_t)js * Tn + pbase + nb;
@@ -381,6 +387,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
         S.mrank = m >> 1;
         S.mlo = -INFINITY;
         S.mhi = INFINITY;
+        S.ncand = 0;
       }
       __syncthreads();
       for (int pass = exact ? 4 : 0; pass < 16; ++pass) {
@@ -390,8 +397,17 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
           int cnt = 0;
           for (int i = tid; i < m; i += kB) {
             const float v = qj[i];
-            if (v < lo) ++cnt;
-            else if (v <= hi) pj[i] = rpf_p64(X + (int64_t)sP[nb + i] * d, r64 + js * d, d);
+            if (v < lo) {
+              ++cnt;
+            } else if (v <= hi) {
+              const double p = rpf_p64(X + (int64_t)sP[nb + i] * d, r64 + js * d, d);
+              pj[i] = p;
+              const int e = atomicAdd(&S.ncand, 1);
+              if (e < kBandSel) {
+                bnd_key[e] = rpf_mkey(p);
+                bnd_id[e] = (uint32_t)sP[nb + i];
+              }
+            }
           }
           for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(RPF_FULL, cnt, off);
           if (lane == 0) wsc[warp] = cnt;
@@ -404,6 +420,25 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
             S.mhi = hi;
           }
           __syncthreads();
+          const int nc = S.ncand;
+          if (nc <= kBandSel) {
+            // a small band: the element with exactly mrank smaller (key,
+            // index) pairs in it, by counting (the pairs are distinct)
+            const int r = S.mrank;
+            for (int e = tid; e < nc; e += kB) {
+              const unsigned long long k = bnd_key[e];
+              const uint32_t id = bnd_id[e];
+              int below = 0;
+              for (int f = 0; f < nc; ++f)
+                below += bnd_key[f] < k || (bnd_key[f] == k && bnd_id[f] < id);
+              if (below == r) {
+                S.mkey = k;
+                S.mid = id;
+              }
+            }
+            __syncthreads();
+            break;
+          }
         }
         for (int b = tid; b < 256; b += kB) mhist[b] = 0;
         __syncthreads();
@@ -503,9 +538,11 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
       __syncthreads();
       if (warp == 0) {
         const int na = S.ncand;
-        for (int q = lane; q < na; q += 32) {
-          const int i = sT[q];
-          sSide[i] = rpf_p64(X + (int64_t)sP[nb + i] * d, r64 + js * d, d) < c ? 1 : 0;
+        for (int q0 = 0; q0 < na; q0 += 2) {  // two undecided points per pass (lanes 0, 1)
+          const int i0 = sT[q0], i1 = q0 + 1 < na ? sT[q0 + 1] : i0;
+          const double v = rpf_p64_pair(X + (int64_t)sP[nb + i0] * d, X + (int64_t)sP[nb + i1] * d,
+                                        r64 + js * d, d, lane);
+          if (lane < 2 && q0 + lane < na) sSide[lane == 0 ? i0 : i1] = v < c ? 1 : 0;
         }
       }
       __syncthreads();
