@@ -161,6 +161,24 @@ __device__ __forceinline__ int rpf_certify_select(int ntry, const double* vhat, 
   return w;
 }
 
+// The tries that can still be Algorithm 2's choice when the certificate
+// fails: those whose upper bound reaches the largest lower bound L (any
+// other try has sqrt(V) <= hi < L <= sqrt(V) of the try holding L, so it is
+// neither the maximum nor tied with it).  Every try if a bound is NaN.
+__device__ __forceinline__ unsigned long long rpf_contenders(int ntry, const float* lo,
+                                                             const float* hi) {
+  const unsigned long long all = ntry >= 64 ? ~0ull : (1ull << ntry) - 1ull;
+  float L = -INFINITY;
+  for (int j = 0; j < ntry; ++j) {
+    if (lo[j] != lo[j] || hi[j] != hi[j]) return all;
+    L = fmaxf(L, lo[j]);
+  }
+  unsigned long long mask = 0ull;
+  for (int j = 0; j < ntry; ++j)
+    if (hi[j] >= L) mask |= 1ull << j;
+  return mask;
+}
+
 // Split point of Algorithm 1 from the exact a = min, b = max.  Returns 1 if
 // an attempt was accepted (c in (a, b]), 0 for a rank split.
 __device__ __forceinline__ int rpf_split_point(uint64_t seed, uint64_t t, uint64_t key, double a,

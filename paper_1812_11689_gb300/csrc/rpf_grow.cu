@@ -52,6 +52,7 @@ struct Level {
   double *fr_mu{}, *fr_min{}, *fr_max{};
   float *fr_tl{}, *fr_tr{}, *fr_rad{}, *fr_wlo{}, *fr_whi{};
   unsigned long long *fr_akey{}, *fr_bkey{};
+  unsigned long long* fr_cmask{};  // tries still in contention at an exact node
   // median rule: selected key, point index and remaining rank per node, and
   // a 256-bin histogram per node for the radix passes
   unsigned long long* md_key{};
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(128) k_certify_a(
     const int32_t* fr_len, const double* cp_s1, const double* cp_s2, const double* cp_a,
     const float* cp_min, const float* cp_max, const float* cp_rad, const double* fr_base,
     int32_t* fr_exact, int32_t* fr_jstar, float* fr_rad, float* fr_wlo, float* fr_whi,
-    unsigned long long* fr_akey, unsigned long long* fr_bkey) {
+    unsigned long long* fr_akey, unsigned long long* fr_bkey, unsigned long long* fr_cmask) {
   __shared__ double s_vh[4][RPF_MAX_TRY];
   __shared__ float s_lo[4][RPF_MAX_TRY], s_hi[4][RPF_MAX_TRY];
   const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -257,7 +258,11 @@ __global__ void __launch_bounds__(128) k_certify_a(
   if (lane == 0) w = exact_only ? -1 : rpf_certify_select(ntry, s_vh[wib], s_lo[wib], s_hi[wib]);
   w = __shfl_sync(RPF_FULL, w, 0);
   if (w < 0) {
-    if (lane == 0) fr_exact[f] = 1;
+    if (lane == 0) {
+      fr_exact[f] = 1;
+      fr_cmask[f] = exact_only ? (ntry >= 64 ? ~0ull : (1ull << ntry) - 1ull)
+                               : rpf_contenders(ntry, s_lo[wib], s_hi[wib]);
+    }
     return;
   }
   float lo = INFINITY, hi = -INFINITY;
@@ -351,12 +356,12 @@ __global__ void k_exact_list(int C, const int32_t* ch_node, const int32_t* fr_ex
 }
 
 // Grid-stride over (listed chunk, slice of 256 positions): canonical FP64
-// projections of every try.
+// projections of every try still in contention.
 __global__ void __launch_bounds__(kBlock) k_proj64(
     const int32_t* list, const int32_t* count, const int32_t* ch_node, const int32_t* ch_start,
     const int32_t* ch_len, const int32_t* fr_tree, const int32_t* fr_begin, const float* X,
     const int32_t* perm_cur, int64_t n, int64_t Tn, int d, int ntry, const double* dir64,
-    double* p64) {
+    const unsigned long long* fr_cmask, double* p64) {
   constexpr int kSlices = RPF_CHUNK / kBlock;
   const int total = *count * kSlices;
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
@@ -366,51 +371,56 @@ __global__ void __launch_bounds__(kBlock) k_proj64(
     const int f = ch_node[c];
     const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
     const float* x = X + (int64_t)perm_cur[base + i] * d;
+    const unsigned long long mask = fr_cmask[f];
     for (int j = 0; j < ntry; ++j)
-      p64[(int64_t)j * Tn + base + i] = rpf_p64(x, dir64 + ((int64_t)f * ntry + j) * d, d);
+      if ((mask >> j) & 1ull)
+        p64[(int64_t)j * Tn + base + i] = rpf_p64(x, dir64 + ((int64_t)f * ntry + j) * d, d);
   }
 }
 
-// One warp per (chunk, try).  pass 0: canonical chunk sum of p and exact
-// min / max; pass 1: canonical chunk sum of (p - mu)^2.
-__global__ void k_csum_chunks(int pass, int C, int ntry, const int32_t* ch_node,
-                              const int32_t* ch_start, const int32_t* ch_len,
-                              const int32_t* fr_tree, const int32_t* fr_begin,
-                              const int32_t* fr_exact, int64_t n, int64_t Tn, const double* p64,
-                              const double* fr_mu, double* cp_sum, double* cp_min,
-                              double* cp_max) {
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// One warp per (listed exact chunk, try in contention), grid-stride.
+// pass 0: canonical chunk sum of p and exact min / max; pass 1: canonical
+// chunk sum of (p - mu)^2.
+__global__ void k_csum_chunks(int pass, const int32_t* list, const int32_t* count, int ntry,
+                              const int32_t* ch_node, const int32_t* ch_start,
+                              const int32_t* ch_len, const int32_t* fr_tree,
+                              const int32_t* fr_begin, const unsigned long long* fr_cmask,
+                              int64_t n, int64_t Tn, const double* p64, const double* fr_mu,
+                              double* cp_sum, double* cp_min, double* cp_max) {
   const int lane = threadIdx.x & 31;
-  if (wid >= (int64_t)C * ntry) return;
-  const int c = (int)(wid / ntry), j = (int)(wid % ntry);
-  const int f = ch_node[c];
-  if (!fr_exact[f]) return;
-  const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
-  const int len = ch_len[c];
-  const double* p = p64 + (int64_t)j * Tn + base;
-  if (pass == 0) {
-    double S = rpf_warp_chunk_sum(len, lane, [&](int64_t k) { return p[k]; });
-    double a = INFINITY, b = -INFINITY;
-    for (int k = lane; k < len; k += 32) {
-      a = fmin(a, p[k]);
-      b = fmax(b, p[k]);
+  const int64_t total = (int64_t)*count * ntry;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wid < total; wid += nw) {
+    const int c = list[wid / ntry], j = (int)(wid % ntry);
+    const int f = ch_node[c];
+    if (!((fr_cmask[f] >> j) & 1ull)) continue;
+    const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
+    const int len = ch_len[c];
+    const double* p = p64 + (int64_t)j * Tn + base;
+    if (pass == 0) {
+      double S = rpf_warp_chunk_sum(len, lane, [&](int64_t k) { return p[k]; });
+      double a = INFINITY, b = -INFINITY;
+      for (int k = lane; k < len; k += 32) {
+        a = fmin(a, p[k]);
+        b = fmax(b, p[k]);
+      }
+      for (int off = 16; off >= 1; off >>= 1) {
+        a = fmin(a, __shfl_xor_sync(RPF_FULL, a, off));
+        b = fmax(b, __shfl_xor_sync(RPF_FULL, b, off));
+      }
+      if (lane == 0) {
+        cp_sum[(int64_t)c * ntry + j] = S;
+        cp_min[(int64_t)c * ntry + j] = a;
+        cp_max[(int64_t)c * ntry + j] = b;
+      }
+    } else {
+      const double mu = fr_mu[(int64_t)f * ntry + j];
+      double V = rpf_warp_chunk_sum(len, lane, [&](int64_t k) {
+        double e = __dsub_rn(p[k], mu);
+        return __dmul_rn(e, e);
+      });
+      if (lane == 0) cp_sum[(int64_t)c * ntry + j] = V;
     }
-    for (int off = 16; off >= 1; off >>= 1) {
-      a = fmin(a, __shfl_xor_sync(RPF_FULL, a, off));
-      b = fmax(b, __shfl_xor_sync(RPF_FULL, b, off));
-    }
-    if (lane == 0) {
-      cp_sum[(int64_t)c * ntry + j] = S;
-      cp_min[(int64_t)c * ntry + j] = a;
-      cp_max[(int64_t)c * ntry + j] = b;
-    }
-  } else {
-    const double mu = fr_mu[(int64_t)f * ntry + j];
-    double V = rpf_warp_chunk_sum(len, lane, [&](int64_t k) {
-      double e = __dsub_rn(p[k], mu);
-      return __dmul_rn(e, e);
-    });
-    if (lane == 0) cp_sum[(int64_t)c * ntry + j] = V;
   }
 }
 
@@ -435,7 +445,8 @@ __device__ double node_reduce(double* part, int64_t nc, int ntry, int lane) {
 // One warp per exact node.  pass 0: S_j -> mu_j, exact min / max; pass 1:
 // V_j and Algorithm 2's choice (first try with V > best, best from 0).
 __global__ void k_csum_nodes(int pass, int F, int ntry, const int32_t* fr_cb, const int32_t* fr_nc,
-                             const int32_t* fr_len, const int32_t* fr_exact, double* cp_sum,
+                             const int32_t* fr_len, const int32_t* fr_exact,
+                             const unsigned long long* fr_cmask, double* cp_sum,
                              const double* cp_min, const double* cp_max, double* fr_mu,
                              double* fr_min, double* fr_max, int32_t* fr_jstar, double* fr_a,
                              double* fr_b) {
@@ -446,7 +457,9 @@ __global__ void k_csum_nodes(int pass, int F, int ntry, const int32_t* fr_cb, co
   const double m = (double)fr_len[f];
   double best = 0.0;
   int js = -1;
+  const unsigned long long mask = fr_cmask[f];
   for (int j = 0; j < ntry; ++j) {
+    if (!((mask >> j) & 1ull)) continue;  // certainly below a contender
     double v = node_reduce(cp_sum + (int64_t)cb * ntry + j, nc, ntry, lane);
     if (pass == 0) {
       double a = INFINITY, b = -INFINITY;
@@ -1096,7 +1109,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
                   lv.fr_rad, lv.fr_wlo, lv.fr_whi, lv.fr_akey, lv.fr_bkey, lv.ch_nleft, lv.ch_loff,
                   lv.cp_sum, lv.cp_min, lv.cp_max, lv.cp_s1, lv.cp_s2, lv.cp_a, lv.cp_min32,
                   lv.cp_max32, lv.cp_rad, lv.dir64, lv.dir32, lv.md_key, lv.md_id, lv.md_rank,
-                  lv.md_hist, lv.md_fk, lv.md_l0, lv.md_lo, lv.md_hi};
+                  lv.md_hist, lv.md_fk, lv.md_l0, lv.md_lo, lv.md_hi, lv.fr_cmask};
     for (void* p : ps) rpf_release(p, s);
     for (int q = 0; q < 2; ++q) {
       void* qs[] = {lv.fr_node[q], lv.fr_tree[q], lv.fr_begin[q], lv.fr_len[q], lv.fr_cb[q],
@@ -1253,6 +1266,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
         if ((r = grow_buf(pp, 0, nf, s, false))) return r;
       if ((r = grow_buf(&lv.fr_akey, 0, nf, s, false))) return r;
       if ((r = grow_buf(&lv.fr_bkey, 0, nf, s, false))) return r;
+      if ((r = grow_buf(&lv.fr_cmask, 0, nf, s, false))) return r;
       if ((r = grow_buf(&lv.md_key, 0, nf, s, false))) return r;
       if ((r = grow_buf(&lv.md_id, 0, nf, s, false))) return r;
       if ((r = grow_buf(&lv.md_rank, 0, nf, s, false))) return r;
@@ -1363,7 +1377,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     RPF_LAUNCH("k_certify_a", s, k_certify_a<<<nblk(F * 32, 128), 128, 0, s>>>(
         Fi, ntry, exact_only, fr_cb, fr_nc, fr_len, lv.cp_s1, lv.cp_s2, lv.cp_a, lv.cp_min32,
         lv.cp_max32, lv.cp_rad, lv.fr_base, lv.fr_exact, lv.fr_jstar, lv.fr_rad, lv.fr_wlo,
-        lv.fr_whi, lv.fr_akey, lv.fr_bkey));
+        lv.fr_whi, lv.fr_akey, lv.fr_bkey, lv.fr_cmask));
     RPF_LAUNCH("k_cand", s, k_cand<<<Ci, kBlock, 0, s>>>(
         ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, lv.fr_jstar, lv.fr_wlo,
         lv.fr_whi, fo->X, perm_cur, n, Tn, d, ntry, p32, lv.dir64, lv.fr_akey, lv.fr_bkey));
@@ -1375,13 +1389,13 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
         Ci, ch_node, lv.fr_exact, lv.ch_loff, ex_count));
     RPF_LAUNCH("k_proj64", s, k_proj64<<<4 * 152, kBlock, 0, s>>>(
         lv.ch_loff, ex_count, ch_node, ch_start, ch_len, fr_tree, fr_begin, fo->X, perm_cur, n,
-        Tn, d, ntry, lv.dir64, p64));
+        Tn, d, ntry, lv.dir64, lv.fr_cmask, p64));
     for (int pass = 0; pass < 2; ++pass) {
-      RPF_LAUNCH("k_csum_chunks", s, k_csum_chunks<<<nblk(C * ntry * 32, 256), 256, 0, s>>>(
-          pass, Ci, ntry, ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, n, Tn, p64,
-          lv.fr_mu, lv.cp_sum, lv.cp_min, lv.cp_max));
+      RPF_LAUNCH("k_csum_chunks", s, k_csum_chunks<<<2 * 152, 256, 0, s>>>(
+          pass, lv.ch_loff, ex_count, ntry, ch_node, ch_start, ch_len, fr_tree, fr_begin,
+          lv.fr_cmask, n, Tn, p64, lv.fr_mu, lv.cp_sum, lv.cp_min, lv.cp_max));
       RPF_LAUNCH("k_csum_nodes", s, k_csum_nodes<<<nblk(F * 32, 256), 256, 0, s>>>(
-          pass, Fi, ntry, fr_cb, fr_nc, fr_len, lv.fr_exact, lv.cp_sum, lv.cp_min, lv.cp_max,
+          pass, Fi, ntry, fr_cb, fr_nc, fr_len, lv.fr_exact, lv.fr_cmask, lv.cp_sum, lv.cp_min, lv.cp_max,
           lv.fr_mu, lv.fr_min, lv.fr_max, lv.fr_jstar, lv.fr_a, lv.fr_b));
     }
     RPF_LAUNCH("k_count_exact", s,

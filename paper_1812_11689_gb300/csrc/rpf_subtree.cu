@@ -11,7 +11,8 @@
 //   3. projects every point: q' = fl32-dot(r32, fl32(x - o)), error radius,
 //      block statistics (FP32 per thread, FP64 across warps)
 //   4. certifies Algorithm 2's choice, or recomputes the node in FP64 with the
-//      canonical reduction (one chunk: the node has <= 4096 points)
+//      canonical reduction (one chunk: the node has <= 4096 points) for the
+//      tries the bounds leave in contention
 //   5. finds the exact min / max (FP64 on the few candidates), draws c
 //   6. decides every point's side (certified from q', else FP64) and
 //      partitions the segment stably
@@ -42,6 +43,7 @@ struct SubState {
   double a, b, c;
   float tl, tr, rad, wlo, whi;
   unsigned long long akey, bkey;
+  unsigned long long cmask;  // tries still in contention at an exact node
   int top, next_id, id_end, next_leaf, leaf_end;
   int leafL, leafR, err, ncand;
   unsigned long long mkey;  // median rule: key, point index and rank being selected
@@ -256,6 +258,8 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     if (tid == 0) {
       const int w = exact_only ? -1 : rpf_certify_select(ntry, svh, slo, shi);
       S.exact = w < 0;
+      S.cmask = exact_only ? (ntry >= 64 ? ~0ull : (1ull << ntry) - 1ull)
+                           : (w < 0 ? rpf_contenders(ntry, slo, shi) : 0ull);
       S.js = w;
       S.rad = radmax;
       if (w >= 0) {
@@ -270,16 +274,18 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
 
     if (S.exact) {
       // canonical FP64 projections and statistics
+      const unsigned long long mask = S.cmask;
       for (int i = tid; i < m; i += kB) {
         const float* x = X + (int64_t)sP[nb + i] * d;
         for (int j = 0; j < ntry; ++j)
-          p64[(int64_t)j * Tn + pbase + nb + i] = rpf_p64(x, r64 + j * d, d);
+          if ((mask >> j) & 1ull) p64[(int64_t)j * Tn + pbase + nb + i] = rpf_p64(x, r64 + j * d, d);
       }
       __syncthreads();
       if (warp == 0) {
         double best = 0.0;
         int js = -1;
         for (int j = 0; j < ntry; ++j) {
+          if (!((mask >> j) & 1ull)) continue;  // certainly below a contender
           const double* p = p64 + (int64_t)j * Tn + pbase + nb;
           const double Ssum = rpf_warp_chunk_sum(m, lane, [&](int64_t k) { return p[k]; });
           const double mu = __ddiv_rn(Ssum, (double)m);
