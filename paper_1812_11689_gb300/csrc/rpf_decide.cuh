@@ -43,6 +43,7 @@ __device__ __forceinline__ void rpf_gauss_pair(uint64_t seed, uint64_t t, uint64
 // 1 / |g| in FP32: |g| = sqrtf(sequential fmaf sum of g_k^2); 0 if g = 0
 __device__ __forceinline__ float rpf_inv_norm32(const float* g, int d) {
   float ss = 0.0f;
+#pragma unroll 8
   for (int k = 0; k < d; ++k) ss = __fmaf_rn(g[k], g[k], ss);
   return ss == 0.0f ? 0.0f : __fdiv_rn(1.0f, __fsqrt_rn(ss));
 }

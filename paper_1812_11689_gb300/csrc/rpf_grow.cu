@@ -106,10 +106,12 @@ __global__ void k_xnorm(const float* X, int64_t n, int d, float* out) {
   out[i] = __fmul_ru(__fsqrt_ru(s), 1.0f + (float)(d + 4) * 0x1p-23f);
 }
 
-// Directions of the frontier nodes and the base projections b_j = p64(o, r_j)
+// Directions of the frontier nodes and the base projections b_j = r_j . o
 // of each node's first member o; one warp per (node, try).  The lanes draw
-// the Box-Muller pairs; the normalisation's sum and b_j keep their sequential
-// order (one lane), so r and b_j equal rpf_gen_direction / rpf_p64 bit for bit.
+// the Box-Muller pairs; the normalisation's sum keeps its sequential order
+// (one lane), so r equals rpf_gen_direction bit for bit.  b_j is summed
+// lane-strided and then by a butterfly (depth ceil(d / 32) + 5): the radius
+// covers b_j summed in any order of depth <= d + 38.
 __global__ void __launch_bounds__(128) k_dirs_a(int F, int ntry, int d, uint64_t seed, int t_base,
                                                 int64_t n,
                                                 const int32_t* fr_tree, const int32_t* fr_begin,
@@ -140,10 +142,14 @@ __global__ void __launch_bounds__(128) k_dirs_a(int F, int ntry, int d, uint64_t
     r32[k] = v;
     r[k] = (double)v;
   }
-  __syncwarp();
+  const int32_t og = perm_cur[(int64_t)tl * n + fr_begin[f]];
+  const float* xo = X + (int64_t)og * d;
+  double b = 0.0;
+  for (int k = lane; k < d; k += 32) b = __fma_rn((double)xo[k], r[k], b);  // r[k]: this lane's
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) b = __dadd_rn(b, __shfl_xor_sync(RPF_FULL, b, off));
   if (lane == 0) {
-    const int32_t og = perm_cur[(int64_t)tl * n + fr_begin[f]];
-    fr_base[g] = rpf_p64(X + (int64_t)og * d, r, d);
+    fr_base[g] = b;
     if (j == 0) fr_ogid[f] = og;
   }
 }
@@ -336,14 +342,6 @@ __global__ void __launch_bounds__(kBlock) k_cand(
       }
     }
   }
-}
-
-__global__ void k_cand_finish(int F, const int32_t* fr_exact, const unsigned long long* fr_akey,
-                              const unsigned long long* fr_bkey, double* fr_a, double* fr_b) {
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= F || fr_exact[f]) return;
-  fr_a[f] = rpf_dkey_inv(fr_akey[f]);
-  fr_b[f] = rpf_dkey_inv(fr_bkey[f]);
 }
 
 // --- exact path: canonical FP64 projections and statistics (Algorithm 2) ---
@@ -661,28 +659,35 @@ __global__ void k_med_rank(int F, const int32_t* fr_len, const int32_t* fr_exact
   md_rank[f] = (fr_len[f] >> 1) - md_l0[f];
 }
 
+// (a, b: the exact path's for exact nodes, else the candidates' extremes;
+// the fallback counter gains the level's exact nodes)
 __global__ void k_split_a(int F, int ntry, uint64_t seed, int t_base, int median,
                           const int32_t* fr_node,
                           const int32_t* fr_tree, const uint64_t* fr_key, const int32_t* fr_exact,
                           const int32_t* fr_jstar, const double* fr_a, const double* fr_b,
+                          const unsigned long long* fr_akey, const unsigned long long* fr_bkey,
                           const double* fr_base, const float* fr_rad,
                           const unsigned long long* md_key, double* fr_c, int32_t* fr_flag,
                           float* fr_tl, float* fr_tr, int32_t* node_jstar, int32_t* node_flag,
-                          double* node_c) {
+                          double* node_c, unsigned long long* n_exact) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= F) return;
   const int js = fr_jstar[f];
+  const int exact = fr_exact[f];
+  if (exact) atomicAdd(n_exact, 1ULL);
   double c = NAN;
   int acc = 0;
   if (js >= 0 && median) {  // c = the p64 of the first point that goes right
     c = rpf_dkey_inv(md_key[f]);
     acc = 1;
   } else if (js >= 0) {
-    acc = rpf_split_point(seed, (uint64_t)(fr_tree[f] + t_base), fr_key[f], fr_a[f], fr_b[f], &c);
+    const double a = exact ? fr_a[f] : rpf_dkey_inv(fr_akey[f]);
+    const double b = exact ? fr_b[f] : rpf_dkey_inv(fr_bkey[f]);
+    acc = rpf_split_point(seed, (uint64_t)(fr_tree[f] + t_base), fr_key[f], a, b, &c);
   }
   fr_c[f] = c;
   fr_flag[f] = acc ? 0 : 1;
-  if (acc && !median && !fr_exact[f]) {
+  if (acc && !median && !exact) {
     float tl, tr;
     rpf_side_thresholds(c, fr_base[(int64_t)f * ntry + js], (double)fr_rad[f], &tl, &tr);
     fr_tl[f] = tl;
@@ -690,7 +695,7 @@ __global__ void k_split_a(int F, int ntry, uint64_t seed, int t_base, int median
   }
   const int id = fr_node[f];
   node_jstar[id] = js;
-  node_flag[id] = (acc ? 0 : 1) | (fr_exact[f] ? 2 : 0);
+  node_flag[id] = (acc ? 0 : 1) | (exact ? 2 : 0);
   node_c[id] = c;
 }
 
@@ -985,11 +990,6 @@ __global__ void __launch_bounds__(1024) k_frontier(
     out->n_leaves_new = run_l;
     out->n_items_new = run_i;
   }
-}
-
-__global__ void k_count_exact(int F, const int32_t* fr_exact, unsigned long long* counter) {
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f < F && fr_exact[f]) atomicAdd(counter, 1ULL);
 }
 
 // --- node table compaction: valid slots (tree >= 0) keep their order -------
@@ -1381,8 +1381,6 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     RPF_LAUNCH("k_cand", s, k_cand<<<Ci, kBlock, 0, s>>>(
         ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, lv.fr_jstar, lv.fr_wlo,
         lv.fr_whi, fo->X, perm_cur, n, Tn, d, ntry, p32, lv.dir64, lv.fr_akey, lv.fr_bkey));
-    RPF_LAUNCH("k_cand_finish", s, k_cand_finish<<<nblk(F, 128), 128, 0, s>>>(
-        Fi, lv.fr_exact, lv.fr_akey, lv.fr_bkey, lv.fr_a, lv.fr_b));
     // the exact-chunk list borrows ch_loff, which k_node_scan fills later
     RPF_TRYCU(cudaMemsetAsync(ex_count, 0, sizeof(int32_t), s));
     RPF_LAUNCH("k_exact_list", s, k_exact_list<<<nblk(C, 256), 256, 0, s>>>(
@@ -1398,8 +1396,6 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
           pass, Fi, ntry, fr_cb, fr_nc, fr_len, lv.fr_exact, lv.fr_cmask, lv.cp_sum, lv.cp_min, lv.cp_max,
           lv.fr_mu, lv.fr_min, lv.fr_max, lv.fr_jstar, lv.fr_a, lv.fr_b));
     }
-    RPF_LAUNCH("k_count_exact", s,
-               k_count_exact<<<nblk(F, 256), 256, 0, s>>>(Fi, lv.fr_exact, d_exact));
     if (median) {
       RPF_LAUNCH("k_med_init", s, k_med_init<<<nblk(F, 128), 128, 0, s>>>(
           Fi, fr_len, lv.md_fk, lv.md_key, lv.md_id, lv.md_rank, lv.md_l0));
@@ -1423,8 +1419,8 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     }
     RPF_LAUNCH("k_split_a", s, k_split_a<<<nblk(F, 128), 128, 0, s>>>(
         Fi, ntry, seed, fo->t_base, median, fr_node, fr_tree, fr_key, lv.fr_exact, lv.fr_jstar, lv.fr_a,
-        lv.fr_b, lv.fr_base, lv.fr_rad, lv.md_key, lv.fr_c, lv.fr_flag, lv.fr_tl, lv.fr_tr,
-        fo->node_jstar, fo->node_flag, fo->node_c));
+        lv.fr_b, lv.fr_akey, lv.fr_bkey, lv.fr_base, lv.fr_rad, lv.md_key, lv.fr_c, lv.fr_flag,
+        lv.fr_tl, lv.fr_tr, fo->node_jstar, fo->node_flag, fo->node_c, d_exact));
     RPF_LAUNCH("k_side_count", s, k_side_count<<<Ci, kBlock, 0, s>>>(
         ch_node, ch_start, ch_len, fr_tree, fr_begin, fr_len, lv.fr_exact, lv.fr_jstar,
         lv.fr_flag, lv.fr_c, lv.fr_tl, lv.fr_tr, fo->X, perm_cur, n, Tn, d, ntry, p32, p64,
