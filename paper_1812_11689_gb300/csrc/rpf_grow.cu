@@ -292,16 +292,20 @@ __global__ void __launch_bounds__(128) k_certify_a(
   }
 }
 
-// Exact FP64 projections of the min / max candidates of certified nodes.
+// Exact FP64 projections of the min / max candidates of certified nodes;
+// chunks of exact nodes are listed instead.
 __global__ void __launch_bounds__(kBlock) k_cand(
     const int32_t* ch_node, const int32_t* ch_start, const int32_t* ch_len, const int32_t* fr_tree,
     const int32_t* fr_begin, const int32_t* fr_exact, const int32_t* fr_jstar, const float* fr_wlo,
     const float* fr_whi, const float* X, const int32_t* perm_cur, int64_t n, int64_t Tn, int d,
     int ntry, const float* p32, const double* dir64, unsigned long long* fr_akey,
-    unsigned long long* fr_bkey) {
+    unsigned long long* fr_bkey, int32_t* ex_list, int32_t* ex_count) {
   const int c = blockIdx.x;
   const int f = ch_node[c];
-  if (fr_exact[f]) return;
+  if (fr_exact[f]) {  // listed for the exact path instead
+    if (threadIdx.x == 0) ex_list[atomicAdd(ex_count, 1)] = c;
+    return;
+  }
   const int js = fr_jstar[f];
   const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
   const int len = ch_len[c];
@@ -345,14 +349,6 @@ __global__ void __launch_bounds__(kBlock) k_cand(
 }
 
 // --- exact path: canonical FP64 projections and statistics (Algorithm 2) ---
-// Chunks of exact nodes, listed so that their FP64 work spreads over the GPU.
-__global__ void k_exact_list(int C, const int32_t* ch_node, const int32_t* fr_exact, int32_t* list,
-                             int32_t* count) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= C || !fr_exact[ch_node[c]]) return;
-  list[atomicAdd(count, 1)] = c;
-}
-
 // Grid-stride over (listed chunk, slice of 256 positions): canonical FP64
 // projections of every try still in contention.
 __global__ void __launch_bounds__(kBlock) k_proj64(
@@ -1378,13 +1374,13 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
         Fi, ntry, exact_only, fr_cb, fr_nc, fr_len, lv.cp_s1, lv.cp_s2, lv.cp_a, lv.cp_min32,
         lv.cp_max32, lv.cp_rad, lv.fr_base, lv.fr_exact, lv.fr_jstar, lv.fr_rad, lv.fr_wlo,
         lv.fr_whi, lv.fr_akey, lv.fr_bkey, lv.fr_cmask));
+    // chunks of exact nodes are listed (in ch_loff, which k_node_scan fills
+    // later) so that their FP64 work spreads over the GPU
+    RPF_TRYCU(cudaMemsetAsync(ex_count, 0, sizeof(int32_t), s));
     RPF_LAUNCH("k_cand", s, k_cand<<<Ci, kBlock, 0, s>>>(
         ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, lv.fr_jstar, lv.fr_wlo,
-        lv.fr_whi, fo->X, perm_cur, n, Tn, d, ntry, p32, lv.dir64, lv.fr_akey, lv.fr_bkey));
-    // the exact-chunk list borrows ch_loff, which k_node_scan fills later
-    RPF_TRYCU(cudaMemsetAsync(ex_count, 0, sizeof(int32_t), s));
-    RPF_LAUNCH("k_exact_list", s, k_exact_list<<<nblk(C, 256), 256, 0, s>>>(
-        Ci, ch_node, lv.fr_exact, lv.ch_loff, ex_count));
+        lv.fr_whi, fo->X, perm_cur, n, Tn, d, ntry, p32, lv.dir64, lv.fr_akey, lv.fr_bkey,
+        lv.ch_loff, ex_count));
     RPF_LAUNCH("k_proj64", s, k_proj64<<<4 * 152, kBlock, 0, s>>>(
         lv.ch_loff, ex_count, ch_node, ch_start, ch_len, fr_tree, fr_begin, fo->X, perm_cur, n,
         Tn, d, ntry, lv.dir64, lv.fr_cmask, p64));
