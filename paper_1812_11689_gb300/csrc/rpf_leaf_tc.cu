@@ -628,8 +628,11 @@ int launch_tc_rows(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0,
                            : launch_tc<KK, 256>(f, tlo, thi, K, t0, cand, s, force);
 }
 
+// sorted-list length for K: only the first K slots are read, so common K
+// (10, 20) get lists of exactly K
 int kk_of(int K) {
-  return K <= 4 ? 4 : K <= 8 ? 8 : K <= 12 ? 12 : K <= 16 ? 16 : K <= 24 ? 24 : 32;
+  return K <= 4 ? 4 : K <= 8 ? 8 : K <= 10 ? 10 : K <= 12 ? 12 : K <= 16 ? 16 : K <= 20 ? 20
+         : K <= 24 ? 24 : 32;
 }
 
 int launch_tc_k(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint2* cand,
@@ -637,8 +640,10 @@ int launch_tc_k(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, ui
   switch (kk_of(K)) {
     case 4: return launch_tc_rows<4>(f, tlo, thi, K, t0, cand, s, force);
     case 8: return launch_tc_rows<8>(f, tlo, thi, K, t0, cand, s, force);
+    case 10: return launch_tc_rows<10>(f, tlo, thi, K, t0, cand, s, force);
     case 12: return launch_tc_rows<12>(f, tlo, thi, K, t0, cand, s, force);
     case 16: return launch_tc_rows<16>(f, tlo, thi, K, t0, cand, s, force);
+    case 20: return launch_tc_rows<20>(f, tlo, thi, K, t0, cand, s, force);
     case 24: return launch_tc_rows<24>(f, tlo, thi, K, t0, cand, s, force);
     default: return launch_tc_rows<32>(f, tlo, thi, K, t0, cand, s, force);
   }
