@@ -60,6 +60,8 @@
 #include "rpf_umma.cuh"
 
 #define TC_SLOTS 32       // exact re-rank candidates per row
+#define TC_SLOT_STRIDE 36 // bytes per row's slots: rows 9 words apart, so a warp's
+                          // slot accesses fall in distinct banks
 #define TC_SEG 4096       // packing segment (positions) per thread
 #define TC_SEG_TILES 72   // >= 2 (TC_SEG + 128) / 128 + 1 tiles per segment
 #define TC_MAX_BIG 8      // leaves of > TC_SLOTS + 1 points in one tile (<= 3)
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
     }
     // (4) per-row candidates: small leaves offer everything; large leaves
     // offer the certified margin around tau
-    unsigned char* my = slots + r * TC_SLOTS;
+    unsigned char* my = slots + r * TC_SLOT_STRIDE;
     int ns = 0;
     float tau2 = 0.0f, eps = 0.0f, eta = 0.0f;
     const bool tc_row = big && cert_ok;
@@ -546,7 +548,7 @@ size_t tc_need(int d, int dp, int rows, int KC) {
   const int d4 = (d + 3) & ~3;
   const size_t a_off = (((size_t)rows * dp * 4) + 1023) & ~(size_t)1023;
   return a_off + (size_t)2 * rows * KC * 2 + (size_t)TC_MAX_BIG * d4 * 4 +
-         (size_t)rows * TC_SLOTS;
+         (size_t)rows * TC_SLOT_STRIDE;
 }
 
 // Dynamic shared memory of a CTA.  128-row tiles: if the tile fits 52 KB,
