@@ -251,7 +251,23 @@ __global__ void __launch_bounds__(128) k_certify_a(
   const double inv_m = 1.0 / (double)m;
   for (int j = lane; j < ntry; j += 32) {
     double a = 0.0, b = 0.0, e = 0.0;
-    for (int c = cb; c < cb + nc; ++c) {
+    int c = cb;
+    for (; c + 3 < cb + nc; c += 4) {  // partials fetched ahead, added in chunk order
+      double va[4], vb[4], ve[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        va[u] = cp_s1[(int64_t)(c + u) * ntry + j];
+        vb[u] = cp_s2[(int64_t)(c + u) * ntry + j];
+        ve[u] = cp_a[(int64_t)(c + u) * ntry + j];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a = __dadd_rn(a, va[u]);
+        b = __dadd_rn(b, vb[u]);
+        e = __dadd_rn(e, ve[u]);
+      }
+    }
+    for (; c < cb + nc; ++c) {
       a = __dadd_rn(a, cp_s1[(int64_t)c * ntry + j]);
       b = __dadd_rn(b, cp_s2[(int64_t)c * ntry + j]);
       e = __dadd_rn(e, cp_a[(int64_t)c * ntry + j]);

@@ -140,12 +140,22 @@ __device__ __forceinline__ void rpf_sincos2pif(float u, float* c_out, float* s_o
 // Canonical FP64 warp sum of one chunk (<= 4096 values): lane l adds
 // v[l], v[l+32], ... in order from +0.0, then the lane sums are folded by
 // xor-butterfly 16, 8, 4, 2, 1 (lane 0 follows s_l += s_{l+off}).  Every lane
-// returns the result.  All 32 lanes must call it.
+// returns the result.  All 32 lanes must call it.  The values are fetched 8
+// at a time ahead of the additions (same order of additions), so the FP64
+// chain does not wait for a load at every step.
 // ---------------------------------------------------------------------------
 template <typename F>
 __device__ __forceinline__ double rpf_warp_chunk_sum(int64_t len, int lane, F val) {
   double a = 0.0;
-  for (int64_t k = lane; k < len; k += 32) a = __dadd_rn(a, val(k));
+  int64_t k = lane;
+  for (; k + 32 * 7 < len; k += 32 * 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = val(k + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a = __dadd_rn(a, v[u]);
+  }
+  for (; k < len; k += 32) a = __dadd_rn(a, val(k));
 #pragma unroll
   for (int off = 16; off >= 1; off >>= 1) a = __dadd_rn(a, __shfl_xor_sync(RPF_FULL, a, off));
   return a;
