@@ -40,6 +40,7 @@
 namespace {
 
 constexpr int kBlock = 256;
+static_assert(RPF_CHUNK % kBlock == 0, "a chunk is a whole number of block strides");
 constexpr int kSub = RPF_CHUNK;
 constexpr int kCandList = 256;  // min / max candidates listed per chunk for the warp pass  // nodes of at most this many points grow in one CTA
 
@@ -729,13 +730,24 @@ __global__ void __launch_bounds__(kBlock) k_side_count(
   const int js = fr_jstar[f];
   const double cc = fr_c[f];
   const float tl = fr_tl[f], tr = fr_tr[f];
+  // the chunk's q' of the winner, fetched at once (<= 16 per thread)
+  constexpr int kPer = RPF_CHUNK / kBlock;
+  float qv[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int i = threadIdx.x + u * kBlock;
+    qv[u] = (!flag && !exact && i < len) ? p32[(int64_t)js * Tn + base + i] : 0.0f;
+  }
   int cnt = 0;
-  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int i = threadIdx.x + u * kBlock;
+    if (i >= len) break;
     bool left;
     if (flag) {
       left = (ch_start[c] + i) < (m >> 1);
     } else if (median) {  // certainly below / above the band, else (key, index) order
-      const float q = p32[(int64_t)js * Tn + base + i];
+      const float q = qv[u];
       if (!exact && q < md_lo[f]) {
         left = true;
       } else if (!exact && q > md_hi[f]) {
@@ -748,7 +760,7 @@ __global__ void __launch_bounds__(kBlock) k_side_count(
     } else if (exact) {
       left = p64[(int64_t)js * Tn + base + i] < cc;
     } else {
-      const float v = p32[(int64_t)js * Tn + base + i];
+      const float v = qv[u];
       if (v < tl) {
         left = true;
       } else if (v >= tr) {
@@ -830,10 +842,23 @@ __global__ void __launch_bounds__(kBlock) k_scatter(
   __shared__ int tile_l;
   int carryL = 0, carryR = 0;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int t0 = 0; t0 < len; t0 += kBlock) {
+  // the chunk's sides and point ids, fetched at once (<= 16 per thread)
+  constexpr int kPer = RPF_CHUNK / kBlock;
+  int sv[kPer];
+  int32_t pv[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int i = u * kBlock + threadIdx.x;
+    sv[u] = i < len ? side[base + i] : 0;
+    pv[u] = i < len ? perm_cur[base + i] : 0;
+  }
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int t0 = u * kBlock;
+    if (t0 >= len) break;
     const int i = t0 + threadIdx.x;
     const bool valid = i < len;
-    const int s = valid ? side[base + i] : 0;
+    const int s = sv[u];
     int x = s;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -854,7 +879,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter(
     __syncthreads();
     const int rankL = x - s + wsum[w];
     if (valid) {
-      const int32_t v = perm_cur[base + i];
+      const int32_t v = pv[u];
       if (s) dstL[tbase + begin + loff + carryL + rankL] = v;
       else dstR[tbase + begin + nl + roff + carryR + (int)threadIdx.x - rankL] = v;
     }
