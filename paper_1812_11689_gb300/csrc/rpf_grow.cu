@@ -334,9 +334,19 @@ __global__ void __launch_bounds__(kBlock) k_cand(
   __shared__ int s_n;
   __shared__ int s_e[kCandList];
   if (threadIdx.x == 0) s_n = 0;
+  constexpr int kPer = RPF_CHUNK / kBlock;
+  float qv[kPer];  // the chunk's q', fetched at once
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int i = threadIdx.x + u * kBlock;
+    qv[u] = i < len ? p[i] : 0.0f;
+  }
   __syncthreads();
-  for (int i = threadIdx.x; i < len; i += blockDim.x) {
-    const float v = p[i];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int i = threadIdx.x + u * kBlock;
+    if (i >= len) break;
+    const float v = qv[u];
     const bool a = v <= lo, b = v >= hi;
     if (!a && !b) continue;
     const int slot = atomicAdd(&s_n, 1);
@@ -555,16 +565,27 @@ __global__ void __launch_bounds__(kBlock) k_med_hist(
   const unsigned long long pk = md_key[f];
   const uint32_t pid = md_id[f];
   const float lo = md_lo[f], hi = md_hi[f];
-  for (int i = threadIdx.x; i < ch_len[c]; i += blockDim.x) {
+  const int len = ch_len[c];
+  constexpr int kPer = RPF_CHUNK / kBlock;
+  float qv[kPer];  // the chunk's q', fetched at once
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int i = threadIdx.x + u * kBlock;
+    qv[u] = (!exact && i < len) ? q[i] : 0.0f;
+  }
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int i = threadIdx.x + u * kBlock;
+    if (i >= len) break;
     int dig;
     bool match;
     if (pass < 4) {
       const int sh = 24 - 8 * pass;
-      const uint32_t k = rpf_fkey(q[i]);
+      const uint32_t k = rpf_fkey(qv[u]);
       dig = (int)((k >> sh) & 255u);
       match = pass == 0 || ((k ^ pf) >> (sh + 8)) == 0u;
     } else {
-      if (!exact && !(q[i] >= lo && q[i] <= hi)) continue;  // decided without p64
+      if (!exact && !(qv[u] >= lo && qv[u] <= hi)) continue;  // decided without p64
       match = rpf_med_digit(pass - 4, rpf_mkey(p[i]), (uint32_t)perm_cur[base + i], pk, pid, &dig);
     }
     if (match) atomicAdd(&h[dig], 1);
@@ -634,9 +655,20 @@ __global__ void __launch_bounds__(kBlock) k_med_band(
   const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
   const double* r = dir64 + ((int64_t)f * ntry + js) * d;
   const float* q = p32 + (int64_t)js * Tn + base;
+  const int len = ch_len[c];
+  constexpr int kPer = RPF_CHUNK / kBlock;
+  float qv[kPer];  // the chunk's q', fetched at once
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int i = threadIdx.x + u * kBlock;
+    qv[u] = i < len ? q[i] : 0.0f;
+  }
   int cnt = 0;
-  for (int i = threadIdx.x; i < ch_len[c]; i += blockDim.x) {
-    const float v = q[i];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int i = threadIdx.x + u * kBlock;
+    if (i >= len) break;
+    const float v = qv[u];
     if (v < lo) {
       ++cnt;
     } else if (v <= hi) {
