@@ -42,7 +42,8 @@ namespace {
 constexpr int kBlock = 256;
 static_assert(RPF_CHUNK % kBlock == 0, "a chunk is a whole number of block strides");
 constexpr int kSub = RPF_CHUNK;
-constexpr int kCandList = 256;  // min / max candidates listed per chunk for the warp pass  // nodes of at most this many points grow in one CTA
+constexpr int kCandList = 256;
+constexpr int kMedList = 256;  // median rule: bands up to this size are selected directly  // min / max candidates listed per chunk for the warp pass  // nodes of at most this many points grow in one CTA
 
 struct Level {
   int64_t cap_f = 0, cap_c = 0, cap_dir = 0;
@@ -60,6 +61,11 @@ struct Level {
   uint32_t *md_id{}, *md_fk{};
   int32_t *md_rank{}, *md_hist{}, *md_l0{};
   float *md_lo{}, *md_hi{};
+  // median rule: each certified node's band as (key, point index) pairs, at
+  // most kMedList of them, and whether the direct selection settled the node
+  int32_t *md_bn{}, *md_done{};
+  unsigned long long* md_bk{};
+  uint32_t* md_bi{};
   int32_t *ch_node[2]{}, *ch_start[2]{}, *ch_len[2]{};
   int32_t *ch_nleft{}, *ch_loff{};
   double *cp_sum{}, *cp_min{}, *cp_max{};
@@ -71,6 +77,7 @@ struct Level {
 
 struct Counts {
   int32_t f_next, c_next, n_leaves_new, n_items_new;
+  int32_t n_radix;  // median rule: nodes whose exact selection needs the radix passes
 };
 
 template <typename T>
@@ -534,7 +541,7 @@ __global__ void k_csum_nodes(int pass, int F, int ntry, const int32_t* fr_cb, co
 // ---------------------------------------------------------------------------
 __global__ void k_med_init(int F, const int32_t* fr_len, uint32_t* md_fk,
                            unsigned long long* md_key, uint32_t* md_id, int32_t* md_rank,
-                           int32_t* md_l0) {
+                           int32_t* md_l0, int32_t* md_bn, int32_t* md_done) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= F) return;
   md_fk[f] = 0u;
@@ -542,6 +549,40 @@ __global__ void k_med_init(int F, const int32_t* fr_len, uint32_t* md_fk,
   md_id[f] = 0u;
   md_rank[f] = fr_len[f] >> 1;
   md_l0[f] = 0;
+  md_bn[f] = 0;
+  md_done[f] = 0;
+}
+
+// Median rule, a node's band of at most kMedList points (one warp per node):
+// the band point with exactly md_rank smaller (key, index) pairs in the band
+// is the selection (the pairs are distinct).  Exact nodes and larger bands
+// are counted for the radix passes.
+__global__ void __launch_bounds__(128) k_med_direct(
+    int F, const int32_t* fr_exact, const int32_t* fr_jstar, const int32_t* md_bn,
+    const unsigned long long* md_bk, const uint32_t* md_bi, const int32_t* md_rank,
+    unsigned long long* md_key, uint32_t* md_id, int32_t* md_done, int32_t* n_radix) {
+  const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (f >= F || fr_jstar[f] < 0) return;  // whole warp
+  const int nb = md_bn[f];
+  if (fr_exact[f] || nb > kMedList) {
+    if (lane == 0) atomicAdd(n_radix, 1);
+    return;
+  }
+  const unsigned long long* K = md_bk + (int64_t)f * kMedList;
+  const uint32_t* I = md_bi + (int64_t)f * kMedList;
+  const int r = md_rank[f];
+  for (int e = lane; e < nb; e += 32) {
+    const unsigned long long k = K[e];
+    const uint32_t id = I[e];
+    int below = 0;
+    for (int g = 0; g < nb; ++g) below += K[g] < k || (K[g] == k && I[g] < id);
+    if (below == r) {
+      md_key[f] = k;
+      md_id[f] = id;
+    }
+  }
+  if (lane == 0) md_done[f] = 1;
 }
 
 __global__ void __launch_bounds__(kBlock) k_med_hist(
@@ -549,13 +590,14 @@ __global__ void __launch_bounds__(kBlock) k_med_hist(
     const int32_t* fr_tree, const int32_t* fr_begin, const int32_t* fr_exact,
     const int32_t* fr_jstar, const int32_t* perm_cur, int64_t n, int64_t Tn, const float* p32,
     const double* p64, const uint32_t* md_fk, const unsigned long long* md_key,
-    const uint32_t* md_id, const float* md_lo, const float* md_hi, int32_t* md_hist) {
+    const uint32_t* md_id, const float* md_lo, const float* md_hi, const int32_t* md_done,
+    int32_t* md_hist) {
   __shared__ int h[256];
   const int c = blockIdx.x;
   const int f = ch_node[c];
   const int js = fr_jstar[f];
   const int exact = fr_exact[f];
-  if (js < 0 || (pass < 4 && exact)) return;  // no median / no FP32 stage
+  if (js < 0 || (pass < 4 && exact) || (pass >= 4 && md_done[f])) return;  // nothing to count
   for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
   __syncthreads();
   const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
@@ -598,12 +640,14 @@ __global__ void __launch_bounds__(kBlock) k_med_hist(
 // one warp per node: the digit whose bin holds the remaining rank; the bins
 // are cleared for the next pass
 __global__ void __launch_bounds__(128) k_med_select(int pass, int F, const int32_t* fr_exact,
-                                                    const int32_t* fr_jstar, uint32_t* md_fk,
-                                                    unsigned long long* md_key, uint32_t* md_id,
-                                                    int32_t* md_rank, int32_t* md_hist) {
+                                                    const int32_t* fr_jstar, const int32_t* md_done,
+                                                    uint32_t* md_fk, unsigned long long* md_key,
+                                                    uint32_t* md_id, int32_t* md_rank,
+                                                    int32_t* md_hist) {
   const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (f >= F || fr_jstar[f] < 0 || (pass < 4 && fr_exact[f])) return;  // whole warp
+  if (f >= F || fr_jstar[f] < 0 || (pass < 4 && fr_exact[f]) || (pass >= 4 && md_done[f]))
+    return;  // whole warp
   int32_t* hb = md_hist + (int64_t)f * 256 + 8 * lane;
   int v[8], sum = 0;
 #pragma unroll
@@ -644,7 +688,7 @@ __global__ void __launch_bounds__(kBlock) k_med_band(
     const int32_t* fr_begin, const int32_t* fr_exact, const int32_t* fr_jstar,
     const float* fr_rad, const float* X, const int32_t* perm_cur, int64_t n, int64_t Tn, int d,
     int ntry, const double* dir64, const float* p32, const uint32_t* md_fk, double* p64,
-    int32_t* md_l0) {
+    int32_t* md_l0, int32_t* md_bn, unsigned long long* md_bk, uint32_t* md_bi) {
   __shared__ int wc[kBlock / 32];
   const int c = blockIdx.x;
   const int f = ch_node[c];
@@ -672,7 +716,14 @@ __global__ void __launch_bounds__(kBlock) k_med_band(
     if (v < lo) {
       ++cnt;
     } else if (v <= hi) {
-      p64[(int64_t)js * Tn + base + i] = rpf_p64(X + (int64_t)perm_cur[base + i] * d, r, d);
+      const int32_t id = perm_cur[base + i];
+      const double pv = rpf_p64(X + (int64_t)id * d, r, d);
+      p64[(int64_t)js * Tn + base + i] = pv;
+      const int e = atomicAdd(&md_bn[f], 1);
+      if (e < kMedList) {
+        md_bk[(int64_t)f * kMedList + e] = rpf_mkey(pv);
+        md_bi[(int64_t)f * kMedList + e] = (uint32_t)id;
+      }
     }
   }
   for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(RPF_FULL, cnt, off);
@@ -1178,7 +1229,8 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
                   lv.fr_rad, lv.fr_wlo, lv.fr_whi, lv.fr_akey, lv.fr_bkey, lv.ch_nleft, lv.ch_loff,
                   lv.cp_sum, lv.cp_min, lv.cp_max, lv.cp_s1, lv.cp_s2, lv.cp_a, lv.cp_min32,
                   lv.cp_max32, lv.cp_rad, lv.dir64, lv.dir32, lv.md_key, lv.md_id, lv.md_rank,
-                  lv.md_hist, lv.md_fk, lv.md_l0, lv.md_lo, lv.md_hi, lv.fr_cmask};
+                  lv.md_hist, lv.md_fk, lv.md_l0, lv.md_lo, lv.md_hi, lv.fr_cmask, lv.md_bn,
+                  lv.md_done, lv.md_bk, lv.md_bi};
     for (void* p : ps) rpf_release(p, s);
     for (int q = 0; q < 2; ++q) {
       void* qs[] = {lv.fr_node[q], lv.fr_tree[q], lv.fr_begin[q], lv.fr_len[q], lv.fr_cb[q],
@@ -1344,6 +1396,12 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
       if ((r = grow_buf(&lv.md_l0, 0, nf, s, false))) return r;
       if ((r = grow_buf(&lv.md_lo, 0, nf, s, false))) return r;
       if ((r = grow_buf(&lv.md_hi, 0, nf, s, false))) return r;
+      if (median) {
+        if ((r = grow_buf(&lv.md_bn, 0, nf, s, false))) return r;
+        if ((r = grow_buf(&lv.md_done, 0, nf, s, false))) return r;
+        if ((r = grow_buf(&lv.md_bk, 0, nf * kMedList, s, false))) return r;
+        if ((r = grow_buf(&lv.md_bi, 0, nf * kMedList, s, false))) return r;
+      }
       lv.cap_f = nf;
     }
     if (F * ntry > lv.cap_dir) {
@@ -1467,23 +1525,36 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     }
     if (median) {
       RPF_LAUNCH("k_med_init", s, k_med_init<<<nblk(F, 128), 128, 0, s>>>(
-          Fi, fr_len, lv.md_fk, lv.md_key, lv.md_id, lv.md_rank, lv.md_l0));
+          Fi, fr_len, lv.md_fk, lv.md_key, lv.md_id, lv.md_rank, lv.md_l0, lv.md_bn, lv.md_done));
       RPF_TRYCU(cudaMemsetAsync(lv.md_hist, 0, sizeof(int32_t) * 256 * (size_t)F, s));
       for (int pass = 0; pass < 16; ++pass) {
-        if (pass == 4) {  // the band around the FP32 median; exact keys only inside it
+        if (pass == 4) {
+          // the band around the FP32 median; exact keys only inside it; a
+          // band of at most kMedList points is settled directly, and the
+          // radix passes run only if some node still needs them
           RPF_LAUNCH("k_med_band", s, k_med_band<<<Ci, kBlock, 0, s>>>(
               ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, lv.fr_jstar, lv.fr_rad,
-              fo->X, perm_cur, n, Tn, d, ntry, lv.dir64, p32, lv.md_fk, p64, lv.md_l0));
+              fo->X, perm_cur, n, Tn, d, ntry, lv.dir64, p32, lv.md_fk, p64, lv.md_l0, lv.md_bn,
+              lv.md_bk, lv.md_bi));
           RPF_LAUNCH("k_med_rank", s, k_med_rank<<<nblk(F, 128), 128, 0, s>>>(
               Fi, fr_len, lv.fr_exact, lv.fr_jstar, lv.fr_rad, lv.md_fk, lv.md_l0, lv.md_rank,
               lv.md_lo, lv.md_hi));
+          RPF_TRYCU(cudaMemsetAsync(&d_cnt->n_radix, 0, sizeof(int32_t), s));
+          RPF_LAUNCH("k_med_direct", s, k_med_direct<<<nblk(F * 32, 128), 128, 0, s>>>(
+              Fi, lv.fr_exact, lv.fr_jstar, lv.md_bn, lv.md_bk, lv.md_bi, lv.md_rank, lv.md_key,
+              lv.md_id, lv.md_done, &d_cnt->n_radix));
+          RPF_TRYCU(cudaMemcpyAsync(&h_cnt->n_radix, &d_cnt->n_radix, sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, s));
+          RPF_TRYCU(cudaStreamSynchronize(s));
+          if (h_cnt->n_radix == 0) break;
         }
         RPF_LAUNCH("k_med_hist", s, k_med_hist<<<Ci, kBlock, 0, s>>>(
             pass, ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_exact, lv.fr_jstar, perm_cur,
-            n, Tn, p32, p64, lv.md_fk, lv.md_key, lv.md_id, lv.md_lo, lv.md_hi, lv.md_hist));
-        RPF_LAUNCH("k_med_select", s, k_med_select<<<nblk(F * 32, 128), 128, 0, s>>>(
-            pass, Fi, lv.fr_exact, lv.fr_jstar, lv.md_fk, lv.md_key, lv.md_id, lv.md_rank,
+            n, Tn, p32, p64, lv.md_fk, lv.md_key, lv.md_id, lv.md_lo, lv.md_hi, lv.md_done,
             lv.md_hist));
+        RPF_LAUNCH("k_med_select", s, k_med_select<<<nblk(F * 32, 128), 128, 0, s>>>(
+            pass, Fi, lv.fr_exact, lv.fr_jstar, lv.md_done, lv.md_fk, lv.md_key, lv.md_id,
+            lv.md_rank, lv.md_hist));
       }
     }
     RPF_LAUNCH("k_split_a", s, k_split_a<<<nblk(F, 128), 128, 0, s>>>(

@@ -420,6 +420,17 @@ def test_median_rule_ties_and_queries():
     assert np.array_equal(qi.cpu().numpy(), oi) and np.array_equal(qd.cpu().numpy(), od)
 
 
+def test_median_rule_mixed_band_sizes_in_one_level():
+    # 3000 copies of one off-centre point among 9000 others: depending on the
+    # tree's direction the root median falls inside the copies (a band far
+    # above 256 points, radix passes) or outside them (a small band, settled
+    # directly), so one level of the level-synchronous phase mixes both
+    X = synth.make("mix50_d96", n=12000)
+    X[9000:] = X[17]
+    o = oracle.Forest(X, 6, 64, 3, seed=21, split_rule=1)
+    compare_trees(_median_forest(X, 6, 64, 3, seed=21), o, 6)
+
+
 @pytest.mark.parametrize("form,split_rule", [(0, 0), (1, 0), (1, 1)])
 def test_add_trees_equals_the_larger_build(form, split_rule):
     # 3 trees, then 2 and 1 more: the forest a 6-tree build grows
