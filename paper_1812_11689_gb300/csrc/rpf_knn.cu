@@ -388,11 +388,12 @@ __global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, in
     if (flag & 1) {  // rank split: every query goes left
       go_left = 1;
     } else {
-      const double e = (double)__fmul_ru(kerr, __fmul_ru(aacc, kA));
-      const double lo = __dsub_rd((double)sacc, e), hi = __dadd_ru((double)sacc, e);
-      if (hi < c) {
+      // q . r lies in [sacc - e, sacc + e]; the test runs in FP32 against
+      // c rounded down / up (a subset of what the FP64 test decides)
+      const float e = __fmul_ru(kerr, __fmul_ru(aacc, kA));
+      if (__fadd_ru(sacc, e) < __double2float_rd(c)) {
         go_left = 1;
-      } else if (lo >= c) {
+      } else if (__fsub_rd(sacc, e) >= __double2float_ru(c)) {
         go_left = 0;
       } else {  // undecided by the bound: the canonical FP64 chain
         int v = 0;
