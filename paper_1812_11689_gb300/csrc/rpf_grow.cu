@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
   float* sr = smf;                   // ntry x d
   float* so = smf + ntry * d;        // d
   float* red = so + ((d + 3) & ~3);  // 8 x TG x 5
+  float* tiles = red + 8 * 5 * 8;     // d % 4 == 0: a 32-row tile per warp
   const int c = blockIdx.x;
   const int f = ch_node[c];
   const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
@@ -203,25 +204,46 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
       mn[q] = INFINITY;
       mx[q] = -INFINITY;
     }
-    for (int u0 = 0; u0 * kBlock < len; u0 += 4) {
-      int gid[4], pos[4];
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        pos[p] = threadIdx.x + kBlock * (u0 + p);
-        gid[p] = pos[p] < len ? perm_cur[base + pos[p]] : -1;
-      }
-      float acc[4][TG], nn[4];
-      rpf_proj4<TG>(X, d, gid, so, sr + j0 * d, nj, acc, nn, j0 == 0);
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        if (gid[p] < 0) continue;
-        if (j0 == 0) radmax = fmaxf(radmax, rpf_point_rad(d, nn[p], xnorm[gid[p]], on));
+    if ((d & 3) == 0) {
+      // batches of 32 positions, one per lane, rows staged per warp
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      float* tile = tiles + warp * 32 * RPF_TILE_STRIDE;
+      for (int b = warp; b * 32 < len; b += kBlock / 32) {
+        const int pos = b * 32 + lane;
+        const int gid = pos < len ? perm_cur[base + pos] : -1;
+        float acc[TG], nn;
+        rpf_proj_tile<TG>(X, d, gid, so, sr + j0 * d, nj, tile, acc, nn, j0 == 0, lane);
+        if (gid < 0) continue;
+        if (j0 == 0) radmax = fmaxf(radmax, rpf_point_rad(d, nn, xnorm[gid], on));
 #pragma unroll
         for (int q = 0; q < TG; ++q) {
           if (q < nj) {
-            const float v = acc[p][q];
-            p32[(int64_t)(j0 + q) * Tn + base + pos[p]] = v;
-            rpf_stat_add(v, s1[q], s2[q], a1[q], mn[q], mx[q]);
+            p32[(int64_t)(j0 + q) * Tn + base + pos] = acc[q];
+            rpf_stat_add(acc[q], s1[q], s2[q], a1[q], mn[q], mx[q]);
+          }
+        }
+      }
+    } else {
+      for (int u0 = 0; u0 * kBlock < len; u0 += 4) {
+        int gid[4], pos[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          pos[p] = threadIdx.x + kBlock * (u0 + p);
+          gid[p] = pos[p] < len ? perm_cur[base + pos[p]] : -1;
+        }
+        float acc[4][TG], nn[4];
+        rpf_proj4<TG>(X, d, gid, so, sr + j0 * d, nj, acc, nn, j0 == 0);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          if (gid[p] < 0) continue;
+          if (j0 == 0) radmax = fmaxf(radmax, rpf_point_rad(d, nn[p], xnorm[gid[p]], on));
+#pragma unroll
+          for (int q = 0; q < TG; ++q) {
+            if (q < nj) {
+              const float v = acc[p][q];
+              p32[(int64_t)(j0 + q) * Tn + base + pos[p]] = v;
+              rpf_stat_add(v, s1[q], s2[q], a1[q], mn[q], mx[q]);
+            }
           }
         }
       }
@@ -1464,7 +1486,8 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     RPF_TRYCU(cudaStreamSynchronize(s));
   }
   const int TG = ntry <= 5 ? ntry : 8;
-  const size_t smem_a = sizeof(float) * ((size_t)ntry * d + ((d + 3) & ~3) + 8 * 5 * 8);
+  const size_t smem_a = sizeof(float) * ((size_t)ntry * d + ((d + 3) & ~3) + 8 * 5 * 8 +
+                                         ((d & 3) == 0 ? (size_t)(kBlock / 32) * 32 * RPF_TILE_STRIDE : 0));
   int32_t* perm_cur = perm_a;
   int32_t* perm_nxt = perm_b;
   while (F > 0) {
