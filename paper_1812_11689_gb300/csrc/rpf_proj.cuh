@@ -74,65 +74,75 @@ __device__ __forceinline__ void rpf_proj4(const float* __restrict__ X, int d, co
   }
 }
 
-// The same projections for a warp's 32 points, one per lane (gid < 0: none),
-// with the rows staged through shared memory (needs d % 4 == 0): every 64-
-// coordinate chunk of the 32 rows is read 16 lanes per row, one coalesced
-// 256-byte read per row, into a padded tile (row stride 68 floats, an odd
-// number of 16-byte units, so that the lanes' row reads fall in distinct
-// banks), and each lane then runs its own point's chains from the tile, over
-// k in order.  Gathering whole rows this way reaches about 4x the L2
-// bandwidth of one 16-byte load per lane per row.  All 32 lanes must call it.
-#define RPF_TILE_DC 64
-#define RPF_TILE_STRIDE 68
+// The same projections for a warp's 32 points, one per lane, with the rows
+// staged through shared memory (needs d % 4 == 0).  Rows are read 8 lanes
+// per 32-coordinate chunk (one coalesced 128-byte line per row) by cp.async
+// straight into a padded tile (row stride 36 floats, an odd number of 16-byte
+// units, so that the lanes' row reads fall in distinct banks); each lane then
+// runs its own point's chains from the tile, over k in order.  Gathering
+// whole lines this way reaches about 4x the L2 bandwidth of one 16-byte load
+// per lane per row, and two tiles per warp let the next chunk's copy overlap
+// the current chunk's arithmetic.
+#define RPF_TILE_DC 32
+#define RPF_TILE_STRIDE 36
+#define RPF_TILE_FLOATS (32 * RPF_TILE_STRIDE)
+
+__device__ __forceinline__ void rpf_cp16(float* sdst, const float* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void rpf_cp_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void rpf_cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Warp-collective: copy coordinates [k0, k0 + 32) of the 32 rows gid (lane
+// l's row to tile row l; gid < 0: none) into the tile.
+__device__ __forceinline__ void rpf_stage_rows(const float* __restrict__ X, int d, int gid, int k0,
+                                               float* tile, int lane) {
+  const int c4 = 4 * (lane & 7);
+  const int kc = min(RPF_TILE_DC, d - k0);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int row = 4 * i + (lane >> 3);
+    const int g = __shfl_sync(RPF_FULL, gid, row);
+    if (g >= 0 && c4 < kc) rpf_cp16(tile + row * RPF_TILE_STRIDE + c4, X + (int64_t)g * d + k0 + c4);
+  }
+}
+
+// Chains of the lane's row over coordinates [k0, k0 + kc) from the tile.
 template <int TG>
-__device__ __forceinline__ void rpf_proj_tile(const float* __restrict__ X, int d, int gid,
-                                              const float* so, const float* sr, int nj,
-                                              float* tile, float (&acc)[TG], float& nn,
-                                              bool want_nn, int lane) {
-  nn = 0.0f;
-#pragma unroll
-  for (int q = 0; q < TG; ++q) acc[q] = 0.0f;
-  const int c4 = 4 * (lane & 15);
-  for (int k0 = 0; k0 < d; k0 += RPF_TILE_DC) {
-    const int kc = min(RPF_TILE_DC, d - k0);
+__device__ __forceinline__ void rpf_tile_chunk(const float* tile, int lane, int k0, int kc,
+                                               const float* so, const float* sr, int d, int nj,
+                                               float (&acc)[TG], float& nn, bool want_nn) {
+  const float* xr = tile + lane * RPF_TILE_STRIDE;
 #pragma unroll 4
-    for (int i = 0; i < 16; ++i) {
-      const int row = 2 * i + (lane >> 4);
-      const int g = __shfl_sync(RPF_FULL, gid, row);
-      if (g >= 0 && c4 < kc)
-        *reinterpret_cast<float4*>(tile + row * RPF_TILE_STRIDE + c4) =
-            __ldg(reinterpret_cast<const float4*>(X + (int64_t)g * d + k0 + c4));
+  for (int k = 0; k < kc; k += 4) {
+    const float4 x4 = *reinterpret_cast<const float4*>(xr + k);
+    const float4 o4 = *reinterpret_cast<const float4*>(so + k0 + k);
+    const float e0 = __fsub_rn(x4.x, o4.x), e1 = __fsub_rn(x4.y, o4.y);
+    const float e2 = __fsub_rn(x4.z, o4.z), e3 = __fsub_rn(x4.w, o4.w);
+    if (want_nn) {
+      nn = __fmaf_rn(e0, e0, nn);
+      nn = __fmaf_rn(e1, e1, nn);
+      nn = __fmaf_rn(e2, e2, nn);
+      nn = __fmaf_rn(e3, e3, nn);
     }
-    __syncwarp();
-    if (gid >= 0) {
-      const float* xr = tile + lane * RPF_TILE_STRIDE;
-#pragma unroll 4
-      for (int k = 0; k < kc; k += 4) {
-        const float4 x4 = *reinterpret_cast<const float4*>(xr + k);
-        const float4 o4 = *reinterpret_cast<const float4*>(so + k0 + k);
-        const float e0 = __fsub_rn(x4.x, o4.x), e1 = __fsub_rn(x4.y, o4.y);
-        const float e2 = __fsub_rn(x4.z, o4.z), e3 = __fsub_rn(x4.w, o4.w);
-        if (want_nn) {
-          nn = __fmaf_rn(e0, e0, nn);
-          nn = __fmaf_rn(e1, e1, nn);
-          nn = __fmaf_rn(e2, e2, nn);
-          nn = __fmaf_rn(e3, e3, nn);
-        }
 #pragma unroll
-        for (int q = 0; q < TG; ++q) {
-          if (q < nj) {
-            const float4 r4 = *reinterpret_cast<const float4*>(sr + q * d + k0 + k);
-            float a = acc[q];
-            a = __fmaf_rn(e0, r4.x, a);
-            a = __fmaf_rn(e1, r4.y, a);
-            a = __fmaf_rn(e2, r4.z, a);
-            a = __fmaf_rn(e3, r4.w, a);
-            acc[q] = a;
-          }
-        }
+    for (int q = 0; q < TG; ++q) {
+      if (q < nj) {
+        const float4 r4 = *reinterpret_cast<const float4*>(sr + q * d + k0 + k);
+        float a = acc[q];
+        a = __fmaf_rn(e0, r4.x, a);
+        a = __fmaf_rn(e1, r4.y, a);
+        a = __fmaf_rn(e2, r4.z, a);
+        a = __fmaf_rn(e3, r4.w, a);
+        acc[q] = a;
       }
     }
-    __syncwarp();
   }
 }
 
