@@ -83,6 +83,8 @@ __device__ __forceinline__ void rpf_proj4(const float* __restrict__ X, int d, co
 // whole lines this way reaches about 4x the L2 bandwidth of one 16-byte load
 // per lane per row, and two tiles per warp let the next chunk's copy overlap
 // the current chunk's arithmetic.
+// DC coordinates per chunk; row stride DC + 4 floats (DC = 16 or 32 keeps it
+// an odd number of 16-byte units)
 #define RPF_TILE_DC 32
 #define RPF_TILE_STRIDE 36
 #define RPF_TILE_FLOATS (32 * RPF_TILE_STRIDE)
@@ -99,26 +101,28 @@ __device__ __forceinline__ void rpf_cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Warp-collective: copy coordinates [k0, k0 + 32) of the 32 rows gid (lane
-// l's row to tile row l; gid < 0: none) into the tile.
+// Warp-collective: copy coordinates [k0, k0 + DC) of the 32 rows gid (lane
+// l's row to tile row l; gid < 0: none) into the tile (DC / 4 lanes per row).
+template <int DC = RPF_TILE_DC>
 __device__ __forceinline__ void rpf_stage_rows(const float* __restrict__ X, int d, int gid, int k0,
                                                float* tile, int lane) {
-  const int c4 = 4 * (lane & 7);
-  const int kc = min(RPF_TILE_DC, d - k0);
+  constexpr int LPR = DC / 4, RPI = 32 / LPR;  // lanes per row, rows per instruction
+  const int c4 = 4 * (lane % LPR);
+  const int kc = min(DC, d - k0);
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int row = 4 * i + (lane >> 3);
+  for (int i = 0; i < 32 / RPI; ++i) {
+    const int row = RPI * i + lane / LPR;
     const int g = __shfl_sync(RPF_FULL, gid, row);
-    if (g >= 0 && c4 < kc) rpf_cp16(tile + row * RPF_TILE_STRIDE + c4, X + (int64_t)g * d + k0 + c4);
+    if (g >= 0 && c4 < kc) rpf_cp16(tile + row * (DC + 4) + c4, X + (int64_t)g * d + k0 + c4);
   }
 }
 
 // Chains of the lane's row over coordinates [k0, k0 + kc) from the tile.
-template <int TG>
+template <int TG, int DC = RPF_TILE_DC>
 __device__ __forceinline__ void rpf_tile_chunk(const float* tile, int lane, int k0, int kc,
                                                const float* so, const float* sr, int d, int nj,
                                                float (&acc)[TG], float& nn, bool want_nn) {
-  const float* xr = tile + lane * RPF_TILE_STRIDE;
+  const float* xr = tile + lane * (DC + 4);
 #pragma unroll 4
   for (int k = 0; k < kc; k += 4) {
     const float4 x4 = *reinterpret_cast<const float4*>(xr + k);
