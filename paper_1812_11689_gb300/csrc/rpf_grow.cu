@@ -41,9 +41,10 @@ namespace {
 
 constexpr int kBlock = 256;
 static_assert(RPF_CHUNK % kBlock == 0, "a chunk is a whole number of block strides");
-constexpr int kSub = RPF_CHUNK;
-constexpr int kCandList = 256;
-constexpr int kMedList = 256;  // median rule: bands up to this size are selected directly  // min / max candidates listed per chunk for the warp pass  // nodes of at most this many points grow in one CTA
+constexpr int kSub = RPF_CHUNK;  // nodes of at most this many points grow in one CTA
+constexpr int kCandList = 256;   // min / max candidates listed per chunk for the warp pass
+constexpr int kMedList = 256;    // median rule: bands up to this size are selected directly
+constexpr int kPaStages = 2;     // row-tile units in flight per warp in k_proj_a
 
 struct Level {
   int64_t cap_f = 0, cap_c = 0, cap_dir = 0;
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
   float* sr = smf;                   // ntry x d
   float* so = smf + ntry * d;        // d
   float* red = so + ((d + 3) & ~3);  // 8 x TG x 5
-  float* tiles = red + 8 * 5 * 8;     // d % 4 == 0: two 32-row tiles per warp
+  float* tiles = red + 8 * 5 * 8;     // d % 4 == 0: kPaStages 32-row tiles per warp
   const int c = blockIdx.x;
   const int f = ch_node[c];
   const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
@@ -205,40 +206,12 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
       mx[q] = -INFINITY;
     }
     if ((d & 3) == 0) {
-      // batches of 32 positions, one per lane; the warp's units (batch,
-      // 32-coordinate chunk) are staged one ahead into two tiles
-      constexpr int NW = kBlock / 32;
+      // batches of 32 positions, one per lane, rows staged through row
+      // tiles, kPaStages units in flight per warp
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      float* tb = tiles + warp * 2 * RPF_TILE_FLOATS;
-      const int nch = (d + RPF_TILE_DC - 1) / RPF_TILE_DC;
-      int b = warp;
-      if (b * 32 < len) {
-        int gid = b * 32 + lane < len ? perm_cur[base + b * 32 + lane] : -1;
-        int bn = b + NW;
-        int gidn = bn * 32 + lane < len ? perm_cur[base + bn * 32 + lane] : -1;
-        rpf_stage_rows(X, d, gid, 0, tb, lane);
-        rpf_cp_commit();
-        int buf = 0;
-        while (true) {
-          float acc[TG], nn = 0.0f;
-#pragma unroll
-          for (int q = 0; q < TG; ++q) acc[q] = 0.0f;
-          for (int c = 0; c < nch; ++c) {
-            float* nxt = tb + (buf ^ 1) * RPF_TILE_FLOATS;
-            if (c + 1 < nch) rpf_stage_rows(X, d, gid, (c + 1) * RPF_TILE_DC, nxt, lane);
-            else if (bn * 32 < len) rpf_stage_rows(X, d, gidn, 0, nxt, lane);
-            rpf_cp_commit();
-            rpf_cp_wait<1>();  // this unit's copies are done
-            __syncwarp();
-            const int k0 = c * RPF_TILE_DC;
-            if (gid >= 0)
-              rpf_tile_chunk<TG>(tb + buf * RPF_TILE_FLOATS, lane, k0, min(RPF_TILE_DC, d - k0), so,
-                                 sr + j0 * d, d, nj, acc, nn, j0 == 0);
-            __syncwarp();  // before this tile takes the unit after next
-            buf ^= 1;
-          }
-          if (gid >= 0) {
-            const int pos = b * 32 + lane;
+      rpf_warp_project<TG, RPF_TILE_DC, kPaStages>(
+          X, d, perm_cur + base, len, warp, kBlock / 32, tiles + warp * kPaStages * RPF_TILE_FLOATS,
+          so, sr + j0 * d, nj, j0 == 0, lane, [&](int pos, int gid, const float(&acc)[TG], float nn) {
             if (j0 == 0) radmax = fmaxf(radmax, rpf_point_rad(d, nn, xnorm[gid], on));
 #pragma unroll
             for (int q = 0; q < TG; ++q) {
@@ -247,15 +220,7 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
                 rpf_stat_add(acc[q], s1[q], s2[q], a1[q], mn[q], mx[q]);
               }
             }
-          }
-          if (bn * 32 >= len) break;
-          b = bn;
-          gid = gidn;
-          bn += NW;
-          gidn = bn * 32 + lane < len ? perm_cur[base + bn * 32 + lane] : -1;
-        }
-        rpf_cp_wait<0>();
-      }
+          });
     } else {
       for (int u0 = 0; u0 * kBlock < len; u0 += 4) {
         int gid[4], pos[4];
@@ -1520,7 +1485,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
   }
   const int TG = ntry <= 5 ? ntry : 8;
   const size_t smem_a = sizeof(float) * ((size_t)ntry * d + ((d + 3) & ~3) + 8 * 5 * 8 +
-                                         ((d & 3) == 0 ? (size_t)(kBlock / 32) * 2 * RPF_TILE_FLOATS : 0));
+                                         ((d & 3) == 0 ? (size_t)(kBlock / 32) * kPaStages * RPF_TILE_FLOATS : 0));
   int32_t* perm_cur = perm_a;
   int32_t* perm_nxt = perm_b;
   while (F > 0) {

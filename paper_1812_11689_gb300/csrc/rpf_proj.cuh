@@ -150,6 +150,76 @@ __device__ __forceinline__ void rpf_tile_chunk(const float* tile, int lane, int 
   }
 }
 
+// Warp-collective driver of the staged projections: the warp's batches of 32
+// positions (batch bfirst + i bstride, position 32 b + lane, point id
+// ids[position]; npos positions) are cut into units (batch, DC-coordinate
+// chunk), and unit u + NS - 1 is copied into tile (u + NS - 1) % NS while
+// unit u is computed (NS tiles of 32 rows x (DC + 4) floats at `tiles`).
+// After a batch's last chunk fin(position, id, acc, nn) runs on every lane
+// whose position holds a point.  Point ids are read NS batches ahead.
+template <int TG, int DC, int NS, typename IdT, typename Fin>
+__device__ __forceinline__ void rpf_warp_project(const float* __restrict__ X, int d, const IdT* ids,
+                                                 int npos, int bfirst, int bstride, float* tiles,
+                                                 const float* so, const float* sr, int nj,
+                                                 bool want_nn, int lane, Fin fin) {
+  constexpr int TF = 32 * (DC + 4);
+  const int nch = (d + DC - 1) / DC;
+  const int nbt = (npos + 31) >> 5;
+  const int nbw = bfirst < nbt ? (nbt - bfirst + bstride - 1) / bstride : 0;
+  if (nbw == 0) return;
+  int g[NS];  // ids of batches i .. i + NS - 1 (-1: none)
+  int pb = bfirst;
+#pragma unroll
+  for (int k = 0; k < NS; ++k, pb += bstride) {
+    const int p = pb * 32 + lane;
+    g[k] = (pb < nbt && p < npos) ? (int)ids[p] : -1;
+  }
+  // the next unit to copy: batch i + sk, chunk sc, into tile ss
+  int sk = 0, sc = 0, ss = 0;
+  auto stage_next = [&](int i) {
+    int gs = g[0];
+#pragma unroll
+    for (int kk = 1; kk < NS; ++kk)
+      if (sk == kk) gs = g[kk];
+    if (i + sk < nbw) rpf_stage_rows<DC>(X, d, gs, sc * DC, tiles + ss * TF, lane);
+    ss = ss + 1 == NS ? 0 : ss + 1;
+    if (++sc == nch) {
+      sc = 0;
+      ++sk;
+    }
+  };
+#pragma unroll
+  for (int v = 0; v < NS - 1; ++v) {
+    stage_next(0);
+    rpf_cp_commit();
+  }
+  int cs = 0;  // tile of the unit being computed
+  for (int i = 0; i < nbw; ++i) {
+    float acc[TG], nn = 0.0f;
+#pragma unroll
+    for (int q = 0; q < TG; ++q) acc[q] = 0.0f;
+    for (int c = 0; c < nch; ++c) {
+      stage_next(i);
+      rpf_cp_commit();
+      rpf_cp_wait<NS - 1>();  // this unit's copies are done
+      __syncwarp();
+      if (g[0] >= 0)
+        rpf_tile_chunk<TG, DC>(tiles + cs * TF, lane, c * DC, min(DC, d - c * DC), so, sr, d, nj,
+                               acc, nn, want_nn);
+      __syncwarp();  // before this tile takes a later unit
+      cs = cs + 1 == NS ? 0 : cs + 1;
+    }
+    if (g[0] >= 0) fin((bfirst + i * bstride) * 32 + lane, g[0], acc, nn);
+#pragma unroll
+    for (int k = 0; k + 1 < NS; ++k) g[k] = g[k + 1];
+    const int p = pb * 32 + lane;
+    g[NS - 1] = (pb < nbt && p < npos) ? (int)ids[p] : -1;
+    pb += bstride;
+    --sk;
+  }
+  rpf_cp_wait<0>();
+}
+
 __device__ __forceinline__ void rpf_stat_add(float v, float& s1, float& s2, float& a1, float& mn,
                                              float& mx) {
   s1 = __fadd_rn(s1, v);

@@ -34,11 +34,13 @@ namespace {
 constexpr int kB = 128;  // 4 warps; 4 CTAs per SM hide each other's serial sections
 constexpr int kSubN = RPF_CHUNK;
 constexpr int kStack = 24;
-constexpr int kBandSel = 256;
-// the projection's row tiles (2 per warp, 32 rows of 16 + 4 floats) live in
-// sT and sSide, which are contiguous and idle during the projection
-static_assert((kB / 32) * 2 * 32 * (16 + 4) * 4 <= 4 * kSubN + kSubN, "row tiles fit sT + sSide");
-static_assert((4 * kSubN) % 16 == 0, "sSide follows sT directly");  // median rule: bands up to this size are selected by counting
+constexpr int kBandSel = 256;  // median rule: bands up to this size are selected by counting
+// the projection's row tiles (kTStages per warp, 32 rows of kTDC + 4 floats)
+// live in sT and sSide, which are contiguous and idle during the projection
+constexpr int kTDC = 16, kTStages = 2;
+static_assert((kB / 32) * kTStages * 32 * (kTDC + 4) * 4 <= 4 * kSubN + kSubN,
+              "row tiles fit sT + sSide");
+static_assert((4 * kSubN) % 16 == 0, "sSide follows sT directly");
 
 struct SubState {
   uint64_t key;
@@ -224,39 +226,12 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
         }
         if ((d & 3) == 0) {
           // batches of 32 positions, one per lane; each warp stages its
-          // units (batch, 16-coordinate chunk) one ahead into two row tiles
-          // held in the partition scratch (sT and sSide, 20 KB, idle here)
-          constexpr int kTDC = 16;
-          float* tb = reinterpret_cast<float*>(smraw + lay.sT) + warp * 2 * 32 * (kTDC + 4);
-          const int nbt = (m + 31) >> 5, nch = (d + kTDC - 1) / kTDC;
-          int b = warp;
-          if (b < nbt) {
-            int gid = b * 32 + lane < m ? sP[nb + b * 32 + lane] : -1;
-            int bn = b + kB / 32;
-            int gidn = bn * 32 + lane < m ? sP[nb + bn * 32 + lane] : -1;
-            rpf_stage_rows<kTDC>(X, d, gid, 0, tb, lane);
-            rpf_cp_commit();
-            int buf = 0;
-            while (true) {
-              float acc[TG], nn = 0.0f;
-#pragma unroll
-              for (int q = 0; q < TG; ++q) acc[q] = 0.0f;
-              for (int c = 0; c < nch; ++c) {
-                float* nxt = tb + (buf ^ 1) * 32 * (kTDC + 4);
-                if (c + 1 < nch) rpf_stage_rows<kTDC>(X, d, gid, (c + 1) * kTDC, nxt, lane);
-                else if (bn < nbt) rpf_stage_rows<kTDC>(X, d, gidn, 0, nxt, lane);
-                rpf_cp_commit();
-                rpf_cp_wait<1>();  // this unit's copies are done
-                __syncwarp();
-                const int k0 = c * kTDC;
-                if (gid >= 0)
-                  rpf_tile_chunk<TG, kTDC>(tb + buf * 32 * (kTDC + 4), lane, k0, min(kTDC, d - k0),
-                                           so, r32 + j0 * d, d, nj, acc, nn, j0 == 0);
-                __syncwarp();  // before this tile takes the unit after next
-                buf ^= 1;
-              }
-              if (gid >= 0) {
-                const int pos = b * 32 + lane;
+          // units (batch, kTDC-coordinate chunk) ahead into row tiles held in
+          // the partition scratch
+          float* tb = reinterpret_cast<float*>(smraw + lay.sT) + warp * kTStages * 32 * (kTDC + 4);
+          rpf_warp_project<TG, kTDC, kTStages>(
+              X, d, sP + nb, m, warp, kB / 32, tb, so, r32 + j0 * d, nj, j0 == 0, lane,
+              [&](int pos, int gid, const float(&acc)[TG], float nn) {
                 if (j0 == 0) radmax = fmaxf(radmax, rpf_point_rad(d, nn, xnorm[gid], on));
 #pragma unroll
                 for (int q = 0; q < TG; ++q) {
@@ -265,15 +240,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
                     rpf_stat_add(acc[q], s1[q], s2[q], a1[q], mn[q], mx[q]);
                   }
                 }
-              }
-              if (bn >= nbt) break;
-              b = bn;
-              gid = gidn;
-              bn += kB / 32;
-              gidn = bn * 32 + lane < m ? sP[nb + bn * 32 + lane] : -1;
-            }
-            rpf_cp_wait<0>();
-          }
+              });
         } else {
           for (int u0 = 0; u0 * kB < m; u0 += 4) {
             int gid[4], pos[4];
