@@ -36,11 +36,15 @@ constexpr int kSubN = RPF_CHUNK;
 constexpr int kStack = 24;
 constexpr int kBandSel = 256;  // median rule: bands up to this size are selected by counting
 // the projection's row tiles (kTStages per warp, 32 rows of kTDC + 4 floats)
-// live in sT and sSide, which are contiguous and idle during the projection
+// live in sT and sSide, which are contiguous and idle during the projection,
+// and in sTx, which follows them
 constexpr int kTDC = 16, kTStages = 2;
-static_assert((kB / 32) * kTStages * 32 * (kTDC + 4) * 4 <= 4 * kSubN + kSubN,
-              "row tiles fit sT + sSide");
-static_assert((4 * kSubN) % 16 == 0, "sSide follows sT directly");
+constexpr size_t kTileBytes = (size_t)(kB / 32) * kTStages * 32 * (kTDC + 4) * 4;
+constexpr size_t kTileExtra = kTileBytes > 5 * (size_t)kSubN ? kTileBytes - 5 * (size_t)kSubN : 0;
+static_assert((4 * kSubN) % 16 == 0 && kSubN % 16 == 0, "sT, sSide and sTx are contiguous");
+// the median rule's band list and histogram also live in sT (idle while the
+// median is selected)
+static_assert(12 * kBandSel + 4 * 256 <= 4 * kSubN, "band list and histogram fit sT");
 
 struct SubState {
   uint64_t key;
@@ -61,7 +65,7 @@ struct SubState {
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct SubLayout {
-  size_t sP, sT, sSide, r64, r32, so, sbase, sS1, sS2, sA, sinv, smn, smx, svh, slo, shi, red,
+  size_t sP, sT, sSide, sTx, r64, r32, so, sbase, sS1, sS2, sA, sinv, smn, smx, svh, slo, shi, red,
       total;
 };
 
@@ -74,6 +78,8 @@ __host__ __device__ inline SubLayout sub_layout(int d, int ntry, int TG) {
   o = align16(o + 4 * (size_t)kSubN);
   l.sSide = o;
   o = align16(o + (size_t)kSubN);
+  l.sTx = o;
+  o = align16(o + kTileExtra);
   l.r64 = o;
   o = align16(o + 8 * (size_t)ntry * d);
   l.r32 = o;
@@ -141,9 +147,10 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
   __shared__ int st_nb[kStack], st_m[kStack], st_id[kStack];
   __shared__ uint64_t st_key[kStack];
   __shared__ int wsc[kB / 32];
-  __shared__ int mhist[256];  // median rule: radix histogram
-  __shared__ unsigned long long bnd_key[kBandSel];  // ... and a small band's keys
-  __shared__ uint32_t bnd_id[kBandSel];
+  // median rule: a small band's keys and point indices, and the radix histogram
+  unsigned long long* bnd_key = reinterpret_cast<unsigned long long*>(smraw + lay.sT);
+  uint32_t* bnd_id = reinterpret_cast<uint32_t*>(smraw + lay.sT + 8 * kBandSel);
+  int* mhist = reinterpret_cast<int*>(smraw + lay.sT + 12 * kBandSel);
   __shared__ int tile_tot;
 
   const int it = blockIdx.x;
