@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
   extern __shared__ __align__(16) float smf[];
   float* sr = smf;                   // ntry x d
   float* so = smf + ntry * d;        // d
-  float* red = so + ((d + 3) & ~3);  // 8 x TG x 5
-  float* tiles = red + 8 * 5 * 8;     // d % 4 == 0: kPaStages 32-row tiles per warp
+  float* red = so + ((d + 3) & ~3);  // 8 x TG x 5 statistics, then 33 for the radius
+  float* tiles = red + 8 * 5 * 8 + 40;  // d % 4 == 0: kPaStages 32-row tiles per warp
   const int c = blockIdx.x;
   const int f = ch_node[c];
   const int64_t base = (int64_t)fr_tree[f] * n + fr_begin[f] + ch_start[c];
@@ -248,9 +248,8 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
     }
     const int64_t o = (int64_t)c * ntry + j0;
     rpf_block_stats<TG>(nj, s1, s2, a1, mn, mx, red, cp_s1 + o, cp_s2 + o, cp_a + o, cp_min + o,
-                        cp_max + o);
+                        cp_max + o, j0 == 0 ? &radmax : nullptr);
   }
-  radmax = rpf_block_max(radmax, red);
   if (threadIdx.x == 0) cp_rad[c] = radmax;
 }
 
@@ -1484,7 +1483,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     RPF_TRYCU(cudaStreamSynchronize(s));
   }
   const int TG = ntry <= 5 ? ntry : 8;
-  const size_t smem_a = sizeof(float) * ((size_t)ntry * d + ((d + 3) & ~3) + 8 * 5 * 8 +
+  const size_t smem_a = sizeof(float) * ((size_t)ntry * d + ((d + 3) & ~3) + 8 * 5 * 8 + 40 +
                                          ((d & 3) == 0 ? (size_t)(kBlock / 32) * kPaStages * RPF_TILE_FLOATS : 0));
   int32_t* perm_cur = perm_a;
   int32_t* perm_nxt = perm_b;

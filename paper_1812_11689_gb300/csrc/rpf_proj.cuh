@@ -231,13 +231,22 @@ __device__ __forceinline__ void rpf_stat_add(float v, float& s1, float& s2, floa
 
 // Block reduction of per-thread statistics for nj tries into o*[q] (written
 // by thread q; visible to all threads after the trailing barrier).
-// red: 8 warps x TG x 5 floats of shared memory.
+// red: 8 warps x TG x 5 floats of shared memory (+ 33 when rad is given).
+// With rad non-null, the block-wide max of the non-negative *rad is folded
+// in (slots 8 TG 5 .. + 32 of red) and returned in *rad to every thread.
 template <int TG>
 __device__ __forceinline__ void rpf_block_stats(int nj, float (&s1)[TG], float (&s2)[TG],
                                                 float (&a1)[TG], float (&mn)[TG], float (&mx)[TG],
                                                 float* red, double* o1, double* o2, double* oa,
-                                                float* omn, float* omx) {
+                                                float* omn, float* omx, float* rad = nullptr) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float* rred = red + 8 * TG * 5;
+  if (rad) {
+    float v = *rad;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v = fmaxf(v, __shfl_xor_sync(RPF_FULL, v, off));
+    if (lane == 0) rred[w] = v;
+  }
 #pragma unroll
   for (int q = 0; q < TG; ++q) {
     if (q >= nj) continue;
@@ -281,23 +290,12 @@ __device__ __forceinline__ void rpf_block_stats(int nj, float (&s1)[TG], float (
       omx[q] = hi;
     }
   }
-  __syncthreads();
-}
-
-// Block-wide max of a non-negative float, returned to every thread.
-// red: at least 33 floats of shared memory (not in use by the caller).
-__device__ __forceinline__ float rpf_block_max(float v, float* red) {
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) v = fmaxf(v, __shfl_xor_sync(RPF_FULL, v, off));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  if (rad && threadIdx.x == 0) {
     float m = 0.0f;
-    for (int u = 0; u < (int)(blockDim.x >> 5); ++u) m = fmaxf(m, red[u]);
-    red[32] = m;
+    for (int u = 0; u < (int)(blockDim.x >> 5); ++u) m = fmaxf(m, rred[u]);
+    rred[32] = m;
   }
   __syncthreads();
-  const float r = red[32];
-  __syncthreads();
-  return r;
+  if (rad) *rad = rred[32];
 }
+

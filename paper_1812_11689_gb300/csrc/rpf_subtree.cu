@@ -151,7 +151,6 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
   unsigned long long* bnd_key = reinterpret_cast<unsigned long long*>(smraw + lay.sT);
   uint32_t* bnd_id = reinterpret_cast<uint32_t*>(smraw + lay.sT + 8 * kBandSel);
   int* mhist = reinterpret_cast<int*>(smraw + lay.sT + 12 * kBandSel);
-  __shared__ int tile_tot;
 
   const int it = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -274,18 +273,20 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
           }
         }
         rpf_block_stats<TG>(nj, s1, s2, a1, mn, mx, red, sS1 + j0, sS2 + j0, sA + j0, smn + j0,
-                            smx + j0);
+                            smx + j0, j0 == 0 ? &radmax : nullptr);
       }
-      radmax = rpf_block_max(radmax, red);
     }
 
     // 4. certify the choice of Algorithm 2
     if (!exact_only) {
+      // bounds of every try; with at most 32 tries warp 0 holds them all
+      // and certifies right after (a warp sync instead of a block barrier)
       const double inv_m = 1.0 / (double)m;
       for (int j = tid; j < ntry; j += kB)
         rpf_try_bounds(m, inv_m, sS1[j], sS2[j], sA[j], (double)on, radmax, &svh[j], &slo[j],
                        &shi[j]);
-      __syncthreads();
+      if (ntry <= 32) __syncwarp();
+      else __syncthreads();
     }
     if (tid == 0) {
       const int w = exact_only ? -1 : rpf_certify_select(ntry, svh, slo, shi);
@@ -584,48 +585,35 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
         }
       }
       __syncthreads();
+      // stable partition from one block-wide scan: thread t takes the run
+      // [t per, (t + 1) per) of positions (per odd, so the runs' shared-
+      // memory reads fall in distinct banks); E = lefts before a position
+      const int per = ((m + kB - 1) / kB) | 1;
+      const int v0 = min(m, tid * per), v1 = min(m, v0 + per);
       int cnt = 0;
-      for (int i = tid; i < m; i += kB) cnt += sSide[i];
-      for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(RPF_FULL, cnt, off);
-      if (lane == 0) wsc[warp] = cnt;
-      __syncthreads();
-      if (tid == 0) {
-        int s = 0;
-        for (int u = 0; u < kB / 32; ++u) s += wsc[u];
-        S.nl = s;
-      }
-      __syncthreads();
-      const int nl = S.nl;
-      int carryL = 0;
-      for (int t0 = 0; t0 < m; t0 += kB) {
-        const int i = t0 + tid;
-        const int s = i < m ? sSide[i] : 0;
-        int x = s;
+      for (int i = v0; i < v1; ++i) cnt += sSide[i];
+      int x = cnt;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const int y = __shfl_up_sync(RPF_FULL, x, off);
-          if (lane >= off) x += y;
-        }
-        if (lane == 31) wsc[warp] = x;
-        __syncthreads();
-        if (tid == 0) {
-          int r = 0;
-          for (int u = 0; u < kB / 32; ++u) {
-            const int v = wsc[u];
-            wsc[u] = r;
-            r += v;
-          }
-          tile_tot = r;
-        }
-        __syncthreads();
-        if (i < m) {
-          const int lbefore = carryL + x - s + wsc[warp];
-          const int dst = s ? lbefore : nl + (i - lbefore);
-          sT[nb + dst] = sP[nb + i];
-        }
-        carryL += tile_tot;
-        __syncthreads();
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(RPF_FULL, x, off);
+        if (lane >= off) x += y;
       }
+      if (lane == 31) wsc[warp] = x;
+      __syncthreads();
+      int E = x - cnt, nl = 0;
+#pragma unroll
+      for (int u = 0; u < kB / 32; ++u) {
+        const int w = wsc[u];
+        if (u < warp) E += w;
+        nl += w;
+      }
+      for (int i = v0; i < v1; ++i) {
+        const int sd = sSide[i];
+        sT[nb + (sd ? E : nl + (i - E))] = sP[nb + i];
+        E += sd;
+      }
+      if (tid == 0) S.nl = nl;
+      __syncthreads();
       for (int i = tid; i < m; i += kB) sP[nb + i] = sT[nb + i];
       __syncthreads();
     }
