@@ -118,14 +118,15 @@ __device__ __forceinline__ float rpf_point_rad(int d, float nn, float xn, float 
 // babs >= |b_j| (|o| bounds it).  With Vhat = S2 - S1^2 / m:
 //   |Vhat - V_q| <= EV   (FP32 sums: gamma (S2 + 2|S1| A / m + gamma A^2 / m),
 //                         plus 1e-14 S2 for the FP64 arithmetic here)
-//   |sqrt(V_q) - sqrt(V_p)| <= sqrt(m) rad    (sqrt of a centred sum of
-//                         squares is 1-Lipschitz in the vector of projections)
+//   |sqrt(V_q) - sqrt(V_p)| <= |q - p|_2 <= min(sqrt(m) rad, l2)
+//                         (sqrt of a centred sum of squares is 1-Lipschitz in
+//                         the vector of projections; l2 >= sqrt(sum rad_i^2))
 //   |sqrt(V) - sqrt(V_p)| <= 1e-12 sqrt(V) + sqrt(m) 1e-13 (|b| + A/m + rad)
 //                         (the canonical FP64 reduction itself)
 // all error terms doubled.  lo / hi are rounded outwards in FP32.
 __device__ __forceinline__ void rpf_try_bounds(int m, double inv_m, double S1, double S2,
-                                               double A, double babs, float rad, double* vhat,
-                                               float* lo, float* hi) {
+                                               double A, double babs, float rad, float l2,
+                                               double* vhat, float* lo, float* hi) {
   const double u = 0x1p-24;
   const double gam = RPF_STAT_DEPTH * u / (1.0 - RPF_STAT_DEPTH * u);
   const double V = S2 - S1 * (S1 * inv_m);
@@ -135,7 +136,7 @@ __device__ __forceinline__ void rpf_try_bounds(int m, double inv_m, double S1, d
       0x1p-50 * S1 * S1 * inv_m;
   const float sqm = __fsqrt_ru(__int2float_ru(m));
   const float vup = __fsqrt_ru(__double2float_ru(fmax(V + EV, 0.0)));
-  const float lip = __fmul_ru(__fmul_ru(2.0f, sqm), rad);
+  const float lip = __fmul_ru(2.0f, fminf(__fmul_ru(sqm, rad), l2));
   const float mid = __fadd_ru(__double2float_ru(fabs(babs) + Am * inv_m), rad);
   const float e64 = __fmul_ru(2.0f, __fadd_ru(__fmul_ru(1e-12f, vup), __fmul_ru(__fmul_ru(sqm, 1e-13f), mid)));
   const float err = __fadd_ru(lip, e64);

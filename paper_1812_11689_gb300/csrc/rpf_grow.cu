@@ -71,7 +71,7 @@ struct Level {
   int32_t *ch_nleft{}, *ch_loff{};
   double *cp_sum{}, *cp_min{}, *cp_max{};
   double *cp_s1{}, *cp_s2{}, *cp_a{};
-  float *cp_min32{}, *cp_max32{}, *cp_rad{};
+  float *cp_min32{}, *cp_max32{}, *cp_rad{}, *cp_rad2{};
   double* dir64{};
   float* dir32{};
 };
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
     const int32_t* fr_begin, const int32_t* fr_ogid, const float* __restrict__ X,
     const int32_t* __restrict__ perm_cur, const float* __restrict__ xnorm, int64_t n, int64_t Tn,
     int d, int ntry, const float* dir32, float* p32, double* cp_s1, double* cp_s2, double* cp_a,
-    float* cp_min, float* cp_max, float* cp_rad) {
+    float* cp_min, float* cp_max, float* cp_rad, float* cp_rad2) {
   extern __shared__ __align__(16) float smf[];
   float* sr = smf;                   // ntry x d
   float* so = smf + ntry * d;        // d
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
   for (int i = threadIdx.x; i < ntry * d; i += blockDim.x) sr[i] = dir32[(int64_t)f * ntry * d + i];
   for (int k = threadIdx.x; k < d; k += blockDim.x) so[k] = X[(int64_t)og * d + k];
   __syncthreads();
-  float radmax = 0.0f;
+  float radmax = 0.0f, rad2 = 0.0f;  // rad2: rounded-up sum of the points' rad^2
   for (int j0 = 0; j0 < ntry; j0 += TG) {
     const int nj = min(TG, ntry - j0);
     float s1[TG], s2[TG], a1[TG], mn[TG], mx[TG];
@@ -212,7 +212,11 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
       rpf_warp_project<TG, RPF_TILE_DC, kPaStages>(
           X, d, perm_cur + base, len, warp, kBlock / 32, tiles + warp * kPaStages * RPF_TILE_FLOATS,
           so, sr + j0 * d, nj, j0 == 0, lane, [&](int pos, int gid, const float(&acc)[TG], float nn) {
-            if (j0 == 0) radmax = fmaxf(radmax, rpf_point_rad(d, nn, xnorm[gid], on));
+            if (j0 == 0) {
+              const float r = rpf_point_rad(d, nn, xnorm[gid], on);
+              radmax = fmaxf(radmax, r);
+              rad2 = __fmaf_ru(r, r, rad2);
+            }
 #pragma unroll
             for (int q = 0; q < TG; ++q) {
               if (q < nj) {
@@ -234,7 +238,11 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           if (gid[p] < 0) continue;
-          if (j0 == 0) radmax = fmaxf(radmax, rpf_point_rad(d, nn[p], xnorm[gid[p]], on));
+          if (j0 == 0) {
+            const float r = rpf_point_rad(d, nn[p], xnorm[gid[p]], on);
+            radmax = fmaxf(radmax, r);
+            rad2 = __fmaf_ru(r, r, rad2);
+          }
 #pragma unroll
           for (int q = 0; q < TG; ++q) {
             if (q < nj) {
@@ -248,9 +256,12 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
     }
     const int64_t o = (int64_t)c * ntry + j0;
     rpf_block_stats<TG>(nj, s1, s2, a1, mn, mx, red, cp_s1 + o, cp_s2 + o, cp_a + o, cp_min + o,
-                        cp_max + o, j0 == 0 ? &radmax : nullptr);
+                        cp_max + o, j0 == 0 ? &radmax : nullptr, &rad2);
   }
-  if (threadIdx.x == 0) cp_rad[c] = radmax;
+  if (threadIdx.x == 0) {
+    cp_rad[c] = radmax;
+    cp_rad2[c] = rad2;
+  }
 }
 
 // Per node: merge the chunk statistics, certify Algorithm 2's choice.  One
@@ -260,7 +271,8 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
 __global__ void __launch_bounds__(128) k_certify_a(
     int F, int ntry, int exact_only, const int32_t* fr_cb, const int32_t* fr_nc,
     const int32_t* fr_len, const double* cp_s1, const double* cp_s2, const double* cp_a,
-    const float* cp_min, const float* cp_max, const float* cp_rad, const double* fr_base,
+    const float* cp_min, const float* cp_max, const float* cp_rad, const float* cp_rad2,
+    const double* fr_base,
     int32_t* fr_exact, int32_t* fr_jstar, float* fr_rad, float* fr_wlo, float* fr_whi,
     unsigned long long* fr_akey, unsigned long long* fr_bkey, unsigned long long* fr_cmask) {
   __shared__ double s_vh[4][RPF_MAX_TRY];
@@ -269,10 +281,17 @@ __global__ void __launch_bounds__(128) k_certify_a(
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   if (f >= F) return;  // whole warp
   const int cb = fr_cb[f], nc = fr_nc[f];
-  float rad = 0.0f;
-  for (int c = cb + lane; c < cb + nc; c += 32) rad = fmaxf(rad, cp_rad[c]);
+  float rad = 0.0f, r2 = 0.0f;  // max radius; rounded-up sum of rad^2
+  for (int c = cb + lane; c < cb + nc; c += 32) {
+    rad = fmaxf(rad, cp_rad[c]);
+    r2 = __fadd_ru(r2, cp_rad2[c]);
+  }
 #pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) rad = fmaxf(rad, __shfl_xor_sync(RPF_FULL, rad, off));
+  for (int off = 16; off >= 1; off >>= 1) {
+    rad = fmaxf(rad, __shfl_xor_sync(RPF_FULL, rad, off));
+    r2 = __fadd_ru(r2, __shfl_xor_sync(RPF_FULL, r2, off));
+  }
+  const float l2 = __fsqrt_ru(r2);
   if (lane == 0) fr_rad[f] = rad;
   const int m = fr_len[f];
   const double inv_m = 1.0 / (double)m;
@@ -299,7 +318,7 @@ __global__ void __launch_bounds__(128) k_certify_a(
       b = __dadd_rn(b, cp_s2[(int64_t)c * ntry + j]);
       e = __dadd_rn(e, cp_a[(int64_t)c * ntry + j]);
     }
-    rpf_try_bounds(m, inv_m, a, b, e, fr_base[(int64_t)f * ntry + j], rad, &s_vh[wib][j],
+    rpf_try_bounds(m, inv_m, a, b, e, fr_base[(int64_t)f * ntry + j], rad, l2, &s_vh[wib][j],
                    &s_lo[wib][j], &s_hi[wib][j]);
   }
   __syncwarp();
@@ -1247,7 +1266,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
                   lv.fr_c, lv.fr_base, lv.fr_mu, lv.fr_min, lv.fr_max, lv.fr_tl, lv.fr_tr,
                   lv.fr_rad, lv.fr_wlo, lv.fr_whi, lv.fr_akey, lv.fr_bkey, lv.ch_nleft, lv.ch_loff,
                   lv.cp_sum, lv.cp_min, lv.cp_max, lv.cp_s1, lv.cp_s2, lv.cp_a, lv.cp_min32,
-                  lv.cp_max32, lv.cp_rad, lv.dir64, lv.dir32, lv.md_key, lv.md_id, lv.md_rank,
+                  lv.cp_max32, lv.cp_rad, lv.cp_rad2, lv.dir64, lv.dir32, lv.md_key, lv.md_id, lv.md_rank,
                   lv.md_hist, lv.md_fk, lv.md_l0, lv.md_lo, lv.md_hi, lv.fr_cmask, lv.md_bn,
                   lv.md_done, lv.md_bk, lv.md_bi};
     for (void* p : ps) rpf_release(p, s);
@@ -1444,6 +1463,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
       if ((r = grow_buf(&lv.cp_min32, 0, ncap * ntry, s, false))) return r;
       if ((r = grow_buf(&lv.cp_max32, 0, ncap * ntry, s, false))) return r;
       if ((r = grow_buf(&lv.cp_rad, 0, ncap, s, false))) return r;
+      if ((r = grow_buf(&lv.cp_rad2, 0, ncap, s, false))) return r;
       lv.cap_c = ncap;
     }
     return RPF_OK;
@@ -1510,7 +1530,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     RPF_LAUNCH("k_proj_a", s, k_proj_a<TGV><<<Ci, kBlock, smem_a, s>>>(                          \
         ch_node, ch_start, ch_len, fr_tree, fr_begin, lv.fr_ogid, fo->X, perm_cur, fo->xnorm, n, \
         Tn, d, ntry, lv.dir32, p32, lv.cp_s1, lv.cp_s2, lv.cp_a, lv.cp_min32, lv.cp_max32,       \
-        lv.cp_rad));                                                                             \
+        lv.cp_rad, lv.cp_rad2));                                                                 \
   } while (0)
     switch (TG) {
       case 1: RPF_PROJ_A(1); break;
@@ -1523,7 +1543,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
 #undef RPF_PROJ_A
     RPF_LAUNCH("k_certify_a", s, k_certify_a<<<nblk(F * 32, 128), 128, 0, s>>>(
         Fi, ntry, exact_only, fr_cb, fr_nc, fr_len, lv.cp_s1, lv.cp_s2, lv.cp_a, lv.cp_min32,
-        lv.cp_max32, lv.cp_rad, lv.fr_base, lv.fr_exact, lv.fr_jstar, lv.fr_rad, lv.fr_wlo,
+        lv.cp_max32, lv.cp_rad, lv.cp_rad2, lv.fr_base, lv.fr_exact, lv.fr_jstar, lv.fr_rad, lv.fr_wlo,
         lv.fr_whi, lv.fr_akey, lv.fr_bkey, lv.fr_cmask));
     // chunks of exact nodes are listed (in ch_loff, which k_node_scan fills
     // later) so that their FP64 work spreads over the GPU

@@ -231,21 +231,29 @@ __device__ __forceinline__ void rpf_stat_add(float v, float& s1, float& s2, floa
 
 // Block reduction of per-thread statistics for nj tries into o*[q] (written
 // by thread q; visible to all threads after the trailing barrier).
-// red: 8 warps x TG x 5 floats of shared memory (+ 33 when rad is given).
-// With rad non-null, the block-wide max of the non-negative *rad is folded
-// in (slots 8 TG 5 .. + 32 of red) and returned in *rad to every thread.
+// red: 8 warps x TG x 5 floats of shared memory (+ 34 when rad is given).
+// With rad non-null, the block-wide max of the non-negative *rad and the sum
+// of *rad2, added with upward rounding (an upper bound of the exact sum), are
+// folded in (slots 8 TG 5 .. + 33 of red) and returned to every thread.
 template <int TG>
 __device__ __forceinline__ void rpf_block_stats(int nj, float (&s1)[TG], float (&s2)[TG],
                                                 float (&a1)[TG], float (&mn)[TG], float (&mx)[TG],
                                                 float* red, double* o1, double* o2, double* oa,
-                                                float* omn, float* omx, float* rad = nullptr) {
+                                                float* omn, float* omx, float* rad = nullptr,
+                                                float* rad2 = nullptr) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float* rred = red + 8 * TG * 5;
   if (rad) {
-    float v = *rad;
+    float v = *rad, q = *rad2;
 #pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) v = fmaxf(v, __shfl_xor_sync(RPF_FULL, v, off));
-    if (lane == 0) rred[w] = v;
+    for (int off = 16; off >= 1; off >>= 1) {
+      v = fmaxf(v, __shfl_xor_sync(RPF_FULL, v, off));
+      q = __fadd_ru(q, __shfl_xor_sync(RPF_FULL, q, off));
+    }
+    if (lane == 0) {
+      rred[w] = v;
+      rred[8 + w] = q;
+    }
   }
 #pragma unroll
   for (int q = 0; q < TG; ++q) {
@@ -291,11 +299,18 @@ __device__ __forceinline__ void rpf_block_stats(int nj, float (&s1)[TG], float (
     }
   }
   if (rad && threadIdx.x == 0) {
-    float m = 0.0f;
-    for (int u = 0; u < (int)(blockDim.x >> 5); ++u) m = fmaxf(m, rred[u]);
+    float m = 0.0f, q = 0.0f;
+    for (int u = 0; u < (int)(blockDim.x >> 5); ++u) {
+      m = fmaxf(m, rred[u]);
+      q = __fadd_ru(q, rred[8 + u]);
+    }
     rred[32] = m;
+    rred[33] = q;
   }
   __syncthreads();
-  if (rad) *rad = rred[32];
+  if (rad) {
+    *rad = rred[32];
+    *rad2 = rred[33];
+  }
 }
 

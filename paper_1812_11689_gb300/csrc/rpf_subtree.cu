@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     const float on = xnorm[og];
 
     // 3. centred FP32 projections and statistics
-    float radmax = 0.0f;
+    float radmax = 0.0f, rad2 = 0.0f;  // rad2: rounded-up sum of the points' rad^2
     if (!exact_only) {
       for (int j0 = 0; j0 < ntry; j0 += TG) {
         const int nj = min(TG, ntry - j0);
@@ -238,7 +238,11 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
           rpf_warp_project<TG, kTDC, kTStages>(
               X, d, sP + nb, m, warp, kB / 32, tb, so, r32 + j0 * d, nj, j0 == 0, lane,
               [&](int pos, int gid, const float(&acc)[TG], float nn) {
-                if (j0 == 0) radmax = fmaxf(radmax, rpf_point_rad(d, nn, xnorm[gid], on));
+                if (j0 == 0) {
+                  const float r = rpf_point_rad(d, nn, xnorm[gid], on);
+                  radmax = fmaxf(radmax, r);
+                  rad2 = __fmaf_ru(r, r, rad2);
+                }
 #pragma unroll
                 for (int q = 0; q < TG; ++q) {
                   if (q < nj) {
@@ -260,7 +264,11 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
               if (gid[p] < 0) continue;
-              if (j0 == 0) radmax = fmaxf(radmax, rpf_point_rad(d, nn[p], xnorm[gid[p]], on));
+              if (j0 == 0) {
+                const float r = rpf_point_rad(d, nn[p], xnorm[gid[p]], on);
+                radmax = fmaxf(radmax, r);
+                rad2 = __fmaf_ru(r, r, rad2);
+              }
 #pragma unroll
               for (int q = 0; q < TG; ++q) {
                 if (q < nj) {
@@ -273,7 +281,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
           }
         }
         rpf_block_stats<TG>(nj, s1, s2, a1, mn, mx, red, sS1 + j0, sS2 + j0, sA + j0, smn + j0,
-                            smx + j0, j0 == 0 ? &radmax : nullptr);
+                            smx + j0, j0 == 0 ? &radmax : nullptr, &rad2);
       }
     }
 
@@ -283,8 +291,8 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
       // and certifies right after (a warp sync instead of a block barrier)
       const double inv_m = 1.0 / (double)m;
       for (int j = tid; j < ntry; j += kB)
-        rpf_try_bounds(m, inv_m, sS1[j], sS2[j], sA[j], (double)on, radmax, &svh[j], &slo[j],
-                       &shi[j]);
+        rpf_try_bounds(m, inv_m, sS1[j], sS2[j], sA[j], (double)on, radmax, __fsqrt_ru(rad2),
+                       &svh[j], &slo[j], &shi[j]);
       if (ntry <= 32) __syncwarp();
       else __syncthreads();
     }
