@@ -9,14 +9,20 @@
 //  positions of one node and runs
 //    k_dirs_a      nTry directions per node (FP64 r, FP32 copy) and the FP64
 //                  projection b_j of the node's first member o
-//    k_proj_a      centred FP32 projections q' = r . (x - o), per-point error
-//                  radius, per-chunk FP32 statistics (sum, sum of squares,
-//                  sum of |q'|, min, max)
+//    k_proj_a      centred FP32 projections q' = r . (x - o) (rows staged per
+//                  warp through shared-memory tiles), per-point error radius,
+//                  per-chunk FP32 statistics (sum, sum of squares, sum of
+//                  |q'|, min, max, max radius, sum of squared radii)
 //    k_certify_a   Algorithm 2's choice certified from the bounds, or the
-//                  node is marked exact
-//    k_cand        exact FP64 min / max among the candidates the bound leaves
-//    k_proj64, k_csum_*   canonical FP64 statistics of exact nodes
-//    k_split_a     c = fma(u, b - a, a) with redraws ("c ~ runif[a, b]")
+//                  node is marked exact with its tries still in contention
+//    k_cand        exact FP64 min / max among the candidates the bound leaves;
+//                  lists the chunks of exact nodes
+//    k_proj64, k_csum_*   canonical FP64 statistics of exact nodes (tries in
+//                  contention only)
+//    k_med_*       median rule: radix selection over q', the band, a direct
+//                  selection for small bands (k_med_direct), exact passes
+//    k_split_a     c = fma(u, b - a, a) with redraws ("c ~ runif[a, b]"), or
+//                  the median
 //    k_side_count  p < c per point (certified from q', else FP64), counts
 //    k_node_scan / k_scatter   stable partition; children of <= 4096 points
 //                  go straight to the final permutation

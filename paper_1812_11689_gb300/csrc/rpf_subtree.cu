@@ -6,14 +6,16 @@
 // depth first from a small stack; after a split the larger child is pushed
 // first so the smaller one is processed next, which keeps the stack depth
 // below log2(4096) + 2.  Per node the CTA
-//   1. draws the nTry candidate directions (FP32 Box-Muller, FP64 normalise)
+//   1. draws the nTry candidate directions (FP32 Box-Muller, FP32 normalise)
 //   2. takes o = the node's first member and b_j = p64(o, r_j)
-//   3. projects every point: q' = fl32-dot(r32, fl32(x - o)), error radius,
-//      block statistics (FP32 per thread, FP64 across warps)
+//   3. projects every point: q' = fl32-dot(r32, fl32(x - o)) with the rows
+//      staged per warp through shared-memory tiles, error radius, block
+//      statistics (FP32 per thread, FP64 across warps)
 //   4. certifies Algorithm 2's choice, or recomputes the node in FP64 with the
 //      canonical reduction (one chunk: the node has <= 4096 points) for the
 //      tries the bounds leave in contention
-//   5. finds the exact min / max (FP64 on the few candidates), draws c
+//   5. finds the exact min / max (FP64 on the few candidates) and draws c,
+//      or selects the median
 //   6. decides every point's side (certified from q', else FP64) and
 //      partitions the segment stably
 //   7. records the node and its children; leaves are written to the final
