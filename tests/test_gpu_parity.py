@@ -95,6 +95,15 @@ def test_trees_bit_exact_workload_shapes(name, n, L, ntry):
         compare_trees(g, o, 4)
 
 
+def test_trees_bit_exact_level_synchronous_odd_dimension():
+    # d = 10 (not a multiple of 4): the level-synchronous projections take
+    # the per-thread path instead of the staged row tiles
+    X = synth.make("mix5_d10", n=12000)
+    o = oracle.Forest(X, 3, 50, 5, seed=3)
+    for growth in (1, 2):
+        compare_trees(gpu_forest(X, 3, 50, 5, seed=3, growth=growth), o, 3)
+
+
 def test_growth_modes_agree_and_certification_skips_fp64():
     X = synth.make("aniso20_d64", n=30000)
     a = gpu_forest(X, 6, 128, 5, growth=1)
