@@ -92,8 +92,10 @@ int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* s
  *   idx,dist : n x K outputs (device or host), sorted as described above.
  *   workspace: device scratch of at least rpf_workspace_bytes(f, 0, K, 1)
  *              bytes, or NULL to let the library allocate (stream-ordered).
- *   stream   : work is enqueued on it; host outputs are complete on return.
- * Errors: RPF_EINVAL, RPF_ENOMEM, RPF_ECUDA.
+ *   stream   : work is enqueued on it; the call synchronises it before
+ *              returning (host outputs are complete on return).
+ * Errors: RPF_EINVAL, RPF_ENOMEM, RPF_ECUDA, RPF_ETIMEOUT (a bounded device
+ * wait of this call gave up; the lists are then unspecified).
  */
 int rpf_all_knn(rpf_forest* f, int32_t K, int32_t* idx, float* dist, void* workspace,
                 size_t ws_bytes, void* stream);
@@ -119,14 +121,20 @@ int rpf_all_knn_trees(rpf_forest* f, int32_t n_trees, int32_t K, int32_t* idx, f
  *   idx,dist : m x K outputs (device or host).
  *   workspace: device scratch of rpf_workspace_bytes(f, m, K, 0) bytes, or
  *              NULL to let the library allocate (stream-ordered).
- * Errors: RPF_EINVAL, RPF_ENOMEM, RPF_ECUDA.
+ * Synchronisation: with host outputs, or with workspace NULL, the call
+ * synchronises `stream` and its return code covers the device work.  With a
+ * caller workspace and device outputs it only enqueues the work; a bounded
+ * device wait that gave up is then reported by rpf_query_status(workspace,
+ * stream) once the work is done.
+ * Errors: RPF_EINVAL, RPF_ENOMEM, RPF_ECUDA, RPF_ETIMEOUT (see above; the
+ * lists are then unspecified but every slot is written).
  */
 int rpf_query(const rpf_forest* f, const float* Q, int64_t m, int32_t K, int32_t* idx,
               float* dist, void* workspace, size_t ws_bytes, void* stream);
 
-/* Allocation-free query.  The paper has no counterpart: this is the query of
- * Sec. 2, Algorithm 3 exactly as rpf_query computes it (same kernels, same
- * results bit for bit), for callers that must not allocate device memory
+/* Allocation-free query.  The paper has no counterpart to this entry point:
+ * it answers the same query as rpf_query, with the same kernels and the same
+ * results bit for bit, for callers that must not allocate device memory
  * while they run -- e.g. a serving process whose free HBM is already handed
  * to its own pool, or a latency-critical thread that cannot take the
  * synchronisation a device allocation may imply.  It calls no cudaMalloc,
@@ -137,22 +145,34 @@ int rpf_query(const rpf_forest* f, const float* Q, int64_t m, int32_t K, int32_t
  *   idx,dist : m x K outputs in DEVICE memory, owned by the caller.
  *   stream   : cudaStream_t (NULL = legacy default stream).
  * Scratch: one fixed array of RPF_STATIC_SCRATCH_BYTES per device, inside
- * the library.  A call needs align256(4 m T) + align256(8 T m K) bytes of it
- * (T = trees of the forest; at T = 32, K = 10 that allows m <= 3120); larger
- * requests return RPF_EINVAL without launching anything -- split them.
- * Nothing in the scratch has to start at zero: every byte a call reads was
- * written earlier in the same call.
+ * the library.  A call needs 256 + align256(4 m T) + align256(8 T m K) bytes
+ * of it (T = trees of the forest; at T = 32, K = 10 that allows m <= 3120);
+ * larger requests return RPF_EINVAL without launching anything -- split
+ * them.  Nothing in the scratch has to start at zero: the call clears its
+ * error word and every other byte it reads was written earlier in the call.
  * Set-up: the first call on a device (that device current, the forest's
  * device) looks the array up once (cudaGetSymbolAddress) and caches its
- * address; make that first call before any stream capture starts.
+ * address; make that first call before any stream capture starts.  The
+ * cached address does not survive a device reset (cudaDeviceReset).
  * Races: the scratch is shared by every call on the device.  Calls that may
  * overlap in time (different streams, different host threads) race on it and
  * corrupt each other's results: issue them on one stream, or serialise them.
+ * The call only enqueues work; rpf_query_status(NULL, stream) reports a
+ * bounded device wait of the last call that gave up (RPF_ETIMEOUT).
  * Errors: RPF_EINVAL (bad argument, host pointer, wrong current device,
  * request larger than the scratch), RPF_ECUDA. */
 #define RPF_STATIC_SCRATCH_BYTES (8 << 20)
 int rpf_query_static(const rpf_forest* f, const float* Q, int64_t m, int32_t K, int32_t* idx,
                      float* dist, void* stream);
+
+/*
+ * rpf_query_status -- outcome of the device work of the last rpf_query that
+ * used `workspace` (or, with workspace NULL, of the last rpf_query_static on
+ * the current device): synchronises `stream` (the stream that query ran on),
+ * then returns RPF_OK, or RPF_ETIMEOUT if one of its bounded device waits
+ * gave up.  Errors: RPF_EINVAL (host pointer), RPF_ECUDA.
+ */
+int rpf_query_status(const void* workspace, void* stream);
 
 /* Scratch bytes rpf_all_knn (for_all_knn = 1, m ignored) or rpf_query needs. */
 size_t rpf_workspace_bytes(const rpf_forest* f, int64_t m, int32_t K, int32_t for_all_knn);
@@ -201,6 +221,28 @@ const char* rpf_error_string(int code);
  */
 int rpf_brute_knn(const float* X, int64_t n, int32_t d, const float* Q, int64_t m,
                   const int32_t* self, int32_t K, int32_t* idx, float* dist, void* stream);
+
+/* ---- failure detection --------------------------------------------------- */
+
+/* Time limit of every bounded device wait (the waits on bulk copies and on
+   tensor-core commits), in nanoseconds of the GPU's global timer; 0 restores
+   the default of 2 s.  A wait that reaches it records RPF_ETIMEOUT, waits
+   once more (bounded) for work in flight, frees what it holds and returns,
+   so the CUDA context stays usable.  Applies to launches made afterwards. */
+void rpf_set_wait_limit(uint64_t limit_ns);
+
+/* Check of the timeout path: one CTA waits, with the given limit, on a
+   barrier that nothing completes (no thread arrives on it, no copy is posted
+   to it, so nothing is in flight).  Returns RPF_ETIMEOUT when the wait gave
+   up as it must, RPF_OK if it ended otherwise, or RPF_ENOMEM / RPF_ECUDA.
+   Synchronises `stream`. */
+int rpf_wait_selftest(uint64_t limit_ns, void* stream);
+
+/* Allocation-failure injection for tests of the error paths: after `after`
+   more device allocations by the library succeed, the next one fails as if
+   the device were out of memory (the call in progress returns RPF_ENOMEM);
+   later allocations succeed again.  -1 switches it off. */
+void rpf_debug_fail_alloc(int64_t after);
 
 /* ---- tracing ---------------------------------------------------------------- */
 

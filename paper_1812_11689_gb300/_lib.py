@@ -58,6 +58,14 @@ def lib() -> ctypes.CDLL:
             L.rpf_query.restype = ctypes.c_int
             L.rpf_query_static.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp]
             L.rpf_query_static.restype = ctypes.c_int
+            L.rpf_query_status.argtypes = [_vp, _vp]
+            L.rpf_query_status.restype = ctypes.c_int
+            L.rpf_set_wait_limit.argtypes = [_u64]
+            L.rpf_set_wait_limit.restype = None
+            L.rpf_wait_selftest.argtypes = [_u64, _vp]
+            L.rpf_wait_selftest.restype = ctypes.c_int
+            L.rpf_debug_fail_alloc.argtypes = [_i64]
+            L.rpf_debug_fail_alloc.restype = None
             L.rpf_workspace_bytes.argtypes = [_vp, _i64, _i32, _i32]
             L.rpf_workspace_bytes.restype = _sz
             L.rpf_autotune.argtypes = [_vp, _i32, _vp, _vp]
@@ -104,7 +112,8 @@ def check(code: int, what: str) -> None:
 
 # names of every symbol include/rpforest.h declares (checked by the CPU tests)
 EXPORTED = ("rpf_default_params", "rpf_build", "rpf_all_knn", "rpf_all_knn_trees", "rpf_query",
-            "rpf_query_static", "rpf_add_trees", "rpf_autotune",
+            "rpf_query_static", "rpf_query_status", "rpf_add_trees", "rpf_autotune",
+            "rpf_set_wait_limit", "rpf_wait_selftest", "rpf_debug_fail_alloc",
             "rpf_workspace_bytes", "rpf_free", "rpf_error_string", "rpf_forest_info",
             "rpf_forest_perm", "rpf_forest_leaves", "rpf_forest_nodes", "rpf_directions",
             "rpf_brute_knn", "rpf_trace_enable", "rpf_launch_count", "rpf_trace_read",

@@ -8,7 +8,20 @@
 #include <new>
 #include <vector>
 
+#include <atomic>
+
 #include "rpf_internal.cuh"
+#include "rpf_tma.cuh"
+
+namespace {
+// limit of every bounded device wait, nanoseconds (0 = the default)
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;
+std::atomic<uint64_t> g_wait_ns{kDefaultWaitNs};
+// allocation-failure injection: allocations left before one fails (-1 = off)
+std::atomic<int64_t> g_fail_after{-1};
+}  // namespace
+
+uint64_t rpf_wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
 
 int rpf_cuda_err(cudaError_t e) {
   if (e == cudaErrorMemoryAllocation) return RPF_ENOMEM;
@@ -42,6 +55,10 @@ int rpf_alloc(void** p, size_t bytes, cudaStream_t s) {
     }
   }
   *p = nullptr;
+  if (g_fail_after.load() >= 0 && g_fail_after.fetch_sub(1) == 0) {
+    g_fail_after.store(-1);  // one injected failure, then normal service
+    return RPF_ENOMEM;
+  }
   if (cudaMallocAsync(p, std::max<size_t>(bytes, 256), s) != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -119,6 +136,16 @@ __global__ void k_shift_tree(int64_t N, int add, const int32_t* in, int32_t* out
   if (i < N) out[i] = in[i] + add;
 }
 
+// One bounded wait on a barrier that nothing completes: no thread arrives on
+// it and no copy is posted to it, so nothing is in flight when the wait gives
+// up and the kernel returns.
+__global__ void k_wait_selftest(uint64_t wlim, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) rpf_mbar_init(&bar, 1);
+  __syncthreads();
+  rpf_mbar_wait(&bar, 0, err, wlim);
+}
+
 }  // namespace
 
 extern "C" {
@@ -132,6 +159,46 @@ void rpf_default_params(rpf_params* p) {
   p->form = 0;
   p->growth = 0;
   p->seed = 0;
+}
+
+void rpf_set_wait_limit(uint64_t limit_ns) {
+  g_wait_ns.store(limit_ns ? limit_ns : kDefaultWaitNs);
+}
+
+int rpf_wait_selftest(uint64_t limit_ns, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  int* d_err = nullptr;
+  int rc = rpf_alloc((void**)&d_err, sizeof(int), s);
+  if (rc) return rc;
+  int h = 0;
+  cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    RPF_LAUNCH("k_wait_selftest", s, k_wait_selftest<<<1, 32, 0, s>>>(limit_ns, d_err));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  rpf_release(d_err, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return rpf_cuda_err(e);
+  return h ? h : RPF_OK;
+}
+
+void rpf_debug_fail_alloc(int64_t after) { g_fail_after.store(after < 0 ? -1 : after); }
+
+int rpf_query_status(const void* scratch, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const void* w = scratch;
+  if (!w) {
+    int rc = RPF_OK;
+    w = rpf_static_scratch(&rc);
+    if (!w) return rc;
+  } else if (!rpf_is_device_ptr(w)) {
+    return RPF_EINVAL;
+  }
+  int h = 0;
+  RPF_CU(cudaMemcpyAsync(&h, w, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RPF_CU(cudaStreamSynchronize(s));
+  return h ? h : RPF_OK;
 }
 
 const char* rpf_error_string(int code) {
@@ -364,14 +431,11 @@ int rpf_all_knn_trees(rpf_forest* f, int32_t n_trees, int32_t K, int32_t* idx, f
   bool own_ws = false;
   if (!ws) {
     wsb = rpf_all_knn_ws(f, K);
-    if (cudaMallocAsync(&ws, wsb, s) != cudaSuccess) {
-      cudaGetLastError();
-      return RPF_ENOMEM;
-    }
+    if (rpf_alloc(&ws, wsb, s)) return RPF_ENOMEM;
     own_ws = true;
   }
   int rc = rpf_all_knn_dev(f, n_trees, K, di, dd, ws, wsb, s);
-  if (own_ws) cudaFreeAsync(ws, s);
+  if (own_ws) rpf_release(ws, s);
   if (rc) return rc;
   if (!dev_out) {
     RPF_CU(cudaMemcpyAsync(idx, di, (size_t)n * K * 4, cudaMemcpyDefault, s));
@@ -393,17 +457,14 @@ int rpf_query(const rpf_forest* f, const float* Q, int64_t m, int32_t K, int32_t
   void* ws = workspace;
   bool own_ws = false;
   if (!ws) {
-    if (cudaMallocAsync(&ws, need, s) != cudaSuccess) {
-      cudaGetLastError();
-      return RPF_ENOMEM;
-    }
+    if (rpf_alloc(&ws, need, s)) return RPF_ENOMEM;
     own_ws = true;
   } else if (ws_bytes < need) {
     return RPF_EINVAL;
   }
   auto a256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
   char* w = (char*)ws;
-  const size_t core = a256((size_t)m * T * 4) + a256((size_t)T * m * K * 8);
+  const size_t core = rpf_query_core_ws(m, T, K);
   float* dQ = (float*)(w + core);
   int32_t* di = (int32_t*)(w + core + a256((size_t)m * f->d * 4));
   float* dd = (float*)(w + core + a256((size_t)m * f->d * 4) + a256((size_t)m * K * 4));
@@ -419,10 +480,17 @@ int rpf_query(const rpf_forest* f, const float* Q, int64_t m, int32_t K, int32_t
       if (e == cudaSuccess) e = cudaMemcpyAsync(dist, dd, (size_t)m * K * 4, cudaMemcpyDefault, s);
     }
   }
-  if (own_ws) cudaFreeAsync(ws, s);
-  if (!o_dev && e == cudaSuccess && !rc) e = cudaStreamSynchronize(s);
+  // the call's error word (first bytes of the scratch) is read whenever the
+  // call synchronises: host outputs, or a scratch the library allocated
+  const bool sync = !o_dev || own_ws;
+  int herr = 0;
+  if (sync && e == cudaSuccess && !rc)
+    e = cudaMemcpyAsync(&herr, ws, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (own_ws) rpf_release(ws, s);
+  if (sync && e == cudaSuccess && !rc) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return rpf_cuda_err(e);
-  return rc;
+  if (rc) return rc;
+  return herr ? herr : RPF_OK;
 }
 
 int rpf_forest_info(const rpf_forest* f, int64_t* n, int32_t* d, int32_t* n_trees,
@@ -488,15 +556,18 @@ int rpf_directions(uint64_t seed, int32_t t, const uint64_t* keys_host, int32_t 
   cudaStream_t s = (cudaStream_t)stream;
   uint64_t* dk = nullptr;
   double* dout = nullptr;
-  RPF_CU(cudaMallocAsync((void**)&dk, 8 * (size_t)n_keys, s));
+  if (rpf_alloc((void**)&dk, 8 * (size_t)n_keys, s)) return RPF_ENOMEM;
   const bool o_dev = rpf_is_device_ptr(out);
-  if (!o_dev) RPF_CU(cudaMallocAsync((void**)&dout, 8 * (size_t)n_keys * d, s));
+  if (!o_dev && rpf_alloc((void**)&dout, 8 * (size_t)n_keys * d, s)) {
+    rpf_release(dk, s);
+    return RPF_ENOMEM;
+  }
   RPF_CU(cudaMemcpyAsync(dk, keys_host, 8 * (size_t)n_keys, cudaMemcpyDefault, s));
   rpf_launch_directions(seed, t, dk, n_keys, j, d, o_dev ? out : dout, s);
   RPF_CU(cudaGetLastError());
   if (!o_dev) RPF_CU(cudaMemcpyAsync(out, dout, 8 * (size_t)n_keys * d, cudaMemcpyDefault, s));
-  cudaFreeAsync(dk, s);
-  if (dout) cudaFreeAsync(dout, s);
+  rpf_release(dk, s);
+  rpf_release(dout, s);
   RPF_CU(cudaStreamSynchronize(s));
   return RPF_OK;
 }
@@ -516,10 +587,7 @@ int rpf_brute_knn(const float* X, int64_t n, int32_t d, const float* Q, int64_t 
   const size_t bs = sd ? 0 : a256((size_t)m * 4), bo = od ? 0 : 2 * a256((size_t)m * K * 4);
   char* w = nullptr;
   if (bx + bq + bs + bo) {
-    if (cudaMallocAsync((void**)&w, bx + bq + bs + bo, s) != cudaSuccess) {
-      cudaGetLastError();
-      return RPF_ENOMEM;
-    }
+    if (rpf_alloc((void**)&w, bx + bq + bs + bo, s)) return RPF_ENOMEM;
   }
   const float* Xd = xd ? X : (const float*)w;
   const float* Qd = qd ? Q : (const float*)(w + bx);
@@ -536,7 +604,7 @@ int rpf_brute_knn(const float* X, int64_t n, int32_t d, const float* Q, int64_t 
     e = cudaMemcpyAsync(idx, Id, (size_t)m * K * 4, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dist, Dd, (size_t)m * K * 4, cudaMemcpyDefault, s);
   }
-  if (w) cudaFreeAsync(w, s);
+  rpf_release(w, s);
   if (e == cudaSuccess && !od) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return rpf_cuda_err(e);
   return rc;

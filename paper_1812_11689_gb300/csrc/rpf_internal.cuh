@@ -22,6 +22,10 @@
 #define RPF_MAX_K 128
 #define RPF_MAX_LEAF 1024  // a leaf is one CTA tile of at most 1024 rows
 #define RPF_FULL 0xffffffffu
+// deferred split points of the subtree kernel: candidates recorded per
+// extreme, and int32 words per record (node id, counts, candidates)
+#define RPF_DEFER_CAND 6
+#define RPF_DEFER_REC 16
 
 // ---------------------------------------------------------------------------
 // Counter-based random numbers for the direction draws and the uniform split
@@ -277,6 +281,8 @@ struct rpf_trace_scope {
   } while (0)
 
 int rpf_cuda_err(cudaError_t e);
+// time limit of every bounded device wait (rpf_set_wait_limit), nanoseconds
+uint64_t rpf_wait_limit_ns();
 bool rpf_is_device_ptr(const void* p);
 // Stream-ordered device allocation from the device's default pool, which is
 // set to keep freed memory cached (repeated builds reuse it without syncs).
@@ -303,5 +309,12 @@ int rpf_brute_dev(const float* X, int64_t n, int d, const float* Q, int64_t m,
                   const int32_t* self, int K, int32_t* idx, float* dist, cudaStream_t s);
 size_t rpf_all_knn_ws(const rpf_forest* f, int K);
 size_t rpf_query_ws(const rpf_forest* f, int64_t m, int K);
+// scratch of rpf_query_dev alone (error word, leaf ids, per-tree lists)
+size_t rpf_query_core_ws(int64_t m, int T, int K);
+// the query error word heads every query scratch
+#define RPF_QERR_BYTES 256
+// device address of the allocation-free query's scratch on the current
+// device (rpf_static.cu), or nullptr with *rc set
+void* rpf_static_scratch(int* rc);
 void rpf_launch_directions(uint64_t seed, int32_t t, const uint64_t* keys_dev, int32_t n_keys,
                            int32_t j, int32_t d, double* out_dev, cudaStream_t s);

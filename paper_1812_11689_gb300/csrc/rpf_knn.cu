@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(128, 4) k_leaf_plain(const int32_t* tile_cnt,
                                                     const int32_t* leaf_begin,
                                                     const int32_t* leaf_len, const int32_t* perm,
                                                     const float* __restrict__ X, int64_t n, int d,
-                                                    int dp, int K, int t0, uint2* cand, int* err) {
+                                                    int dp, int K, int t0, uint2* cand, int* err,
+                                                    uint64_t wlim) {
   extern __shared__ __align__(16) float xs[];
   __shared__ int leaf_off[257];  // a tile starts at most 256 leaves
   __shared__ int item_off[257];
@@ -157,7 +158,12 @@ __global__ void __launch_bounds__(128, 4) k_leaf_plain(const int32_t* tile_cnt,
       rpf_bulk_g2s(xs + r * dp, X + (int64_t)prow[r] * d, (uint32_t)d * 4u, &bar);
     for (int r = threadIdx.x; r < rows; r += blockDim.x)
       for (int k = d; k < dp; ++k) xs[r * dp + k] = 0.0f;
-    if (!rpf_mbar_wait(&bar, 0, err)) return;
+    // the whole CTA gives up together: one more bounded wait for copies in
+    // flight, then return (the error word reports the call as failed)
+    if (!__syncthreads_and(rpf_mbar_wait(&bar, 0, err, wlim))) {
+      rpf_mbar_wait(&bar, 0, nullptr, wlim);
+      return;
+    }
   } else if (STAGE) {
     for (int r = warp; r < rows; r += nwarp) {
       const float* src = X + (int64_t)prow[r] * d;
@@ -425,7 +431,7 @@ __global__ void __launch_bounds__(QS_T) k_qscan_cta(const float* __restrict__ Q,
                                                     const int32_t* node_len,
                                                     const int32_t* __restrict__ perm,
                                                     const float* __restrict__ X, int64_t n,
-                                                    uint2* cand, int* err) {
+                                                    uint2* cand, int* err, uint64_t wlim) {
   extern __shared__ __align__(16) float qs_rows[];  // QS_T x dp, then the query (dp)
   __shared__ unsigned long long keys[QS_T];
   __shared__ int pid[QS_T];
@@ -449,9 +455,11 @@ __global__ void __launch_bounds__(QS_T) k_qscan_cta(const float* __restrict__ Q,
     rpf_bulk_g2s(qs_rows + tid * dp, X + (int64_t)pid[tid] * d, (uint32_t)d * 4u, &bar);
     for (int k = d; k < dp; ++k) qs_rows[tid * dp + k] = 0.0f;
   }
-  const bool ok = __syncthreads_and(rpf_mbar_wait(&bar, 0, err)) != 0;
+  const bool ok = __syncthreads_and(rpf_mbar_wait(&bar, 0, err, wlim)) != 0;
   if (!ok) {  // one more bounded wait for copies in flight, then give up
-    rpf_mbar_wait(&bar, 0, nullptr);
+    rpf_mbar_wait(&bar, 0, nullptr, wlim);
+    // empty list for this (query, tree): the merge still reads defined slots
+    if (tid < K) cand[((int64_t)t * m + q) * K + tid] = make_uint2(0x7f800000u, 0xffffffffu);
     return;
   }
   unsigned long long key = ~0ull;
@@ -611,7 +619,7 @@ void launch_leaf(const rpf_forest* f, int64_t tb, int64_t nt, int K, int t0, uin
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SM));              \
     RPF_LAUNCH("k_leaf_plain", s, k_leaf_plain<KMAX, REGV, STAGEV><<<(unsigned)nt, 128, SM, s>>>( \
         f->tile_cnt, f->tile_off, f->tile_leaf, tb, f->leaf_tree, f->leaf_begin, f->leaf_len,  \
-        f->perm, f->X, f->n, f->d, dp, K, t0, cand, err));                                     \
+        f->perm, f->X, f->n, f->d, dp, K, t0, cand, err, rpf_wait_limit_ns()));                \
   } while (0)
   if (smem > 200 * 1024) RPF_LEAF(false, false, 0);   // rows read from global memory
   else if (dp == 68) RPF_LEAF(true, true, smem);      // 64-float rows held in registers
@@ -755,19 +763,26 @@ int rpf_all_knn_dev(rpf_forest* f, int T, int K, int32_t* idx, float* dist, void
   return RPF_OK;
 }
 
-size_t rpf_query_ws(const rpf_forest* f, int64_t m, int K) {
-  const int T = f->prm.n_trees;
-  return align256((size_t)m * T * 4) + align256((size_t)T * m * K * 8) +
-         align256((size_t)m * f->d * 4) + align256((size_t)m * K * 4) +
-         align256((size_t)m * K * 4);
+size_t rpf_query_core_ws(int64_t m, int T, int K) {
+  return RPF_QERR_BYTES + align256((size_t)m * T * 4) + align256((size_t)T * m * K * 8);
 }
 
+size_t rpf_query_ws(const rpf_forest* f, int64_t m, int K) {
+  return rpf_query_core_ws(m, f->prm.n_trees, K) + align256((size_t)m * f->d * 4) +
+         align256((size_t)m * K * 4) + align256((size_t)m * K * 4);
+}
+
+// Query scratch: [error word (RPF_QERR_BYTES)][leaf id per (query, tree)]
+// [per-tree candidate lists].  The error word is cleared here and set by a
+// bounded device wait that gave up, so it describes this call only.
 int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t* idx,
                   float* dist, void* ws, size_t ws_bytes, cudaStream_t s) {
   const int T = f->prm.n_trees;
-  if (ws_bytes < align256((size_t)m * T * 4) + align256((size_t)T * m * K * 8)) return RPF_EINVAL;
-  int32_t* qleaf = (int32_t*)ws;
-  uint2* cand = (uint2*)((char*)ws + align256((size_t)m * T * 4));
+  if (ws_bytes < rpf_query_core_ws(m, T, K)) return RPF_EINVAL;
+  int* qerr = (int*)ws;
+  RPF_CU(cudaMemsetAsync(qerr, 0, sizeof(int), s));
+  int32_t* qleaf = (int32_t*)((char*)ws + RPF_QERR_BYTES);
+  uint2* cand = (uint2*)((char*)qleaf + align256((size_t)m * T * 4));
   RPF_LAUNCH("k_route_w", s, k_route_w<<<nblk(m * T * RW, 256), 256, 0, s>>>(
       Q, m, f->d, T, f->node_left, f->node_right, f->node_flag, f->node_c, f->node_dir,
       f->node_dir32, qleaf));
@@ -777,7 +792,7 @@ int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t
     cudaFuncSetAttribute(k_qscan_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
     RPF_LAUNCH("k_qscan_cta", s, k_qscan_cta<<<(unsigned)(m * T), QS_T, qsm, s>>>(
         Q, m, f->d, dp, T, K, qleaf, f->node_tree, f->node_begin, f->node_len, f->perm, f->X,
-        f->n, cand, f->d_err));
+        f->n, cand, qerr, rpf_wait_limit_ns()));
   } else {
     RPF_KDISPATCH(K, launch_qscan, f, Q, m, K, qleaf, cand, s);
   }

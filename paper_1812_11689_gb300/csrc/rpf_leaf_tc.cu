@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
     const int4* __restrict__ tiles, int64_t tlo, int64_t thi, const uint32_t* __restrict__ bits,
     int64_t nwords, const int32_t* __restrict__ perm, const float* __restrict__ X, int64_t n,
     int d, int dp, int d16, int KC, int K, int t0, uint2* cand, int* err,
-    unsigned long long* fallbacks) {
+    unsigned long long* fallbacks, uint64_t wlim) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   constexpr int RG = ROWS / 8;                  // 8-row groups of the BF16 tiles
   constexpr uint32_t TCOLS = ROWS == 128 ? 128u : 512u;
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
       big_le[sidx] = le;
     }
     {
-      const bool w = rpf_mbar_wait(&bar_tma, tma_phase, err);
+      const bool w = rpf_mbar_wait(&bar_tma, tma_phase, err, wlim);
       tma_phase ^= 1u;
       tma_pending = false;
       ok = __syncthreads_and(w) != 0;
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
       float yy = 0.0f;
       for (int k0 = 0; k0 < d16 && ok; k0 += KC) {
         if (k0 > 0) {  // the previous chunk's MMAs must be done reading the tiles
-          const bool w = rpf_mbar_wait(&bar_mma, mma_phase, err);
+          const bool w = rpf_mbar_wait(&bar_mma, mma_phase, err, wlim);
           mma_phase ^= 1u;
           mma_pending = false;
           ok = __syncthreads_and(w) != 0;
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
       ynm[r] = __fsqrt_ru(yup);
       if (bslot >= 0) atomicMax(&nmax_bits[bslot], __float_as_uint(yup));
       {
-        const bool w = rpf_mbar_wait(&bar_mma, mma_phase, err);
+        const bool w = rpf_mbar_wait(&bar_mma, mma_phase, err, wlim);
         mma_phase ^= 1u;
         mma_pending = false;
         ok = __syncthreads_and(w) != 0;
@@ -534,8 +534,8 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
     __syncthreads();
   }
   // after a timed-out wait: one more bounded wait for work in flight
-  if (tma_pending) rpf_mbar_wait(&bar_tma, tma_phase, nullptr);
-  if (mma_pending) rpf_mbar_wait(&bar_mma, mma_phase, nullptr);
+  if (tma_pending) rpf_mbar_wait(&bar_tma, tma_phase, nullptr, wlim);
+  if (mma_pending) rpf_mbar_wait(&bar_mma, mma_phase, nullptr, wlim);
   rpf_tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -619,7 +619,7 @@ int launch_tc(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint
   const int64_t grid = std::min<int64_t>(thi - tlo, (int64_t)sms * occ);
   RPF_LAUNCH("k_leaf_tc", s, k_leaf_tc<KK, ROWS><<<(unsigned)grid, ROWS, smem, s>>>(
       f->pk_tiles, tlo, thi, f->pk_bits, f->pk_nwords, f->perm, f->X, f->n, d, dp, d16, KC, K,
-      t0, cand, f->d_err, f->d_fallback));
+      t0, cand, f->d_err, f->d_fallback, rpf_wait_limit_ns()));
   return RPF_OK;
 }
 

@@ -13,7 +13,10 @@
 // The first call on a device, with that device current, looks the array up
 // with cudaGetSymbolAddress and caches the address; that first call should be
 // made before any stream capture begins.  Later calls on the device only
-// reuse the cached address.
+// reuse the cached address.  The cache does not survive a device reset
+// (cudaDeviceReset, or the primary context released and created again): the
+// array may then live at another address, so a process that resets a device
+// must not call rpf_query_static on it afterwards.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -31,35 +34,48 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
-size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
-
 }  // namespace
+
+void* rpf_static_scratch(int* rc) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    *rc = rpf_cuda_err(e);
+    return nullptr;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    *rc = RPF_EINVAL;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_query_scratch);
+    if (e != cudaSuccess) {
+      *rc = rpf_cuda_err(e);
+      return nullptr;
+    }
+    g_addr[dev] = p;
+  }
+  return g_addr[dev];
+}
 
 extern "C" int rpf_query_static(const rpf_forest* f, const float* Q, int64_t m, int32_t K,
                                 int32_t* idx, float* dist, void* stream) {
   if (!f || K < 1 || K > RPF_MAX_K || m < 0) return RPF_EINVAL;
   if (m == 0) return RPF_OK;
   if (!Q || !idx || !dist) return RPF_EINVAL;
-  const int T = f->prm.n_trees;
-  // leaf id per (query, tree), then T per-tree candidate lists of K entries
-  const size_t need = a256((size_t)m * T * 4) + a256((size_t)T * m * K * 8);
-  if (need > (size_t)RPF_STATIC_SCRATCH_BYTES) return RPF_EINVAL;
+  // error word, leaf id per (query, tree), T per-tree candidate lists of K
+  if (rpf_query_core_ws(m, f->prm.n_trees, K) > (size_t)RPF_STATIC_SCRATCH_BYTES)
+    return RPF_EINVAL;
   if (!rpf_is_device_ptr(Q) || !rpf_is_device_ptr(idx) || !rpf_is_device_ptr(dist))
     return RPF_EINVAL;
   int dev = -1;
   RPF_CU(cudaGetDevice(&dev));
-  if (dev != f->device || dev < 0 || dev >= kMaxDevices) return RPF_EINVAL;
-  void* ws = nullptr;
-  {
-    std::lock_guard<std::mutex> g(g_mu);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_query_scratch);
-      if (e != cudaSuccess) return rpf_cuda_err(e);
-      g_addr[dev] = p;
-    }
-    ws = g_addr[dev];
-  }
+  if (dev != f->device) return RPF_EINVAL;
+  int rc = RPF_OK;
+  void* ws = rpf_static_scratch(&rc);
+  if (!ws) return rc;
   return rpf_query_dev(f, Q, m, K, idx, dist, ws, (size_t)RPF_STATIC_SCRATCH_BYTES,
                        (cudaStream_t)stream);
 }

@@ -4,13 +4,12 @@
 // A CTA stages up to blockDim rows at once: thread 0 posts the expected byte
 // count, every thread then issues the bulk copy of its own row (one 16-byte
 // aligned, 16-byte-multiple global span), and all threads wait on the
-// barrier's phase.  Every wait is bounded: after RPF_WAIT_LIMIT polls the
+// barrier's phase.  Every wait is bounded in time: after `limit_ns`
+// nanoseconds of the global timer (rpf_set_wait_limit; 2 s by default) the
 // thread records RPF_ETIMEOUT in the error word and gives up.
 #pragma once
 
 #include "rpf_internal.cuh"
-
-#define RPF_WAIT_LIMIT (1u << 26)
 
 __device__ __forceinline__ uint32_t rpf_smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -40,11 +39,26 @@ __device__ __forceinline__ bool rpf_mbar_try_wait(uint64_t* bar, uint32_t parity
   return ok != 0;
 }
 
-// Bounded wait for the given phase parity; returns false (and sets *err) on
+__device__ __forceinline__ uint64_t rpf_globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the given phase parity: polls until the phase completes or
+// limit_ns nanoseconds of the global timer have passed (checked every 64
+// polls; at most 2^24 checks in any case).  Returns false and sets *err on
 // timeout.
-__device__ __forceinline__ bool rpf_mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-  for (uint32_t it = 0; it < RPF_WAIT_LIMIT; ++it)
-    if (rpf_mbar_try_wait(bar, parity)) return true;
+__device__ __forceinline__ bool rpf_mbar_wait(uint64_t* bar, uint32_t parity, int* err,
+                                              uint64_t limit_ns) {
+  if (rpf_mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = rpf_globaltimer();
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
+#pragma unroll 1
+    for (int p = 0; p < 64; ++p)
+      if (rpf_mbar_try_wait(bar, parity)) return true;
+    if (rpf_globaltimer() - t0 > limit_ns) break;
+  }
   if (err) atomicExch(err, RPF_ETIMEOUT);
   return false;
 }

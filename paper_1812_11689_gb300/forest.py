@@ -48,6 +48,44 @@ def _as_points(X):
     return X.contiguous()
 
 
+def _check_buffer(name, t, shape, dtype, device=None):
+    """Checks of a caller buffer before any launch: type, dtype, contiguity,
+    shape, then (for the allocation-free path) that it lives on `device`."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError("%s must be a torch.Tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must have dtype %s, not %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, not %s" % (name, tuple(shape), tuple(t.shape)))
+    if device is not None and (not t.is_cuda or t.device != device):
+        raise ValueError("%s must be a CUDA tensor on %s" % (name, device))
+
+
+def _check_out(name, t, shape, dtype):
+    """An output buffer of rpf_query: a contiguous tensor or array of the
+    right dtype and shape (device or host)."""
+    if isinstance(t, np.ndarray):
+        if t.dtype != np.dtype(dtype) or not t.flags.c_contiguous or t.shape != tuple(shape):
+            raise ValueError("%s must be a contiguous %s array of shape %s"
+                             % (name, np.dtype(dtype), tuple(shape)))
+        return
+    _check_buffer(name, t, shape, {np.int32: torch.int32, np.float32: torch.float32}[dtype])
+
+
+def _check_query_static(d, Q, K, idx, dist, device):
+    """Arguments of rpf_query_static: Q (m x d float32), idx (m x K int32) and
+    dist (m x K float32), contiguous CUDA tensors on the forest's device."""
+    if not isinstance(Q, torch.Tensor) or Q.dim() != 2:
+        raise ValueError("Q must be a 2-D torch.Tensor")
+    m = int(Q.shape[0])
+    _check_buffer("Q", Q, (m, d), torch.float32, device)
+    _check_buffer("idx", idx, (m, K), torch.int32, device)
+    _check_buffer("dist", dist, (m, K), torch.float32, device)
+    return m
+
+
 class Forest:
     """T random projection trees over X (n x d, float32; device or host)."""
 
@@ -56,6 +94,8 @@ class Forest:
                  stream=None, split_rule: int = SPLIT_UNIFORM):
         X = _as_points(X)
         self.n, self.d = int(X.shape[0]), int(X.shape[1])
+        self.device = X.device if isinstance(X, torch.Tensor) and X.is_cuda else \
+            torch.device("cuda", torch.cuda.current_device())
         self.params = rpf_params(n_trees, leaf_max, n_try, split_rule, form, growth, seed)
         h = ctypes.c_void_p()
         check(_lib.lib().rpf_build(_ptr(X), self.n, self.d, ctypes.byref(self.params),
@@ -116,8 +156,19 @@ class Forest:
         self.params.n_trees += int(n_new)
 
     def query(self, Q, K: int, idx=None, dist=None, workspace=None, stream=None):
+        """rpf_query.  With a workspace and device outputs the call only
+        enqueues the work; query_status(workspace) reports its outcome."""
         Q = _as_points(Q)
         m = int(Q.shape[0])
+        if Q.shape[1] != self.d:
+            raise ValueError("Q must have %d columns, not %d" % (self.d, Q.shape[1]))
+        if idx is not None:
+            _check_out("idx", idx, (m, K), np.int32)
+        if dist is not None:
+            _check_out("dist", dist, (m, K), np.float32)
+        if workspace is not None and (not isinstance(workspace, torch.Tensor) or not
+                                      workspace.is_cuda or not workspace.is_contiguous()):
+            raise ValueError("workspace must be a contiguous CUDA tensor")
         on_dev = isinstance(Q, torch.Tensor) and Q.is_cuda
         if idx is None:
             idx = (torch.empty((m, K), dtype=torch.int32, device=Q.device) if on_dev
@@ -132,13 +183,21 @@ class Forest:
                                    ws or None, wsb, _stream_handle(stream)), "rpf_query")
         return idx, dist
 
+    def query_status(self, workspace=None, stream=None) -> None:
+        """rpf_query_status: waits for the stream and raises if a bounded
+        device wait of the last query on `workspace` (None: the last
+        query_static on this device) gave up."""
+        check(_lib.lib().rpf_query_status(None if workspace is None else _ptr(workspace),
+                                          _stream_handle(stream)), "rpf_query_status")
+
     def query_static(self, Q, K: int, idx, dist, stream=None):
         """rpf_query_static: the query with the library's fixed device scratch.
 
-        Q, idx and dist are caller-owned CUDA tensors; nothing is allocated.
-        Calls that may overlap in time share the scratch and must be
-        serialised (one stream)."""
-        m = int(Q.shape[0])
+        Q, idx and dist are caller-owned contiguous CUDA tensors on the
+        forest's device (checked here, before anything is launched); nothing
+        is allocated.  Calls that may overlap in time share the scratch and
+        must be serialised (one stream)."""
+        m = _check_query_static(self.d, Q, K, idx, dist, self.device)
         check(_lib.lib().rpf_query_static(self._h, _ptr(Q) if m else None, m, K,
                                           _ptr(idx) if m else None, _ptr(dist) if m else None,
                                           _stream_handle(stream)), "rpf_query_static")
@@ -218,6 +277,21 @@ def brute_knn(X, Q, K: int, self_idx=None, stream=None):
                                    _ptr(idx) if m else None, _ptr(dist) if m else None,
                                    _stream_handle(stream)), "rpf_brute_knn")
     return idx, dist
+
+
+def set_wait_limit(limit_ns: int = 0) -> None:
+    """rpf_set_wait_limit: time limit of every bounded device wait (0: 2 s)."""
+    _lib.lib().rpf_set_wait_limit(int(limit_ns))
+
+
+def wait_selftest(limit_ns: int, stream=None) -> int:
+    """rpf_wait_selftest: return code of one bounded wait that nothing completes."""
+    return int(_lib.lib().rpf_wait_selftest(int(limit_ns), _stream_handle(stream)))
+
+
+def debug_fail_alloc(after: int) -> None:
+    """rpf_debug_fail_alloc: the allocation after `after` more succeed fails (-1: off)."""
+    _lib.lib().rpf_debug_fail_alloc(int(after))
 
 
 class Trace:

@@ -55,6 +55,7 @@ class _Slot:
     host_idx: torch.Tensor = None
     host_dist: torch.Tensor = None
     keep: list = field(default_factory=list)   # device buffers alive until done
+    seq: int = 0                                # launch order
 
 
 class Server:
@@ -74,6 +75,7 @@ class Server:
         self.max_inflight = 0
         self.deferred_for_memory = 0
         self.stalled = False  # the oldest batch does not fit even with nothing in flight
+        self.deferred_now = False  # the last admission was held back for memory
         self.t0 = time.perf_counter()
 
     def now(self) -> float:
@@ -142,6 +144,7 @@ class Server:
             slot.event.record(slot.stream)
         slot.keep = [Qd, idx, dist, ws, hidx, hdist]
         slot.reqs, slot.rows, slot.K = batch, rows, K
+        slot.seq = self.n_batches
         for r in batch:
             r.batch = self.n_batches
         self.n_batches += 1
@@ -156,6 +159,7 @@ class Server:
             batch, rows, K = self._form_batch()
             if self._free_bytes() - self._need_bytes(rows, K) < self.reserve:
                 self.deferred_for_memory += 1
+                self.deferred_now = True
                 self.stalled = not any(x.reqs for x in self.slots)
                 return
             self.stalled = False
@@ -167,6 +171,9 @@ class Server:
         for slot in self.slots:
             if not slot.reqs or not slot.event.query():
                 continue
+            # the batch's device work is done: a bounded wait of it that gave
+            # up would be reported here (raises), never silently served
+            self.forest.query_status(slot.keep[3], stream=slot.stream)
             t = self.now()
             hidx, hdist = slot.keep[4], slot.keep[5]
             o = 0
@@ -180,6 +187,7 @@ class Server:
             slot.reqs, slot.keep = [], []
 
     def step(self) -> None:
+        self.deferred_now = False
         self._retire()
         self._admit()
 
@@ -206,7 +214,27 @@ class Server:
             if self.stalled:
                 raise RuntimeError("a batch needs more free device memory than the device has "
                                    "with nothing in flight; lower max_batch or reserve")
+            nxt = (float(arrivals[order[k]]) - self.now()
+                   if k < len(order) and arrivals is not None else None)
+            self._idle(nxt)
         return self.finished
+
+    def _idle(self, nxt) -> None:
+        """Block until something can change instead of polling: with every
+        slot busy, or requests held back for memory, wait on the oldest batch's
+        event; with a free slot and nothing waiting, sleep until the next
+        arrival (in steps of at most 100 us while batches are in flight)."""
+        inflight = [s for s in self.slots if s.reqs]
+        if not inflight:
+            if nxt is not None and nxt > 0:
+                time.sleep(nxt)
+            return
+        if self.waiting and (len(inflight) < len(self.slots)) and not self.deferred_now:
+            return  # admissible work is waiting: step again at once
+        if len(inflight) == len(self.slots) or self.waiting or nxt is None:
+            min(inflight, key=lambda s: s.seq).event.synchronize()
+        elif nxt > 0:
+            time.sleep(min(nxt, 1e-4))
 
 
 def latency_summary(reqs) -> dict:

@@ -12,10 +12,9 @@ import torch
 
 import oracle
 from paper_1812_11689_gb300 import synth
+from _parity import REL_TOL_FP64, check_knn, compare_trees  # noqa: F401
 
 pytestmark = pytest.mark.gpu
-
-REL_TOL_FP64 = 1e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -32,34 +31,6 @@ def F(*a, **k):
 def gpu_forest(X, T, L, ntry, seed=0, growth=0, form=0):
     return F(torch.from_numpy(np.ascontiguousarray(X)).cuda(), n_trees=T, leaf_max=L,
              n_try=ntry, seed=seed, growth=growth, form=form)
-
-
-def compare_trees(g, o, T):
-    nodes = g.nodes()
-    for t in range(T):
-        assert np.array_equal(g.perm(t), o.perm(t)), "perm of tree %d differs" % t
-    tr, b, ln = g.leaves()
-    for t in range(T):
-        ob, ol = o.leaves(t)
-        sel = tr == t
-        order = np.argsort(b[sel])
-        assert np.array_equal(b[sel][order], ob) and np.array_equal(ln[sel][order], ol)
-    # split records keyed by (tree, node key)
-    gi = {}
-    for i in range(len(nodes["key"])):
-        if nodes["left"][i] >= 0:
-            gi[(int(nodes["tree"][i]), int(nodes["key"][i]))] = (
-                int(nodes["jstar"][i]), int(nodes["flag"][i]) & 1, nodes["c"][i])
-    count = 0
-    for t in range(T):
-        on = o.nodes(t)
-        for i in np.where(on["leaf"] == 0)[0]:
-            js, fl, c = gi[(t, int(on["key"][i]))]
-            assert js == int(on["jstar"][i]) and fl == int(on["flag"][i])
-            if not fl:
-                assert c == on["c"][i]
-            count += 1
-    assert count == len(gi)
 
 
 @pytest.mark.parametrize("d", [1, 2, 10, 64, 127])
@@ -125,19 +96,6 @@ def test_growth_modes_agree_and_certification_skips_fp64():
                               nb[f][kb] >= 0 if f == "left" else nb[f][kb]), f
     assert np.array_equal(na["flag"][ka] & 1, nb["flag"][kb] & 1)
     assert np.array_equal(na["c"][ka].view(np.uint64), nb["c"][kb].view(np.uint64))
-
-
-def check_knn(gi, gd, oi, od, X, rows=None):
-    assert np.array_equal(gi, oi)
-    assert np.array_equal(gd, od)
-    # distances vs FP64 (non-padded slots)
-    rows = np.arange(len(gi)) if rows is None else rows
-    ok = gi >= 0
-    xi = X[np.repeat(rows, gi.shape[1])[ok.ravel()]].astype(np.float64)
-    xj = X[gi[ok]].astype(np.float64)
-    d64 = np.sqrt(((xi - xj) ** 2).sum(1))
-    rel = np.abs(gd[ok].astype(np.float64) - d64) / np.maximum(d64, 1e-30)
-    assert rel.max() <= REL_TOL_FP64
 
 
 @pytest.mark.parametrize("form", [0, 1])

@@ -187,6 +187,27 @@ def test_all_knn_equals_union_of_leaves_definition():
     assert np.array_equal(idx, pi) and np.array_equal(dist, pd)
 
 
+def test_all_knn_rows_equals_all_knn_and_the_union_definition(cfg1):
+    # orc_all_knn_rows answers chosen rows of Algorithm 3 with Q = U (the
+    # sampled form used at large n): on the 2,000-point workload, every row in
+    # a shuffled order with repeats matches orc_all_knn element by element,
+    # for several K, and a sample matches the Python union-of-leaves search
+    X, F = cfg1
+    rng = np.random.default_rng(7)
+    rows = np.concatenate([rng.permutation(F.n), rng.integers(0, F.n, 300)]).astype(np.int32)
+    for K in (1, 5, 17):
+        idx, dist = F.all_knn(K)
+        ri, rd = F.all_knn_rows(rows, K)
+        assert np.array_equal(ri, idx[rows]) and np.array_equal(rd.view(np.uint32),
+                                                                 dist[rows].view(np.uint32))
+    Xs = synth.make("mix5_d10", n=600)
+    Fs = oracle.Forest(Xs, 4, 20, 3, seed=4)
+    pi, pd = _python_union_knn(Fs, Xs, 5)
+    sub = np.array([0, 3, 599, 250, 3], np.int32)
+    ri, rd = Fs.all_knn_rows(sub, 5)
+    assert np.array_equal(ri, pi[sub]) and np.array_equal(rd, pd[sub])
+
+
 def test_per_tree_truncation_is_exact_and_sound(cfg1):
     X, F = cfg1
     K = 5

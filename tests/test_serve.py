@@ -28,6 +28,7 @@ def _server(free_bytes, slots=2, max_batch=100, reserve=0):
     s.waiting = collections.deque()
     s.finished, s.n_batches, s.max_inflight, s.deferred_for_memory = [], 0, 0, 0
     s.stalled = False
+    s.deferred_now = False
     s.launched = []
     s._free_bytes = lambda: free_bytes
 

@@ -45,7 +45,7 @@ def test_query_static_rejects_oversized_and_host_requests():
     import torch
     f = _forest()
     K = 10
-    # need = align256(4 m T) + align256(8 T m K) > 8 MiB at T = 8, K = 10
+    # need = 256 + align256(4 m T) + align256(8 T m K) > 8 MiB at T = 8, K = 10
     m = 13000
     Qd = torch.zeros((m, 96), dtype=torch.float32, device="cuda")
     idx = torch.full((m, K), -7, dtype=torch.int32, device="cuda")
@@ -54,7 +54,13 @@ def test_query_static_rejects_oversized_and_host_requests():
         f.query_static(Qd, K, idx, dist)
     torch.cuda.synchronize()
     assert bool((idx == -7).all())  # nothing was launched
+    # host queries are refused before anything is launched
     Qh = torch.zeros((10, 96), dtype=torch.float32)
-    with pytest.raises(RuntimeError):
+    with pytest.raises(ValueError):
         f.query_static(Qh, K, idx[:10], dist[:10])
+    torch.cuda.synchronize()
+    assert bool((idx == -7).all())
+    # the status of the last allocation-free query on this device
+    f.query_static(Qd[:100], K, idx[:100], dist[:100])
+    f.query_status(None)
     f.close()
