@@ -48,8 +48,11 @@ def parse():
                     help="skip the serving measurement (resident 2M-point forest)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--profile-step", action="store_true",
-                    help="one warm-up step and one step of the chosen form, nothing else "
-                         "(the command the ncu summaries under profiles/ are taken from)")
+                    help="one warm-up step and one step of the chosen form at the operating "
+                         "point, nothing else (the command the ncu summaries under profiles/ "
+                         "are taken from)")
+    ap.add_argument("--profile-trees", type=int, default=0,
+                    help="tree count of --profile-step (default: the operating point)")
     return ap.parse_args()
 
 
@@ -87,28 +90,64 @@ def peaks():
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle on a bounded sample (cpu_baseline and --impl reference)
+# CPU oracle (cpu_baseline of the GPU arm and every step of --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_sample(X, w, threads, t_sample=16, rows_sample=20000, seed=0):
+ORACLE_ROWS_FRACTION = 0.25   # share of the points whose all-kNN lists one step answers
+
+
+def oracle_step(X, w, n_trees, threads, rows_fraction=ORACLE_ROWS_FRACTION, seed=0):
+    """One timed pass of the oracle over the workload: all n_trees trees grown
+    on all n points (one tree per thread, the paper's multicore scheme), then
+    the all-kNN lists of a seeded sample of the points over those trees.  The
+    trees are not sampled; the answering time is scaled by n / rows (every
+    point's answer is independent work, spread over the threads dynamically).
+    Returns the throughput of the whole job (build + all n answers)."""
     import oracle
     oracle.build()
     n = X.shape[0]
-    Ts = min(t_sample, w.n_trees)
+    nr = n if rows_fraction >= 1.0 else max(1, int(n * rows_fraction))
+    rows = np.sort(np.random.default_rng(seed).choice(n, size=nr, replace=False)).astype(np.int32)
     t0 = time.perf_counter()
-    F = oracle.Forest(X, Ts, w.leaf_max, w.n_try, seed=seed, threads=threads)
+    F = oracle.Forest(X, n_trees, w.leaf_max, w.n_try, seed=seed, threads=threads)
     t_grow = time.perf_counter() - t0
-    rows = np.random.default_rng(seed).choice(n, size=min(rows_sample, n), replace=False)
-    rows = np.sort(rows).astype(np.int32)
     t0 = time.perf_counter()
-    F.all_knn_rows(rows, w.k)
+    if nr == n:
+        F.all_knn(w.k)
+    else:
+        F.all_knn_rows(rows, w.k)
     t_rows = time.perf_counter() - t0
-    # growth cost is linear in T (trees are independent); search cost is
-    # linear in the answered rows and in T (union size ~ T leaves)
-    t_full = t_grow * (w.n_trees / Ts) + t_rows * (n / len(rows)) * (w.n_trees / Ts)
-    sample = ("%d of %d trees grown on all %d points, all-kNN for %d sampled points over "
-              "those trees; scaled by trees and points" % (Ts, w.n_trees, n, len(rows)))
+    del F
+    t_full = t_grow + t_rows * (n / nr)
+    sample = ("all %d trees grown on all %d points with %d threads; all-kNN answered for %d "
+              "sampled points (%.0f %%) over those trees, the answering time scaled by n / rows"
+              % (n_trees, n, threads, nr, 100.0 * nr / n))
     return {"value": n / t_full, "unit": "queries/s", "cores": threads, "kind": "oracle",
-            "sample": sample, "sample_seconds": t_grow + t_rows, "scaled_seconds": t_full}
+            "sample": sample, "n_trees": n_trees, "step_seconds": round(t_grow + t_rows, 3),
+            "grow_seconds": round(t_grow, 3), "answer_seconds": round(t_rows, 3),
+            "full_workload_seconds": round(t_full, 3)}
+
+
+def oracle_single_thread(X, w, n_trees, seed=0, trees=2, rows=2000):
+    """The oracle on one thread, on a stated sample: `trees` trees grown on all
+    points and the all-kNN lists of `rows` sampled points over them, scaled by
+    trees (growth and answering both grow linearly with the tree count) and
+    by rows."""
+    import oracle
+    oracle.build()
+    n = X.shape[0]
+    r = np.sort(np.random.default_rng(seed).choice(n, size=rows, replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    F = oracle.Forest(X, trees, w.leaf_max, w.n_try, seed=seed, threads=1)
+    t_grow = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    F.all_knn_rows(r, w.k)
+    t_rows = time.perf_counter() - t0
+    t_full = (t_grow + t_rows * (n / rows)) * (n_trees / trees)
+    return {"value": n / t_full, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": "%d trees grown on all %d points and all-kNN for %d sampled points over "
+                      "them, one thread; scaled by trees (to %d) and by n / rows"
+                      % (trees, n, rows, n_trees),
+            "sample_seconds": round(t_grow + t_rows, 3)}
 
 
 # ---------------------------------------------------------------------------
@@ -161,6 +200,7 @@ class Clocks:
 
 
 SUBTREE_MAX = 4096          # nodes of at most this many points grow CTA-locally
+T_GRID = (40, 48, 56, 64, 72, 80, 88, 96, 104, 112, 120, 128)  # nested ensembles swept
 FP32_LANES = 152 * 128      # FP32 lanes of a GB300 (152 SMs x 128)
 BF16_TFLOPS = (1900.0, "fallback (dense BF16, one earlier GB300 measurement)")
 SM_MAX_GHZ = 2.07
@@ -213,10 +253,10 @@ def work_model(fo, w, n):
     kids = kids[kids >= 0]
     rb = int(ln[kids][(ln[kids] <= SUBTREE_MAX) & internal[kids]].sum())
     if n <= SUBTREE_MAX and n > w.leaf_max:  # every root is a subtree root
-        rb += n * w.n_trees
+        rb += n * fo.info()["n_trees"]
     pl_a, pl_b = int(ln[A].sum()), int(ln[B].sum())
     leaf_len = ln[~internal]
-    d, T, K, nt = w.d, w.n_trees, w.k, w.n_try
+    d, T, K, nt = w.d, fo.info()["n_trees"], w.k, w.n_try
     return {
         "k_subtree": {"bytes": pl_b * (4 * d + 4) + rb * 8},
         "k_proj_a": {"bytes": pl_a * (4 * d + 4 + 4 + 4 * nt)},
@@ -292,6 +332,34 @@ def rooflines(trace, work, hbm_peak, peak_kind, steps, workload):
     return out
 
 
+def missing_counts(found, true):
+    """m(i) = |trueK(i) minus found(i)| for every row (Sec. 5.1), as index
+    sets; -1 pads of the true lists are not neighbours, -1 pads of the found
+    lists match nothing."""
+    hit = (true[:, :, None] == found[:, None, :]).any(-1)
+    return ((~hit) & (true >= 0)).sum(1)
+
+
+def nested_sweep(forest_mod, Xd, w, rule, bi, bd, form, seed):
+    """One forest of max(T_GRID) trees under split rule `rule`; all-kNN over
+    its first T trees (the T-tree forest: nested ensembles) for every T of
+    the grid, with the missing rate and distance discrepancy over all n
+    points against exact brute force.  Returns the sweep and the smallest T
+    whose missing rate is at most 1 %."""
+    f = forest_mod.Forest(Xd, n_trees=max(T_GRID), leaf_max=w.leaf_max, n_try=w.n_try,
+                          seed=seed, form=form, split_rule=rule)
+    sweep, t_op = [], None
+    for T in T_GRID:
+        i, d = f.all_knn(w.k, n_trees=T)
+        m = float(missing_counts(i.cpu().numpy(), bi).sum()) / bi.size
+        sweep.append({"n_trees": T, "missing_rate": round(m, 6),
+                      "knn_distance_discrepancy": discrepancy_full(d.cpu().numpy(), bd)[0]})
+        if t_op is None and m <= 0.01:
+            t_op = T
+    f.close()
+    return sweep, t_op
+
+
 def run_gb300(args, rank, world, local_rank):
     import torch
     from paper_1812_11689_gb300 import forest, synth
@@ -304,26 +372,48 @@ def run_gb300(args, rank, world, local_rank):
     Xd = torch.from_numpy(X).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
-    kw = dict(n_trees=w.n_trees, leaf_max=w.leaf_max, n_try=w.n_try, seed=args.seed)
+    chosen, plain = forest.FORM_CHOSEN, forest.FORM_PLAIN
+
+    # ground truth over all n points: exact brute force (d32 order, self excluded)
+    allrows = torch.arange(n, dtype=torch.int32, device=dev)
+    bi, bd = forest.brute_knn(Xd, Xd, w.k, self_idx=allrows)
+    bi, bd = bi.cpu().numpy(), bd.cpu().numpy()
+
+    # the metric's operating point: the smallest nested T whose all-kNN lists
+    # miss at most 1 % of the true neighbours, under Algorithm 1's uniform
+    # split point (exact over all n points)
+    sweep_u, t_op = nested_sweep(forest, Xd, w, forest.SPLIT_UNIFORM, bi, bd, chosen, args.seed)
+    stated = w.extra.get("n_trees_le_1pct")
+    verified = t_op is not None and t_op == stated
+    if t_op is None:
+        t_op = max(T_GRID)
+    if world > 1:  # every replica times the same T: the largest any rank needs
+        t = torch.tensor([t_op], dtype=torch.int64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_op = int(t.item())
+    kw = dict(n_trees=t_op, leaf_max=w.leaf_max, n_try=w.n_try, seed=args.seed)
     ws = {}
 
-    def step(form):
-        f = forest.Forest(Xd, form=form, **kw)
-        if form not in ws:
-            ws[form] = torch.empty(f.workspace_bytes(w.k), dtype=torch.uint8, device=dev)
-        out = f.all_knn(w.k, workspace=ws[form])
+    def step(form, kwt=None):
+        f = forest.Forest(Xd, form=form, **(kwt or kw))
+        if (form, f.params.n_trees) not in ws:
+            ws[(form, f.params.n_trees)] = torch.empty(f.workspace_bytes(w.k), dtype=torch.uint8,
+                                                       device=dev)
+        out = f.all_knn(w.k, workspace=ws[(form, f.params.n_trees)])
         return f, out
 
-    def timed(form, K, trace=False, kwt=None, wst=None):
+    def timed(form, K, kwt=None):
+        kwt = kwt or kw
+        wst = ws[(form, kwt["n_trees"])]
         times, b_ms, a_ms = [], [], []
         for _ in range(K):
             flush.fill_(1)
             torch.cuda.synchronize()
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
-            f = forest.Forest(Xd, form=form, **(kwt or kw))
+            f = forest.Forest(Xd, form=form, **kwt)
             e1.record(stream)
-            f.all_knn(w.k, workspace=ws[form] if wst is None else wst)
+            f.all_knn(w.k, workspace=wst)
             e2.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e2))
@@ -332,7 +422,6 @@ def run_gb300(args, rank, world, local_rank):
             f.close()
         return times, b_ms, a_ms
 
-    chosen, plain = forest.FORM_CHOSEN, forest.FORM_PLAIN
     tuned = None
     for _ in range(args.warmup):
         for form in (chosen, plain):
@@ -361,7 +450,7 @@ def run_gb300(args, rank, world, local_rank):
     trace = forest.Trace.read()
     ms_step, value = replica_value(sum(times), n, args.steps, world, dev)
 
-    # plain FP32 form on the same workload
+    # plain FP32 form at the same T
     p_times, p_b, p_a = timed(plain, args.steps)
     forest.Trace.read()
     forest.Trace.enable(True)
@@ -380,74 +469,65 @@ def run_gb300(args, rank, world, local_rank):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         f = forest.Forest(Xh, form=chosen, **kw)
-        f.all_knn(w.k, idx=ih, dist=dh, workspace=ws[chosen])
+        f.all_knn(w.k, idx=ih, dist=dh, workspace=ws[(chosen, t_op)])
         torch.cuda.synchronize()
         if it:
             e2e_t.append(time.perf_counter() - t0)
         f.close()
     e2e_s = sum(e2e_t) / len(e2e_t)
 
-    # accuracy: chosen == plain bit for bit; missing rate vs exact brute force
+    # accuracy at the operating point: chosen == plain bit for bit; missing
+    # rate and discrepancy over all n points
     fc, (ci, cd) = step(chosen)
     fp, (pi, pd) = step(plain)
     same = bool(torch.equal(ci, pi) and torch.equal(cd, pd))
-    rows = torch.from_numpy(np.sort(np.random.default_rng(1).choice(n, 2000, replace=False))
-                            .astype(np.int32)).to(dev)
-    bi, bd = forest.brute_knn(Xd, Xd[rows.long()].contiguous(), w.k, self_idx=rows)
-    ci_s, cd_s = ci[rows.long()].cpu().numpy(), cd[rows.long()].cpu().numpy()
-    bi, bd = bi.cpu().numpy(), bd.cpu().numpy()
-
-    def missing(found):
-        return sum(len(set(bi[r]) - set(found[r])) for r in range(len(bi))) / float(bi.size)
-
-    def discrepancy(found_d):
-        return discrepancy_full(found_d, bd)[0]
-
-    miss, disc = missing(ci_s), discrepancy(cd_s)
-    # The first T' trees of a forest are the T'-tree forest (node keys and
-    # draws depend on the tree index only), so growing the ensemble finds the
-    # smallest T with a missing rate <= 1 %; that T is then timed like the
-    # configured one.
-    def at_one_percent(rule):
-        """Smallest nested T (first T' trees of a forest = the T'-tree forest)
-        whose missing rate is <= 1 %, with that step timed like the
-        configured one; for one split rule."""
-        res, sweep = None, []
-        for Tn in (w.n_trees, 48, 64, 80, 96, 128, 160, 192, 256, 384, 512):
-            if Tn < w.n_trees or (Tn == w.n_trees and sweep):
-                continue
-            kwt = dict(kw, n_trees=Tn, split_rule=rule)
-            f2 = forest.Forest(Xd, form=chosen, **kwt)
-            wst = torch.empty(f2.workspace_bytes(w.k), dtype=torch.uint8, device=dev)
-            i2, d2 = f2.all_knn(w.k, workspace=wst)
-            m2 = missing(i2[rows.long()].cpu().numpy())
-            sweep.append({"n_trees": Tn, "missing_rate": round(m2, 5)})
-            f2.close()
-            if m2 <= 0.01:
-                t2, b2, a2 = timed(chosen, args.steps, kwt=kwt, wst=wst)
-                ms2 = sum(t2) / len(t2)
-                pt2, _, pa2 = timed(plain, args.steps, kwt=kwt, wst=wst)
-                res = {"n_trees": Tn, "missing_rate": round(m2, 5),
-                       "knn_distance_discrepancy": discrepancy(d2[rows.long()].cpu().numpy()),
-                       "value": round(world * n / (ms2 * 1e-3), 1), "ms_per_step": round(ms2, 3),
-                       "stage_ms": {"build": round(sum(b2) / len(b2), 3),
-                                    "all_knn": round(sum(a2) / len(a2), 3)},
-                       "plain": {"value": round(world * n / (sum(pt2) / len(pt2) * 1e-3), 1),
-                                 "all_knn_ms": round(sum(pa2) / len(pa2), 3)}}
-                break
-            del wst
-        if res is None:
-            res = {"not_reached_by_n_trees": 512}
-        res["sweep"] = sweep
-        return res
-
-    at1 = None
-    if miss > 0.01:
-        at1 = {"uniform": at_one_percent(forest.SPLIT_UNIFORM),
-               "median": at_one_percent(forest.SPLIT_MEDIAN)}
-        vals = {k: v.get("value", 0.0) for k, v in at1.items()}
-        at1["best_split_rule"] = max(vals, key=vals.get)
+    ci_h, cd_h = ci.cpu().numpy(), cd.cpu().numpy()
+    miss = float(missing_counts(ci_h, bi).sum()) / bi.size
+    disc, short = discrepancy_full(cd_h, bd)
+    rel = None
+    ok = ci_h >= 0
+    if ok.any():  # reported distances against FP64 on a sample of rows
+        r = np.random.default_rng(1).choice(n, 2000, replace=False)
+        ii, dd, oo = ci_h[r], cd_h[r], ok[r]
+        xi = X[np.repeat(r, w.k).reshape(-1, w.k)[oo]].astype(np.float64)
+        xj = X[ii[oo]].astype(np.float64)
+        d64 = np.sqrt(((xi - xj) ** 2).sum(1))
+        rel = float((np.abs(dd[oo].astype(np.float64) - d64) / np.maximum(d64, 1e-30)).max())
     info = fc.info()
+
+    # the configured T (fewer trees, higher missing rate), timed the same way
+    kw_c = dict(kw, n_trees=w.n_trees)
+    for form in (chosen, plain):
+        f, _ = step(form, kw_c)
+        f.close()
+    c_t, c_b, c_a = timed(chosen, args.steps, kw_c)
+    cp_t, _, _ = timed(plain, args.steps, kw_c)
+    at_cfg = {"n_trees": w.n_trees,
+              "missing_rate": next(x["missing_rate"] for x in sweep_u if x["n_trees"] == w.n_trees),
+              "value": round(world * n / (sum(c_t) / len(c_t) * 1e-3), 1),
+              "ms_per_step": round(sum(c_t) / len(c_t), 3),
+              "stage_ms": {"build": round(sum(c_b) / len(c_b), 3),
+                           "all_knn": round(sum(c_a) / len(c_a), 3)},
+              "plain_value": round(world * n / (sum(cp_t) / len(cp_t) * 1e-3), 1)}
+
+    # the median split rule (the paper's other usual split point) at its own
+    # operating point
+    med = None
+    if not args.no_sweep:
+        sweep_m, t_m = nested_sweep(forest, Xd, w, forest.SPLIT_MEDIAN, bi, bd, chosen, args.seed)
+        med = {"sweep": sweep_m, "n_trees": t_m}
+        if t_m is not None:
+            kw_m = dict(kw, n_trees=t_m, split_rule=forest.SPLIT_MEDIAN)
+            for form in (chosen, plain):
+                f, _ = step(form, kw_m)
+                f.close()
+            m_t, m_b, m_a = timed(chosen, args.steps, kw_m)
+            mp_t, _, _ = timed(plain, args.steps, kw_m)
+            med.update({"value": round(world * n / (sum(m_t) / len(m_t) * 1e-3), 1),
+                        "ms_per_step": round(sum(m_t) / len(m_t), 3),
+                        "stage_ms": {"build": round(sum(m_b) / len(m_b), 3),
+                                     "all_knn": round(sum(m_a) / len(m_a), 3)},
+                        "plain_value": round(world * n / (sum(mp_t) / len(mp_t) * 1e-3), 1)})
 
     hbm_peak, peak_kind = peaks()
     work = work_model(fc, w, n)
@@ -460,6 +540,9 @@ def run_gb300(args, rank, world, local_rank):
         roof.update({"kernel": top["kernel"], "share": top["share"], "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": top["algorithmic_bytes_per_launch"],
                      "ms_per_launch": top["ms_per_launch"]})
+        for k in ("l2_row_gather", "fp32_alu", "tensor_bf16"):
+            if k in top:
+                roof[k] = top[k]
     fc.close()
     fp.close()
 
@@ -475,11 +558,26 @@ def run_gb300(args, rank, world, local_rank):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
+        "precision": "split decisions with FP64 semantics (certified FP32, FP64 fallback); "
+                     "distances FP32 (canonical d32 key), BF16 tensor-core shortlist re-ranked "
+                     "exactly",
         "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "d": d, "n_trees": w.n_trees,
-                   "leaf_max": w.leaf_max, "k": w.k, "n_try": w.n_try, "form": "chosen",
+        "config": {"workload": args.workload, "n": n, "d": d, "n_trees": t_op,
+                   "leaf_max": w.leaf_max, "k": w.k, "n_try": w.n_try, "split_rule": "uniform",
+                   "form": "chosen",
+                   "n_trees_rule": "smallest T of %s with missing rate <= 1 %% (nested "
+                                   "ensembles, exact over all n points)" % (list(T_GRID),),
+                   "configured_n_trees": w.n_trees,
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
+        "missing_rate": round(miss, 6),
+        "knn_distance_discrepancy": disc,
+        "points_with_short_lists": short,
+        "max_rel_distance_error_vs_fp64": rel,
+        "accuracy": "missing rate and discrepancy over all %d points against exact brute force "
+                    "(rpf_brute_knn); FP64 distance error on 2,000 rows" % n,
+        "operating_point": {"n_trees": t_op, "stated_n_trees": stated,
+                            "verified_smallest_in_grid": verified, "sweep_uniform": sweep_u},
         "stage_ms": {"build": round(sum(b_ms) / len(b_ms), 3),
                      "all_knn": round(sum(a_ms) / len(a_ms), 3)},
         "plain": {"value": round(world * n / (p_ms * 1e-3), 1), "ms_per_step": round(p_ms, 3),
@@ -487,10 +585,8 @@ def run_gb300(args, rank, world, local_rank):
                                "all_knn": round(sum(p_a) / len(p_a), 3)}},
         "chosen_equals_plain": same,
         "autotune": tuned,
-        "missing_rate": round(miss, 5),
-        "knn_distance_discrepancy": disc,
-        "at_missing_rate_le_1pct": at1,
-        "accuracy_sample": "2000 points vs exact brute force (rpf_brute_knn)",
+        "at_configured_n_trees": at_cfg,
+        "median_split_rule": med,
         "forest": info,
         "e2e": {"value": round(world * n / e2e_s, 1), "unit": "queries/s",
                 "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(n * w.k * 8)},
@@ -513,14 +609,23 @@ def run_gb300(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_serve:
         line["serving"] = run_serving(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(X, w, os.cpu_count() or 1)
+        threads = os.cpu_count() or 1
+        cb = oracle_step(X, w, t_op, threads, seed=args.seed)
+        cb["single_thread"] = oracle_single_thread(X, w, t_op, seed=args.seed)
+        line["cpu_baseline"] = cb
     return line
 
 
+SERVE_T_GRID = (32, 64, 128, 256, 384, 512)  # nested ensembles of the serving workload
+
+
 def run_serving(args, dev, n_requests=300):
-    """Serving on the resident-forest workload: saturation throughput (all
-    requests at once), then Poisson arrivals at 0.5 / 0.8 / 0.95 of it, for
-    each K; p50 / p99 from arrival to results ready on the host."""
+    """Serving on the resident-forest workload (2M x 96, leaf bound 128):
+    saturation throughput (all requests at once), then Poisson arrivals at
+    0.5 / 0.8 / 0.95 of it, for each K; p50 / p99 from arrival to results
+    ready on the host.  Measured at the configured T = 32 and at the
+    operating point: the forest grows (rpf_add_trees, nested ensembles) until
+    the missing rate of 500 held-out queries at K = 10 is at most 1 %."""
     import torch
     from paper_1812_11689_gb300 import forest, serve, synth
     w = synth.WORKLOADS["mix50_d96"]
@@ -531,38 +636,63 @@ def run_serving(args, dev, n_requests=300):
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     sizes = synth.request_sizes(n_requests, seed=args.seed, max_size=w.extra["max_request"])
-    out = {"workload": "mix50_d96", "n": w.n, "d": w.d, "n_trees": w.n_trees,
-           "leaf_max": w.leaf_max, "requests_per_run": n_requests,
-           "request_sizes": "floor(exp(U(0, ln 4097))) clamped to [1, 4096]",
-           "build_s": round(build_s, 3), "slots": 4, "max_batch": 8192, "runs": {}}
+    Qs = torch.from_numpy(synth.queries("mix50_d96", 500, seed=args.seed, stream=9999)).to(dev)
+    truth = {K: forest.brute_knn(X, Qs, K)[0].cpu().numpy() for K in w.extra["k_set"]}
+
+    def missing(K):
+        qi, _ = f.query(Qs, K)
+        return round(float(missing_counts(qi.cpu().numpy(), truth[K]).sum()) / truth[K].size, 5)
 
     def make_reqs(K, stream0):
         return [serve.Request(i, synth.queries("mix50_d96", int(m), seed=args.seed,
                                                stream=stream0 + i), K, 0.0)
                 for i, m in enumerate(sizes)]
 
-    for K in w.extra["k_set"]:
-        serve.Server(f, slots=4).run(make_reqs(K, 1000)[:20])  # warm-up
-        srv = serve.Server(f, slots=4, max_batch=8192)
-        sat = serve.latency_summary(srv.run(make_reqs(K, 2000)))
-        runs = {"saturation": sat}
+    def runs_at():
+        runs = {}
         mean_m = float(np.mean(sizes))
-        for load in (0.5, 0.8, 0.95):
-            rate = load * sat["queries_per_s"] / mean_m
-            arr = synth.poisson_arrivals(n_requests, rate_per_s=rate, seed=args.seed + 1)
+        for K in w.extra["k_set"]:
+            serve.Server(f, slots=4).run(make_reqs(K, 1000)[:20])  # warm-up
             srv = serve.Server(f, slots=4, max_batch=8192)
-            res = serve.latency_summary(srv.run(make_reqs(K, 3000), arr))
-            res["offered_requests_per_s"] = round(rate, 1)
-            res["batches"] = srv.n_batches
-            runs["load_%.2f" % load] = res
-        # accuracy of the served answers on a sample, against exact brute force
-        Qs = torch.from_numpy(synth.queries("mix50_d96", 500, seed=args.seed, stream=9999)).to(dev)
-        qi, _ = f.query(Qs, K)
-        bi, _ = forest.brute_knn(X, Qs, K)
-        qi, bi = qi.cpu().numpy(), bi.cpu().numpy()
-        runs["missing_rate_sample_500"] = round(
-            sum(len(set(bi[r]) - set(qi[r])) for r in range(len(bi))) / float(bi.size), 5)
-        out["runs"]["K=%d" % K] = runs
+            sat = serve.latency_summary(srv.run(make_reqs(K, 2000)))
+            r = {"saturation": sat}
+            for load in (0.5, 0.8, 0.95):
+                rate = load * sat["queries_per_s"] / mean_m
+                arr = synth.poisson_arrivals(n_requests, rate_per_s=rate, seed=args.seed + 1)
+                srv = serve.Server(f, slots=4, max_batch=8192)
+                res = serve.latency_summary(srv.run(make_reqs(K, 3000), arr))
+                res["offered_requests_per_s"] = round(rate, 1)
+                res["batches"] = srv.n_batches
+                r["load_%.2f" % load] = res
+            r["missing_rate_sample_500"] = missing(K)
+            runs["K=%d" % K] = r
+        return runs
+
+    out = {"workload": "mix50_d96", "n": w.n, "d": w.d, "leaf_max": w.leaf_max,
+           "requests_per_run": n_requests,
+           "request_sizes": "floor(exp(U(0, ln 4097))) clamped to [1, 4096]",
+           "build_s_32_trees": round(build_s, 3), "slots": 4, "max_batch": 8192,
+           "accuracy_sample": "500 held-out queries vs exact brute force (rpf_brute_knn)",
+           "configured": {"n_trees": w.n_trees, "runs": runs_at()}}
+    sweep, t_op = [], None
+    T = w.n_trees
+    for Tn in SERVE_T_GRID:
+        if Tn > T:
+            t0 = time.perf_counter()
+            f.add_trees(Tn - T)
+            torch.cuda.synchronize()
+            sweep.append({"added_trees": Tn - T, "add_s": round(time.perf_counter() - t0, 3)})
+            T = Tn
+        m10 = missing(10)
+        sweep.append({"n_trees": T, "missing_rate_k10": m10})
+        if m10 <= 0.01:
+            t_op = T
+            break
+    out["sweep"] = sweep
+    if t_op is not None:
+        out["operating_point"] = {"n_trees": t_op, "runs": runs_at()}
+    else:
+        out["operating_point"] = {"not_reached_by_n_trees": max(SERVE_T_GRID)}
     f.close()
     return out
 
@@ -761,7 +891,8 @@ def run_profile_step(args):
     from paper_1812_11689_gb300 import forest, synth
     w = synth.WORKLOADS[args.workload]
     X = torch.from_numpy(synth.make(args.workload, seed=args.seed)).cuda()
-    kw = dict(n_trees=w.n_trees, leaf_max=w.leaf_max, n_try=w.n_try, seed=args.seed,
+    T = args.profile_trees or w.extra.get("n_trees_le_1pct", w.n_trees)
+    kw = dict(n_trees=T, leaf_max=w.leaf_max, n_try=w.n_try, seed=args.seed,
               form=forest.FORM_CHOSEN)
     counts = []
     for _ in range(2):
@@ -771,31 +902,46 @@ def run_profile_step(args):
         torch.cuda.synchronize()
         counts.append(forest.Trace.launch_count() - l0)
         f.close()
-    return {"profile_step": True, "workload": args.workload, "launches_per_step": counts}
+    return {"profile_step": True, "workload": args.workload, "n_trees": T,
+            "launches_per_step": counts}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle, as it stands, on the host cores, at
+    the GPU arm's operating point (same workload and tree count); every step
+    is one oracle_step (all trees grown in full, a quarter of the points
+    answered).  Warm-up steps run the same function on a small sample (8
+    trees, 1 % of the points) to page the data and the library in."""
     from paper_1812_11689_gb300 import synth
     if rank != 0:
         return None
     w = synth.WORKLOADS[args.workload]
     X = synth.make(args.workload, seed=args.seed)
+    T = w.extra.get("n_trees_le_1pct", w.n_trees)
     threads = os.cpu_count() or 1
-    res = []
     for _ in range(args.warmup):
-        oracle_sample(X, w, threads, t_sample=4, rows_sample=5000)
+        oracle_step(X, w, min(8, T), threads, rows_fraction=0.01, seed=args.seed)
+    res, step_s = [], []
     for _ in range(args.steps):
-        res.append(oracle_sample(X, w, threads, t_sample=4, rows_sample=5000))
+        t0 = time.perf_counter()
+        res.append(oracle_step(X, w, T, threads, seed=args.seed))
+        step_s.append(time.perf_counter() - t0)
     v = statistics.median(r["value"] for r in res)
     cb = dict(res[-1])
     cb["value"] = v
     return {"impl": "reference", "metric": "all-kNN queries/s at <=1% missing rate "
             "(chosen vs plain FP32 form)", "value": round(v, 2), "unit": "queries/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(1e3 * w.n / v, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": w.n, "d": w.d, "n_trees": w.n_trees,
-                       "leaf_max": w.leaf_max, "k": w.k, "n_try": w.n_try},
+            "ms_per_step": round(1e3 * sum(step_s) / len(step_s), 3),
+            "ms_per_step_is": "wall time of one oracle step (all trees, sampled answers); "
+                              "value = n / the step's full-workload time",
+            "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "precision": "split decisions FP64, distances FP32 (canonical d32 key)",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": w.n, "d": w.d, "n_trees": T,
+                       "leaf_max": w.leaf_max, "k": w.k, "n_try": w.n_try,
+                       "split_rule": "uniform", "form": "oracle (exact union of leaves)"},
             "cpu_baseline": cb,
             "e2e": {"value": round(v, 2), "unit": "queries/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}

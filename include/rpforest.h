@@ -86,6 +86,19 @@ int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* s
               rpf_forest** out);
 
 /*
+ * rpf_build_shard -- rpf_build for trees tree_first .. tree_first + n_trees - 1
+ * of the ensemble.  Every random draw of tree t is keyed by its global index
+ * t, so these are exactly the trees a forest of tree_first + n_trees trees
+ * holds at those indexes: the trees of Algorithm 3 are independent (Sec. 2,
+ * Sec. 5.3), and a forest can be split by tree across processes or GPUs
+ * whose per-point lists are then merged (rpf_all_knn_keys, rpf_merge_keys).
+ *   tree_first : >= 0, tree_first + n_trees <= 2^20.
+ * Other arguments and errors as rpf_build.
+ */
+int rpf_build_shard(const float* X, int64_t n, int32_t d, const rpf_params* p,
+                    int32_t tree_first, void* stream, rpf_forest** out);
+
+/*
  * rpf_all_knn -- K nearest neighbours of every data point among the union of
  * its T leaves, the point itself excluded (Algorithm 3 with Q = U).
  *   K        : 1 <= K <= 128.
@@ -110,6 +123,34 @@ int rpf_all_knn(rpf_forest* f, int32_t K, int32_t* idx, float* dist, void* works
  */
 int rpf_all_knn_trees(rpf_forest* f, int32_t n_trees, int32_t K, int32_t* idx, float* dist,
                       void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * rpf_all_knn_keys -- the lists of rpf_all_knn with the ranking key itself:
+ * for every point, its K nearest in the union of its leaves over this
+ * forest's trees, as n x K pairs of int32 (bits of the FP32 squared distance
+ * d32, index), ascending by (d32, index), empty slots (+inf bits, -1).  These
+ * are the lists a group of trees contributes to the union over a larger
+ * forest (Algorithm 3): merging the groups' lists per point with
+ * rpf_merge_keys gives exactly the larger forest's lists, because a point in
+ * the K nearest of the whole union is in the K nearest of every group's
+ * union that contains it.
+ *   keys      : n x K x 2 int32 (device or host).
+ *   workspace : as rpf_all_knn.  Synchronises `stream`.
+ * Errors: as rpf_all_knn.
+ */
+int rpf_all_knn_keys(rpf_forest* f, int32_t K, int32_t* keys, void* workspace, size_t ws_bytes,
+                     void* stream);
+
+/*
+ * rpf_merge_keys -- merge n_lists key lists per point (rpf_all_knn_keys
+ * layout, list-major: lists[(g * n + i) * K + k] is pair k of point i in list
+ * g) into the final lists: the K smallest distinct (d32, index) pairs, as
+ * indices and Euclidean distances sqrtf(d32), padded with (-1, +inf).
+ *   n >= 0, 1 <= K <= 128, n_lists >= 1; pointers device or host.
+ * Errors: RPF_EINVAL, RPF_ENOMEM, RPF_ECUDA.
+ */
+int rpf_merge_keys(int64_t n, int32_t K, int32_t n_lists, const int32_t* lists, int32_t* idx,
+                   float* dist, void* stream);
 
 /*
  * rpf_query -- K nearest neighbours of m new points Q among the data, found
@@ -178,16 +219,22 @@ int rpf_query_status(const void* workspace, void* stream);
 size_t rpf_workspace_bytes(const rpf_forest* f, int64_t m, int32_t K, int32_t for_all_knn);
 
 /*
- * rpf_autotune -- pick the tile launch configuration of the chosen form's
- * leaf kernel (Gram coordinates per tensor-core chunk, CTAs per SM) by
- * timing every candidate on this forest's own tiles (its first trees) with
- * K neighbours.  All candidates give identical lists; the fastest is kept for
- * the rest of the process for forests with the same dimension, tile rows and
- * K bucket, so later rpf_all_knn calls (of this forest or of new ones of the
- * same shape) use it.  A forest of the plain form, or one the tensor-core
- * kernel does not cover, has nothing to tune (chosen = {0, 0}).
- *   chosen : NULL or int32[2] receiving {Gram chunk, CTAs per SM}.
- * Allocates a scratch list for the first trees; synchronises `stream`.
+ * rpf_autotune -- pick the leaf-tile configuration by timing every candidate
+ * on this forest's own tiles (its first trees) with K neighbours; all
+ * candidates give identical lists.
+ *   plain form  : the tile region R (leaves of a tree starting in one region
+ *                 of R positions form a tile; multiples of 32).
+ *   chosen form : tile rows (128 or 256, where the leaf bound allows both),
+ *                 Gram coordinates per tensor-core chunk, CTAs per SM.
+ * The tile shape is kept for the rest of the process for forests of the same
+ * dimension and leaf bound (later builds use it) and this forest's tiles are
+ * rebuilt with it; the launch choice is kept per (dimension, tile rows, K
+ * bucket).  A chosen-form forest the tensor-core kernel does not cover has
+ * nothing to tune (chosen all 0).
+ *   chosen : NULL or int32[4] receiving {Gram chunk, CTAs per SM, tile rows,
+ *            tile region R} (0 where not tuned).
+ * Allocates a scratch list for the first trees; synchronises `stream`; no
+ * other call may use the forest meanwhile.
  * Errors: RPF_EINVAL, RPF_ENOMEM, RPF_ECUDA.
  */
 int rpf_autotune(rpf_forest* f, int32_t K, void* stream, int32_t* chosen);
@@ -272,7 +319,9 @@ int rpf_forest_info(const rpf_forest* f, int64_t* n, int32_t* d, int32_t* n_tree
 /* Counters (host, first n_out of): [0] nodes decided by the FP64 fallback,
    [1] rows the BF16 form rescanned exactly because its certificate failed
    (cumulative over rpf_all_knn calls), [2] level-synchronous growth levels,
-   [3] leaf-tile region R. */
+   [3] leaf-tile region R, [4] tree groups of rpf_all_knn calls on a
+   chosen-form forest that ran the plain form instead (leaf bound above 256,
+   K above 32, or rows too wide for the tensor-core tile; cumulative). */
 int rpf_forest_counters(const rpf_forest* f, int64_t* out, int32_t n_out);
 
 /* Final permutation of tree t (n int32, host): every leaf is a contiguous

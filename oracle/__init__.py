@@ -84,6 +84,13 @@ def lib():
             L.orc_build.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_int32, ctypes.c_int32, _u64, ctypes.c_int32,
                                     ctypes.c_int32]
+            L.orc_build_range.restype = ctypes.c_void_p
+            L.orc_build_range.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _u64,
+                                          ctypes.c_int32, ctypes.c_int32]
+            L.orc_all_knn_keys.restype = None
+            L.orc_all_knn_keys.argtypes = [ctypes.c_void_p, _f32p, _i32p, ctypes.c_int64,
+                                           ctypes.c_int32, _i32p, _f32p, ctypes.c_int32]
             L.orc_free.restype = None
             L.orc_free.argtypes = [ctypes.c_void_p]
             L.orc_n_nodes.restype = ctypes.c_int64
@@ -189,14 +196,18 @@ class Forest:
     """
 
     def __init__(self, X: np.ndarray, n_trees: int, leaf_max: int, n_try: int,
-                 seed: int = 0, threads: int | None = None, split_rule: int = 0):
+                 seed: int = 0, threads: int | None = None, split_rule: int = 0,
+                 tree_first: int = 0):
+        """tree_first: global index of the first tree grown; the forest then
+        holds trees tree_first .. tree_first + n_trees - 1 of the ensemble."""
         self.X = np.ascontiguousarray(X, np.float32)
         self.n, self.d = self.X.shape
         self.T, self.L, self.n_try, self.seed = n_trees, leaf_max, n_try, seed
         self.split_rule = split_rule
+        self.tree_first = tree_first
         self.threads = threads or default_threads()
-        h = lib().orc_build(_p(self.X, _f32p), self.n, self.d, n_trees, leaf_max, n_try,
-                            seed, self.threads, split_rule)
+        h = lib().orc_build_range(_p(self.X, _f32p), self.n, self.d, tree_first, n_trees,
+                                  leaf_max, n_try, seed, self.threads, split_rule)
         if not h:
             raise ValueError("orc_build rejected its arguments")
         self._h = ctypes.c_void_p(h)
@@ -249,6 +260,18 @@ class Forest:
                                _p(idx, _i32p), _p(dist, _f32p), self.threads)
         return idx, dist
 
+    def all_knn_keys(self, K: int, rows=None):
+        """Per-point lists over this forest's trees with the squared key d32
+        (FP32) instead of the distance: (idx int32, d32 float32), rows of all
+        points unless `rows` is given."""
+        rows = (np.arange(self.n, dtype=np.int32) if rows is None
+                else np.ascontiguousarray(rows, np.int32))
+        idx = np.empty((rows.size, K), np.int32)
+        d32 = np.empty((rows.size, K), np.float32)
+        lib().orc_all_knn_keys(self._h, _p(self.X, _f32p), _p(rows, _i32p), rows.size, K,
+                               _p(idx, _i32p), _p(d32, _f32p), self.threads)
+        return idx, d32
+
     def route(self, t: int, q: np.ndarray) -> int:
         q = np.ascontiguousarray(q, np.float32)
         return int(lib().orc_route(self._h, t, _p(q, _f32p)))
@@ -286,6 +309,28 @@ def brute_knn(X: np.ndarray, K: int, rows=None, Q=None, threads: int | None = No
     lib().orc_brute_knn(_p(X, _f32p), n, d, _p(Qa, _f32p), nr, selfp, K, _p(idx, _i32p),
                         _p(dist, _f32p), _p(d64, _f64p), threads or default_threads())
     return idx, dist, d64
+
+
+def merge_key_lists(idx_lists, d32_lists, K: int):
+    """The K nearest of the union of several candidate lists per point
+    (Algorithm 3's N_q = union of leaves, taken over groups of trees): for
+    each point, the distinct (d32, index) pairs of all lists in ascending
+    order, the first K, padded with (-1, +inf); distances are sqrtf(d32).
+    idx_lists / d32_lists: G arrays of shape (n, K')."""
+    n = idx_lists[0].shape[0]
+    idx = np.full((n, K), -1, np.int32)
+    dist = np.full((n, K), np.inf, np.float32)
+    for i in range(n):
+        pairs = set()
+        for il, dl in zip(idx_lists, d32_lists):
+            for j, v in zip(il[i], dl[i]):
+                if j >= 0:
+                    pairs.add((float(v), int(j)))
+        best = sorted(pairs)[:K]
+        for k, (v, j) in enumerate(best):
+            idx[i, k] = j
+            dist[i, k] = np.sqrt(np.float32(v))
+    return idx, dist
 
 
 # --------------------------------------------------------------------------

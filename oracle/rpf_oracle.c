@@ -267,6 +267,7 @@ typedef struct {
 typedef struct {
   int64_t n;
   int32_t d, T, L, ntry;
+  int32_t t0;         /* global index of the first tree (draws are keyed by it) */
   int32_t split_rule; /* 0: c ~ U[a, b]; 1: median of the projections */
   uint64_t seed;
   orc_tree* trees;
@@ -328,7 +329,7 @@ static void orc_split(const orc_forest* F, orc_tree* tr, int64_t t, int64_t ni,
   for (int j = 0; j < ntry; ++j) {
     double* r = rbuf + (size_t)j * d;
     double* p = pbuf + (size_t)j * m;
-    orc_direction(F->seed, (uint64_t)t, nd->key, (uint64_t)j, d, r);
+    orc_direction(F->seed, (uint64_t)(t + F->t0), nd->key, (uint64_t)j, d, r);
     for (int64_t i = 0; i < m; ++i) p[i] = orc_proj(F->X + (size_t)mem[i] * d, r, d);
     double S = orc_csum(p, m);
     double mu = S / (double)m;
@@ -357,7 +358,8 @@ static void orc_split(const orc_forest* F, orc_tree* tr, int64_t t, int64_t ni,
       if (p[i] > b) b = p[i];
     }
     for (int att = 0; F->split_rule == 0 && att < ORC_SPLIT_ATTEMPTS; ++att) {
-      double u = orc_u53(orc_word(F->seed, ORC_TAG_SPLIT, (uint64_t)t, nd->key, (uint64_t)att, 0));
+      double u = orc_u53(orc_word(F->seed, ORC_TAG_SPLIT, (uint64_t)(t + F->t0), nd->key,
+                                  (uint64_t)att, 0));
       double cc = fma(u, b - a, a);
       if (cc > a && cc <= b) {
         c = cc;
@@ -482,13 +484,18 @@ static void orc_grow_tree(const orc_forest* F, int64_t t) {
   free(tmp);
 }
 
-/* Build T trees (Algorithm 3, first loop).  Trees are independent, so with
-   OpenMP they are grown one per thread -- the multicore scheme of Sec. 5.3. */
-orc_forest* orc_build(const float* X, int64_t n, int32_t d, int32_t T, int32_t L,
-                      int32_t ntry, uint64_t seed, int32_t threads, int32_t split_rule) {
-  if (!X || n < 1 || d < 1 || T < 1 || L < 1 || ntry < 1) return NULL;
+/* Build trees t0 .. t0 + T - 1 of the ensemble (Algorithm 3, first loop):
+   every draw of tree t is keyed by its global index t, so these are exactly
+   the trees a forest of t0 + T trees holds at those indexes.  Trees are
+   independent, so with OpenMP they are grown one per thread -- the multicore
+   scheme of Sec. 5.3. */
+orc_forest* orc_build_range(const float* X, int64_t n, int32_t d, int32_t t0, int32_t T,
+                            int32_t L, int32_t ntry, uint64_t seed, int32_t threads,
+                            int32_t split_rule) {
+  if (!X || n < 1 || d < 1 || t0 < 0 || T < 1 || L < 1 || ntry < 1) return NULL;
   if (split_rule < 0 || split_rule > 1) return NULL;
   orc_forest* F = (orc_forest*)calloc(1, sizeof(orc_forest));
+  F->t0 = t0;
   F->split_rule = split_rule;
   F->n = n;
   F->d = d;
@@ -506,6 +513,12 @@ orc_forest* orc_build(const float* X, int64_t n, int32_t d, int32_t T, int32_t L
   (void)threads;
   F->X = NULL;
   return F;
+}
+
+/* The first T trees of the ensemble. */
+orc_forest* orc_build(const float* X, int64_t n, int32_t d, int32_t T, int32_t L,
+                      int32_t ntry, uint64_t seed, int32_t threads, int32_t split_rule) {
+  return orc_build_range(X, n, d, 0, T, L, ntry, seed, threads, split_rule);
 }
 
 void orc_free(orc_forest* F) {
@@ -581,7 +594,7 @@ static void orc_topk_insert(float* kd, int32_t* ki, int K, float dv, int32_t j) 
 static void orc_knn_from_union(const float* X, int d, const float* q, int32_t self,
                                int32_t* const* leaf_members, const int64_t* leaf_len,
                                int32_t T, int32_t K, int32_t* stamp, int32_t stamp_id,
-                               int32_t* idx_out, float* dist_out) {
+                               int32_t* idx_out, float* dist_out, int squared) {
   float* kd = (float*)malloc(sizeof(float) * (size_t)K);
   for (int k = 0; k < K; ++k) {
     kd[k] = INFINITY;
@@ -596,7 +609,8 @@ static void orc_knn_from_union(const float* X, int d, const float* q, int32_t se
       orc_topk_insert(kd, idx_out, K, orc_d32(q, X + (size_t)j * d, d), j);
     }
   }
-  for (int k = 0; k < K; ++k) dist_out[k] = idx_out[k] < 0 ? INFINITY : sqrtf(kd[k]);
+  for (int k = 0; k < K; ++k)
+    dist_out[k] = idx_out[k] < 0 ? INFINITY : (squared ? kd[k] : sqrtf(kd[k]));
   free(kd);
 }
 
@@ -640,7 +654,7 @@ void orc_all_knn(const orc_forest* F, const float* X, int32_t K, int32_t* idx,
         len[t] = ll[(size_t)i * T + t];
       }
       orc_knn_from_union(X, F->d, X + (size_t)i * F->d, (int32_t)i, mem, len, T, K, stamp,
-                         (int32_t)i, idx + (size_t)i * K, dist + (size_t)i * K);
+                         (int32_t)i, idx + (size_t)i * K, dist + (size_t)i * K, 0);
     }
     free(stamp);
     free(mem);
@@ -650,9 +664,11 @@ void orc_all_knn(const orc_forest* F, const float* X, int32_t K, int32_t* idx,
 }
 
 /* All-kNN answers for the data points rows[0..nr) only (same definition as
-   orc_all_knn; used to check large instances on a sample). */
-void orc_all_knn_rows(const orc_forest* F, const float* X, const int32_t* rows, int64_t nr,
-                      int32_t K, int32_t* idx, float* dist, int32_t threads) {
+   orc_all_knn; used to check large instances on a sample).  squared = 1
+   reports the d32 key itself instead of its square root. */
+static void orc_all_knn_rows_impl(const orc_forest* F, const float* X, const int32_t* rows,
+                                  int64_t nr, int32_t K, int32_t* idx, float* dist,
+                                  int32_t threads, int squared) {
   const int64_t n = F->n;
   const int T = F->T;
   /* position of every point in every tree's permutation */
@@ -693,7 +709,7 @@ void orc_all_knn_rows(const orc_forest* F, const float* X, const int32_t* rows, 
         len[t] = leaf_l[t][a];
       }
       orc_knn_from_union(X, F->d, X + (size_t)i * F->d, i, mem, len, T, K, stamp, (int32_t)r,
-                         idx + (size_t)r * K, dist + (size_t)r * K);
+                         idx + (size_t)r * K, dist + (size_t)r * K, squared);
     }
     free(stamp);
     free(mem);
@@ -707,6 +723,19 @@ void orc_all_knn_rows(const orc_forest* F, const float* X, const int32_t* rows, 
   free(leaf_l);
   free(pos);
   (void)threads;
+}
+
+void orc_all_knn_rows(const orc_forest* F, const float* X, const int32_t* rows, int64_t nr,
+                      int32_t K, int32_t* idx, float* dist, int32_t threads) {
+  orc_all_knn_rows_impl(F, X, rows, nr, K, idx, dist, threads, 0);
+}
+
+/* The same lists as orc_all_knn_rows with the squared key d32 in place of the
+   distance: the per-point lists a set of trees contributes to a union over
+   more trees (a forest split into groups of trees). */
+void orc_all_knn_keys(const orc_forest* F, const float* X, const int32_t* rows, int64_t nr,
+                      int32_t K, int32_t* idx, float* d32, int32_t threads) {
+  orc_all_knn_rows_impl(F, X, rows, nr, K, idx, d32, threads, 1);
 }
 
 /* Drop a point through tree t (Algorithm 3, "let q fall through tree t_i"):
@@ -752,7 +781,7 @@ void orc_query(const orc_forest* F, const float* X, const float* Q, int64_t m,
         len[t] = lf->len;
       }
       orc_knn_from_union(X, F->d, q, -1, mem, len, T, K, stamp, (int32_t)qi,
-                         idx + (size_t)qi * K, dist + (size_t)qi * K);
+                         idx + (size_t)qi * K, dist + (size_t)qi * K, 0);
     }
     free(stamp);
     free(mem);

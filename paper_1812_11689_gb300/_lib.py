@@ -50,6 +50,13 @@ def lib() -> ctypes.CDLL:
             L.rpf_build.argtypes = [_vp, _i64, _i32, ctypes.POINTER(rpf_params), _vp,
                                     ctypes.POINTER(_vp)]
             L.rpf_build.restype = ctypes.c_int
+            L.rpf_build_shard.argtypes = [_vp, _i64, _i32, ctypes.POINTER(rpf_params), _i32,
+                                          _vp, ctypes.POINTER(_vp)]
+            L.rpf_build_shard.restype = ctypes.c_int
+            L.rpf_all_knn_keys.argtypes = [_vp, _i32, _vp, _vp, _sz, _vp]
+            L.rpf_all_knn_keys.restype = ctypes.c_int
+            L.rpf_merge_keys.argtypes = [_i64, _i32, _i32, _vp, _vp, _vp, _vp]
+            L.rpf_merge_keys.restype = ctypes.c_int
             L.rpf_all_knn.argtypes = [_vp, _i32, _vp, _vp, _vp, _sz, _vp]
             L.rpf_all_knn.restype = ctypes.c_int
             L.rpf_all_knn_trees.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp, _sz, _vp]
@@ -111,7 +118,8 @@ def check(code: int, what: str) -> None:
 
 
 # names of every symbol include/rpforest.h declares (checked by the CPU tests)
-EXPORTED = ("rpf_default_params", "rpf_build", "rpf_all_knn", "rpf_all_knn_trees", "rpf_query",
+EXPORTED = ("rpf_default_params", "rpf_build", "rpf_build_shard", "rpf_all_knn",
+            "rpf_all_knn_keys", "rpf_merge_keys", "rpf_all_knn_trees", "rpf_query",
             "rpf_query_static", "rpf_query_status", "rpf_add_trees", "rpf_autotune",
             "rpf_set_wait_limit", "rpf_wait_selftest", "rpf_debug_fail_alloc",
             "rpf_workspace_bytes", "rpf_free", "rpf_error_string", "rpf_forest_info",

@@ -213,11 +213,17 @@ const char* rpf_error_string(int code) {
   }
 }
 
-int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* stream,
-              rpf_forest** out) {
+}  // extern "C"
+
+namespace {
+// Grow trees t_base .. t_base + p->n_trees - 1 of the ensemble (every draw of
+// tree t is keyed by its global index).
+int build_impl(const float* X, int64_t n, int32_t d, const rpf_params* p, int32_t t_base,
+               void* stream, rpf_forest** out) {
   if (!out) return RPF_EINVAL;
   *out = nullptr;
   if (!X || !p || n < 1 || d < 1 || d > RPF_MAX_D) return RPF_EINVAL;
+  if (t_base < 0 || (int64_t)t_base + p->n_trees > (1 << 20)) return RPF_EINVAL;
   if (p->n_trees < 1 || p->leaf_max < 1 || p->leaf_max > RPF_MAX_LEAF || p->n_try < 1 || p->n_try > RPF_MAX_TRY) return RPF_EINVAL;
   if (p->split_rule < 0 || p->split_rule > 1 || p->form < 0 || p->form > 1 || p->growth < 0 || p->growth > 2)
     return RPF_EINVAL;
@@ -228,6 +234,7 @@ int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* s
   f->n = n;
   f->d = d;
   f->prm = *p;
+  f->t_base = t_base;
   if (f->prm.growth == 0) f->prm.growth = 2;
   // the G-B projection kernel stages nTry x d FP32 directions in shared memory
   if (f->prm.growth == 2 && (size_t)p->n_try * d * 4 + 2048 > 200 * 1024) f->prm.growth = 1;
@@ -259,6 +266,19 @@ int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* s
   }
   *out = f;
   return RPF_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int rpf_build(const float* X, int64_t n, int32_t d, const rpf_params* p, void* stream,
+              rpf_forest** out) {
+  return build_impl(X, n, d, p, 0, stream, out);
+}
+
+int rpf_build_shard(const float* X, int64_t n, int32_t d, const rpf_params* p,
+                    int32_t tree_first, void* stream, rpf_forest** out) {
+  return build_impl(X, n, d, p, tree_first, stream, out);
 }
 
 void rpf_free(rpf_forest* f) { free_forest(f); }
@@ -446,6 +466,66 @@ int rpf_all_knn_trees(rpf_forest* f, int32_t n_trees, int32_t K, int32_t* idx, f
   return RPF_OK;
 }
 
+int rpf_all_knn_keys(rpf_forest* f, int32_t K, int32_t* keys, void* workspace, size_t ws_bytes,
+                     void* stream) {
+  if (!f || !keys || K < 1 || K > RPF_MAX_K) return RPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = f->n;
+  const bool dev_out = rpf_is_device_ptr(keys);
+  const size_t need = (size_t)n * K * 8;
+  void* ws = workspace;
+  size_t wsb = ws_bytes;
+  bool own_ws = false;
+  if (!ws) {
+    wsb = rpf_all_knn_ws(f, K);
+    if (rpf_alloc(&ws, wsb, s)) return RPF_ENOMEM;
+    own_ws = true;
+  }
+  void* kd = keys;
+  if (!dev_out && rpf_alloc(&kd, need, s)) {
+    if (own_ws) rpf_release(ws, s);
+    return RPF_ENOMEM;
+  }
+  int rc = rpf_all_knn_dev(f, f->prm.n_trees, K, nullptr, nullptr, ws, wsb, s, (uint2*)kd);
+  cudaError_t e = cudaSuccess;
+  if (!rc && !dev_out) e = cudaMemcpyAsync(keys, kd, need, cudaMemcpyDefault, s);
+  if (own_ws) rpf_release(ws, s);
+  if (!dev_out) rpf_release(kd, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return rpf_cuda_err(e);
+  return rc;
+}
+
+int rpf_merge_keys(int64_t n, int32_t K, int32_t n_lists, const int32_t* lists, int32_t* idx,
+                   float* dist, void* stream) {
+  if (n < 0 || K < 1 || K > RPF_MAX_K || n_lists < 1) return RPF_EINVAL;
+  if (n == 0) return RPF_OK;
+  if (!lists || !idx || !dist) return RPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t lb = (size_t)n_lists * n * K * 8, ob = (size_t)n * K * 4;
+  const bool ld = rpf_is_device_ptr(lists);
+  const bool od = rpf_is_device_ptr(idx) && rpf_is_device_ptr(dist);
+  auto a256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t bl = ld ? 0 : a256(lb), bo = od ? 0 : 2 * a256(ob);
+  char* w = nullptr;
+  if (bl + bo && rpf_alloc((void**)&w, bl + bo, s)) return RPF_ENOMEM;
+  const int32_t* L = ld ? lists : (const int32_t*)w;
+  int32_t* I = od ? idx : (int32_t*)(w + bl);
+  float* D = od ? dist : (float*)(w + bl + bo / 2);
+  cudaError_t e = cudaSuccess;
+  if (!ld) e = cudaMemcpyAsync((void*)L, lists, lb, cudaMemcpyDefault, s);
+  int rc = RPF_OK;
+  if (e == cudaSuccess) rc = rpf_merge_dev(n, K, n_lists, (const uint2*)L, I, D, s);
+  if (e == cudaSuccess && !rc && !od) {
+    e = cudaMemcpyAsync(idx, I, ob, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dist, D, ob, cudaMemcpyDefault, s);
+  }
+  rpf_release(w, s);
+  if (e == cudaSuccess && !od) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return rpf_cuda_err(e);
+  return rc;
+}
+
 int rpf_query(const rpf_forest* f, const float* Q, int64_t m, int32_t K, int32_t* idx,
               float* dist, void* workspace, size_t ws_bytes, void* stream) {
   if (!f || K < 1 || K > RPF_MAX_K || m < 0) return RPF_EINVAL;
@@ -511,8 +591,8 @@ int rpf_forest_counters(const rpf_forest* f, int64_t* out, int32_t n_out) {
   if (!f || !out || n_out < 0) return RPF_EINVAL;
   unsigned long long fb = 0;
   RPF_CU(cudaMemcpy(&fb, f->d_fallback, sizeof(fb), cudaMemcpyDeviceToHost));
-  const int64_t v[4] = {f->n_exact, (int64_t)fb, f->max_depth, f->tile_region};
-  for (int i = 0; i < n_out && i < 4; ++i) out[i] = v[i];
+  const int64_t v[5] = {f->n_exact, (int64_t)fb, f->max_depth, f->tile_region, f->plain_groups};
+  for (int i = 0; i < n_out && i < 5; ++i) out[i] = v[i];
   return RPF_OK;
 }
 

@@ -1234,7 +1234,9 @@ int rpf_grow_subtrees(rpf_forest* fo, int64_t n_items, const int32_t* it_node,
                       const int32_t* it_tree, const int32_t* it_begin, const int32_t* it_len,
                       const uint64_t* it_key, const int32_t* it_nbase, const int32_t* it_lbase,
                       float* p32, double* p64, unsigned long long* d_exact, int* d_err,
-                      cudaStream_t s);
+                      int32_t* dfr, int* dfr_cnt, int dfr_cap, cudaStream_t s);
+int rpf_split_deferred(rpf_forest* fo, const int32_t* dfr, const int* dfr_cnt, int dfr_cap,
+                       const int32_t* new_id, int* d_err, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 int rpf_grow(rpf_forest* fo, cudaStream_t s) {
@@ -1644,6 +1646,9 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
 
   // ---- phase B: every item's subtree inside one CTA -----------------------
   int64_t nodes_used = n_nodes, leaves_used = n_leaves;
+  int32_t* dfr = nullptr;
+  int* dfr_cnt = nullptr;
+  int dfr_cap = 0;
   if (n_items > 0) {
     std::vector<int32_t> ilen(n_items), nb(n_items), lb(n_items);
     RPF_TRYCU(cudaMemcpyAsync(ilen.data(), it_len, 4 * n_items, cudaMemcpyDeviceToHost, s));
@@ -1663,8 +1668,20 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     RPF_TRY(ensure_leaves(lrun));
     RPF_TRYCU(cudaMemcpyAsync(it_nbase, nb.data(), 4 * n_items, cudaMemcpyHostToDevice, s));
     RPF_TRYCU(cudaMemcpyAsync(it_lbase, lb.data(), 4 * n_items, cudaMemcpyHostToDevice, s));
+    // records of the deferred split points: room for four split nodes per
+    // leaf-bound's worth of phase-B points (at most 64 MB); a subtree that
+    // finds the list full decides its split point in place
+    if (fo->prm.growth != 1 && fo->prm.split_rule == 0) {
+      int64_t pts = 0;
+      for (int64_t i = 0; i < n_items; ++i) pts += ilen[i];
+      dfr_cap = (int)std::min<int64_t>(4 * pts / std::max(L, 1) + 1024,
+                                       (64ll << 20) / (4 * RPF_DEFER_REC));
+      RPF_TRY(talloc((void**)&dfr, 4 * (size_t)RPF_DEFER_REC * dfr_cap));
+      RPF_TRY(talloc((void**)&dfr_cnt, sizeof(int)));
+      RPF_TRYCU(cudaMemsetAsync(dfr_cnt, 0, sizeof(int), s));
+    }
     RPF_TRY(rpf_grow_subtrees(fo, n_items, it_node, it_tree, it_begin, it_len, it_key, it_nbase,
-                              it_lbase, p32, p64, d_exact, d_err, s));
+                              it_lbase, p32, p64, d_exact, d_err, dfr, dfr_cnt, dfr_cap, s));
     nodes_used = nrun;
     leaves_used = lrun;
   }
@@ -1737,6 +1754,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     RPF_LAUNCH("k_node_dirs", s, k_node_dirs<<<nblk((int64_t)total * 32, 128), 128, 0, s>>>(
         total, d, seed, fo->t_base, fo->node_key, fo->node_tree, fo->node_left, fo->node_jstar, fo->node_flag,
         fo->node_dir, fo->node_dir32));
+    RPF_TRY(rpf_split_deferred(fo, dfr, dfr_cnt, dfr_cap, new_id, d_err, s));
 
     // leaves: keep the used slots (len > 0) in slot order
     const int64_t S = leaves_used;
@@ -1770,8 +1788,14 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
   }
   {
     unsigned long long ex = 0;
+    int err_h = 0;  // also covers the deferred split points
     RPF_TRYCU(cudaMemcpyAsync(&ex, d_exact, sizeof(ex), cudaMemcpyDeviceToHost, s));
+    RPF_TRYCU(cudaMemcpyAsync(&err_h, d_err, 4, cudaMemcpyDeviceToHost, s));
     RPF_TRYCU(cudaStreamSynchronize(s));
+    if (err_h) {
+      cleanup();
+      return RPF_EINTERNAL;
+    }
     fo->n_exact = (int64_t)ex;
     fo->max_depth = level;  // phase-A levels
   }

@@ -252,6 +252,9 @@ struct rpf_forest {
 
   int* d_err = nullptr;  // device error word (RPF_ETIMEOUT from bounded waits)
   unsigned long long* d_fallback = nullptr;  // rows the BF16 form rescanned exactly
+  // tree groups of rpf_all_knn calls that asked for the chosen form and ran
+  // the plain one (leaf bound > 256, K > 32, or a row too wide for the tile)
+  int64_t plain_groups = 0;
 
   // staging for host outputs of rpf_all_knn
   void* stage = nullptr;
@@ -291,18 +294,30 @@ void rpf_release(void* p, cudaStream_t s);
 
 // growth (rpf_grow.cu)
 int rpf_grow(rpf_forest* f, cudaStream_t s);
-// leaf tiles + merge + query (rpf_knn.cu)
-int rpf_build_tiles(rpf_forest* f, cudaStream_t s);
-// chosen-form leaf tiles (rpf_leaf_tc.cu)
-int rpf_build_packs(rpf_forest* f, cudaStream_t s);
+// leaf tiles + merge + query (rpf_knn.cu); R_force > 0 sets the tile region
+int rpf_build_tiles(rpf_forest* f, cudaStream_t s, int R_force = 0);
+int rpf_region_cap(int L);
+// plain-form leaf tiles of trees [t0, t0 + g) into cand
+int rpf_leaf_plain(const rpf_forest* f, int t0, int g, int K, uint2* cand, cudaStream_t s);
+// chosen-form leaf tiles (rpf_leaf_tc.cu); rows_force > 0 sets the tile rows
+int rpf_build_packs(rpf_forest* f, cudaStream_t s, int rows_force = 0);
+// build-time tile choices the autotuner kept for (d, leaf bound), 0 if none
+int rpf_tuned_region(int d, int L);
+int rpf_tuned_rows(int d, int L);
 bool rpf_tc_supported(const rpf_forest* f, int K);
 int rpf_leaf_tc(const rpf_forest* f, int t0, int g, int K, uint2* cand, cudaStream_t s);
-// times the chosen-form launch configurations on f's tiles, keeps the fastest
-// for its (d, tile rows, K) for the rest of the process; chosen = {chunk, CTAs}
-int rpf_tc_autotune(const rpf_forest* f, int K, cudaStream_t s, int32_t* chosen);
+// times the leaf-tile configurations on f's tiles (plain: region; chosen:
+// rows, Gram chunk, CTAs per SM), keeps the fastest for the rest of the
+// process and applies the tile shape to f; chosen = {chunk, CTAs, rows, R}
+int rpf_tc_autotune(rpf_forest* f, int K, cudaStream_t s, int32_t* chosen);
 // all-kNN over the first T trees (T <= n_trees: nested ensembles)
+// keys != nullptr: the final lists go there as (d32 bits, index) pairs
+// instead of (idx, dist)
 int rpf_all_knn_dev(rpf_forest* f, int T, int K, int32_t* idx, float* dist, void* ws,
-                    size_t ws_bytes, cudaStream_t s);
+                    size_t ws_bytes, cudaStream_t s, uint2* keys = nullptr);
+// merge of G sorted (d32 bits, index) lists per point into the final lists
+int rpf_merge_dev(int64_t n, int K, int G, const uint2* lists, int32_t* idx, float* dist,
+                  cudaStream_t s);
 int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t* idx, float* dist,
                   void* ws, size_t ws_bytes, cudaStream_t s);
 int rpf_brute_dev(const float* X, int64_t n, int d, const float* Q, int64_t m,

@@ -277,10 +277,12 @@ __device__ __forceinline__ void rpf_row_exact(const float* xs, int dp, int d4, i
 }
 
 // Merge G per-tree lists (sorted, padded with (inf, -1)) into the running list
-// of each point.  first: no running list yet; last: write the final outputs.
+// of each point, read from run_in and written to run_out (each thread reads
+// its point's list before writing, so the two may coincide).  first: no
+// running list yet; last: write the final outputs instead of run_out.
 template <int KMAX>
-__global__ void k_merge(int64_t n, int K, int G, const uint2* cand, uint2* run, bool first,
-                        bool last, int32_t* idx, float* dist) {
+__global__ void k_merge(int64_t n, int K, int G, const uint2* cand, const uint2* run_in,
+                        uint2* run_out, bool first, bool last, int32_t* idx, float* dist) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   TopK<KMAX> tk;
@@ -289,7 +291,7 @@ __global__ void k_merge(int64_t n, int K, int G, const uint2* cand, uint2* run, 
 #pragma unroll
     for (int q = 0; q < KMAX; ++q)
       if (q < K) {
-        const uint2 e = run[i * K + q];
+        const uint2 e = run_in[i * K + q];
         tk.kd[q] = __uint_as_float(e.x);
         tk.ki[q] = (int)e.y;
       }
@@ -313,7 +315,7 @@ __global__ void k_merge(int64_t n, int K, int G, const uint2* cand, uint2* run, 
         dist[i * K + q] = tk.ki[q] < 0 ? INFINITY : __fsqrt_rn(tk.kd[q]);
       }
   } else {
-    tk.store(K, run + i * K);
+    tk.store(K, run_out + i * K);
   }
 }
 
@@ -628,9 +630,11 @@ void launch_leaf(const rpf_forest* f, int64_t tb, int64_t nt, int K, int t0, uin
 }
 
 template <int KMAX>
-void launch_merge(int64_t n, int K, int G, const uint2* cand, uint2* run, bool first, bool last,
-                  int32_t* idx, float* dist, cudaStream_t s) {
-  RPF_LAUNCH("k_merge", s, k_merge<KMAX><<<nblk(n, 128), 128, 0, s>>>(n, K, G, cand, run, first, last, idx, dist));
+void launch_merge(int64_t n, int K, int G, const uint2* cand, const uint2* run_in,
+                  uint2* run_out, bool first, bool last, int32_t* idx, float* dist,
+                  cudaStream_t s) {
+  RPF_LAUNCH("k_merge", s, k_merge<KMAX><<<nblk(n, 128), 128, 0, s>>>(
+      n, K, G, cand, run_in, run_out, first, last, idx, dist));
 }
 
 template <int KMAX>
@@ -678,14 +682,28 @@ __global__ void k_tile_fill(int64_t nl, const int32_t* leaf_tree, const int32_t*
 // largest multiple of 32 up to the leaf bound for which the tile's rows fit in
 // shared memory.
 // ---------------------------------------------------------------------------
-int rpf_build_tiles(rpf_forest* f, cudaStream_t s) {
+// The largest valid tile region for leaf bound L: a multiple of 32, at most
+// 256 (leaves starting in one tile) and with R + L - 1 <= 1024 rows.
+int rpf_region_cap(int L) {
+  const int R = std::min(256, 1024 - L + 1 > 0 ? std::max(32, ((1024 - L + 1) / 32) * 32) : 32);
+  return std::max(32, R);
+}
+
+int rpf_build_tiles(rpf_forest* f, cudaStream_t s, int R_force) {
   const int T = f->prm.n_trees, L = f->prm.leaf_max;
   const int dp = ((f->d + 3) & ~3) + 4;
-  // prefer tiles small enough for four CTAs per SM (<= 56 KB of rows)
+  // prefer tiles small enough for four CTAs per SM (<= 56 KB of rows),
+  // unless the autotuner chose a region for this (d, L) or the caller forces one
   int R = std::max(32, ((L + 31) / 32) * 32);
   while (R > 32 && (size_t)(R + L - 1) * dp * 4 > 56 * 1024) R -= 32;
-  R = std::min(R, 1024 - L + 1 > 0 ? std::max(32, ((1024 - L + 1) / 32) * 32) : 32);
-  R = std::min(R, 256);  // at most 256 leaves start in one tile
+  const int tuned = R_force > 0 ? R_force : rpf_tuned_region(f->d, L);
+  if (tuned > 0) R = tuned;
+  R = std::min(std::max(32, R & ~31), rpf_region_cap(L));
+  // a rebuild replaces the previous tables (stream-ordered)
+  rpf_release(f->tile_cnt, s);
+  rpf_release(f->tile_off, s);
+  rpf_release(f->tile_leaf, s);
+  f->tile_cnt = f->tile_off = f->tile_leaf = nullptr;
   const int64_t ntile = (f->n + R - 1) / R;
   const int64_t N = (int64_t)T * ntile;
   const int64_t nl = f->n_leaves;
@@ -726,8 +744,22 @@ size_t rpf_all_knn_ws(const rpf_forest* f, int K) {
   return align256((size_t)T * n * K * 8) + align256((size_t)n * K * 8);
 }
 
+int rpf_leaf_plain(const rpf_forest* f, int t0, int g, int K, uint2* cand, cudaStream_t s) {
+  const int64_t tb = (int64_t)t0 * f->tiles_per_tree, nt = (int64_t)g * f->tiles_per_tree;
+  if (nt > 0) RPF_KDISPATCH(K, launch_leaf, f, tb, nt, K, t0, cand, f->d_err, s);
+  RPF_CU(cudaGetLastError());
+  return RPF_OK;
+}
+
+int rpf_merge_dev(int64_t n, int K, int G, const uint2* lists, int32_t* idx, float* dist,
+                  cudaStream_t s) {
+  RPF_KDISPATCH(K, launch_merge, n, K, G, lists, nullptr, nullptr, true, true, idx, dist, s);
+  RPF_CU(cudaGetLastError());
+  return RPF_OK;
+}
+
 int rpf_all_knn_dev(rpf_forest* f, int T, int K, int32_t* idx, float* dist, void* ws,
-                    size_t ws_bytes, cudaStream_t s) {
+                    size_t ws_bytes, cudaStream_t s, uint2* keys) {
   const int64_t n = f->n;
   const size_t run_b = align256((size_t)n * K * 8);
   const size_t per_tree = (size_t)n * K * 8;
@@ -745,11 +777,15 @@ int rpf_all_knn_dev(rpf_forest* f, int T, int K, int32_t* idx, float* dist, void
         const int rc = rpf_leaf_tc(f, t0, g, K, cand, s);
         if (rc) return rc;
       } else {
+        if (f->prm.form == 1) ++f->plain_groups;  // chosen form not available here
         RPF_KDISPATCH(K, launch_leaf, f, tb, nt, K, t0, cand, f->d_err, s);
       }
     }
     const bool first = t0 == 0, last = t0 + g >= T;
-    RPF_KDISPATCH(K, launch_merge, n, K, g, cand, run, first, last, idx, dist, s);
+    // with keys, the last merge writes the running list into the caller's keys
+    uint2* out_run = (last && keys) ? keys : run;
+    RPF_KDISPATCH(K, launch_merge, n, K, g, cand, run, out_run, first, last && !keys, idx, dist,
+                  s);
   }
   RPF_CU(cudaGetLastError());
   // a bounded device wait that gave up is reported here
@@ -802,7 +838,7 @@ int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t
     RPF_LAUNCH("k_qmerge_cta", s, k_qmerge_cta<<<(unsigned)m, QM_T, (size_t)N * 8, s>>>(
         m, K, T, N, cand, idx, dist));
   } else {
-    RPF_KDISPATCH(K, launch_merge, m, K, T, cand, nullptr, true, true, idx, dist, s);
+    RPF_KDISPATCH(K, launch_merge, m, K, T, cand, nullptr, nullptr, true, true, idx, dist, s);
   }
   RPF_CU(cudaGetLastError());
   return RPF_OK;

@@ -8,7 +8,8 @@
 // tiles of at most 128 rows (a leaf never straddles two tiles); k_leaf_tc is a
 // persistent kernel whose CTAs take tiles in turn.  Per tile (128 threads,
 // thread r = row r):
-//   1. rows are staged in shared memory by bulk copies (TMA engine, mbarrier);
+//   1. rows are staged in shared memory by bulk copies (TMA engine, mbarrier)
+//      when a row is a 16-byte multiple (d % 4 == 0), else by warp loads;
 //      leaf boundaries come from a per-tree bitmask of leaf starts.
 //   2. Leaves of at most TC_SLOTS + 1 points ("small") need no arithmetic
 //      shortcut: every row offers all of its leaf to the exact re-rank.
@@ -293,16 +294,27 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
     }
     const uint32_t bal = __ballot_sync(RPF_FULL, start);
     if (lane == 0) wmask[warp] = bal;
+    // rows of 16-byte multiples go by bulk copy (TMA engine); other rows are
+    // not 16-byte aligned in X, so the warps load them (the barrier's phase
+    // then completes on thread 0's arrival alone)
+    const bool bulk = (d & 3) == 0;
     if (tid == 0) {
       nbig = 0;
-      rpf_mbar_arrive_expect_tx(&bar_tma, (uint32_t)rows * (uint32_t)d * 4u);
+      rpf_mbar_arrive_expect_tx(&bar_tma, bulk ? (uint32_t)rows * (uint32_t)d * 4u : 0u);
     }
     if (tid < TC_MAX_BIG) nmax_bits[tid] = 0u;
     __syncthreads();
-    for (int q = tid; q < rows; q += ROWS)
-      rpf_bulk_g2s(xs + q * dp, X + (int64_t)prow_s[q] * d, (uint32_t)d * 4u, &bar_tma);
-    tma_pending = true;
-    for (int k = d; k < dp; ++k) xs[r * dp + k] = 0.0f;
+    if (bulk) {
+      for (int q = tid; q < rows; q += ROWS)
+        rpf_bulk_g2s(xs + q * dp, X + (int64_t)prow_s[q] * d, (uint32_t)d * 4u, &bar_tma);
+      for (int k = d; k < dp; ++k) xs[r * dp + k] = 0.0f;
+    } else {
+      for (int q = warp; q < rows; q += ROWS / 32) {
+        const float* src = X + (int64_t)prow_s[q] * d;
+        for (int k = lane; k < dp; k += 32) xs[q * dp + k] = k < d ? src[k] : 0.0f;
+      }
+    }
+    tma_pending = bulk;
     // leaf [lb, le) of row r (tile-relative)
     int lb = 0, le = rows;
     if (r < rows) {
@@ -583,6 +595,12 @@ struct TcConf {
 };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, TcConf> g_tune;
+// build-time tile shapes per (d, leaf bound): chosen-form tile rows and the
+// plain form's tile region (0: the heuristic)
+struct ShapeConf {
+  int rows = 0, region = 0;
+};
+std::map<std::pair<int, int>, ShapeConf> g_shape;
 
 template <int KK, int ROWS>
 int launch_tc(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint2* cand,
@@ -653,19 +671,35 @@ int launch_tc_k(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, ui
 
 }  // namespace
 
-bool rpf_tc_supported(const rpf_forest* f, int K) {
-  const int rows = f->prm.leaf_max <= 128 ? 128 : 256;
-  return f->pk_tiles != nullptr && f->prm.leaf_max <= 256 && K <= 32 && (f->d % 4) == 0 &&
-         tc_chunk(f->d, rows) > 0;
+int rpf_tuned_region(int d, int L) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_shape.find(std::make_pair(d, L));
+  return it == g_shape.end() ? 0 : it->second.region;
 }
 
-int rpf_build_packs(rpf_forest* f, cudaStream_t s) {
+int rpf_tuned_rows(int d, int L) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_shape.find(std::make_pair(d, L));
+  return it == g_shape.end() ? 0 : it->second.rows;
+}
+
+bool rpf_tc_supported(const rpf_forest* f, int K) {
+  return f->pk_tiles != nullptr && f->prm.leaf_max <= 256 && K <= 32 &&
+         tc_chunk(f->d, f->pk_rows) > 0;
+}
+
+int rpf_build_packs(rpf_forest* f, cudaStream_t s, int rows_force) {
   const int T = f->prm.n_trees;
   const int64_t n = f->n, nl = f->n_leaves;
   const int64_t nwords = (n + 31) >> 5, nseg = (n + TC_SEG - 1) / TC_SEG;
   const int64_t G = (int64_t)T * nseg;
   int2* slot = nullptr;
   int32_t *cnt = nullptr, *off = nullptr, *blk = nullptr, *tot = nullptr;
+  // a rebuild replaces the previous tables (stream-ordered)
+  rpf_release(f->pk_bits, s);
+  rpf_release(f->pk_tiles, s);
+  f->pk_bits = nullptr;
+  f->pk_tiles = nullptr;
   if (rpf_alloc((void**)&f->pk_bits, 4 * (size_t)(T * nwords), s) ||
       rpf_alloc((void**)&slot, 8 * (size_t)G * TC_SEG_TILES, s) ||
       rpf_alloc((void**)&cnt, 4 * (size_t)G, s) || rpf_alloc((void**)&off, 4 * (size_t)G, s) ||
@@ -681,7 +715,12 @@ int rpf_build_packs(rpf_forest* f, cudaStream_t s) {
   RPF_CU(cudaMemsetAsync(f->pk_bits, 0, 4 * (size_t)(T * nwords), s));
   RPF_LAUNCH("k_leaf_bits", s, k_leaf_bits<<<nblk(nl, 256), 256, 0, s>>>(
       nl, f->leaf_tree, f->leaf_begin, nwords, f->pk_bits));
-  f->pk_rows = f->prm.leaf_max <= 128 ? 128 : 256;
+  // tile rows: 128 for leaf bounds up to 128, else 256; leaves of up to 128
+  // points may also go in 256-row tiles when the autotuner found them faster
+  int rows = f->prm.leaf_max <= 128 ? 128 : 256;
+  const int want = rows_force > 0 ? rows_force : rpf_tuned_rows(f->d, f->prm.leaf_max);
+  if (want == 256) rows = 256;
+  f->pk_rows = rows;
   RPF_LAUNCH("k_pack_tiles", s, k_pack_tiles<<<nblk(G, 128), 128, 0, s>>>(
       T, n, nseg, nwords, f->pk_bits, f->pk_rows, slot, cnt));
   const int32_t* cn = cnt;
@@ -731,51 +770,109 @@ int rpf_leaf_tc(const rpf_forest* f, int t0, int g, int K, uint2* cand, cudaStre
   return launch_tc_k(f, f->pk_tree_off[t0], f->pk_tree_off[t0 + g], K, t0, cand, s);
 }
 
-int rpf_tc_autotune(const rpf_forest* f, int K, cudaStream_t s, int32_t* chosen) {
-  if (chosen) chosen[0] = chosen[1] = 0;
-  if (!rpf_tc_supported(f, K)) return RPF_OK;  // the plain form runs: nothing to tune
-  const int d = f->d, dp = ((d + 3) & ~3) + 4, d16 = (d + 15) & ~15, rows = f->pk_rows;
+namespace {
+// best of three timed runs (the first warms caches) of fn on stream s, ms
+template <typename Fn>
+int time_best(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, Fn fn, float* best) {
+  *best = INFINITY;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, s);
+    const int rc = fn();
+    cudaEventRecord(e1, s);
+    if (rc) return rc;
+    if (cudaEventSynchronize(e1) != cudaSuccess) return RPF_ECUDA;
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (rep > 0) *best = std::min(*best, t);
+  }
+  return RPF_OK;
+}
+}  // namespace
+
+// Autotuner of the leaf tiles, timed on the forest's own tiles (its first
+// trees).  Plain form: the tile region R (multiples of 32 up to the cap).
+// Chosen form: tile rows (128 or 256 where the leaf bound allows both), Gram
+// coordinates per chunk, CTAs per SM.  Every candidate gives the same lists.
+// The tile shape is kept per (d, leaf bound) for later builds and applied to
+// this forest; the launch choice per (d, tile rows, K bucket).
+int rpf_tc_autotune(rpf_forest* f, int K, cudaStream_t s, int32_t* chosen) {
+  if (chosen) chosen[0] = chosen[1] = chosen[2] = chosen[3] = 0;
+  const int d = f->d, L = f->prm.leaf_max;
   const int g = std::min(f->prm.n_trees, 4);  // the tiles of the first trees
   uint2* cand = nullptr;
   if (rpf_alloc((void**)&cand, (size_t)g * f->n * K * 8, s)) return RPF_ENOMEM;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  TcConf best;
-  float best_ms = INFINITY;
   int rc = RPF_OK;
-  const int max_occ = rows == 128 ? 4 : 1;
-  for (int kc = 16; kc <= std::min(d16, 128) && !rc; kc += 16) {
-    if (tc_smem(d, dp, rows, kc) > 220 * 1024) continue;
-    for (int occ = 1; occ <= max_occ && !rc; ++occ) {
-      const TcConf c{kc, occ};
+  if (f->prm.form == 0) {
+    int best_r = 0;
+    float best_ms = INFINITY;
+    for (int R = 32; R <= rpf_region_cap(L) && !rc; R += 32) {
+      rc = rpf_build_tiles(f, s, R);
       float ms = INFINITY;
-      for (int rep = 0; rep < 3 && !rc; ++rep) {  // the first run warms caches
-        cudaEventRecord(e0, s);
-        rc = launch_tc_k(f, f->pk_tree_off[0], f->pk_tree_off[g], K, 0, cand, s, &c);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) rc = RPF_ECUDA;
-        float t = 0.0f;
-        cudaEventElapsedTime(&t, e0, e1);
-        if (rep > 0) ms = std::min(ms, t);
-      }
+      if (!rc) rc = time_best(s, e0, e1, [&] { return rpf_leaf_plain(f, 0, g, K, cand, s); }, &ms);
       if (!rc && ms < best_ms) {
         best_ms = ms;
-        best = c;
+        best_r = R;
       }
+    }
+    if (!rc) {
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_shape[std::make_pair(d, L)].region = best_r;
+      }
+      rc = rpf_build_tiles(f, s, best_r);
+    }
+    if (chosen && !rc) chosen[3] = best_r;
+  } else if (rpf_tc_supported(f, K)) {
+    const int dp = ((d + 3) & ~3) + 4, d16 = (d + 15) & ~15;
+    TcConf best;
+    int best_rows = f->pk_rows;
+    float best_ms = INFINITY;
+    const int rows_opts[2] = {128, 256};
+    for (int ri = 0; ri < 2 && !rc; ++ri) {
+      const int rows = rows_opts[ri];
+      if ((rows == 128 && L > 128) || tc_chunk(d, rows) == 0) continue;
+      rc = rpf_build_packs(f, s, rows);
+      const int max_occ = rows == 128 ? 4 : 1;
+      for (int kc = 16; kc <= std::min(d16, 128) && !rc; kc += 16) {
+        if (tc_smem(d, dp, rows, kc) > 220 * 1024) continue;
+        for (int occ = 1; occ <= max_occ && !rc; ++occ) {
+          const TcConf c{kc, occ};
+          float ms = INFINITY;
+          rc = time_best(s, e0, e1, [&] {
+            return launch_tc_k(f, f->pk_tree_off[0], f->pk_tree_off[g], K, 0, cand, s, &c);
+          }, &ms);
+          if (!rc && ms < best_ms) {
+            best_ms = ms;
+            best = c;
+            best_rows = rows;
+          }
+        }
+      }
+    }
+    if (!rc) {
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[std::make_tuple(d, best_rows, kk_of(K))] = best;
+        g_shape[std::make_pair(d, L)].rows = best_rows;
+      }
+      rc = rpf_build_packs(f, s, best_rows);
+    }
+    if (chosen && !rc) {
+      chosen[0] = best.kc;
+      chosen[1] = best.occ;
+      chosen[2] = best_rows;
+      chosen[3] = f->tile_region;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   rpf_release(cand, s);
-  if (rc) return rc;
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[std::make_tuple(d, rows, kk_of(K))] = best;
+  if (!rc) {
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = rpf_cuda_err(e);
   }
-  if (chosen) {
-    chosen[0] = best.kc;
-    chosen[1] = best.occ;
-  }
-  return RPF_OK;
+  return rc;
 }

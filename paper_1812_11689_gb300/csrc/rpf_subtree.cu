@@ -37,6 +37,7 @@ constexpr int kB = 128;  // 4 warps; 4 CTAs per SM hide each other's serial sect
 constexpr int kSubN = RPF_CHUNK;
 constexpr int kStack = 24;
 constexpr int kBandSel = 256;  // median rule: bands up to this size are selected by counting
+constexpr int kDefCand = RPF_DEFER_CAND;  // candidates per extreme of a deferred split point
 // the projection's row tiles (kTStages per warp, 32 rows of kTDC + 4 floats)
 // live in sT and sSide, which are contiguous and idle during the projection,
 // and in sTx, which follows them
@@ -62,6 +63,11 @@ struct SubState {
   uint32_t mid, mfk;        // ... and the FP32 key of the band's centre
   int mrank;
   float mlo, mhi;           // band of q' outside which the side is certain
+  // deferred split point: certified interval thresholds of the sides and the
+  // candidates of the exact minimum / maximum
+  int defer, nmin, nmax;
+  float dtl, dtr;
+  int cmin[kDefCand], cmax[kDefCand];
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -125,7 +131,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     uint64_t* node_key, int32_t* node_tree, int32_t* node_begin, int32_t* node_len,
     int32_t* node_left, int32_t* node_right, int32_t* node_jstar, int32_t* node_flag,
     double* node_c, int32_t* leaf_tree, int32_t* leaf_begin, int32_t* leaf_len,
-    unsigned long long* d_exact, int* d_err) {
+    unsigned long long* d_exact, int* d_err, int32_t* dfr, int* dfr_cnt, int dfr_cap) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const SubLayout lay = sub_layout(d, ntry, TG);
   int32_t* sP = reinterpret_cast<int32_t*>(smraw + lay.sP);
@@ -192,28 +198,29 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     const int nb = S.nb, m = S.m, id = S.id;
     const uint64_t key = S.key;
 
-    // 1. candidate directions, all in FP32 (r32), widened copy in r64
-    for (int idx = tid; idx < ntry * npairs; idx += kB) {
-      const int j = idx / npairs, i = idx - j * npairs;
-      float g0, g1;
-      rpf_gauss_pair(seed, (uint64_t)(t + t_base), key, (uint64_t)j, i, &g0, &g1);
-      r32[j * d + 2 * i] = g0;
-      if (2 * i + 1 < d) r32[j * d + 2 * i + 1] = g1;
+    // 1. candidate directions, all in FP32 (r32), widened copy in r64: one
+    // warp per try draws the Box-Muller pairs, its lane 0 forms the
+    // sequential FP32 norm (the shuffle of 1/|g| orders the scaling after
+    // it), so only one block barrier is needed; 2. with it, the centre o =
+    // the node's first member
+    for (int j = warp; j < ntry; j += kB / 32) {
+      float* g = r32 + j * d;
+      for (int i = lane; i < npairs; i += 32) {
+        float g0, g1;
+        rpf_gauss_pair(seed, (uint64_t)(t + t_base), key, (uint64_t)j, i, &g0, &g1);
+        g[2 * i] = g0;
+        if (2 * i + 1 < d) g[2 * i + 1] = g1;
+      }
+      __syncwarp();
+      float inv = 0.0f;
+      if (lane == 0) inv = rpf_inv_norm32(g, d);
+      inv = __shfl_sync(RPF_FULL, inv, 0);
+      for (int k = lane; k < d; k += 32) {
+        const float v = inv == 0.0f ? (k == 0 ? 1.0f : 0.0f) : __fmul_rn(g[k], inv);
+        g[k] = v;
+        r64[j * d + k] = (double)v;
+      }
     }
-    __syncthreads();
-    float* sinv32 = reinterpret_cast<float*>(sinv);
-    for (int j = tid; j < ntry; j += kB) sinv32[j] = rpf_inv_norm32(r32 + j * d, d);
-    __syncthreads();
-    for (int idx = tid; idx < ntry * d; idx += kB) {
-      const int j = idx / d, k = idx - j * d;
-      const float inv = sinv32[j];
-      const float v = inv == 0.0f ? (k == 0 ? 1.0f : 0.0f) : __fmul_rn(r32[idx], inv);
-      r32[idx] = v;
-      r64[idx] = (double)v;
-    }
-    __syncthreads();
-
-    // 2. centre o = the node's first member
     const int og = sP[nb];
     const float* xo = X + (int64_t)og * d;
     for (int k = tid; k < d; k += kB) so[k] = xo[k];
@@ -305,16 +312,93 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
                            : (w < 0 ? rpf_contenders(ntry, slo, shi) : 0ull);
       S.js = w;
       S.rad = radmax;
+      S.defer = 0;
+      S.nmin = 0;
+      S.nmax = 0;
       if (w >= 0) {
         const float r2 = __fmul_ru(2.0f, radmax);
         S.wlo = __fadd_ru(smn[w], r2);
         S.whi = __fsub_rd(smx[w], r2);
         S.akey = rpf_dkey(INFINITY);
         S.bkey = rpf_dkey(-INFINITY);
+        if (!median && dfr_cap > 0) {
+          // With beta = p64(o, r_w) and R the largest radius, every p64 lies
+          // within R of beta + q', so the exact extremes a, b lie within R of
+          // beta + min / max q', and c = fma(u, b - a, a) (attempt 0) within
+          // R + 2^-52 (|beta| + |min| + |max| + 2R) of beta + mid, mid =
+          // min + u (max - min) (computed here within 2^-52 (|min| + |max|)).
+          // So with e = 2R + 2^-48 mag, q' < mid - e puts p64 < c, q' >=
+          // mid + e puts p64 >= c, and mid - e > min, mid + e < max make
+          // attempt 0 accepted (a < c <= b).  |beta| <= |o| |r| <= 1.01 on.
+          const double mn = (double)smn[w], mx = (double)smx[w], R = (double)radmax;
+          const double u0 =
+              rpf_u53(rpf_word(seed, RPF_TAG_SPLIT, (uint64_t)(t + t_base), key, 0, 0));
+          const double mid = __fma_rn(u0, __dsub_rn(mx, mn), mn);
+          const double mag = __dadd_ru(__dadd_ru(__dmul_ru(1.01, (double)on), fabs(mn)),
+                                       __dadd_ru(fabs(mx), R));
+          const double e = __fma_ru(0x1p-48, mag, 2.0 * R);
+          const double lo = __dsub_rd(mid, e), hi = __dadd_ru(mid, e);
+          if (lo > mn && hi < mx) {
+            S.defer = 1;
+            S.dtl = __double2float_rd(lo);
+            S.dtr = __double2float_ru(hi);
+          }
+        }
       }
     }
     __syncthreads();
 
+    // 4d. deferred split point (uniform rule, certified choice): the sides
+    // follow from the interval of c alone when no point lies inside it; the
+    // exact extremes -- and c -- are then computed after growth from the
+    // few candidates recorded here (k_split_deferred), off this CTA's
+    // critical path.  Otherwise the node takes the exact path below.
+    if (S.defer) {
+      const int w = S.js;
+      const float tl = S.dtl, tr = S.dtr, lo = S.wlo, hi = S.whi;
+      const float* p = p32 + (int64_t)w * Tn + pbase + nb;
+      int und = 0;
+      for (int i = tid; i < m; i += kB) {
+        const float v = p[i];
+        sSide[i] = (uint8_t)(v < tl ? 1 : 0);
+        und |= (v >= tl && v < tr) ? 1 : 0;
+        if (v <= lo) {
+          const int k = atomicAdd(&S.nmin, 1);
+          if (k < kDefCand) S.cmin[k] = sP[nb + i];
+        }
+        if (v >= hi) {
+          const int k = atomicAdd(&S.nmax, 1);
+          if (k < kDefCand) S.cmax[k] = sP[nb + i];
+        }
+      }
+      if (__syncthreads_or(und)) {
+        if (tid == 0) S.defer = 0;
+      } else if (tid == 0) {
+        int ok = S.nmin <= kDefCand && S.nmax <= kDefCand;
+        int slot = -1;
+        if (ok) {
+          slot = atomicAdd(dfr_cnt, 1);
+          ok = slot < dfr_cap;
+        }
+        if (ok) {
+          int32_t* r = dfr + (int64_t)slot * RPF_DEFER_REC;
+          r[0] = id;
+          r[1] = S.nmin | (S.nmax << 8);
+          for (int k = 0; k < kDefCand; ++k) {
+            r[2 + k] = k < S.nmin ? S.cmin[k] : -1;
+            r[2 + kDefCand + k] = k < S.nmax ? S.cmax[k] : -1;
+          }
+          node_jstar[id] = w;
+          node_flag[id] = 0;
+          node_c[id] = NAN;  // k_split_deferred writes c
+        }
+        S.defer = ok;
+        S.flag = 0;
+      }
+      __syncthreads();
+    }
+
+    if (!S.defer) {
     if (S.exact) {
       // canonical FP64 projections and statistics
       const unsigned long long mask = S.cmask;
@@ -595,6 +679,9 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
         }
       }
       __syncthreads();
+    }
+    }  // !S.defer
+    {
       // stable partition from one block-wide scan: thread t takes the run
       // [t per, (t + 1) per) of positions (per odd, so the runs' shared-
       // memory reads fall in distinct banks); E = lefts before a position
@@ -699,7 +786,50 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
   if (tid == 0 && S.err) atomicExch(d_err, 1);
 }
 
+// The deferred split points, after growth (node tables compacted, chosen
+// directions regenerated): one thread per record evaluates the canonical
+// FP64 projections of its candidates in turn (an FP64 warp instruction costs
+// the same whatever its active lanes, so all 32 lanes carry a record), takes
+// the exact minimum a and maximum b, and forms c = fma(u, b - a, a) of
+// attempt 0, which the certified interval already showed to be accepted
+// (checked again here: a failure is an internal error).
+__global__ void __launch_bounds__(128) k_split_deferred(
+    const int32_t* dfr, const int* dfr_cnt, int dfr_cap, const int32_t* new_id,
+    const uint64_t* node_key, const int32_t* node_tree, const double* node_dir,
+    const float* __restrict__ X, int d, uint64_t seed, int t_base, double* node_c, int* d_err) {
+  const int64_t rec = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (rec >= min(*dfr_cnt, dfr_cap)) return;
+  const int32_t* r = dfr + rec * RPF_DEFER_REC;
+  const int nid = new_id[r[0]];
+  const int nmin = r[1] & 255, nmax = (r[1] >> 8) & 255;
+  const double* dir = node_dir + (int64_t)nid * d;
+  unsigned long long ak = rpf_dkey(INFINITY), bk = rpf_dkey(-INFINITY);
+  for (int c = 0; c < nmin + nmax; ++c) {
+    const int pt = c < nmin ? r[2 + c] : r[2 + kDefCand + (c - nmin)];
+    const unsigned long long k = rpf_dkey(rpf_p64(X + (int64_t)pt * d, dir, d));
+    if (c < nmin) ak = min(ak, k);
+    else bk = max(bk, k);
+  }
+  const double a = rpf_dkey_inv(ak), b = rpf_dkey_inv(bk);
+  const uint64_t t = (uint64_t)(node_tree[nid] + t_base);
+  const double u = rpf_u53(rpf_word(seed, RPF_TAG_SPLIT, t, node_key[nid], 0, 0));
+  const double c = __fma_rn(u, __dsub_rn(b, a), a);
+  if (!(c > a && c <= b) || nmin < 1 || nmax < 1) atomicExch(d_err, 1);
+  node_c[nid] = c;
+}
+
 }  // namespace
+
+int rpf_split_deferred(rpf_forest* fo, const int32_t* dfr, const int* dfr_cnt, int dfr_cap,
+                       const int32_t* new_id, int* d_err, cudaStream_t s) {
+  if (dfr_cap <= 0) return RPF_OK;
+  RPF_LAUNCH("k_split_deferred", s,
+             k_split_deferred<<<(unsigned)(((int64_t)dfr_cap + 127) / 128), 128, 0, s>>>(
+                 dfr, dfr_cnt, dfr_cap, new_id, fo->node_key, fo->node_tree, fo->node_dir, fo->X,
+                 fo->d, fo->prm.seed, fo->t_base, fo->node_c, d_err));
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RPF_OK : rpf_cuda_err(e);
+}
 
 bool rpf_subtree_fits(int d, int ntry) {
   return sub_layout(d, ntry, 8).total <= 200 * 1024;
@@ -709,7 +839,7 @@ int rpf_grow_subtrees(rpf_forest* fo, int64_t n_items, const int32_t* it_node,
                       const int32_t* it_tree, const int32_t* it_begin, const int32_t* it_len,
                       const uint64_t* it_key, const int32_t* it_nbase, const int32_t* it_lbase,
                       float* p32, double* p64, unsigned long long* d_exact, int* d_err,
-                      cudaStream_t s) {
+                      int32_t* dfr, int* dfr_cnt, int dfr_cap, cudaStream_t s) {
   const int d = fo->d, ntry = fo->prm.n_try, L = fo->prm.leaf_max;
   const int64_t n = fo->n, Tn = n * fo->prm.n_trees;
   const int exact_only = fo->prm.growth == 1 ? 1 : 0;
@@ -726,7 +856,8 @@ int rpf_grow_subtrees(rpf_forest* fo, int64_t n_items, const int32_t* it_node,
         fo->node_key,                                                                             \
         fo->node_tree,                                                                            \
         fo->node_begin, fo->node_len, fo->node_left, fo->node_right, fo->node_jstar,              \
-        fo->node_flag, fo->node_c, fo->leaf_tree, fo->leaf_begin, fo->leaf_len, d_exact, d_err)); \
+        fo->node_flag, fo->node_c, fo->leaf_tree, fo->leaf_begin, fo->leaf_len, d_exact, d_err,   \
+        dfr, dfr_cnt, dfr_cap));                                                                  \
   } while (0)
   switch (TG) {
     case 1: RPF_SUB(1); break;

@@ -91,15 +91,23 @@ class Forest:
 
     def __init__(self, X, n_trees: int = 10, leaf_max: int = 50, n_try: int = 5,
                  form: int = FORM_PLAIN, growth: int = GROWTH_DEFAULT, seed: int = 0,
-                 stream=None, split_rule: int = SPLIT_UNIFORM):
+                 stream=None, split_rule: int = SPLIT_UNIFORM, tree_first: int = 0):
+        """tree_first > 0 grows trees tree_first .. tree_first + n_trees - 1
+        of the ensemble (rpf_build_shard)."""
         X = _as_points(X)
         self.n, self.d = int(X.shape[0]), int(X.shape[1])
         self.device = X.device if isinstance(X, torch.Tensor) and X.is_cuda else \
             torch.device("cuda", torch.cuda.current_device())
         self.params = rpf_params(n_trees, leaf_max, n_try, split_rule, form, growth, seed)
         h = ctypes.c_void_p()
-        check(_lib.lib().rpf_build(_ptr(X), self.n, self.d, ctypes.byref(self.params),
-                                   _stream_handle(stream), ctypes.byref(h)), "rpf_build")
+        self.tree_first = int(tree_first)
+        if self.tree_first:
+            check(_lib.lib().rpf_build_shard(_ptr(X), self.n, self.d, ctypes.byref(self.params),
+                                             self.tree_first, _stream_handle(stream),
+                                             ctypes.byref(h)), "rpf_build_shard")
+        else:
+            check(_lib.lib().rpf_build(_ptr(X), self.n, self.d, ctypes.byref(self.params),
+                                       _stream_handle(stream), ctypes.byref(h)), "rpf_build")
         self._h = h
 
     # ---- lifetime ---------------------------------------------------------
@@ -140,13 +148,27 @@ class Forest:
                   "rpf_all_knn_trees")
         return idx, dist
 
+    def all_knn_keys(self, K: int, keys=None, workspace=None, stream=None):
+        """rpf_all_knn_keys: (n, K, 2) int32 pairs (d32 bits, index) per point."""
+        if keys is None:
+            keys = torch.empty((self.n, K, 2), dtype=torch.int32, device=self.device)
+        else:
+            _check_out("keys", keys, (self.n, K, 2), np.int32)
+        ws, wsb = (0, 0) if workspace is None else (_ptr(workspace), workspace.numel()
+                                                     * workspace.element_size())
+        check(_lib.lib().rpf_all_knn_keys(self._h, K, _ptr(keys), ws or None, wsb,
+                                          _stream_handle(stream)), "rpf_all_knn_keys")
+        return keys
+
     def autotune(self, K: int, stream=None) -> dict:
-        """rpf_autotune: time the chosen form's tile launch configurations on
-        this forest and keep the fastest for forests of this shape."""
-        chosen = (ctypes.c_int32 * 2)()
+        """rpf_autotune: time the leaf tiles' configurations on this forest
+        (plain: tile region; chosen: tile rows, Gram chunk, CTAs per SM) and
+        keep the fastest for forests of this shape."""
+        chosen = (ctypes.c_int32 * 4)()
         check(_lib.lib().rpf_autotune(self._h, K, _stream_handle(stream), chosen),
               "rpf_autotune")
-        return {"gram_chunk": chosen[0], "ctas_per_sm": chosen[1]}
+        return {"gram_chunk": chosen[0], "ctas_per_sm": chosen[1], "tile_rows": chosen[2],
+                "tile_region": chosen[3]}
 
     def add_trees(self, n_new: int, stream=None) -> None:
         """rpf_add_trees: grow n_new more trees (the same forest that a build
@@ -214,10 +236,11 @@ class Forest:
                 "n_leaves": nl.value, "max_depth": md.value, "n_exact_nodes": ne.value}
 
     def counters(self) -> dict:
-        out = np.zeros(4, np.int64)
-        check(_lib.lib().rpf_forest_counters(self._h, out.ctypes.data, 4), "counters")
+        out = np.zeros(5, np.int64)
+        check(_lib.lib().rpf_forest_counters(self._h, out.ctypes.data, 5), "counters")
         return {"exact_nodes": int(out[0]), "bf16_fallback_rows": int(out[1]),
-                "phase_a_levels": int(out[2]), "tile_region": int(out[3])}
+                "phase_a_levels": int(out[2]), "tile_region": int(out[3]),
+                "chosen_form_plain_groups": int(out[4])}
 
     def perm(self, t: int) -> np.ndarray:
         out = np.empty(self.n, np.int32)
@@ -276,6 +299,26 @@ def brute_knn(X, Q, K: int, self_idx=None, stream=None):
                                    _ptr(Q) if m else None, m, sp, K,
                                    _ptr(idx) if m else None, _ptr(dist) if m else None,
                                    _stream_handle(stream)), "rpf_brute_knn")
+    return idx, dist
+
+
+def merge_keys(lists, K: int, idx=None, dist=None, stream=None):
+    """rpf_merge_keys: lists (G, n, K, 2) int32 (d32 bits, index) -> final
+    (idx, dist) of the n points (the union over the G groups of trees)."""
+    if lists.dim() != 4 or lists.shape[2] != K or lists.shape[3] != 2:
+        raise ValueError("lists must have shape (G, n, K, 2)")
+    lists = lists.contiguous()
+    G, n = int(lists.shape[0]), int(lists.shape[1])
+    dev = lists.device
+    if idx is None:
+        idx = torch.empty((n, K), dtype=torch.int32, device=dev)
+    if dist is None:
+        dist = torch.empty((n, K), dtype=torch.float32, device=dev)
+    _check_out("idx", idx, (n, K), np.int32)
+    _check_out("dist", dist, (n, K), np.float32)
+    check(_lib.lib().rpf_merge_keys(n, K, G, _ptr(lists) if n else None, _ptr(idx) if n else None,
+                                    _ptr(dist) if n else None, _stream_handle(stream)),
+          "rpf_merge_keys")
     return idx, dist
 
 

@@ -438,7 +438,38 @@ def test_autotune_picks_a_configuration_and_keeps_the_lists():
     ci0, cd0 = c.all_knn(10)
     ch = c.autotune(10)
     assert ch["gram_chunk"] in (16, 32, 48, 64) and 1 <= ch["ctas_per_sm"] <= 4
+    assert ch["tile_rows"] in (128, 256)
     ci1, cd1 = c.all_knn(10)
     assert torch.equal(ci0, ci1) and torch.equal(cd0, cd1)
+    # a new forest of the same shape takes the tuned tile rows
+    c2 = gpu_forest(X, 4, 128, 5, seed=3, form=1)
+    ci2, cd2 = c2.all_knn(10)
+    assert torch.equal(ci0, ci2) and torch.equal(cd0, cd2)
     p = gpu_forest(X, 4, 128, 5, seed=3, form=0)
-    assert p.autotune(10) == {"gram_chunk": 0, "ctas_per_sm": 0}
+    pi0, pd0 = p.all_knn(10)
+    ph = p.autotune(10)
+    assert ph["gram_chunk"] == 0 and ph["tile_region"] % 32 == 0 and ph["tile_region"] >= 32
+    assert p.counters()["tile_region"] == ph["tile_region"]
+    pi1, pd1 = p.all_knn(10)
+    assert torch.equal(pi0, pi1) and torch.equal(pd0, pd1) and torch.equal(pi0, ci0)
+
+
+@pytest.mark.parametrize("d", [3, 10, 13, 30])
+def test_chosen_form_runs_the_tensor_path_at_any_dimension(d):
+    # rows of d % 4 != 0 floats are not 16-byte multiples: the tile kernel
+    # loads them with the warps instead of bulk copies; lists stay bit-exact
+    rng = np.random.default_rng(d)
+    X = (rng.standard_normal((6000, d)) * rng.uniform(0.5, 2.0, d)).astype(np.float32)
+    X[:40] = X[40:80]  # duplicates: equal keys across rows
+    g = gpu_forest(X, 4, 100, 3, form=1)
+    gi, gd = g.all_knn(8)
+    o = oracle.Forest(X, 4, 100, 3, seed=0)
+    oi, od = o.all_knn(8)
+    check_knn(gi.cpu().numpy(), gd.cpu().numpy(), oi, od, X)
+    c = g.counters()
+    assert c["chosen_form_plain_groups"] == 0  # the tensor path ran
+    # K above the tensor path's 32: the plain form runs, and is counted
+    gi, gd = g.all_knn(40)
+    oi, od = o.all_knn(40)
+    assert np.array_equal(gi.cpu().numpy(), oi) and np.array_equal(gd.cpu().numpy(), od)
+    assert g.counters()["chosen_form_plain_groups"] >= 1
