@@ -27,10 +27,11 @@
 
 // Box-Muller pair i of the direction for (tree t, node key, try j): FP32
 // from the top 24 bits of the words 2i and 2i+1 (u1 in (0, 1], u2 in [0, 1)).
-__device__ __forceinline__ void rpf_gauss_pair(uint64_t seed, uint64_t t, uint64_t key, uint64_t j,
-                                               int i, float* g0, float* g1) {
-  const uint64_t w1 = rpf_word(seed, RPF_TAG_DIR, t, key, j, (uint64_t)(2 * i));
-  const uint64_t w2 = rpf_word(seed, RPF_TAG_DIR, t, key, j, (uint64_t)(2 * i + 1));
+// h = rpf_word_prefix(seed, RPF_TAG_DIR, t, key, j), shared by all pairs of
+// one (node, try).
+__device__ __forceinline__ void rpf_gauss_pair_h(uint64_t h, int i, float* g0, float* g1) {
+  const uint64_t w1 = rpf_word_last(h, (uint64_t)(2 * i));
+  const uint64_t w2 = rpf_word_last(h, (uint64_t)(2 * i + 1));
   const float u1 = __fmul_rn((float)((w1 >> 40) + 1), 0x1p-24f);
   const float u2 = __fmul_rn((float)(w2 >> 40), 0x1p-24f);
   const float rho = __fsqrt_rn(__fmul_rn(-2.0f, rpf_lnf(u1)));
@@ -38,6 +39,10 @@ __device__ __forceinline__ void rpf_gauss_pair(uint64_t seed, uint64_t t, uint64
   rpf_sincos2pif(u2, &c, &s);
   *g0 = __fmul_rn(rho, c);
   *g1 = __fmul_rn(rho, s);
+}
+__device__ __forceinline__ void rpf_gauss_pair(uint64_t seed, uint64_t t, uint64_t key, uint64_t j,
+                                               int i, float* g0, float* g1) {
+  rpf_gauss_pair_h(rpf_word_prefix(seed, RPF_TAG_DIR, t, key, j), i, g0, g1);
 }
 
 // 1 / |g| in FP32: |g| = sqrtf(sequential fmaf sum of g_k^2); 0 if g = 0

@@ -217,9 +217,10 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
       rpf_warp_project<TG, RPF_TILE_DC, kPaStages>(
           X, d, perm_cur + base, len, warp, kBlock / 32, tiles + warp * kPaStages * RPF_TILE_FLOATS,
-          so, sr + j0 * d, nj, j0 == 0, lane, [&](int pos, int gid, const float(&acc)[TG], float nn) {
+          so, sr + j0 * d, nj, j0 == 0, lane, j0 == 0 ? xnorm : nullptr,
+          [&](int pos, int gid, const float(&acc)[TG], float nn, float xn) {
             if (j0 == 0) {
-              const float r = rpf_point_rad(d, nn, xnorm[gid], on);
+              const float r = rpf_point_rad(d, nn, xn, on);
               radmax = fmaxf(radmax, r);
               rad2 = __fmaf_ru(r, r, rad2);
             }

@@ -40,15 +40,23 @@ __host__ __device__ __forceinline__ uint64_t rpf_mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-__host__ __device__ __forceinline__ uint64_t rpf_word(uint64_t seed, uint64_t tag, uint64_t t,
-                                                      uint64_t key, uint64_t j, uint64_t c) {
+// word() in two parts: the chain over (tag, t, key, j), shared by every
+// counter c of one (node, try), then the last field
+__host__ __device__ __forceinline__ uint64_t rpf_word_prefix(uint64_t seed, uint64_t tag,
+                                                             uint64_t t, uint64_t key, uint64_t j) {
   uint64_t h = seed;
   h = rpf_mix64((h ^ tag) + RPF_GAMMA);
   h = rpf_mix64((h ^ t) + RPF_GAMMA);
   h = rpf_mix64((h ^ key) + RPF_GAMMA);
   h = rpf_mix64((h ^ j) + RPF_GAMMA);
-  h = rpf_mix64((h ^ c) + RPF_GAMMA);
   return h;
+}
+__host__ __device__ __forceinline__ uint64_t rpf_word_last(uint64_t h, uint64_t c) {
+  return rpf_mix64((h ^ c) + RPF_GAMMA);
+}
+__host__ __device__ __forceinline__ uint64_t rpf_word(uint64_t seed, uint64_t tag, uint64_t t,
+                                                      uint64_t key, uint64_t j, uint64_t c) {
+  return rpf_word_last(rpf_word_prefix(seed, tag, t, key, j), c);
 }
 
 __host__ __device__ __forceinline__ uint64_t rpf_child_key(uint64_t key, int side) {

@@ -155,24 +155,28 @@ __device__ __forceinline__ void rpf_tile_chunk(const float* tile, int lane, int 
 // ids[position]; npos positions) are cut into units (batch, DC-coordinate
 // chunk), and unit u + NS - 1 is copied into tile (u + NS - 1) % NS while
 // unit u is computed (NS tiles of 32 rows x (DC + 4) floats at `tiles`).
-// After a batch's last chunk fin(position, id, acc, nn) runs on every lane
-// whose position holds a point.  Point ids are read NS batches ahead.
+// After a batch's last chunk fin(position, id, acc, nn, xn) runs on every
+// lane whose position holds a point, xn = xnorm[id] (0 when xnorm is null).
+// Point ids and their norms are read NS batches ahead.
 template <int TG, int DC, int NS, typename IdT, typename Fin>
 __device__ __forceinline__ void rpf_warp_project(const float* __restrict__ X, int d, const IdT* ids,
                                                  int npos, int bfirst, int bstride, float* tiles,
                                                  const float* so, const float* sr, int nj,
-                                                 bool want_nn, int lane, Fin fin) {
+                                                 bool want_nn, int lane,
+                                                 const float* __restrict__ xnorm, Fin fin) {
   constexpr int TF = 32 * (DC + 4);
   const int nch = (d + DC - 1) / DC;
   const int nbt = (npos + 31) >> 5;
   const int nbw = bfirst < nbt ? (nbt - bfirst + bstride - 1) / bstride : 0;
   if (nbw == 0) return;
-  int g[NS];  // ids of batches i .. i + NS - 1 (-1: none)
+  int g[NS];     // ids of batches i .. i + NS - 1 (-1: none)
+  float xv[NS];  // their norms
   int pb = bfirst;
 #pragma unroll
   for (int k = 0; k < NS; ++k, pb += bstride) {
     const int p = pb * 32 + lane;
     g[k] = (pb < nbt && p < npos) ? (int)ids[p] : -1;
+    xv[k] = (xnorm && g[k] >= 0) ? xnorm[g[k]] : 0.0f;
   }
   // the next unit to copy: batch i + sk, chunk sc, into tile ss
   int sk = 0, sc = 0, ss = 0;
@@ -209,11 +213,15 @@ __device__ __forceinline__ void rpf_warp_project(const float* __restrict__ X, in
       __syncwarp();  // before this tile takes a later unit
       cs = cs + 1 == NS ? 0 : cs + 1;
     }
-    if (g[0] >= 0) fin((bfirst + i * bstride) * 32 + lane, g[0], acc, nn);
+    if (g[0] >= 0) fin((bfirst + i * bstride) * 32 + lane, g[0], acc, nn, xv[0]);
 #pragma unroll
-    for (int k = 0; k + 1 < NS; ++k) g[k] = g[k + 1];
+    for (int k = 0; k + 1 < NS; ++k) {
+      g[k] = g[k + 1];
+      xv[k] = xv[k + 1];
+    }
     const int p = pb * 32 + lane;
     g[NS - 1] = (pb < nbt && p < npos) ? (int)ids[p] : -1;
+    xv[NS - 1] = (xnorm && g[NS - 1] >= 0) ? xnorm[g[NS - 1]] : 0.0f;
     pb += bstride;
     --sk;
   }

@@ -67,14 +67,15 @@ struct SubState {
   // candidates of the exact minimum / maximum
   int defer, nmin, nmax;
   float dtl, dtr;
+  double u0;  // uniform of split attempt 0
   int cmin[kDefCand], cmax[kDefCand];
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct SubLayout {
-  size_t sP, sT, sSide, sTx, r64, r32, so, sbase, sS1, sS2, sA, sinv, smn, smx, svh, slo, shi, red,
-      total;
+  size_t sP, sT, sSide, sTx, r64, r32, so, sbase, sS1, sS2, sA, sinv, smn, smx, svh, slo, shi, sdtl,
+      sdtr, red, total;
 };
 
 __host__ __device__ inline SubLayout sub_layout(int d, int ntry, int TG) {
@@ -114,6 +115,10 @@ __host__ __device__ inline SubLayout sub_layout(int d, int ntry, int TG) {
   o = align16(o + 4 * (size_t)ntry);
   l.shi = o;
   o = align16(o + 4 * (size_t)ntry);
+  l.sdtl = o;
+  o = align16(o + 4 * (size_t)ntry);
+  l.sdtr = o;
+  o = align16(o + 4 * (size_t)ntry);
   l.red = o;
   o = align16(o + 4 * (size_t)(8 * TG * 5 + 40));
   l.total = o;
@@ -150,6 +155,8 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
   double* svh = reinterpret_cast<double*>(smraw + lay.svh);
   float* slo = reinterpret_cast<float*>(smraw + lay.slo);
   float* shi = reinterpret_cast<float*>(smraw + lay.shi);
+  float* sdtl = reinterpret_cast<float*>(smraw + lay.sdtl);
+  float* sdtr = reinterpret_cast<float*>(smraw + lay.sdtr);
   float* red = reinterpret_cast<float*>(smraw + lay.red);
   __shared__ SubState S;
   __shared__ int st_nb[kStack], st_m[kStack], st_id[kStack];
@@ -203,11 +210,18 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     // sequential FP32 norm (the shuffle of 1/|g| orders the scaling after
     // it), so only one block barrier is needed; 2. with it, the centre o =
     // the node's first member
+    // the centre's row and norm are requested first, so their loads overlap
+    // the draws
+    const int og = sP[nb];
+    const float* xo = X + (int64_t)og * d;
+    float oreg = tid < d ? xo[tid] : 0.0f;
+    const float on = xnorm[og];
     for (int j = warp; j < ntry; j += kB / 32) {
       float* g = r32 + j * d;
+      const uint64_t hj = rpf_word_prefix(seed, RPF_TAG_DIR, (uint64_t)(t + t_base), key, (uint64_t)j);
       for (int i = lane; i < npairs; i += 32) {
         float g0, g1;
-        rpf_gauss_pair(seed, (uint64_t)(t + t_base), key, (uint64_t)j, i, &g0, &g1);
+        rpf_gauss_pair_h(hj, i, &g0, &g1);
         g[2 * i] = g0;
         if (2 * i + 1 < d) g[2 * i + 1] = g1;
       }
@@ -221,11 +235,12 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
         r64[j * d + k] = (double)v;
       }
     }
-    const int og = sP[nb];
-    const float* xo = X + (int64_t)og * d;
-    for (int k = tid; k < d; k += kB) so[k] = xo[k];
+    // attempt 0's uniform of the split point, drawn by the last warp (it has
+    // the fewest tries to draw when nTry is not a multiple of the warps)
+    if (tid == kB - 32) S.u0 = rpf_u53(rpf_word(seed, RPF_TAG_SPLIT, (uint64_t)(t + t_base), key, 0, 0));
+    if (tid < d) so[tid] = oreg;
+    for (int k = tid + kB; k < d; k += kB) so[k] = xo[k];
     __syncthreads();
-    const float on = xnorm[og];
 
     // 3. centred FP32 projections and statistics
     float radmax = 0.0f, rad2 = 0.0f;  // rad2: rounded-up sum of the points' rad^2
@@ -246,9 +261,10 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
           float* tb = reinterpret_cast<float*>(smraw + lay.sT) + warp * kTStages * 32 * (kTDC + 4);
           rpf_warp_project<TG, kTDC, kTStages>(
               X, d, sP + nb, m, warp, kB / 32, tb, so, r32 + j0 * d, nj, j0 == 0, lane,
-              [&](int pos, int gid, const float(&acc)[TG], float nn) {
+              j0 == 0 ? xnorm : nullptr,
+              [&](int pos, int gid, const float(&acc)[TG], float nn, float xn) {
                 if (j0 == 0) {
-                  const float r = rpf_point_rad(d, nn, xnorm[gid], on);
+                  const float r = rpf_point_rad(d, nn, xn, on);
                   radmax = fmaxf(radmax, r);
                   rad2 = __fmaf_ru(r, r, rad2);
                 }
@@ -299,9 +315,31 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
       // bounds of every try; with at most 32 tries warp 0 holds them all
       // and certifies right after (a warp sync instead of a block barrier)
       const double inv_m = 1.0 / (double)m;
-      for (int j = tid; j < ntry; j += kB)
+      for (int j = tid; j < ntry; j += kB) {
         rpf_try_bounds(m, inv_m, sS1[j], sS2[j], sA[j], (double)on, radmax, __fsqrt_ru(rad2),
                        &svh[j], &slo[j], &shi[j]);
+        // the deferred split point's interval for every try, in parallel
+        // (independent of the bounds above, so the two chains overlap)
+        if (!median && dfr_cap > 0) {
+          // With beta = p64(o, r_j) and R the largest radius, every p64 lies
+          // within R of beta + q', so the exact extremes a, b lie within R of
+          // beta + min / max q', and c = fma(u, b - a, a) (attempt 0) within
+          // R + 2^-52 (|beta| + |min| + |max| + 2R) of beta + mid, mid =
+          // min + u (max - min) (computed here within 2^-52 (|min| + |max|)).
+          // So with e = 2R + 2^-48 mag, q' < mid - e puts p64 < c, q' >=
+          // mid + e puts p64 >= c, and mid - e > min, mid + e < max make
+          // attempt 0 accepted (a < c <= b).  |beta| <= |o| |r| <= 1.01 on.
+          const double mn = (double)smn[j], mx = (double)smx[j], R = (double)radmax;
+          const double mid = __fma_rn(S.u0, __dsub_rn(mx, mn), mn);
+          const double mag = __dadd_ru(__dadd_ru(__dmul_ru(1.01, (double)on), fabs(mn)),
+                                       __dadd_ru(fabs(mx), R));
+          const double e = __fma_ru(0x1p-48, mag, 2.0 * R);
+          const double lo = __dsub_rd(mid, e), hi = __dadd_ru(mid, e);
+          const bool ok = lo > mn && hi < mx;
+          sdtl[j] = ok ? __double2float_rd(lo) : NAN;
+          sdtr[j] = __double2float_ru(hi);
+        }
+      }
       if (ntry <= 32) __syncwarp();
       else __syncthreads();
     }
@@ -321,28 +359,10 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
         S.whi = __fsub_rd(smx[w], r2);
         S.akey = rpf_dkey(INFINITY);
         S.bkey = rpf_dkey(-INFINITY);
-        if (!median && dfr_cap > 0) {
-          // With beta = p64(o, r_w) and R the largest radius, every p64 lies
-          // within R of beta + q', so the exact extremes a, b lie within R of
-          // beta + min / max q', and c = fma(u, b - a, a) (attempt 0) within
-          // R + 2^-52 (|beta| + |min| + |max| + 2R) of beta + mid, mid =
-          // min + u (max - min) (computed here within 2^-52 (|min| + |max|)).
-          // So with e = 2R + 2^-48 mag, q' < mid - e puts p64 < c, q' >=
-          // mid + e puts p64 >= c, and mid - e > min, mid + e < max make
-          // attempt 0 accepted (a < c <= b).  |beta| <= |o| |r| <= 1.01 on.
-          const double mn = (double)smn[w], mx = (double)smx[w], R = (double)radmax;
-          const double u0 =
-              rpf_u53(rpf_word(seed, RPF_TAG_SPLIT, (uint64_t)(t + t_base), key, 0, 0));
-          const double mid = __fma_rn(u0, __dsub_rn(mx, mn), mn);
-          const double mag = __dadd_ru(__dadd_ru(__dmul_ru(1.01, (double)on), fabs(mn)),
-                                       __dadd_ru(fabs(mx), R));
-          const double e = __fma_ru(0x1p-48, mag, 2.0 * R);
-          const double lo = __dsub_rd(mid, e), hi = __dadd_ru(mid, e);
-          if (lo > mn && hi < mx) {
-            S.defer = 1;
-            S.dtl = __double2float_rd(lo);
-            S.dtr = __double2float_ru(hi);
-          }
+        if (!median && dfr_cap > 0 && !(sdtl[w] != sdtl[w])) {  // interval of the winner
+          S.defer = 1;
+          S.dtl = sdtl[w];
+          S.dtr = sdtr[w];
         }
       }
     }
