@@ -475,18 +475,26 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
                                   2.0f * eta);
         tau2 = __fadd_ru(eps, __fmul_ru(s, s));
       }
+      // the columns within the margin, eight at a time as a bit mask; the
+      // few set bits are then written out (no divergent store per column)
+      const int cl = tc_row ? lb : 0, ch = tc_row ? le : 0;
 #pragma unroll 1
       for (int c0 = lo; c0 < hi; c0 += 8) {
         float g[8];
         rpf_tmem_ld8(tlane + (uint32_t)c0, g);
+        uint32_t msk = 0u;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int c = c0 + j;
           const float D = __fmaf_rn(-2.0f, g[j], __fadd_rn(nr, nrm[c < ROWS ? c : 0]));
-          if (tc_row && c >= lb && c < le && c != r && D <= tau2) {
-            if (ns < TC_SLOTS) my[ns] = (unsigned char)c;
-            ++ns;
-          }
+          const bool take = c >= cl && c < ch && c != r && D <= tau2;
+          msk |= (uint32_t)take << j;
+        }
+        while (msk) {
+          const int j = __ffs(msk) - 1;
+          msk &= msk - 1u;
+          if (ns < TC_SLOTS) my[ns] = (unsigned char)(c0 + j);
+          ++ns;
         }
       }
     }
