@@ -89,7 +89,7 @@ void free_forest(rpf_forest* f) {
   if (!f) return;
   for (void* p : f->owned) rpf_release(p, 0);
   void* ps[] = {f->node_key,  f->node_tree,  f->node_begin, f->node_len,  f->node_left,
-                f->node_right, f->node_jstar, f->node_flag, f->node_c,    f->node_dir,
+                f->node_right, f->node_jstar, f->node_flag, f->node_c,    f->node_route,
                 f->node_dir32, f->leaf_tree,  f->leaf_begin, f->leaf_len, f->tile_cnt,
                 f->tile_off,  f->tile_leaf,  f->stage,      f->pk_tiles, f->pk_bits};
   for (void* p : ps) rpf_release(p, 0);
@@ -109,10 +109,10 @@ __global__ void k_merge_nodes(int64_t N, int is_b, int T, int dT, int64_t Na, in
                               const uint64_t* key, const int32_t* tree, const int32_t* begin,
                               const int32_t* len, const int32_t* left, const int32_t* right,
                               const int32_t* jstar, const int32_t* flag, const double* c,
-                              const double* dir, const float* dir32, uint64_t* okey,
+                              const float* dir32, uint64_t* okey,
                               int32_t* otree, int32_t* obegin, int32_t* olen, int32_t* oleft,
                               int32_t* oright, int32_t* ojstar, int32_t* oflag, double* oc,
-                              double* odir, float* odir32) {
+                              float* odir32) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int64_t o = merged_id(i, is_b != 0, T, dT, Na);
@@ -125,10 +125,7 @@ __global__ void k_merge_nodes(int64_t N, int is_b, int T, int dT, int64_t Na, in
   ojstar[o] = jstar[i];
   oflag[o] = flag[i];
   oc[o] = c[i];
-  for (int k = 0; k < d; ++k) {
-    odir[o * d + k] = dir[i * d + k];
-    odir32[o * d + k] = dir32[i * d + k];
-  }
+  for (int k = 0; k < d; ++k) odir32[o * d + k] = dir32[i * d + k];
 }
 
 __global__ void k_shift_tree(int64_t N, int add, const int32_t* in, int32_t* out) {
@@ -322,18 +319,17 @@ int rpf_add_trees(rpf_forest* f, int32_t n_new, void* stream) {
   uint64_t* key = nullptr;
   int32_t *tree = nullptr, *begin = nullptr, *len = nullptr, *left = nullptr, *right = nullptr,
           *jstar = nullptr, *flag = nullptr, *ltree = nullptr, *lbegin = nullptr, *llen = nullptr;
-  double *c = nullptr, *dir = nullptr;
+  double* c = nullptr;
   float* dir32 = nullptr;
   void** bufs[] = {(void**)&perm, (void**)&key, (void**)&tree, (void**)&begin, (void**)&len,
                    (void**)&left, (void**)&right, (void**)&jstar, (void**)&flag, (void**)&c,
-                   (void**)&dir, (void**)&dir32, (void**)&ltree, (void**)&lbegin,
-                   (void**)&llen};
+                   (void**)&dir32, (void**)&ltree, (void**)&lbegin, (void**)&llen};
   const size_t sizes[] = {4 * (size_t)(T + n_new) * n, 8 * (size_t)N, 4 * (size_t)N,
                           4 * (size_t)N, 4 * (size_t)N, 4 * (size_t)N, 4 * (size_t)N,
-                          4 * (size_t)N, 4 * (size_t)N, 8 * (size_t)N, 8 * (size_t)N * d,
+                          4 * (size_t)N, 4 * (size_t)N, 8 * (size_t)N,
                           4 * (size_t)N * d, 4 * (size_t)(La + Lb), 4 * (size_t)(La + Lb),
                           4 * (size_t)(La + Lb)};
-  for (int i = 0; i < 15 && !rc; ++i) rc = rpf_alloc(bufs[i], sizes[i], s);
+  for (int i = 0; i < 14 && !rc; ++i) rc = rpf_alloc(bufs[i], sizes[i], s);
   if (rc) {
     for (auto b : bufs) rpf_release(*b, s);
     g->X = nullptr;
@@ -351,8 +347,8 @@ int rpf_add_trees(rpf_forest* f, int32_t n_new, void* stream) {
     if (Nq > 0) {
       k_merge_nodes<<<(unsigned)((Nq + 127) / 128), 128, 0, s>>>(
           Nq, b, T, n_new, Na, d, q->node_key, q->node_tree, q->node_begin, q->node_len,
-          q->node_left, q->node_right, q->node_jstar, q->node_flag, q->node_c, q->node_dir,
-          q->node_dir32, key, tree, begin, len, left, right, jstar, flag, c, dir, dir32);
+          q->node_left, q->node_right, q->node_jstar, q->node_flag, q->node_c,
+          q->node_dir32, key, tree, begin, len, left, right, jstar, flag, c, dir32);
       e = cudaGetLastError();
     }
   }
@@ -377,7 +373,7 @@ int rpf_add_trees(rpf_forest* f, int32_t n_new, void* stream) {
   for (auto& o : f->owned)
     if (o == f->perm) o = perm;
   void* olds[] = {f->perm, f->node_key, f->node_tree, f->node_begin, f->node_len, f->node_left,
-                  f->node_right, f->node_jstar, f->node_flag, f->node_c, f->node_dir,
+                  f->node_right, f->node_jstar, f->node_flag, f->node_c, f->node_route,
                   f->node_dir32, f->leaf_tree, f->leaf_begin, f->leaf_len, f->tile_cnt,
                   f->tile_off, f->tile_leaf, f->pk_tiles, f->pk_bits};
   for (void* o : olds) rpf_release(o, s);
@@ -391,7 +387,7 @@ int rpf_add_trees(rpf_forest* f, int32_t n_new, void* stream) {
   f->node_jstar = jstar;
   f->node_flag = flag;
   f->node_c = c;
-  f->node_dir = dir;
+  f->node_route = nullptr;
   f->node_dir32 = dir32;
   f->leaf_tree = ltree;
   f->leaf_begin = lbegin;
@@ -407,7 +403,8 @@ int rpf_add_trees(rpf_forest* f, int32_t n_new, void* stream) {
   g->X = nullptr;
   g->xnorm = nullptr;
   free_forest(g);  // its own tables only (X, norms and error words are f's)
-  if ((rc = rpf_build_tiles(f, s)) || (f->prm.form == 1 && (rc = rpf_build_packs(f, s))))
+  if ((rc = rpf_build_route(f, s)) || (rc = rpf_build_tiles(f, s)) ||
+      (f->prm.form == 1 && (rc = rpf_build_packs(f, s))))
     return rc;
   e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaGetLastError();

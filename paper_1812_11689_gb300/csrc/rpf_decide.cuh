@@ -74,6 +74,12 @@ __device__ __forceinline__ double rpf_p64(const float* x, const double* r, int d
   for (int k = 0; k < d; ++k) p = __fma_rn((double)__ldg(x + k), r[k], p);
   return p;
 }
+// the same from the FP32 direction values (widened exactly)
+__device__ __forceinline__ double rpf_p64f(const float* x, const float* r, int d) {
+  double p = 0.0;
+  for (int k = 0; k < d; ++k) p = __fma_rn((double)__ldg(x + k), (double)__ldg(r + k), p);
+  return p;
+}
 
 // Warp-collective canonical FP64 projections of two rows x0, x1 on r; lane 0
 // returns p64(x0, r), lane 1 p64(x1, r).  With x_k and r_k FP32 values the

@@ -1195,17 +1195,13 @@ __global__ void k_compact_leaves(int64_t S, const int32_t* pos, const int32_t* t
 __global__ void __launch_bounds__(128) k_node_dirs(int64_t N, int d, uint64_t seed, int t_base,
                                                    const uint64_t* key, const int32_t* tree,
                                                    const int32_t* left, const int32_t* jstar,
-                                                   const int32_t* flag, double* dir, float* dir32) {
+                                                   const int32_t* flag, float* dir32) {
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= N) return;  // whole warp
-  double* r = dir + i * d;
   float* r32 = dir32 + i * d;
   if (left[i] < 0 || (flag[i] & 1) || jstar[i] < 0) {
-    for (int k = lane; k < d; k += 32) {
-      r[k] = 0.0;
-      r32[k] = 0.0f;
-    }
+    for (int k = lane; k < d; k += 32) r32[k] = 0.0f;
     return;
   }
   const uint64_t t = (uint64_t)(tree[i] + t_base), kk = key[i], j = (uint64_t)jstar[i];
@@ -1220,14 +1216,36 @@ __global__ void __launch_bounds__(128) k_node_dirs(int64_t N, int d, uint64_t se
   if (lane == 0) inv = rpf_inv_norm32(r32, d);
   inv = __shfl_sync(RPF_FULL, inv, 0);
   __syncwarp();
-  for (int k = lane; k < d; k += 32) {
-    const float v = inv == 0.0f ? (k == 0 ? 1.0f : 0.0f) : __fmul_rn(r32[k], inv);
-    r32[k] = v;
-    r[k] = (double)v;
-  }
+  for (int k = lane; k < d; k += 32)
+    r32[k] = inv == 0.0f ? (k == 0 ? 1.0f : 0.0f) : __fmul_rn(r32[k], inv);
+}
+
+// Routing record of every node: c (two words), left child, and the right
+// child -- or the left one for a rank split, which sends every query left.
+__global__ void k_route_table(int64_t N, const int32_t* left, const int32_t* right,
+                              const int32_t* flag, const double* c, int4* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double cc = c[i];
+  const int l = left[i];
+  const int r = (l >= 0 && (flag[i] & 1)) ? l : right[i];
+  out[i] = make_int4(__double2loint(cc), __double2hiint(cc), l, r);
 }
 
 }  // namespace
+
+int rpf_build_route(rpf_forest* f, cudaStream_t s) {
+  rpf_release(f->node_route, s);
+  f->node_route = nullptr;
+  const int64_t N = f->n_nodes;
+  if (rpf_alloc((void**)&f->node_route, sizeof(int4) * (size_t)std::max<int64_t>(N, 1), s))
+    return RPF_ENOMEM;
+  if (N > 0)
+    RPF_LAUNCH("k_route_table", s, k_route_table<<<nblk(N, 256), 256, 0, s>>>(
+        N, f->node_left, f->node_right, f->node_flag, f->node_c, f->node_route));
+  RPF_CU(cudaGetLastError());
+  return RPF_OK;
+}
 
 // Phase B (rpf_subtree.cu)
 bool rpf_subtree_fits(int d, int ntry);
@@ -1747,15 +1765,15 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
     fo->node_c = oc;
     fo->n_nodes = total;
     fo->nodes_cap = total;
-    if (rpf_alloc((void**)&fo->node_dir, sizeof(double) * M * d, s) ||
-        rpf_alloc((void**)&fo->node_dir32, sizeof(float) * M * d, s)) {
+    if (rpf_alloc((void**)&fo->node_dir32, sizeof(float) * M * d, s)) {
       cleanup();
       return RPF_ENOMEM;
     }
     RPF_LAUNCH("k_node_dirs", s, k_node_dirs<<<nblk((int64_t)total * 32, 128), 128, 0, s>>>(
         total, d, seed, fo->t_base, fo->node_key, fo->node_tree, fo->node_left, fo->node_jstar, fo->node_flag,
-        fo->node_dir, fo->node_dir32));
+        fo->node_dir32));
     RPF_TRY(rpf_split_deferred(fo, dfr, dfr_cnt, dfr_cap, new_id, d_err, s));
+    RPF_TRY(rpf_build_route(fo, s));
 
     // leaves: keep the used slots (len > 0) in slot order
     const int64_t S = leaves_used;

@@ -231,8 +231,14 @@ struct rpf_forest {
   int32_t* node_jstar = nullptr;
   int32_t* node_flag = nullptr;
   double* node_c = nullptr;
-  double* node_dir = nullptr;  // n_nodes x d (FP64 r*), zeros for leaves
-  float* node_dir32 = nullptr; // n_nodes x d (FP32 copy for query filtering)
+  // n_nodes x d: r* of every split node (zeros for leaves and rank splits);
+  // the directions are FP32 values, so widening them gives the FP64 r*
+  // exactly
+  float* node_dir32 = nullptr;
+  // per node, what routing reads at one step: (c as two words, left child,
+  // right child); a rank split stores its left child on both sides, a leaf
+  // has left = -1 (rpf_build_route)
+  int4* node_route = nullptr;
 
   // leaves
   int64_t n_leaves = 0;
@@ -339,5 +345,7 @@ size_t rpf_query_core_ws(int64_t m, int T, int K);
 // device address of the allocation-free query's scratch on the current
 // device (rpf_static.cu), or nullptr with *rc set
 void* rpf_static_scratch(int* rc);
+// the routing records of every node (after growth or a merge of tables)
+int rpf_build_route(rpf_forest* f, cudaStream_t s);
 void rpf_launch_directions(uint64_t seed, int32_t t, const uint64_t* keys_dev, int32_t n_keys,
                            int32_t j, int32_t d, double* out_dev, cudaStream_t s);

@@ -343,24 +343,22 @@ __global__ void k_qscan(const float* Q, int64_t m, int d, int T, int K, const in
 
 // Routing, one group of RW = 8 lanes per (query q, tree t) (Sec. 2,
 // Algorithm 3); a warp walks four (query, tree) paths at once, so four
-// chains of dependent node loads are in flight.  At a split node the decision
-// is r* . q < c with the canonical FP64 chain p64 (fold of
-// fma((double)q_k, r_k, p) over k in order).  The directions are FP32 values
-// widened to double, so the group first forms s = r* . q in FP32 (lane-
-// strided fmaf over at most ceil(d / 8) terms, then a 3-level butterfly) with
+// chains of dependent node loads are in flight.  A step reads the node's
+// 16-byte routing record (c, left, right) and its FP32 direction, both
+// addressed by the node id alone, so one round trip per level.  At a split
+// node the decision is r* . q < c with the canonical FP64 chain p64 (fold of
+// fma((double)q_k, r_k, p) over k in order).  The directions are FP32
+// values, so the group first forms s = r* . q in FP32 (lane-strided fmaf
+// over at most ceil(d / 8) terms, then a 3-level butterfly) with
 // A = sum |q_k r_k|; p64 lies within
 //   e = (ceil(d / 8) + 7) 2^-24 A_up
 // of s (FP32 error of s: (ceil(d/8) + 3) u A; FP64 error of p64: d 2^-53 A;
 // A_up bounds A despite its own rounding).  Only when c falls inside
-// [s - e, s + e] does the group's first lane evaluate p64 itself.  Rank-split
-// nodes send every query left.
+// [s - e, s + e] does the group's first lane evaluate p64 itself.  A rank
+// split stores its left child on both sides (every query goes left).
 #define RW 8
 __global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, int64_t m, int d,
-                                                 int T, const int32_t* __restrict__ node_left,
-                                                 const int32_t* __restrict__ node_right,
-                                                 const int32_t* __restrict__ node_flag,
-                                                 const double* __restrict__ node_c,
-                                                 const double* __restrict__ node_dir,
+                                                 int T, const int4* __restrict__ node_route,
                                                  const float* __restrict__ node_dir32,
                                                  int32_t* qleaf) {
   const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / RW;
@@ -374,12 +372,9 @@ __global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, in
   const float kerr = (float)(per + 7) * 0x1p-24f;
   const float kA = 1.0f + (float)(per + 6) * 0x1p-23f;
   int node = t;
-  int left = node_left[node];
-  while (left >= 0) {
-    // every field of the node is requested at once (one round trip per level)
-    const int flag = node_flag[node];
-    const int right = node_right[node];
-    const double c = node_c[node];
+  int4 rec = __ldg(node_route + node);
+  while (rec.z >= 0) {
+    const double c = __hiloint2double(rec.y, rec.x);
     const float* r32 = node_dir32 + (int64_t)node * d;
     float sacc = 0.0f, aacc = 0.0f;
     for (int k = sub; k < d; k += RW) {
@@ -393,7 +388,7 @@ __global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, in
       aacc = __fadd_rn(aacc, __shfl_xor_sync(gmask, aacc, off, RW));
     }
     int go_left;
-    if (flag & 1) {  // rank split: every query goes left
+    if (rec.z == rec.w) {  // rank split: every query goes left
       go_left = 1;
     } else {
       // q . r lies in [sacc - e, sacc + e]; the test runs in FP32 against
@@ -406,16 +401,15 @@ __global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, in
       } else {  // undecided by the bound: the canonical FP64 chain
         int v = 0;
         if (sub == 0) {
-          const double* r = node_dir + (int64_t)node * d;
           double p = 0.0;
-          for (int k = 0; k < d; ++k) p = __fma_rn((double)__ldg(x + k), r[k], p);
+          for (int k = 0; k < d; ++k) p = __fma_rn((double)__ldg(x + k), (double)__ldg(r32 + k), p);
           v = p < c;
         }
         go_left = __shfl_sync(gmask, v, 0, RW);
       }
     }
-    node = go_left ? left : right;
-    left = node_left[node];
+    node = go_left ? rec.z : rec.w;
+    rec = __ldg(node_route + node);
   }
   if (sub == 0) qleaf[g] = node;
 }
@@ -820,8 +814,7 @@ int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t
   int32_t* qleaf = (int32_t*)((char*)ws + RPF_QERR_BYTES);
   uint2* cand = (uint2*)((char*)qleaf + align256((size_t)m * T * 4));
   RPF_LAUNCH("k_route_w", s, k_route_w<<<nblk(m * T * RW, 256), 256, 0, s>>>(
-      Q, m, f->d, T, f->node_left, f->node_right, f->node_flag, f->node_c, f->node_dir,
-      f->node_dir32, qleaf));
+      Q, m, f->d, T, f->node_route, f->node_dir32, qleaf));
   const int dp = ((f->d + 3) & ~3) + 4;
   const size_t qsm = (size_t)(QS_T + 1) * dp * 4;
   if (f->prm.leaf_max <= QS_T && (f->d % 4) == 0 && qsm <= 200 * 1024) {

@@ -815,18 +815,18 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
 // (checked again here: a failure is an internal error).
 __global__ void __launch_bounds__(128) k_split_deferred(
     const int32_t* dfr, const int* dfr_cnt, int dfr_cap, const int32_t* new_id,
-    const uint64_t* node_key, const int32_t* node_tree, const double* node_dir,
+    const uint64_t* node_key, const int32_t* node_tree, const float* node_dir32,
     const float* __restrict__ X, int d, uint64_t seed, int t_base, double* node_c, int* d_err) {
   const int64_t rec = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (rec >= min(*dfr_cnt, dfr_cap)) return;
   const int32_t* r = dfr + rec * RPF_DEFER_REC;
   const int nid = new_id[r[0]];
   const int nmin = r[1] & 255, nmax = (r[1] >> 8) & 255;
-  const double* dir = node_dir + (int64_t)nid * d;
+  const float* dir = node_dir32 + (int64_t)nid * d;
   unsigned long long ak = rpf_dkey(INFINITY), bk = rpf_dkey(-INFINITY);
   for (int c = 0; c < nmin + nmax; ++c) {
     const int pt = c < nmin ? r[2 + c] : r[2 + kDefCand + (c - nmin)];
-    const unsigned long long k = rpf_dkey(rpf_p64(X + (int64_t)pt * d, dir, d));
+    const unsigned long long k = rpf_dkey(rpf_p64f(X + (int64_t)pt * d, dir, d));
     if (c < nmin) ak = min(ak, k);
     else bk = max(bk, k);
   }
@@ -845,7 +845,7 @@ int rpf_split_deferred(rpf_forest* fo, const int32_t* dfr, const int* dfr_cnt, i
   if (dfr_cap <= 0) return RPF_OK;
   RPF_LAUNCH("k_split_deferred", s,
              k_split_deferred<<<(unsigned)(((int64_t)dfr_cap + 127) / 128), 128, 0, s>>>(
-                 dfr, dfr_cnt, dfr_cap, new_id, fo->node_key, fo->node_tree, fo->node_dir, fo->X,
+                 dfr, dfr_cnt, dfr_cap, new_id, fo->node_key, fo->node_tree, fo->node_dir32, fo->X,
                  fo->d, fo->prm.seed, fo->t_base, fo->node_c, d_err));
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? RPF_OK : rpf_cuda_err(e);
