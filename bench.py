@@ -665,6 +665,11 @@ def run_serving(args, dev, n_requests=300):
                 res["batches"] = srv.n_batches
                 r["load_%.2f" % load] = res
             r["missing_rate_sample_500"] = missing(K)
+            # the plain FP32 form of the same forest (identical lists), saturated
+            f.set_form(forest.FORM_PLAIN)
+            srv = serve.Server(f, slots=4, max_batch=8192)
+            r["plain_saturation"] = serve.latency_summary(srv.run(make_reqs(K, 2000)))
+            f.set_form(forest.FORM_CHOSEN)
             runs["K=%d" % K] = r
         return runs
 

@@ -56,9 +56,10 @@ typedef struct {
                          floor(m/2) points smallest in (projection, point index)
                          order go left, c = the first right point's projection,
                          so queries go left iff their projection is below c. */
-  int32_t form;       /* leaf distance tiles: 0 = plain FP32 SIMT; 1 = BF16       */
-                      /* tensor-core Gram + exact FP32 re-rank of a shortlist.    */
-                      /* Both return identical lists.                             */
+  int32_t form;       /* leaf distances: 0 = plain FP32 SIMT; 1 = BF16 tensor-core */
+                      /* Gram (all-kNN) and BF16 rows (queries), each with an     */
+                      /* exact FP32 re-rank of a certified shortlist.  Both       */
+                      /* return identical lists.                                  */
   int32_t growth;     /* 0 = default (2); 1 = every split decided in FP64 (G-A);  */
                       /* 2 = FP32 projections with a certified error bound and    */
                       /* FP64 recompute of every undecided case (G-B).  1 and 2   */
@@ -251,6 +252,17 @@ int rpf_autotune(rpf_forest* f, int32_t K, void* stream, int32_t* chosen);
  * RPF_ECUDA; on an error the forest keeps its first T trees.
  */
 int rpf_add_trees(rpf_forest* f, int32_t n_new, void* stream);
+
+/*
+ * rpf_set_form -- switch the leaf-distance form of a built forest: 0 = plain
+ * FP32, 1 = the chosen form (BF16 tensor-core tiles for all-kNN, BF16 rows
+ * for queries, each with a certified exact FP32 re-rank).  Both give the same
+ * lists bit for bit; switching to 1 builds the tile packing and the BF16
+ * copy of the data if the forest has none.  No other call may use the forest
+ * meanwhile; synchronises `stream`.
+ * Errors: RPF_EINVAL, RPF_ENOMEM, RPF_ECUDA.
+ */
+int rpf_set_form(rpf_forest* f, int32_t form, void* stream);
 
 /* Release the forest and its device memory.  NULL is a no-op. */
 void rpf_free(rpf_forest* f);

@@ -91,7 +91,8 @@ void free_forest(rpf_forest* f) {
   void* ps[] = {f->node_key,  f->node_tree,  f->node_begin, f->node_len,  f->node_left,
                 f->node_right, f->node_jstar, f->node_flag, f->node_c,    f->node_route,
                 f->node_dir32, f->leaf_tree,  f->leaf_begin, f->leaf_len, f->tile_cnt,
-                f->tile_off,  f->tile_leaf,  f->stage,      f->pk_tiles, f->pk_bits};
+                f->tile_off,  f->tile_leaf,  f->stage,      f->pk_tiles, f->pk_bits,
+                f->X16};
   for (void* p : ps) rpf_release(p, 0);
   delete f;
 }
@@ -251,7 +252,8 @@ int build_impl(const float* X, int64_t n, int32_t d, const rpf_params* p, int32_
     return rpf_cuda_err(e);
   }
   if ((rc = rpf_grow(f, s)) || (rc = rpf_build_tiles(f, s)) ||
-      (f->prm.form == 1 && (rc = rpf_build_packs(f, s)))) {
+      (f->prm.form == 1 && (rc = rpf_build_packs(f, s))) ||
+      (f->prm.form == 1 && (rc = rpf_build_x16(f, s)))) {
     free_forest(f);
     return rc;
   }
@@ -279,6 +281,18 @@ int rpf_build_shard(const float* X, int64_t n, int32_t d, const rpf_params* p,
 }
 
 void rpf_free(rpf_forest* f) { free_forest(f); }
+
+int rpf_set_form(rpf_forest* f, int32_t form, void* stream) {
+  if (!f || form < 0 || form > 1) return RPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = RPF_OK;
+  if (form == 1 && !f->pk_tiles) rc = rpf_build_packs(f, s);
+  if (!rc && form == 1 && !f->X16) rc = rpf_build_x16(f, s);
+  if (rc) return rc;
+  f->prm.form = form;
+  RPF_CU(cudaStreamSynchronize(s));
+  return RPF_OK;
+}
 
 int rpf_autotune(rpf_forest* f, int32_t K, void* stream, int32_t* chosen) {
   if (!f || K < 1 || K > RPF_MAX_K) return RPF_EINVAL;

@@ -218,6 +218,9 @@ struct rpf_forest {
 
   float* X = nullptr;         // n x d
   float* xnorm = nullptr;     // n: upper bound of |x|_2
+  // chosen form: BF16 copy of X (bits), rows padded to d8 = 8 ceil(d / 8)
+  uint16_t* X16 = nullptr;
+  int32_t d8 = 0;
   int32_t* perm = nullptr;    // T x n final permutation
 
   // node table (capacity nodes_cap)
@@ -347,5 +350,11 @@ size_t rpf_query_core_ws(int64_t m, int T, int K);
 void* rpf_static_scratch(int* rc);
 // the routing records of every node (after growth or a merge of tables)
 int rpf_build_route(rpf_forest* f, cudaStream_t s);
+// chosen-form query scan (rpf_qscan_bf.cu): the BF16 copy of X, whether the
+// scan covers (f, K), and the launch over m x T (query, tree) leaves
+int rpf_build_x16(rpf_forest* f, cudaStream_t s);
+bool rpf_qscan_bf_ok(const rpf_forest* f, int K);
+int rpf_qscan_bf(const rpf_forest* f, const float* Q, int64_t m, int K, const int32_t* qleaf,
+                 uint2* cand, int* err, cudaStream_t s);
 void rpf_launch_directions(uint64_t seed, int32_t t, const uint64_t* keys_dev, int32_t n_keys,
                            int32_t j, int32_t d, double* out_dev, cudaStream_t s);

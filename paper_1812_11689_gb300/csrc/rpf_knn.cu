@@ -414,11 +414,40 @@ __global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, in
   if (sub == 0) qleaf[g] = node;
 }
 
+// Ascending bitonic sort of one 64-bit key per lane (all 32 lanes).
+__device__ __forceinline__ unsigned long long rpf_warp_sort(unsigned long long v, int lane) {
+#pragma unroll
+  for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(RPF_FULL, v, j);
+      const bool keep_min = ((lane & j) == 0) == ((lane & kk) == 0);
+      v = keep_min ? min(v, o) : max(v, o);
+    }
+  }
+  return v;
+}
+
+// The 32 smallest keys of two ascending lists a, b (lane l holds element l
+// of each), ascending: min(a_l, b_{31-l}) holds them as a bitonic sequence,
+// which a bitonic merge sorts.
+__device__ __forceinline__ unsigned long long rpf_warp_merge_min(unsigned long long a,
+                                                                 unsigned long long b, int lane) {
+  unsigned long long v = min(a, __shfl_sync(RPF_FULL, b, 31 - lane));
+#pragma unroll
+  for (int j = 16; j > 0; j >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(RPF_FULL, v, j);
+    v = (lane & j) == 0 ? min(v, o) : max(v, o);
+  }
+  return v;
+}
+
 // Leaf scan for queries, one CTA of QS_T threads per (query q, tree t): the
 // leaf's rows are staged in shared memory by bulk copies, thread j computes
 // the canonical d32 of q and leaf point j, and a bitonic sort of the 64-bit
 // keys (d32 bits << 32 | index, ordered exactly like (d32, index)) gives the
-// leaf's top-K.  Leaves of at most QS_T points.
+// leaf's top-K (for K <= 32: register sorts per warp and a merge of the four
+// warps' lists).  Leaves of at most QS_T points.
 #define QS_T 128
 __global__ void __launch_bounds__(QS_T) k_qscan_cta(const float* __restrict__ Q, int64_t m, int d,
                                                     int dp, int T, int K, const int32_t* qleaf,
@@ -472,6 +501,22 @@ __global__ void __launch_bounds__(QS_T) k_qscan_cta(const float* __restrict__ Q,
       e = __fsub_rn(a.w, b.w); acc = __fmaf_rn(e, e, acc);
     }
     key = ((unsigned long long)__float_as_uint(acc) << 32) | (unsigned)pid[tid];
+  }
+  if (K <= 32) {
+    // every warp sorts its 32 keys in registers; warp 0 merges the four
+    // sorted lists, keeping the 32 smallest at each merge (one barrier)
+    keys[tid] = rpf_warp_sort(key, tid & 31);
+    __syncthreads();
+    if (tid < 32) {
+      unsigned long long v = keys[tid];
+#pragma unroll
+      for (int w = 1; w < QS_T / 32; ++w) v = rpf_warp_merge_min(v, keys[32 * w + tid], tid);
+      if (tid < K)
+        cand[((int64_t)t * m + q) * K + tid] =
+            v == ~0ull ? make_uint2(0x7f800000u, 0xffffffffu)
+                       : make_uint2((unsigned)(v >> 32), (unsigned)v);
+    }
+    return;
   }
   keys[tid] = key;
   __syncthreads();
@@ -817,7 +862,10 @@ int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t
       Q, m, f->d, T, f->node_route, f->node_dir32, qleaf));
   const int dp = ((f->d + 3) & ~3) + 4;
   const size_t qsm = (size_t)(QS_T + 1) * dp * 4;
-  if (f->prm.leaf_max <= QS_T && (f->d % 4) == 0 && qsm <= 200 * 1024) {
+  if (f->prm.form == 1 && rpf_qscan_bf_ok(f, K)) {  // chosen form: BF16 rows, exact re-rank
+    const int rc = rpf_qscan_bf(f, Q, m, K, qleaf, cand, qerr, s);
+    if (rc) return rc;
+  } else if (f->prm.leaf_max <= QS_T && (f->d % 4) == 0 && qsm <= 200 * 1024) {
     cudaFuncSetAttribute(k_qscan_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
     RPF_LAUNCH("k_qscan_cta", s, k_qscan_cta<<<(unsigned)(m * T), QS_T, qsm, s>>>(
         Q, m, f->d, dp, T, K, qleaf, f->node_tree, f->node_begin, f->node_len, f->perm, f->X,

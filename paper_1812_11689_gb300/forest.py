@@ -170,6 +170,11 @@ class Forest:
         return {"gram_chunk": chosen[0], "ctas_per_sm": chosen[1], "tile_rows": chosen[2],
                 "tile_region": chosen[3]}
 
+    def set_form(self, form: int, stream=None) -> None:
+        """rpf_set_form: switch between the plain and the chosen form."""
+        check(_lib.lib().rpf_set_form(self._h, int(form), _stream_handle(stream)), "rpf_set_form")
+        self.params.form = int(form)
+
     def add_trees(self, n_new: int, stream=None) -> None:
         """rpf_add_trees: grow n_new more trees (the same forest that a build
         with n_trees + n_new trees gives)."""

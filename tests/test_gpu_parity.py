@@ -473,3 +473,59 @@ def test_chosen_form_runs_the_tensor_path_at_any_dimension(d):
     oi, od = o.all_knn(40)
     assert np.array_equal(gi.cpu().numpy(), oi) and np.array_equal(gd.cpu().numpy(), od)
     assert g.counters()["chosen_form_plain_groups"] >= 1
+
+
+@pytest.mark.parametrize("name,n,L,Ks", [("mix50_d96", 20000, 128, (1, 10, 32, 50)),
+                                         ("aniso20_d64", 12000, 128, (10, 20)),
+                                         ("mix5_d10", 3000, 50, (5, 12))])
+def test_chosen_form_queries_bf16_scan_bit_exact(name, n, L, Ks):
+    # the chosen form's query scan reads BF16 rows and re-ranks a certified
+    # shortlist exactly: the lists equal the plain form's and the oracle's
+    X = synth.make(name, n=n)
+    Q = synth.queries(name, 600, stream=31)
+    c = gpu_forest(X, 5, L, 5, form=1)
+    p = gpu_forest(X, 5, L, 5, form=0)
+    o = oracle.Forest(X, 5, L, 5, seed=0)
+    Qd = torch.from_numpy(Q).cuda()
+    for K in Ks:
+        ci, cd = c.query(Qd, K)
+        pi, pd = p.query(Qd, K)
+        oi, od = o.query(Q, K)
+        assert torch.equal(ci, pi) and torch.equal(cd, pd), K
+        assert np.array_equal(ci.cpu().numpy(), oi) and np.array_equal(cd.cpu().numpy(), od), K
+
+
+def test_chosen_form_queries_long_shortlist_falls_back_exactly():
+    # points on a thin shell around the origin, queried at the origin: every
+    # leaf point is within the certified margin of the K-th, so each leaf is
+    # rescanned exactly (counted) and the lists stay bit-exact
+    rng = np.random.default_rng(5)
+    g = rng.standard_normal((4000, 64))
+    X = (g / np.linalg.norm(g, axis=1, keepdims=True) * (1.0 + 1e-4 * rng.random((4000, 1))))
+    X = X.astype(np.float32)
+    Q = np.zeros((50, 64), np.float32)
+    Q[1:] = 1e-3 * rng.standard_normal((49, 64)).astype(np.float32)
+    c = gpu_forest(X, 3, 128, 3, form=1)
+    o = oracle.Forest(X, 3, 128, 3, seed=0)
+    before = c.counters()["bf16_fallback_rows"]
+    ci, cd = c.query(torch.from_numpy(Q).cuda(), 10)
+    oi, od = o.query(Q, 10)
+    assert np.array_equal(ci.cpu().numpy(), oi) and np.array_equal(cd.cpu().numpy(), od)
+    assert c.counters()["bf16_fallback_rows"] > before
+
+
+def test_set_form_switches_a_built_forest_and_keeps_the_lists():
+    X = synth.make("aniso20_d64", n=9000)
+    Q = torch.from_numpy(synth.queries("aniso20_d64", 300, stream=4)).cuda()
+    f = gpu_forest(X, 4, 128, 5, form=0)
+    pi, pd = f.all_knn(10)
+    qi, qd = f.query(Q, 10)
+    f.set_form(1)  # builds the tile packing and the BF16 copy
+    ci, cd = f.all_knn(10)
+    ri, rd = f.query(Q, 10)
+    assert torch.equal(pi, ci) and torch.equal(pd, cd)
+    assert torch.equal(qi, ri) and torch.equal(qd, rd)
+    assert f.counters()["chosen_form_plain_groups"] == 0
+    f.set_form(0)
+    ai, ad = f.all_knn(10)
+    assert torch.equal(pi, ai) and torch.equal(pd, ad)
