@@ -652,6 +652,7 @@ def run_serving(args, dev, n_requests=300):
         runs = {}
         mean_m = float(np.mean(sizes))
         for K in w.extra["k_set"]:
+            tuned = f.autotune(K)  # the query scan of the chosen form, among others
             serve.Server(f, slots=4).run(make_reqs(K, 1000)[:20])  # warm-up
             srv = serve.Server(f, slots=4, max_batch=8192)
             sat = serve.latency_summary(srv.run(make_reqs(K, 2000)))
@@ -665,6 +666,7 @@ def run_serving(args, dev, n_requests=300):
                 res["batches"] = srv.n_batches
                 r["load_%.2f" % load] = res
             r["missing_rate_sample_500"] = missing(K)
+            r["autotune"] = tuned
             # the plain FP32 form of the same forest (identical lists), saturated
             f.set_form(forest.FORM_PLAIN)
             srv = serve.Server(f, slots=4, max_batch=8192)

@@ -226,14 +226,18 @@ size_t rpf_workspace_bytes(const rpf_forest* f, int64_t m, int32_t K, int32_t fo
  *   plain form  : the tile region R (leaves of a tree starting in one region
  *                 of R positions form a tile; multiples of 32).
  *   chosen form : tile rows (128 or 256, where the leaf bound allows both),
- *                 Gram coordinates per tensor-core chunk, CTAs per SM.
+ *                 Gram coordinates per tensor-core chunk, CTAs per SM, and
+ *                 the query leaf scan (BF16 rows with the certified re-rank,
+ *                 or FP32 rows), timed with the first data points as
+ *                 queries; untuned, the chosen form scans BF16 rows.
  * The tile shape is kept for the rest of the process for forests of the same
  * dimension and leaf bound (later builds use it) and this forest's tiles are
  * rebuilt with it; the launch choice is kept per (dimension, tile rows, K
  * bucket).  A chosen-form forest the tensor-core kernel does not cover has
  * nothing to tune (chosen all 0).
- *   chosen : NULL or int32[4] receiving {Gram chunk, CTAs per SM, tile rows,
- *            tile region R} (0 where not tuned).
+ *   chosen : NULL or int32[5] receiving {Gram chunk, CTAs per SM, tile rows,
+ *            tile region R, query scan (1 = BF16, 0 = FP32, -1 = not
+ *            tuned)} (0 where not tuned).
  * Allocates a scratch list for the first trees; synchronises `stream`; no
  * other call may use the forest meanwhile.
  * Errors: RPF_EINVAL, RPF_ENOMEM, RPF_ECUDA.
@@ -263,6 +267,17 @@ int rpf_add_trees(rpf_forest* f, int32_t n_new, void* stream);
  * Errors: RPF_EINVAL, RPF_ENOMEM, RPF_ECUDA.
  */
 int rpf_set_form(rpf_forest* f, int32_t form, void* stream);
+
+/*
+ * rpf_set_query_scan -- which leaf scan rpf_query and rpf_query_static use
+ * in the chosen form: -1 = the one rpf_autotune found faster for the
+ * forest's (d, leaf bound, K) shape, or BF16 rows where it has not been run
+ * (the default); 0 = FP32 rows; 1 = BF16 rows with the certified exact
+ * re-rank (where K > 32 or the leaf bound exceeds 128 the FP32 scan runs).
+ * All give the same lists bit for bit.  Takes effect on later calls; no
+ * device work.  Errors: RPF_EINVAL.
+ */
+int rpf_set_query_scan(rpf_forest* f, int32_t mode);
 
 /* Release the forest and its device memory.  NULL is a no-op. */
 void rpf_free(rpf_forest* f);

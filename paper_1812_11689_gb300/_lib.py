@@ -81,6 +81,8 @@ def lib() -> ctypes.CDLL:
             L.rpf_add_trees.restype = ctypes.c_int
             L.rpf_set_form.argtypes = [_vp, _i32, _vp]
             L.rpf_set_form.restype = ctypes.c_int
+            L.rpf_set_query_scan.argtypes = [_vp, _i32]
+            L.rpf_set_query_scan.restype = ctypes.c_int
             L.rpf_free.argtypes = [_vp]
             L.rpf_free.restype = None
             L.rpf_forest_info.argtypes = [_vp] + [_vp] * 7
@@ -124,6 +126,7 @@ EXPORTED = ("rpf_default_params", "rpf_build", "rpf_build_shard", "rpf_all_knn",
             "rpf_all_knn_keys", "rpf_merge_keys", "rpf_all_knn_trees", "rpf_query",
             "rpf_query_static", "rpf_query_status", "rpf_add_trees", "rpf_autotune",
             "rpf_set_wait_limit", "rpf_wait_selftest", "rpf_debug_fail_alloc", "rpf_set_form",
+            "rpf_set_query_scan",
             "rpf_workspace_bytes", "rpf_free", "rpf_error_string", "rpf_forest_info",
             "rpf_forest_perm", "rpf_forest_leaves", "rpf_forest_nodes", "rpf_directions",
             "rpf_brute_knn", "rpf_trace_enable", "rpf_launch_count", "rpf_trace_read",

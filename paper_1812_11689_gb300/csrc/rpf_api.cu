@@ -294,6 +294,12 @@ int rpf_set_form(rpf_forest* f, int32_t form, void* stream) {
   return RPF_OK;
 }
 
+int rpf_set_query_scan(rpf_forest* f, int32_t mode) {
+  if (!f || mode < -1 || mode > 1) return RPF_EINVAL;
+  f->qscan_mode = mode;
+  return RPF_OK;
+}
+
 int rpf_autotune(rpf_forest* f, int32_t K, void* stream, int32_t* chosen) {
   if (!f || K < 1 || K > RPF_MAX_K) return RPF_EINVAL;
   return rpf_tc_autotune(f, K, (cudaStream_t)stream, chosen);

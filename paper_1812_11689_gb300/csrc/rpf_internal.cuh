@@ -272,6 +272,9 @@ struct rpf_forest {
   // tree groups of rpf_all_knn calls that asked for the chosen form and ran
   // the plain one (leaf bound > 256, K > 32, or a row too wide for the tile)
   int64_t plain_groups = 0;
+  // query leaf scan of the chosen form: -1 = the autotuner's pick (BF16 rows
+  // when untuned), 0 = FP32 rows, 1 = BF16 rows (rpf_set_query_scan)
+  int32_t qscan_mode = -1;
 
   // staging for host outputs of rpf_all_knn
   void* stage = nullptr;
@@ -356,5 +359,13 @@ int rpf_build_x16(rpf_forest* f, cudaStream_t s);
 bool rpf_qscan_bf_ok(const rpf_forest* f, int K);
 int rpf_qscan_bf(const rpf_forest* f, const float* Q, int64_t m, int K, const int32_t* qleaf,
                  uint2* cand, int* err, cudaStream_t s);
+// the query path in parts (rpf_knn.cu): routing, and the leaf scan in the
+// BF16 (bf) or FP32 form
+int rpf_route_dev(const rpf_forest* f, const float* Q, int64_t m, int32_t* qleaf, cudaStream_t s);
+int rpf_qscan_dev(const rpf_forest* f, const float* Q, int64_t m, int K, const int32_t* qleaf,
+                  uint2* cand, int* qerr, bool bf, cudaStream_t s);
+// the query scan the autotuner kept for (d, leaf bound, K): 1 = BF16 rows,
+// 0 = FP32 rows, -1 = not tuned
+int rpf_tuned_qscan(int d, int L, int K);
 void rpf_launch_directions(uint64_t seed, int32_t t, const uint64_t* keys_dev, int32_t n_keys,
                            int32_t j, int32_t d, double* out_dev, cudaStream_t s);

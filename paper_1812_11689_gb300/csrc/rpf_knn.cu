@@ -847,9 +847,43 @@ size_t rpf_query_ws(const rpf_forest* f, int64_t m, int K) {
          align256((size_t)m * K * 4) + align256((size_t)m * K * 4);
 }
 
+// Leaf ids of m queries in every tree (k_route_w) into qleaf (m x T).
+int rpf_route_dev(const rpf_forest* f, const float* Q, int64_t m, int32_t* qleaf, cudaStream_t s) {
+  const int T = f->prm.n_trees;
+  RPF_LAUNCH("k_route_w", s, k_route_w<<<nblk(m * T * RW, 256), 256, 0, s>>>(
+      Q, m, f->d, T, f->node_route, f->node_dir32, qleaf));
+  RPF_CU(cudaGetLastError());
+  return RPF_OK;
+}
+
+// Per-tree lists of the leaves in qleaf: the chosen form's BF16 scan when
+// `bf` (and the scan covers (f, K)), else the FP32 scan.
+int rpf_qscan_dev(const rpf_forest* f, const float* Q, int64_t m, int K, const int32_t* qleaf,
+                  uint2* cand, int* qerr, bool bf, cudaStream_t s) {
+  const int T = f->prm.n_trees;
+  const int dp = ((f->d + 3) & ~3) + 4;
+  const size_t qsm = (size_t)(QS_T + 1) * dp * 4;
+  if (bf && rpf_qscan_bf_ok(f, K)) {  // BF16 rows, certified exact re-rank
+    const int rc = rpf_qscan_bf(f, Q, m, K, qleaf, cand, qerr, s);
+    if (rc) return rc;
+  } else if (f->prm.leaf_max <= QS_T && (f->d % 4) == 0 && qsm <= 200 * 1024) {
+    RPF_CU(cudaFuncSetAttribute(k_qscan_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
+    RPF_LAUNCH("k_qscan_cta", s, k_qscan_cta<<<(unsigned)(m * T), QS_T, qsm, s>>>(
+        Q, m, f->d, dp, T, K, qleaf, f->node_tree, f->node_begin, f->node_len, f->perm, f->X,
+        f->n, cand, qerr, rpf_wait_limit_ns()));
+  } else {
+    RPF_KDISPATCH(K, launch_qscan, f, Q, m, K, qleaf, cand, s);
+  }
+  RPF_CU(cudaGetLastError());
+  return RPF_OK;
+}
+
 // Query scratch: [error word (RPF_QERR_BYTES)][leaf id per (query, tree)]
 // [per-tree candidate lists].  The error word is cleared here and set by a
-// bounded device wait that gave up, so it describes this call only.
+// bounded device wait that gave up, so it describes this call only.  The
+// chosen form scans the BF16 rows unless the forest asks for the FP32 scan,
+// or leaves the pick to the autotuner and it found the FP32 scan faster for
+// this shape (both give the same lists).
 int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t* idx,
                   float* dist, void* ws, size_t ws_bytes, cudaStream_t s) {
   const int T = f->prm.n_trees;
@@ -858,21 +892,11 @@ int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t
   RPF_CU(cudaMemsetAsync(qerr, 0, sizeof(int), s));
   int32_t* qleaf = (int32_t*)((char*)ws + RPF_QERR_BYTES);
   uint2* cand = (uint2*)((char*)qleaf + align256((size_t)m * T * 4));
-  RPF_LAUNCH("k_route_w", s, k_route_w<<<nblk(m * T * RW, 256), 256, 0, s>>>(
-      Q, m, f->d, T, f->node_route, f->node_dir32, qleaf));
-  const int dp = ((f->d + 3) & ~3) + 4;
-  const size_t qsm = (size_t)(QS_T + 1) * dp * 4;
-  if (f->prm.form == 1 && rpf_qscan_bf_ok(f, K)) {  // chosen form: BF16 rows, exact re-rank
-    const int rc = rpf_qscan_bf(f, Q, m, K, qleaf, cand, qerr, s);
-    if (rc) return rc;
-  } else if (f->prm.leaf_max <= QS_T && (f->d % 4) == 0 && qsm <= 200 * 1024) {
-    cudaFuncSetAttribute(k_qscan_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
-    RPF_LAUNCH("k_qscan_cta", s, k_qscan_cta<<<(unsigned)(m * T), QS_T, qsm, s>>>(
-        Q, m, f->d, dp, T, K, qleaf, f->node_tree, f->node_begin, f->node_len, f->perm, f->X,
-        f->n, cand, qerr, rpf_wait_limit_ns()));
-  } else {
-    RPF_KDISPATCH(K, launch_qscan, f, Q, m, K, qleaf, cand, s);
-  }
+  int rc = rpf_route_dev(f, Q, m, qleaf, s);
+  if (rc) return rc;
+  const bool bf = f->prm.form == 1 && (f->qscan_mode >= 0 ? f->qscan_mode == 1
+                                                           : rpf_tuned_qscan(f->d, f->prm.leaf_max, K) != 0);
+  if ((rc = rpf_qscan_dev(f, Q, m, K, qleaf, cand, qerr, bf, s))) return rc;
   if ((int64_t)T * K <= QM_MAX) {
     int N = 1;
     while (N < T * K) N <<= 1;

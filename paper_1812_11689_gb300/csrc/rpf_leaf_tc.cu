@@ -609,6 +609,8 @@ struct ShapeConf {
   int rows = 0, region = 0;
 };
 std::map<std::pair<int, int>, ShapeConf> g_shape;
+// query leaf scan per (d, leaf bound, K bucket): 1 = BF16 rows, 0 = FP32 rows
+std::map<std::tuple<int, int, int>, int> g_qscan;
 
 template <int KK, int ROWS>
 int launch_tc(const rpf_forest* f, int64_t tlo, int64_t thi, int K, int t0, uint2* cand,
@@ -689,6 +691,12 @@ int rpf_tuned_rows(int d, int L) {
   std::lock_guard<std::mutex> g(g_tune_mu);
   auto it = g_shape.find(std::make_pair(d, L));
   return it == g_shape.end() ? 0 : it->second.rows;
+}
+
+int rpf_tuned_qscan(int d, int L, int K) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_qscan.find(std::make_tuple(d, L, kk_of(K)));
+  return it == g_qscan.end() ? -1 : it->second;
 }
 
 bool rpf_tc_supported(const rpf_forest* f, int K) {
@@ -800,11 +808,15 @@ int time_best(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, Fn fn, float* best
 // Autotuner of the leaf tiles, timed on the forest's own tiles (its first
 // trees).  Plain form: the tile region R (multiples of 32 up to the cap).
 // Chosen form: tile rows (128 or 256 where the leaf bound allows both), Gram
-// coordinates per chunk, CTAs per SM.  Every candidate gives the same lists.
+// coordinates per chunk, CTAs per SM, and the query leaf scan (BF16 or FP32
+// rows).  Every candidate gives the same lists.
 // The tile shape is kept per (d, leaf bound) for later builds and applied to
 // this forest; the launch choice per (d, tile rows, K bucket).
 int rpf_tc_autotune(rpf_forest* f, int K, cudaStream_t s, int32_t* chosen) {
-  if (chosen) chosen[0] = chosen[1] = chosen[2] = chosen[3] = 0;
+  if (chosen) {
+    chosen[0] = chosen[1] = chosen[2] = chosen[3] = 0;
+    chosen[4] = -1;
+  }
   const int d = f->d, L = f->prm.leaf_max;
   const int g = std::min(f->prm.n_trees, 4);  // the tiles of the first trees
   uint2* cand = nullptr;
@@ -873,6 +885,41 @@ int rpf_tc_autotune(rpf_forest* f, int K, cudaStream_t s, int32_t* chosen) {
       chosen[1] = best.occ;
       chosen[2] = best_rows;
       chosen[3] = f->tile_region;
+    }
+    // the query leaf scan: BF16 rows with the certified re-rank against the
+    // FP32 rows, timed on the first (up to 4096) data points as queries
+    if (!rc && rpf_qscan_bf_ok(f, K)) {
+      const int T = f->prm.n_trees;
+      const int64_t mq = std::min<int64_t>(f->n, 4096);
+      int32_t* qleaf = nullptr;
+      uint2* qc = nullptr;
+      int* qe = nullptr;
+      if (rpf_alloc((void**)&qleaf, 4 * (size_t)mq * T, s) ||
+          rpf_alloc((void**)&qc, 8 * (size_t)mq * T * K, s) || rpf_alloc((void**)&qe, 4, s)) {
+        rc = RPF_ENOMEM;
+      } else {
+        rc = rpf_route_dev(f, f->X, mq, qleaf, s);
+        float ms_bf = INFINITY, ms_32 = INFINITY;
+        if (!rc)
+          rc = time_best(s, e0, e1, [&] {
+            return rpf_qscan_dev(f, f->X, mq, K, qleaf, qc, qe, true, s);
+          }, &ms_bf);
+        if (!rc)
+          rc = time_best(s, e0, e1, [&] {
+            return rpf_qscan_dev(f, f->X, mq, K, qleaf, qc, qe, false, s);
+          }, &ms_32);
+        if (!rc) {
+          const int pick = ms_bf < ms_32 ? 1 : 0;
+          {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_qscan[std::make_tuple(d, L, kk_of(K))] = pick;
+          }
+          if (chosen) chosen[4] = pick;
+        }
+      }
+      rpf_release(qleaf, s);
+      rpf_release(qc, s);
+      rpf_release(qe, s);
     }
   }
   cudaEventDestroy(e0);

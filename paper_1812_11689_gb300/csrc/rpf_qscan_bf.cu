@@ -23,7 +23,8 @@
 //      the K-th smallest d32 is <= U, and a point with D~_j - eps_j > U has
 //      d32_j > U: it cannot be among the K nearest.  The others (the
 //      shortlist) are re-ranked with the canonical FP32 d32 from their FP32
-//      rows and sorted as 64-bit keys (d32 bits << 32 | index).
+//      rows (staged with coalesced reads) and sorted as 64-bit keys (d32 bits
+//      << 32 | index).
 //   5. a shortlist longer than 32 (or any non-finite value) sends the leaf to
 //      the exact scan of all its FP32 rows (counted with the all-kNN
 //      rescans).
@@ -204,13 +205,39 @@ __global__ void __launch_bounds__(QB_T) k_qscan_bf(
   if (take) slist[base + __popc(bal & ((1u << lane) - 1u))] = tid;
   __syncthreads();
   if (C <= 32 && U < INFINITY) {
-    // 5. exact re-rank of the shortlist, one lane per point
+    // 5. exact re-rank of the shortlist: its FP32 rows are staged in the
+    // (now idle) BF16 row area, one warp per row (coalesced reads), then one
+    // lane per point runs the canonical chain from shared memory
+    float* fr = reinterpret_cast<float*>(qb_raw);
+    const int dpf = ((d + 3) & ~3) + 4;
+    for (int c = warp; c < C; c += QB_T / 32) {
+      const float* src = X + (int64_t)pid[slist[c]] * d;
+      for (int k = lane; k < d; k += 32) fr[c * dpf + k] = __ldg(src + k);
+    }
+    __syncthreads();
     if (tid < 32) {
       unsigned long long v = ~0ull;
       if (tid < C) {
         const int j = pid[slist[tid]];
-        v = ((unsigned long long)__float_as_uint(qb_d32(qv, X + (int64_t)j * d, d)) << 32) |
-            (unsigned)j;
+        const float* y = fr + tid * dpf;  // row stride an odd number of 16-byte units
+        float acc = 0.0f;
+        int k = 0;
+        if ((d & 3) == 0) {
+          for (; k < d; k += 4) {
+            const float4 v4 = *reinterpret_cast<const float4*>(y + k);
+            const float4 q4 = *reinterpret_cast<const float4*>(qv + k);
+            float e;
+            e = __fsub_rn(q4.x, v4.x); acc = __fmaf_rn(e, e, acc);
+            e = __fsub_rn(q4.y, v4.y); acc = __fmaf_rn(e, e, acc);
+            e = __fsub_rn(q4.z, v4.z); acc = __fmaf_rn(e, e, acc);
+            e = __fsub_rn(q4.w, v4.w); acc = __fmaf_rn(e, e, acc);
+          }
+        }
+        for (; k < d; ++k) {
+          const float e = __fsub_rn(qv[k], y[k]);
+          acc = __fmaf_rn(e, e, acc);
+        }
+        v = ((unsigned long long)__float_as_uint(acc) << 32) | (unsigned)j;
       }
       v = warp_sort64(v, tid);
       if (tid < K)

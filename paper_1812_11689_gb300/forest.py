@@ -164,16 +164,23 @@ class Forest:
         """rpf_autotune: time the leaf tiles' configurations on this forest
         (plain: tile region; chosen: tile rows, Gram chunk, CTAs per SM) and
         keep the fastest for forests of this shape."""
-        chosen = (ctypes.c_int32 * 4)()
+        chosen = (ctypes.c_int32 * 5)()
         check(_lib.lib().rpf_autotune(self._h, K, _stream_handle(stream), chosen),
               "rpf_autotune")
         return {"gram_chunk": chosen[0], "ctas_per_sm": chosen[1], "tile_rows": chosen[2],
-                "tile_region": chosen[3]}
+                "tile_region": chosen[3],
+                "query_scan": {1: "bf16", 0: "fp32", -1: None}[chosen[4]]}
 
     def set_form(self, form: int, stream=None) -> None:
         """rpf_set_form: switch between the plain and the chosen form."""
         check(_lib.lib().rpf_set_form(self._h, int(form), _stream_handle(stream)), "rpf_set_form")
         self.params.form = int(form)
+
+    def set_query_scan(self, mode) -> None:
+        """rpf_set_query_scan: the chosen form's query leaf scan; None = the
+        autotuner's pick, "fp32" or "bf16"."""
+        code = {None: -1, "fp32": 0, "bf16": 1}[mode]
+        check(_lib.lib().rpf_set_query_scan(self._h, code), "rpf_set_query_scan")
 
     def add_trees(self, n_new: int, stream=None) -> None:
         """rpf_add_trees: grow n_new more trees (the same forest that a build

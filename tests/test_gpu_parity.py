@@ -436,9 +436,14 @@ def test_autotune_picks_a_configuration_and_keeps_the_lists():
     X = synth.make("aniso20_d64", n=20000)
     c = gpu_forest(X, 4, 128, 5, seed=3, form=1)
     ci0, cd0 = c.all_knn(10)
+    Qd = torch.from_numpy(synth.queries("aniso20_d64", 400, stream=8)).cuda()
+    qi0, qd0 = c.query(Qd, 10)
     ch = c.autotune(10)
     assert ch["gram_chunk"] in (16, 32, 48, 64) and 1 <= ch["ctas_per_sm"] <= 4
     assert ch["tile_rows"] in (128, 256)
+    assert ch["query_scan"] in ("bf16", "fp32")
+    qi1, qd1 = c.query(Qd, 10)  # whichever scan was kept: the same lists
+    assert torch.equal(qi0, qi1) and torch.equal(qd0, qd1)
     ci1, cd1 = c.all_knn(10)
     assert torch.equal(ci0, ci1) and torch.equal(cd0, cd1)
     # a new forest of the same shape takes the tuned tile rows
@@ -488,11 +493,14 @@ def test_chosen_form_queries_bf16_scan_bit_exact(name, n, L, Ks):
     o = oracle.Forest(X, 5, L, 5, seed=0)
     Qd = torch.from_numpy(Q).cuda()
     for K in Ks:
-        ci, cd = c.query(Qd, K)
         pi, pd = p.query(Qd, K)
         oi, od = o.query(Q, K)
-        assert torch.equal(ci, pi) and torch.equal(cd, pd), K
-        assert np.array_equal(ci.cpu().numpy(), oi) and np.array_equal(cd.cpu().numpy(), od), K
+        assert np.array_equal(pi.cpu().numpy(), oi) and np.array_equal(pd.cpu().numpy(), od), K
+        # each scan of the chosen form, whatever an earlier autotune picked
+        for mode in ("bf16", "fp32", None):
+            c.set_query_scan(mode)
+            ci, cd = c.query(Qd, K)
+            assert torch.equal(ci, pi) and torch.equal(cd, pd), (K, mode)
 
 
 def test_chosen_form_queries_long_shortlist_falls_back_exactly():
@@ -506,6 +514,7 @@ def test_chosen_form_queries_long_shortlist_falls_back_exactly():
     Q = np.zeros((50, 64), np.float32)
     Q[1:] = 1e-3 * rng.standard_normal((49, 64)).astype(np.float32)
     c = gpu_forest(X, 3, 128, 3, form=1)
+    c.set_query_scan("bf16")
     o = oracle.Forest(X, 3, 128, 3, seed=0)
     before = c.counters()["bf16_fallback_rows"]
     ci, cd = c.query(torch.from_numpy(Q).cuda(), 10)
