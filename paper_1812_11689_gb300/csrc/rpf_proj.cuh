@@ -79,7 +79,8 @@ __device__ __forceinline__ void rpf_proj4(const float* __restrict__ X, int d, co
 // per 32-coordinate chunk (one coalesced 128-byte line per row) by cp.async
 // straight into a padded tile (row stride 36 floats, an odd number of 16-byte
 // units, so that the lanes' row reads fall in distinct banks); each lane then
-// runs its own point's chains from the tile, over k in order.  Gathering
+// runs its own point's chains from the tile (even and odd coordinates in
+// order, see rpf_tile_chunk).  Gathering
 // whole lines this way reaches about 4x the L2 bandwidth of one 16-byte load
 // per lane per row, and two tiles per warp let the next chunk's copy overlap
 // the current chunk's arithmetic.
@@ -117,34 +118,52 @@ __device__ __forceinline__ void rpf_stage_rows(const float* __restrict__ X, int 
   }
 }
 
+// Packed FP32 pair arithmetic (one instruction, two lanes of work each, each
+// half rounded exactly as the scalar operation would round it).
+__device__ __forceinline__ float2 rpf_sub2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 a, b, r;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+      "sub.rn.f32x2 r, a, b;\n\tmov.b64 {%0, %1}, r;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 rpf_fma2(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{\n\t.reg .b64 a, b, c, r;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+      "mov.b64 c, {%6, %7};\n\tfma.rn.f32x2 r, a, b, c;\n\tmov.b64 {%0, %1}, r;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+
 // Chains of the lane's row over coordinates [k0, k0 + kc) from the tile.
+// Every dot product (and the sum of squares) runs as two FP32 chains, one
+// over the even and one over the odd coordinates, in packed pair
+// instructions; the caller adds the halves.  Each half has at most d / 2
+// terms, so the computed value obeys the error bound of a d-term sequential
+// chain that the radius and the statistics bounds assume.
 template <int TG, int DC = RPF_TILE_DC>
 __device__ __forceinline__ void rpf_tile_chunk(const float* tile, int lane, int k0, int kc,
                                                const float* so, const float* sr, int d, int nj,
-                                               float (&acc)[TG], float& nn, bool want_nn) {
+                                               float2 (&acc)[TG], float2& nn, bool want_nn) {
   const float* xr = tile + lane * (DC + 4);
 #pragma unroll 4
   for (int k = 0; k < kc; k += 4) {
     const float4 x4 = *reinterpret_cast<const float4*>(xr + k);
     const float4 o4 = *reinterpret_cast<const float4*>(so + k0 + k);
-    const float e0 = __fsub_rn(x4.x, o4.x), e1 = __fsub_rn(x4.y, o4.y);
-    const float e2 = __fsub_rn(x4.z, o4.z), e3 = __fsub_rn(x4.w, o4.w);
+    const float2 e01 = rpf_sub2(make_float2(x4.x, x4.y), make_float2(o4.x, o4.y));
+    const float2 e23 = rpf_sub2(make_float2(x4.z, x4.w), make_float2(o4.z, o4.w));
     if (want_nn) {
-      nn = __fmaf_rn(e0, e0, nn);
-      nn = __fmaf_rn(e1, e1, nn);
-      nn = __fmaf_rn(e2, e2, nn);
-      nn = __fmaf_rn(e3, e3, nn);
+      nn = rpf_fma2(e01, e01, nn);
+      nn = rpf_fma2(e23, e23, nn);
     }
 #pragma unroll
     for (int q = 0; q < TG; ++q) {
       if (q < nj) {
         const float4 r4 = *reinterpret_cast<const float4*>(sr + q * d + k0 + k);
-        float a = acc[q];
-        a = __fmaf_rn(e0, r4.x, a);
-        a = __fmaf_rn(e1, r4.y, a);
-        a = __fmaf_rn(e2, r4.z, a);
-        a = __fmaf_rn(e3, r4.w, a);
-        acc[q] = a;
+        acc[q] = rpf_fma2(e23, make_float2(r4.z, r4.w),
+                          rpf_fma2(e01, make_float2(r4.x, r4.y), acc[q]));
       }
     }
   }
@@ -199,9 +218,9 @@ __device__ __forceinline__ void rpf_warp_project(const float* __restrict__ X, in
   }
   int cs = 0;  // tile of the unit being computed
   for (int i = 0; i < nbw; ++i) {
-    float acc[TG], nn = 0.0f;
+    float2 acc2[TG], nn2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int q = 0; q < TG; ++q) acc[q] = 0.0f;
+    for (int q = 0; q < TG; ++q) acc2[q] = make_float2(0.0f, 0.0f);
     for (int c = 0; c < nch; ++c) {
       stage_next(i);
       rpf_cp_commit();
@@ -209,11 +228,16 @@ __device__ __forceinline__ void rpf_warp_project(const float* __restrict__ X, in
       __syncwarp();
       if (g[0] >= 0)
         rpf_tile_chunk<TG, DC>(tiles + cs * TF, lane, c * DC, min(DC, d - c * DC), so, sr, d, nj,
-                               acc, nn, want_nn);
+                               acc2, nn2, want_nn);
       __syncwarp();  // before this tile takes a later unit
       cs = cs + 1 == NS ? 0 : cs + 1;
     }
-    if (g[0] >= 0) fin((bfirst + i * bstride) * 32 + lane, g[0], acc, nn, xv[0]);
+    if (g[0] >= 0) {
+      float acc[TG];
+#pragma unroll
+      for (int q = 0; q < TG; ++q) acc[q] = __fadd_rn(acc2[q].x, acc2[q].y);
+      fin((bfirst + i * bstride) * 32 + lane, g[0], acc, __fadd_rn(nn2.x, nn2.y), xv[0]);
+    }
 #pragma unroll
     for (int k = 0; k + 1 < NS; ++k) {
       g[k] = g[k + 1];
