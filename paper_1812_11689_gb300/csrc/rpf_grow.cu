@@ -1249,7 +1249,7 @@ int rpf_build_route(rpf_forest* f, cudaStream_t s) {
 
 // Phase B (rpf_subtree.cu)
 bool rpf_subtree_fits(int d, int ntry);
-int rpf_grow_subtrees(rpf_forest* fo, int64_t n_items, const int32_t* it_node,
+int rpf_grow_subtrees(rpf_forest* fo, int64_t n_items, const int32_t* ilen, const int32_t* it_node,
                       const int32_t* it_tree, const int32_t* it_begin, const int32_t* it_len,
                       const uint64_t* it_key, const int32_t* it_nbase, const int32_t* it_lbase,
                       float* p32, double* p64, unsigned long long* d_exact, int* d_err,
@@ -1699,7 +1699,7 @@ int rpf_grow(rpf_forest* fo, cudaStream_t s) {
       RPF_TRY(talloc((void**)&dfr_cnt, sizeof(int)));
       RPF_TRYCU(cudaMemsetAsync(dfr_cnt, 0, sizeof(int), s));
     }
-    RPF_TRY(rpf_grow_subtrees(fo, n_items, it_node, it_tree, it_begin, it_len, it_key, it_nbase,
+    RPF_TRY(rpf_grow_subtrees(fo, n_items, ilen.data(), it_node, it_tree, it_begin, it_len, it_key, it_nbase,
                               it_lbase, p32, p64, d_exact, d_err, dfr, dfr_cnt, dfr_cap, s));
     nodes_used = nrun;
     leaves_used = lrun;

@@ -34,6 +34,7 @@
 namespace {
 
 constexpr int kB = 128;  // 4 warps; 4 CTAs per SM hide each other's serial sections
+constexpr int kSmallB = 32;  // small subtrees: one warp per CTA, many CTAs per SM
 constexpr int kSubN = RPF_CHUNK;
 constexpr int kStack = 24;
 constexpr int kBandSel = 256;  // median rule: bands up to this size are selected by counting
@@ -42,12 +43,13 @@ constexpr int kDefCand = RPF_DEFER_CAND;  // candidates per extreme of a deferre
 // live in sT and sSide, which are contiguous and idle during the projection,
 // and in sTx, which follows them
 constexpr int kTDC = 16, kTStages = 2;
-constexpr size_t kTileBytes = (size_t)(kB / 32) * kTStages * 32 * (kTDC + 4) * 4;
-constexpr size_t kTileExtra = kTileBytes > 5 * (size_t)kSubN ? kTileBytes - 5 * (size_t)kSubN : 0;
-static_assert((4 * kSubN) % 16 == 0 && kSubN % 16 == 0, "sT, sSide and sTx are contiguous");
+__host__ __device__ constexpr size_t tile_bytes(int nt) {
+  return (size_t)(nt / 32) * kTStages * 32 * (kTDC + 4) * 4;
+}
 // the median rule's band list and histogram also live in sT (idle while the
-// median is selected)
-static_assert(12 * kBandSel + 4 * 256 <= 4 * kSubN, "band list and histogram fit sT");
+// median is selected): sT must hold them
+constexpr int kBandBytes = 12 * kBandSel + 4 * 256;
+static_assert(kBandBytes <= 4 * kSubN, "band list and histogram fit sT");
 
 struct SubState {
   uint64_t key;
@@ -78,17 +80,20 @@ struct SubLayout {
       sdtr, red, total;
 };
 
-__host__ __device__ inline SubLayout sub_layout(int d, int ntry, int TG) {
+// subn: the most points of a subtree (sP and sT hold one int per point, a
+// multiple of 16); nt: threads of the CTA
+__host__ __device__ inline SubLayout sub_layout(int d, int ntry, int TG, int nt, int subn) {
   SubLayout l{};
   size_t o = 0;
+  const size_t tb = tile_bytes(nt);
   l.sP = o;
-  o = align16(o + 4 * (size_t)kSubN);
+  o = align16(o + 4 * (size_t)subn);
   l.sT = o;
-  o = align16(o + 4 * (size_t)kSubN);
+  o = align16(o + 4 * (size_t)subn);
   l.sSide = o;
-  o = align16(o + (size_t)kSubN);
+  o = align16(o + (size_t)subn);
   l.sTx = o;
-  o = align16(o + kTileExtra);
+  o = align16(o + (tb > 5 * (size_t)subn ? tb - 5 * (size_t)subn : 0));
   l.r64 = o;
   o = align16(o + 8 * (size_t)ntry * d);
   l.r32 = o;
@@ -125,10 +130,24 @@ __host__ __device__ inline SubLayout sub_layout(int d, int ntry, int TG) {
   return l;
 }
 
-template <int TG>
-__global__ void __launch_bounds__(kB, 4) k_subtree(
-    const int32_t* it_node, const int32_t* it_tree, const int32_t* it_begin, const int32_t* it_len,
-    const uint64_t* it_key, const int32_t* it_nbase, const int32_t* it_lbase,
+// Subtree items: (root node id, tree, begin in the tree's permutation, point
+// count, root key, first node id and first leaf slot reserved for it).
+struct SubItems {
+  int32_t *node, *tree, *begin, *len;
+  uint64_t* key;
+  int32_t *nbase, *lbase;
+};
+
+// NT threads per CTA.  Items: it_idx[blockIdx.x] of `in` (one per CTA) when
+// it_count is null; else items 0 .. *it_count - 1 of `in`, CTAs taking them
+// in turn.  subn: capacity of the shared permutation segment.  defer_max > 0:
+// an inner node of at most defer_max points is not grown here; its segment is
+// written back, 2m - 2 node ids and m leaf slots are reserved for it, and it
+// becomes an item of `out` (slot from *out_cnt, at most out_cap).
+template <int TG, int NT>
+__global__ void __launch_bounds__(NT, NT == 32 ? 16 : 4) k_subtree(
+    SubItems in, const int32_t* it_idx, int n_items, const int* it_count, int subn,
+    int defer_max, SubItems out, int* out_cnt, int out_cap,
     const float* __restrict__ X, const float* __restrict__ xnorm, int64_t n, int64_t Tn, int d,
     int ntry, int L, uint64_t seed, int t_base, int exact_only, int median, int32_t* perm_final,
     float* p32,
@@ -138,7 +157,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     double* node_c, int32_t* leaf_tree, int32_t* leaf_begin, int32_t* leaf_len,
     unsigned long long* d_exact, int* d_err, int32_t* dfr, int* dfr_cnt, int dfr_cap) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const SubLayout lay = sub_layout(d, ntry, TG);
+  const SubLayout lay = sub_layout(d, ntry, TG, NT, subn);
   int32_t* sP = reinterpret_cast<int32_t*>(smraw + lay.sP);
   int32_t* sT = reinterpret_cast<int32_t*>(smraw + lay.sT);
   uint8_t* sSide = smraw + lay.sSide;
@@ -149,7 +168,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
   double* sS1 = reinterpret_cast<double*>(smraw + lay.sS1);
   double* sS2 = reinterpret_cast<double*>(smraw + lay.sS2);
   double* sA = reinterpret_cast<double*>(smraw + lay.sA);
-  double* sinv = reinterpret_cast<double*>(smraw + lay.sinv);
+  float* sinv = reinterpret_cast<float*>(smraw + lay.sinv);
   float* smn = reinterpret_cast<float*>(smraw + lay.smn);
   float* smx = reinterpret_cast<float*>(smraw + lay.smx);
   double* svh = reinterpret_cast<double*>(smraw + lay.svh);
@@ -161,28 +180,30 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
   __shared__ SubState S;
   __shared__ int st_nb[kStack], st_m[kStack], st_id[kStack];
   __shared__ uint64_t st_key[kStack];
-  __shared__ int wsc[kB / 32];
+  __shared__ int wsc[NT / 32];
   // median rule: a small band's keys and point indices, and the radix histogram
   unsigned long long* bnd_key = reinterpret_cast<unsigned long long*>(smraw + lay.sT);
   uint32_t* bnd_id = reinterpret_cast<uint32_t*>(smraw + lay.sT + 8 * kBandSel);
   int* mhist = reinterpret_cast<int*>(smraw + lay.sT + 12 * kBandSel);
 
-  const int it = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int t = it_tree[it];
-  const int m0 = it_len[it];
-  const int64_t pbase = (int64_t)t * n + it_begin[it];
-  for (int i = tid; i < m0; i += kB) sP[i] = perm_final[pbase + i];
+  const int nit = it_count ? *it_count : n_items;
+  for (int ii = blockIdx.x; ii < nit; ii += gridDim.x) {
+  const int it = it_idx ? it_idx[ii] : ii;
+  const int t = in.tree[it];
+  const int m0 = in.len[it];
+  const int64_t pbase = (int64_t)t * n + in.begin[it];
+  for (int i = tid; i < m0; i += NT) sP[i] = perm_final[pbase + i];
   if (tid == 0) {
     S.top = 1;
     st_nb[0] = 0;
     st_m[0] = m0;
-    st_id[0] = it_node[it];
-    st_key[0] = it_key[it];
-    S.next_id = it_nbase[it];
-    S.id_end = it_nbase[it] + 2 * m0 - 2;
-    S.next_leaf = it_lbase[it];
-    S.leaf_end = it_lbase[it] + m0;
+    st_id[0] = in.node[it];
+    st_key[0] = in.key[it];
+    S.next_id = in.nbase[it];
+    S.id_end = in.nbase[it] + 2 * m0 - 2;
+    S.next_leaf = in.lbase[it];
+    S.leaf_end = in.lbase[it] + m0;
     S.err = 0;
   }
   __syncthreads();
@@ -205,41 +226,61 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     const int nb = S.nb, m = S.m, id = S.id;
     const uint64_t key = S.key;
 
-    // 1. candidate directions, all in FP32 (r32), widened copy in r64: one
-    // warp per try draws the Box-Muller pairs, its lane 0 forms the
-    // sequential FP32 norm (the shuffle of 1/|g| orders the scaling after
-    // it), so only one block barrier is needed; 2. with it, the centre o =
-    // the node's first member
-    // the centre's row and norm are requested first, so their loads overlap
-    // the draws
+    if (m <= defer_max) {  // a small subtree: handed to the one-warp kernel
+      for (int i = tid; i < m; i += NT) perm_final[pbase + nb + i] = sP[nb + i];
+      if (tid == 0) {
+        const int nbase = S.next_id, lbase = S.next_leaf;
+        S.next_id += 2 * m - 2;
+        S.next_leaf += m;
+        const int slot = S.next_id > S.id_end || S.next_leaf > S.leaf_end ? out_cap
+                                                                           : atomicAdd(out_cnt, 1);
+        if (slot >= out_cap) {
+          S.err = 1;
+        } else {
+          out.node[slot] = id;
+          out.tree[slot] = t;
+          out.begin[slot] = in.begin[it] + nb;
+          out.len[slot] = m;
+          out.key[slot] = key;
+          out.nbase[slot] = nbase;
+          out.lbase[slot] = lbase;
+        }
+      }
+      __syncthreads();
+      continue;
+    }
+
+    // 1. candidate directions, all in FP32 (r32), widened copy in r64: the
+    // Box-Muller pairs of all tries are spread over the threads, thread j
+    // forms try j's sequential FP32 norm, then every value is scaled; 2. with
+    // it, the centre o = the node's first member (its row and norm are
+    // requested first, so their loads overlap the draws) and attempt 0's
+    // uniform of the split point
     const int og = sP[nb];
     const float* xo = X + (int64_t)og * d;
     float oreg = tid < d ? xo[tid] : 0.0f;
     const float on = xnorm[og];
-    for (int j = warp; j < ntry; j += kB / 32) {
-      float* g = r32 + j * d;
+    if (tid == NT - 1) S.u0 = rpf_u53(rpf_word(seed, RPF_TAG_SPLIT, (uint64_t)(t + t_base), key, 0, 0));
+    for (int w = tid; w < ntry * npairs; w += NT) {
+      const int j = w / npairs, i = w - j * npairs;
       const uint64_t hj = rpf_word_prefix(seed, RPF_TAG_DIR, (uint64_t)(t + t_base), key, (uint64_t)j);
-      for (int i = lane; i < npairs; i += 32) {
-        float g0, g1;
-        rpf_gauss_pair_h(hj, i, &g0, &g1);
-        g[2 * i] = g0;
-        if (2 * i + 1 < d) g[2 * i + 1] = g1;
-      }
-      __syncwarp();
-      float inv = 0.0f;
-      if (lane == 0) inv = rpf_inv_norm32(g, d);
-      inv = __shfl_sync(RPF_FULL, inv, 0);
-      for (int k = lane; k < d; k += 32) {
-        const float v = inv == 0.0f ? (k == 0 ? 1.0f : 0.0f) : __fmul_rn(g[k], inv);
-        g[k] = v;
-        r64[j * d + k] = (double)v;
-      }
+      float g0, g1;
+      rpf_gauss_pair_h(hj, i, &g0, &g1);
+      r32[j * d + 2 * i] = g0;
+      if (2 * i + 1 < d) r32[j * d + 2 * i + 1] = g1;
     }
-    // attempt 0's uniform of the split point, drawn by the last warp (it has
-    // the fewest tries to draw when nTry is not a multiple of the warps)
-    if (tid == kB - 32) S.u0 = rpf_u53(rpf_word(seed, RPF_TAG_SPLIT, (uint64_t)(t + t_base), key, 0, 0));
     if (tid < d) so[tid] = oreg;
-    for (int k = tid + kB; k < d; k += kB) so[k] = xo[k];
+    for (int k = tid + NT; k < d; k += NT) so[k] = xo[k];
+    __syncthreads();
+    if (tid < ntry) sinv[tid] = rpf_inv_norm32(r32 + tid * d, d);
+    __syncthreads();
+    for (int w = tid; w < ntry * d; w += NT) {
+      const int j = w / d, k = w - j * d;
+      const float inv = sinv[j];
+      const float v = inv == 0.0f ? (k == 0 ? 1.0f : 0.0f) : __fmul_rn(r32[w], inv);
+      r32[w] = v;
+      r64[w] = (double)v;
+    }
     __syncthreads();
 
     // 3. centred FP32 projections and statistics
@@ -260,7 +301,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
           // the partition scratch
           float* tb = reinterpret_cast<float*>(smraw + lay.sT) + warp * kTStages * 32 * (kTDC + 4);
           rpf_warp_project<TG, kTDC, kTStages>(
-              X, d, sP + nb, m, warp, kB / 32, tb, so, r32 + j0 * d, nj, j0 == 0, lane,
+              X, d, sP + nb, m, warp, NT / 32, tb, so, r32 + j0 * d, nj, j0 == 0, lane,
               j0 == 0 ? xnorm : nullptr,
               [&](int pos, int gid, const float(&acc)[TG], float nn, float xn) {
                 if (j0 == 0) {
@@ -277,11 +318,11 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
                 }
               });
         } else {
-          for (int u0 = 0; u0 * kB < m; u0 += 4) {
+          for (int u0 = 0; u0 * NT < m; u0 += 4) {
             int gid[4], pos[4];
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
-              pos[p] = tid + kB * (u0 + p);
+              pos[p] = tid + NT * (u0 + p);
               gid[p] = pos[p] < m ? sP[nb + pos[p]] : -1;
             }
             float acc[4][TG], nn[4];
@@ -315,7 +356,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
       // bounds of every try; with at most 32 tries warp 0 holds them all
       // and certifies right after (a warp sync instead of a block barrier)
       const double inv_m = 1.0 / (double)m;
-      for (int j = tid; j < ntry; j += kB) {
+      for (int j = tid; j < ntry; j += NT) {
         rpf_try_bounds(m, inv_m, sS1[j], sS2[j], sA[j], (double)on, radmax, __fsqrt_ru(rad2),
                        &svh[j], &slo[j], &shi[j]);
         // the deferred split point's interval for every try, in parallel
@@ -378,7 +419,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
       const float tl = S.dtl, tr = S.dtr, lo = S.wlo, hi = S.whi;
       const float* p = p32 + (int64_t)w * Tn + pbase + nb;
       int und = 0;
-      for (int i = tid; i < m; i += kB) {
+      for (int i = tid; i < m; i += NT) {
         const float v = p[i];
         sSide[i] = (uint8_t)(v < tl ? 1 : 0);
         und |= (v >= tl && v < tr) ? 1 : 0;
@@ -422,7 +463,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     if (S.exact) {
       // canonical FP64 projections and statistics
       const unsigned long long mask = S.cmask;
-      for (int i = tid; i < m; i += kB) {
+      for (int i = tid; i < m; i += NT) {
         const float* x = X + (int64_t)sP[nb + i] * d;
         for (int j = 0; j < ntry; ++j)
           if ((mask >> j) & 1ull) p64[(int64_t)j * Tn + pbase + nb + i] = rpf_p64(x, r64 + j * d, d);
@@ -474,7 +515,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
       const float* p = p32 + (int64_t)w * Tn + pbase + nb;
       if (tid == 0) S.ncand = 0;
       __syncthreads();
-      for (int i = tid; i < m; i += kB) {
+      for (int i = tid; i < m; i += NT) {
         const float v = p[i];
         const int code = (v <= lo ? 1 : 0) | (v >= hi ? 2 : 0);
         if (code) {
@@ -505,7 +546,8 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
           S.a = rpf_dkey_inv(ak);
           S.b = rpf_dkey_inv(bk);
         }
-      } else if (warp == 1) {
+      }
+      if (warp == (NT > 32 ? 1 : 0)) {
         // b_w = r_w . o in FP64 (any order: the radius covers it)
         double acc = 0.0;
         for (int k = lane; k < d; k += 32) acc = __fma_rn((double)so[k], r64[w * d + k], acc);
@@ -548,7 +590,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
           float lo, hi;
           rpf_med_band(S.mfk, S.rad, &lo, &hi);
           int cnt = 0;
-          for (int i = tid; i < m; i += kB) {
+          for (int i = tid; i < m; i += NT) {
             const float v = qj[i];
             if (v < lo) {
               ++cnt;
@@ -567,7 +609,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
           __syncthreads();
           if (tid == 0) {
             int t = 0;
-            for (int u = 0; u < kB / 32; ++u) t += wsc[u];
+            for (int u = 0; u < NT / 32; ++u) t += wsc[u];
             S.mrank = (m >> 1) - t;
             S.mlo = lo;
             S.mhi = hi;
@@ -578,7 +620,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
             // a small band: the element with exactly mrank smaller (key,
             // index) pairs in it, by counting (the pairs are distinct)
             const int r = S.mrank;
-            for (int e = tid; e < nc; e += kB) {
+            for (int e = tid; e < nc; e += NT) {
               const unsigned long long k = bnd_key[e];
               const uint32_t id = bnd_id[e];
               int below = 0;
@@ -593,13 +635,13 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
             break;
           }
         }
-        for (int b = tid; b < 256; b += kB) mhist[b] = 0;
+        for (int b = tid; b < 256; b += NT) mhist[b] = 0;
         __syncthreads();
         const uint32_t pf = S.mfk;
         const unsigned long long pk = S.mkey;
         const uint32_t pid = S.mid;
         const float lo = S.mlo, hi = S.mhi;
-        for (int i = tid; i < m; i += kB) {
+        for (int i = tid; i < m; i += NT) {
           int dig;
           bool match;
           if (pass < 4) {
@@ -659,7 +701,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
       const float tl = S.tl, tr = S.tr;
       if (tid == 0) S.ncand = 0;
       __syncthreads();
-      for (int i = tid; i < m; i += kB) {
+      for (int i = tid; i < m; i += NT) {
         int left;
         if (flag) {
           left = i < (m >> 1);
@@ -705,7 +747,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
       // stable partition from one block-wide scan: thread t takes the run
       // [t per, (t + 1) per) of positions (per odd, so the runs' shared-
       // memory reads fall in distinct banks); E = lefts before a position
-      const int per = ((m + kB - 1) / kB) | 1;
+      const int per = ((m + NT - 1) / NT) | 1;
       const int v0 = min(m, tid * per), v1 = min(m, v0 + per);
       int cnt = 0;
       for (int i = v0; i < v1; ++i) cnt += sSide[i];
@@ -719,7 +761,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
       __syncthreads();
       int E = x - cnt, nl = 0;
 #pragma unroll
-      for (int u = 0; u < kB / 32; ++u) {
+      for (int u = 0; u < NT / 32; ++u) {
         const int w = wsc[u];
         if (u < warp) E += w;
         nl += w;
@@ -731,7 +773,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
       }
       if (tid == 0) S.nl = nl;
       __syncthreads();
-      for (int i = tid; i < m; i += kB) sP[nb + i] = sT[nb + i];
+      for (int i = tid; i < m; i += NT) sP[nb + i] = sT[nb + i];
       __syncthreads();
     }
 
@@ -745,7 +787,7 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
         S.next_id += 2;
         node_left[id] = idL;
         node_right[id] = idR;
-        const int bL = it_begin[it] + nb, bR = bL + nl;
+        const int bL = in.begin[it] + nb, bR = bL + nl;
         node_key[idL] = rpf_child_key(key, 0);
         node_key[idR] = rpf_child_key(key, 1);
         node_tree[idL] = node_tree[idR] = t;
@@ -798,12 +840,14 @@ __global__ void __launch_bounds__(kB, 4) k_subtree(
     __syncthreads();
     if (S.err) break;
     if (S.leafL)
-      for (int i = tid; i < S.nl; i += kB) perm_final[pbase + nb + i] = sP[nb + i];
+      for (int i = tid; i < S.nl; i += NT) perm_final[pbase + nb + i] = sP[nb + i];
     if (S.leafR)
-      for (int i = tid; i < m - S.nl; i += kB) perm_final[pbase + nb + S.nl + i] = sP[nb + S.nl + i];
+      for (int i = tid; i < m - S.nl; i += NT) perm_final[pbase + nb + S.nl + i] = sP[nb + S.nl + i];
     __syncthreads();
   }
   if (tid == 0 && S.err) atomicExch(d_err, 1);
+  __syncthreads();  // before the next item takes the shared state
+  }
 }
 
 // The deferred split points, after growth (node tables compacted, chosen
@@ -852,10 +896,42 @@ int rpf_split_deferred(rpf_forest* fo, const int32_t* dfr, const int* dfr_cnt, i
 }
 
 bool rpf_subtree_fits(int d, int ntry) {
-  return sub_layout(d, ntry, 8).total <= 200 * 1024;
+  return sub_layout(d, ntry, 8, kB, kSubN).total <= 200 * 1024;
 }
 
-int rpf_grow_subtrees(rpf_forest* fo, int64_t n_items, const int32_t* it_node,
+namespace {
+
+// Largest subtree (points) given to the one-warp kernel: above the leaf
+// bound (so that it is an inner node), at most 1024 points (32 positions per
+// lane in the statistics), and at least 1024 under the median rule (its
+// band list lives in sT); 0: none.
+int small_subtree_max(int L, int median) {
+  const int m = median ? 1024 : ((std::max(512, 2 * L) + 15) & ~15);
+  return m > 1024 || m <= L ? 0 : m;
+}
+
+__global__ void k_seed_small(int n_small, const int32_t* idx, SubItems in, SubItems out, int* cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *cnt = n_small;
+  if (i >= n_small) return;
+  const int j = idx[i];
+  out.node[i] = in.node[j];
+  out.tree[i] = in.tree[j];
+  out.begin[i] = in.begin[j];
+  out.len[i] = in.len[j];
+  out.key[i] = in.key[j];
+  out.nbase[i] = in.nbase[j];
+  out.lbase[i] = in.lbase[j];
+}
+
+}  // namespace
+
+// Phase B: items of more than S points (S = small_subtree_max) are grown by
+// the four-warp kernel, which hands every node of at most S points to the
+// one-warp kernel (items of at most S points go there directly).  Both
+// reserve node ids and leaf slots by subtree size, so the forest does not
+// depend on the order in which the small subtrees are taken.
+int rpf_grow_subtrees(rpf_forest* fo, int64_t n_items, const int32_t* ilen, const int32_t* it_node,
                       const int32_t* it_tree, const int32_t* it_begin, const int32_t* it_len,
                       const uint64_t* it_key, const int32_t* it_nbase, const int32_t* it_lbase,
                       float* p32, double* p64, unsigned long long* d_exact, int* d_err,
@@ -865,19 +941,101 @@ int rpf_grow_subtrees(rpf_forest* fo, int64_t n_items, const int32_t* it_node,
   const int exact_only = fo->prm.growth == 1 ? 1 : 0;
   const int median = fo->prm.split_rule == 1 ? 1 : 0;
   const int TG = ntry <= 5 ? ntry : 8;
-  const size_t smem = sub_layout(d, ntry, TG).total;
+  const size_t smem = sub_layout(d, ntry, TG, kB, kSubN).total;
   if (smem > 200 * 1024) return RPF_EINVAL;
-#define RPF_SUB(TGV)                                                                              \
-  do {                                                                                            \
-    cudaFuncSetAttribute(k_subtree<TGV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    RPF_LAUNCH("k_subtree", s, k_subtree<TGV><<<(unsigned)n_items, kB, smem, s>>>(                \
-        it_node, it_tree, it_begin, it_len, it_key, it_nbase, it_lbase, fo->X, fo->xnorm, n, Tn,  \
-        d, ntry, L, fo->prm.seed, fo->t_base, exact_only, median, fo->perm, p32, p64,            \
-        fo->node_key,                                                                             \
-        fo->node_tree,                                                                            \
-        fo->node_begin, fo->node_len, fo->node_left, fo->node_right, fo->node_jstar,              \
-        fo->node_flag, fo->node_c, fo->leaf_tree, fo->leaf_begin, fo->leaf_len, d_exact, d_err,   \
-        dfr, dfr_cnt, dfr_cap));                                                                  \
+  int S = small_subtree_max(L, median);
+  const size_t smem_s = S ? sub_layout(d, ntry, TG, kSmallB, S).total : 0;
+  if (smem_s > 48 * 1024) S = 0;
+
+  std::vector<int32_t> big, small;
+  int64_t big_pts = 0;
+  for (int64_t i = 0; i < n_items; ++i) {
+    if (ilen[i] > S) {
+      big.push_back((int32_t)i);
+      big_pts += ilen[i];
+    } else {
+      small.push_back((int32_t)i);
+    }
+  }
+  // deferred nodes are disjoint segments of more than L points
+  const int64_t cap = S ? (int64_t)small.size() + big_pts / (L + 1) + 1 : 0;
+  if (cap >= ((int64_t)1 << 31)) return RPF_EINVAL;
+  SubItems in{const_cast<int32_t*>(it_node), const_cast<int32_t*>(it_tree),
+              const_cast<int32_t*>(it_begin), const_cast<int32_t*>(it_len),
+              const_cast<uint64_t*>(it_key),  const_cast<int32_t*>(it_nbase),
+              const_cast<int32_t*>(it_lbase)};
+  SubItems sm{};
+  int32_t *d_big = nullptr, *d_small = nullptr;
+  int* sm_cnt = nullptr;
+  void* bufs[10] = {};
+  auto release_all = [&]() {
+    for (void* p : bufs) rpf_release(p, s);
+  };
+#define SUB_CU(call)                  \
+  do {                                \
+    cudaError_t e_ = (call);          \
+    if (e_ != cudaSuccess) {          \
+      release_all();                  \
+      return rpf_cuda_err(e_);        \
+    }                                 \
+  } while (0)
+  int rc = RPF_OK;
+  if (!big.empty()) rc = rpf_alloc((void**)&d_big, 4 * big.size(), s);
+  bufs[0] = d_big;
+  if (!rc && S) {
+    rc = rpf_alloc((void**)&d_small, 4 * std::max<size_t>(small.size(), 1), s);
+    bufs[1] = d_small;
+    int32_t** f32[6] = {&sm.node, &sm.tree, &sm.begin, &sm.len, &sm.nbase, &sm.lbase};
+    for (int k = 0; k < 6 && !rc; ++k) {
+      rc = rpf_alloc((void**)f32[k], 4 * (size_t)cap, s);
+      bufs[2 + k] = *f32[k];
+    }
+    if (!rc) rc = rpf_alloc((void**)&sm.key, 8 * (size_t)cap, s);
+    bufs[8] = sm.key;
+    if (!rc) rc = rpf_alloc((void**)&sm_cnt, sizeof(int), s);
+    bufs[9] = sm_cnt;
+  }
+  if (rc) {
+    release_all();
+    return rc;
+  }
+  if (!big.empty())
+    SUB_CU(cudaMemcpyAsync(d_big, big.data(), 4 * big.size(), cudaMemcpyHostToDevice, s));
+  if (S) {
+    if (!small.empty())
+      SUB_CU(cudaMemcpyAsync(d_small, small.data(), 4 * small.size(), cudaMemcpyHostToDevice, s));
+    const int ns = (int)small.size();
+    RPF_LAUNCH("k_seed_small", s, k_seed_small<<<(unsigned)(ns / 256 + 1), 256, 0, s>>>(
+        ns, d_small, in, sm, sm_cnt));
+  }
+  // (copies from pageable memory have read their source when they return)
+  int dev = 0, n_sm = 1, occ = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+#define RPF_SUB(TGV)                                                                               \
+  do {                                                                                             \
+    SUB_CU(cudaFuncSetAttribute(k_subtree<TGV, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                (int)smem));                                                       \
+    if (!big.empty())                                                                              \
+      RPF_LAUNCH("k_subtree", s, k_subtree<TGV, kB><<<(unsigned)big.size(), kB, smem, s>>>(        \
+          in, d_big, (int)big.size(), nullptr, kSubN, S, sm, sm_cnt, (int)cap, fo->X, fo->xnorm, n, \
+          Tn, d, ntry, L, fo->prm.seed, fo->t_base, exact_only, median, fo->perm, p32, p64,       \
+          fo->node_key, fo->node_tree, fo->node_begin, fo->node_len, fo->node_left,                \
+          fo->node_right, fo->node_jstar, fo->node_flag, fo->node_c, fo->leaf_tree,               \
+          fo->leaf_begin, fo->leaf_len, d_exact, d_err, dfr, dfr_cnt, dfr_cap));                  \
+    if (S) {                                                                                       \
+      SUB_CU(cudaFuncSetAttribute(k_subtree<TGV, kSmallB>,                                         \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s));      \
+      SUB_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_subtree<TGV, kSmallB>,          \
+                                                           kSmallB, smem_s));                      \
+      const int64_t grid = std::min<int64_t>((int64_t)std::max(occ, 1) * n_sm, cap);             \
+      RPF_LAUNCH("k_subtree_w", s, k_subtree<TGV, kSmallB><<<(unsigned)grid, kSmallB, smem_s, s>>>( \
+          sm, nullptr, 0, sm_cnt, S, 0, sm, sm_cnt, 0, fo->X, fo->xnorm, n, Tn, d, ntry, L,       \
+          fo->prm.seed, fo->t_base, exact_only, median, fo->perm, p32, p64, fo->node_key,         \
+          fo->node_tree, fo->node_begin, fo->node_len, fo->node_left, fo->node_right,             \
+          fo->node_jstar, fo->node_flag, fo->node_c, fo->leaf_tree, fo->leaf_begin, fo->leaf_len, \
+          d_exact, d_err, dfr, dfr_cnt, dfr_cap));                                                 \
+    }                                                                                              \
   } while (0)
   switch (TG) {
     case 1: RPF_SUB(1); break;
@@ -888,6 +1046,8 @@ int rpf_grow_subtrees(rpf_forest* fo, int64_t n_items, const int32_t* it_node,
     default: RPF_SUB(8); break;
   }
 #undef RPF_SUB
+#undef SUB_CU
+  release_all();
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? RPF_OK : rpf_cuda_err(e);
 }
