@@ -200,6 +200,14 @@ class Clocks:
 
 
 SUBTREE_MAX = 4096          # nodes of at most this many points grow CTA-locally
+TC_BIG_MIN = 12             # leaves of at least this many points take the tensor path
+
+
+def small_subtree_max(L, median):
+    """Largest subtree the library grows with one warp per CTA (k_subtree_w):
+    above the leaf bound, at most 1024 points, 1024 under the median rule."""
+    m = 1024 if median else (max(512, 2 * L) + 15) // 16 * 16
+    return 0 if (m > 1024 or m <= L) else m
 T_GRID = (40, 48, 56, 64, 72, 80, 88, 96, 104, 112, 120, 128)  # nested ensembles swept
 FP32_LANES = 152 * 128      # FP32 lanes of a GB300 (152 SMs x 128)
 BF16_TFLOPS = (1900.0, "fallback (dense BF16, one earlier GB300 measurement)")
@@ -239,7 +247,8 @@ def work_model(fo, w, n):
     Growth: every point of an internal node is projected once per level; its
     X row (4d B) is the minimum read.  Phase A (nodes > 4096 points) also
     reads perm and the point norm and writes nTry FP32 projections; phase B
-    reads perm and writes the final permutation once per subtree.  Leaf
+    reads perm and writes the final permutation once per subtree (the
+    four-warp kernel writes back the segments it hands to the one-warp one).  Leaf
     tiles: every point's row once per tree plus its perm entry and its
     per-tree top-K list (8K B); FLOPs 2 d m^2 per leaf of m points.  Merge:
     T per-tree lists in, the final list out.
@@ -249,16 +258,26 @@ def work_model(fo, w, n):
     internal = nd["left"] >= 0
     A = internal & (ln > SUBTREE_MAX)
     B = internal & (ln <= SUBTREE_MAX)
-    kids = np.concatenate([nd["left"][A], nd["right"][A]])
-    kids = kids[kids >= 0]
-    rb = int(ln[kids][(ln[kids] <= SUBTREE_MAX) & internal[kids]].sum())
-    if n <= SUBTREE_MAX and n > w.leaf_max:  # every root is a subtree root
-        rb += n * fo.info()["n_trees"]
+    Sw = small_subtree_max(w.leaf_max, fo.params.split_rule == 1)
+    Bw = B & (ln <= Sw)  # grown by the one-warp kernel
+    Bb = B & ~Bw
+    # subtree roots: the perm segment is read once and written once (final
+    # permutation, or handed over to the one-warp kernel)
+    par = np.full(len(ln), SUBTREE_MAX + 1, np.int64)
+    for side in ("left", "right"):
+        ch = nd[side][internal]
+        ok = ch >= 0
+        par[ch[ok]] = ln[internal][ok]
+    handed = Bw & (par > Sw) & (par <= SUBTREE_MAX)
+    rb = 8 * int(ln[Bb & (par > SUBTREE_MAX)].sum()) + 4 * int(ln[handed].sum())
+    rw = 8 * int(ln[Bw & (par > Sw)].sum())
     pl_a, pl_b = int(ln[A].sum()), int(ln[B].sum())
+    pl_bb, pl_bw = int(ln[Bb].sum()), int(ln[Bw].sum())
     leaf_len = ln[~internal]
     d, T, K, nt = w.d, fo.info()["n_trees"], w.k, w.n_try
     return {
-        "k_subtree": {"bytes": pl_b * (4 * d + 4) + rb * 8},
+        "k_subtree": {"bytes": pl_bb * (4 * d + 4) + rb},
+        "k_subtree_w": {"bytes": pl_bw * (4 * d + 4) + rw},
         "k_proj_a": {"bytes": pl_a * (4 * d + 4 + 4 + 4 * nt)},
         "k_side_count": {"bytes": pl_a * (4 + 4 + 1)},
         "k_scatter": {"bytes": pl_a * (1 + 4 + 4)},
@@ -267,9 +286,9 @@ def work_model(fo, w, n):
         "k_leaf_tc": {"bytes": n * T * (4 * d + 4 + 8 * K),
                       "flops": 2 * d * int((leaf_len ** 2).sum()),
                       "tensor_flops": 3 * 2 * ((d + 15) // 16 * 16)
-                      * int((leaf_len[leaf_len > 33] ** 2).sum())},
+                      * int((leaf_len[(leaf_len >= TC_BIG_MIN) & (leaf_len > K + 1)] ** 2).sum())},
         "k_merge": {"bytes": n * (T * 8 * K + 8 * K)},
-        "_point_levels": {"phase_a": pl_a, "phase_b": pl_b,
+        "_point_levels": {"phase_a": pl_a, "phase_b": pl_b, "phase_b_one_warp": pl_bw,
                           "leaf_m2_per_point_per_tree": float((leaf_len ** 2).sum()) / (n * T)},
     }
 
@@ -322,7 +341,7 @@ def rooflines(trace, work, hbm_peak, peak_kind, steps, workload):
                                 "unit": "TFLOP/s", "frac": round(tf / bp, 5),
                                 "peak_source": bsrc,
                                 "flops": "3 BF16 products (split hi/lo) x 2 d16 m^2 per "
-                                         "leaf of more than 33 points"}
+                                         "leaf of at least 12 points and more than K + 1"}
         if "flops" in work[k]:
             fl = work[k]["flops"] * steps / t["launches"] / (ms_launch * 1e-3) / 1e12
             r["fp32_alu"] = {"achieved": round(fl, 2), "peak": round(fp32_peak, 1),

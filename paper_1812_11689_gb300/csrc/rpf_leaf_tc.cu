@@ -11,8 +11,9 @@
 //   1. rows are staged in shared memory by bulk copies (TMA engine, mbarrier)
 //      when a row is a 16-byte multiple (d % 4 == 0), else by warp loads;
 //      leaf boundaries come from a per-tree bitmask of leaf starts.
-//   2. Leaves of at most TC_SLOTS + 1 points ("small") need no arithmetic
-//      shortcut: every row offers all of its leaf to the exact re-rank.
+//   2. Leaves of fewer than TC_BIG_MIN points, or of at most K + 1 ("small"),
+//      need no arithmetic shortcut: every row offers all of its leaf to the
+//      exact re-rank.
 //   3. Rows of larger leaves are centred on their leaf's FP32 mean (y = x - c)
 //      and split into BF16 pairs y ~ hi + lo; G = hi hi^T + hi lo^T + lo hi^T
 //      is accumulated by tcgen05.mma (kind::f16, M = 128, N = rows padded to
@@ -65,7 +66,8 @@
                           // slot accesses fall in distinct banks
 #define TC_SEG 4096       // packing segment (positions) per thread
 #define TC_SEG_TILES 72   // >= 2 (TC_SEG + 128) / 128 + 1 tiles per segment
-#define TC_MAX_BIG 8      // leaves of > TC_SLOTS + 1 points in one tile (<= 3)
+#define TC_BIG_MIN 12     // leaves of at least this many points take the tensor path
+static_assert(TC_BIG_MIN >= 2 && TC_BIG_MIN <= TC_SLOTS + 2, "a small leaf fits the slots");
 
 namespace {
 
@@ -253,13 +255,14 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
   const size_t a_off = (((size_t)ROWS * dp * 4) + 1023) & ~(size_t)1023;
   __nv_bfloat16* Ahi = reinterpret_cast<__nv_bfloat16*>(smraw + a_off);
   __nv_bfloat16* Alo = Ahi + ROWS * KC;
-  float* cen = reinterpret_cast<float*>(Alo + ROWS * KC);  // TC_MAX_BIG x d4
-  unsigned char* slots = reinterpret_cast<unsigned char*>(cen + TC_MAX_BIG * d4);
+  constexpr int MAXBIG = ROWS / TC_BIG_MIN + 1;  // large leaves in one tile
+  float* cen = reinterpret_cast<float*>(Alo + ROWS * KC);  // MAXBIG x d4
+  unsigned char* slots = reinterpret_cast<unsigned char*>(cen + MAXBIG * d4);
   __shared__ float nrm[ROWS], ynm[ROWS];
   __shared__ int prow_s[ROWS], big_of_start[ROWS];
   __shared__ uint32_t wmask[ROWS / 32];
-  __shared__ unsigned nmax_bits[TC_MAX_BIG];
-  __shared__ int big_lb[TC_MAX_BIG], big_le[TC_MAX_BIG], nbig;
+  __shared__ unsigned nmax_bits[MAXBIG];
+  __shared__ int big_lb[MAXBIG], big_le[MAXBIG], nbig;
   __shared__ __align__(8) uint64_t bar_tma, bar_mma;
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
       nbig = 0;
       rpf_mbar_arrive_expect_tx(&bar_tma, bulk ? (uint32_t)rows * (uint32_t)d * 4u : 0u);
     }
-    if (tid < TC_MAX_BIG) nmax_bits[tid] = 0u;
+    if (tid < MAXBIG) nmax_bits[tid] = 0u;
     __syncthreads();
     if (bulk) {
       for (int q = tid; q < rows; q += ROWS)
@@ -330,9 +333,9 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
     }
     const int m = le - lb;
     const bool live = r < rows;
-    const bool big = live && m - 1 > TC_SLOTS;
+    const bool big = live && m >= TC_BIG_MIN && m - 1 > K;
     if (big && r == lb) {
-      const int sidx = atomicAdd(&nbig, 1);  // at most ROWS / 34 leaves of > 33 rows
+      const int sidx = atomicAdd(&nbig, 1);  // at most ROWS / TC_BIG_MIN large leaves
       big_of_start[r] = sidx;
       big_lb[sidx] = lb;
       big_le[sidx] = le;
@@ -567,7 +570,7 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
 size_t tc_need(int d, int dp, int rows, int KC) {
   const int d4 = (d + 3) & ~3;
   const size_t a_off = (((size_t)rows * dp * 4) + 1023) & ~(size_t)1023;
-  return a_off + (size_t)2 * rows * KC * 2 + (size_t)TC_MAX_BIG * d4 * 4 +
+  return a_off + (size_t)2 * rows * KC * 2 + (size_t)(rows / TC_BIG_MIN + 1) * d4 * 4 +
          (size_t)rows * TC_SLOT_STRIDE;
 }
 
