@@ -107,6 +107,20 @@ struct Top64 {
   }
 };
 
+// D~ = (n_r + n_c) - 2 G_rc for the eight columns c0 .. c0 + 7 (c0 a multiple
+// of 8; nrm has room for them), in packed pair instructions
+__device__ __forceinline__ void tc_dist8(const float (&g)[8], float nr, const float* nrm, int c0,
+                                         float (&D)[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    const float2 nc = *reinterpret_cast<const float2*>(nrm + c0 + j);
+    const float2 s = rpf_add2(make_float2(nr, nr), nc);
+    const float2 v = rpf_fma2(make_float2(-2.0f, -2.0f), make_float2(g[j], g[j + 1]), s);
+    D[j] = v.x;
+    D[j + 1] = v.y;
+  }
+}
+
 __device__ __forceinline__ unsigned long long key64(float d32, int idx) {
   return ((unsigned long long)__float_as_uint(d32) << 32) | (unsigned)idx;
 }
@@ -258,7 +272,8 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
   constexpr int MAXBIG = ROWS / TC_BIG_MIN + 1;  // large leaves in one tile
   float* cen = reinterpret_cast<float*>(Alo + ROWS * KC);  // MAXBIG x d4
   unsigned char* slots = reinterpret_cast<unsigned char*>(cen + MAXBIG * d4);
-  __shared__ float nrm[ROWS], ynm[ROWS];
+  __shared__ __align__(16) float nrm[ROWS];
+  __shared__ float ynm[ROWS];
   __shared__ int prow_s[ROWS], big_of_start[ROWS];
   __shared__ uint32_t wmask[ROWS / 32];
   __shared__ unsigned nmax_bits[MAXBIG];
@@ -283,18 +298,31 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
   bool ok = true, tma_pending = false, mma_pending = false;
   const int r = tid;
 
-  for (int64_t tile = tlo + blockIdx.x; tile < thi && ok; tile += gridDim.x) {
-    const int4 tl = tiles[tile];
-    const int t = tl.x, p0 = tl.y, rows = tl.z;
-    const int32_t* pt = perm + (int64_t)t * n + p0;
-    const uint32_t* bt = bits + (int64_t)t * nwords;
-    // (1) rows, leaf starts, staging
-    bool start = false;
-    if (r < rows) {
-      prow_s[r] = pt[r];
-      const int64_t p = (int64_t)p0 + r;
-      start = (bt[p >> 5] >> (p & 31)) & 1u;
+  // a tile's row ids and leaf-start bits, read one tile ahead
+  auto fetch_rows = [&](const int4& tv, int& prow, bool& st) {
+    prow = 0;
+    st = false;
+    if (r < tv.z) {
+      const int64_t p = (int64_t)tv.y + r;
+      prow = perm[(int64_t)tv.x * n + p];
+      st = (bits[(int64_t)tv.x * nwords + (p >> 5)] >> (p & 31)) & 1u;
     }
+  };
+  int64_t tile = tlo + blockIdx.x;
+  int4 tl_c = make_int4(0, 0, 0, 0);
+  int prow_c = 0;
+  bool start_c = false;
+  if (tile < thi) {
+    tl_c = tiles[tile];
+    fetch_rows(tl_c, prow_c, start_c);
+  }
+  for (; tile < thi && ok; tile += gridDim.x) {
+    const int4 tl = tl_c;
+    const int t = tl.x, rows = tl.z;
+    // (1) rows, leaf starts, staging
+    const bool start = start_c;
+    if (r < rows) prow_s[r] = prow_c;
+    if (tile + gridDim.x < thi) tl_c = tiles[tile + gridDim.x];  // its rows: before (5)
     const uint32_t bal = __ballot_sync(RPF_FULL, start);
     if (lane == 0) wmask[warp] = bal;
     // rows of 16-byte multiples go by bulk copy (TMA engine); other rows are
@@ -351,20 +379,27 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
     const int bslot = big ? big_of_start[lb] : -1;
     bool cert_ok = true;  // the leaf is in the tensor path's certified range
     if (nb > 0) {
-      // (2) FP32 mean of every large leaf
-      for (int j = 0; j < nb; ++j) {
+      // (2) FP32 mean of every large leaf: one thread per (leaf, coordinate),
+      // two chains (even and odd rows; any fixed order serves as a centre)
+      for (int w = tid; w < nb * d; w += ROWS) {
+        const int j = w / d, k = w - j * d;
         const int b0 = big_lb[j], b1 = big_le[j];
-        for (int k = tid; k < d; k += ROWS) {
-          float s = 0.0f;
-          for (int q = b0; q < b1; ++q) s = __fadd_rn(s, xs[q * dp + k]);
-          cen[j * d4 + k] = __fdiv_rn(s, (float)(b1 - b0));
+        float s0 = 0.0f, s1 = 0.0f;
+        int q = b0;
+        for (; q + 1 < b1; q += 2) {
+          s0 = __fadd_rn(s0, xs[q * dp + k]);
+          s1 = __fadd_rn(s1, xs[(q + 1) * dp + k]);
         }
+        if (q < b1) s0 = __fadd_rn(s0, xs[q * dp + k]);
+        cen[j * d4 + k] = __fdiv_rn(__fadd_rn(s0, s1), (float)(b1 - b0));
       }
+      for (int w = tid; w < nb * (d4 - d); w += ROWS)  // pairs read past d see zeros
+        cen[(w / (d4 - d)) * d4 + d + w % (d4 - d)] = 0.0f;
       __syncthreads();
       // (3) centred split-BF16 tiles, FP32 squared norms, Gram on the tensor core
       const int npad = (rows + 15) & ~15;
       const uint32_t idesc = rpf_umma_idesc_bf16(128, npad);
-      float yy = 0.0f;
+      float2 yy2 = make_float2(0.0f, 0.0f);  // squared norm: even and odd coordinates
       for (int k0 = 0; k0 < d16 && ok; k0 += KC) {
         if (k0 > 0) {  // the previous chunk's MMAs must be done reading the tiles
           const bool w = rpf_mbar_wait(&bar_mma, mma_phase, err, wlim);
@@ -377,20 +412,19 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
           uint32_t hp[4], lp[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            float y2[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int k = k0 + kk + 2 * u + h;
-              float y = 0.0f;
-              if (bslot >= 0 && k < d) y = __fsub_rn(xs[r * dp + k], cen[bslot * d4 + k]);
-              yy = __fmaf_rn(y, y, yy);
-              y2[h] = y;
-            }
-            const __nv_bfloat16 h0 = __float2bfloat16_rn(y2[0]), h1 = __float2bfloat16_rn(y2[1]);
-            const __nv_bfloat16 l0 = __float2bfloat16_rn(__fsub_rn(y2[0], __bfloat162float(h0)));
-            const __nv_bfloat16 l1 = __float2bfloat16_rn(__fsub_rn(y2[1], __bfloat162float(h1)));
-            hp[u] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            lp[u] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            // coordinates k, k + 1 as one pair (rows and centres are zero
+            // beyond d): y = x - c, hi = bf16(y), lo = bf16(y - hi)
+            const int k = k0 + kk + 2 * u;
+            float2 y2 = make_float2(0.0f, 0.0f);
+            if (bslot >= 0 && k < d)
+              y2 = rpf_sub2(*reinterpret_cast<const float2*>(xs + r * dp + k),
+                            *reinterpret_cast<const float2*>(cen + bslot * d4 + k));
+            yy2 = rpf_fma2(y2, y2, yy2);
+            hp[u] = rpf_bf16x2(y2.x, y2.y);
+            const float2 h2 = make_float2(__uint_as_float(hp[u] << 16),
+                                          __uint_as_float(hp[u] & 0xffff0000u));
+            const float2 l2 = rpf_sub2(y2, h2);
+            lp[u] = rpf_bf16x2(l2.x, l2.y);
           }
           const int idx = rpf_umma_index(r, kk, RG);  // 8 consecutive k: 16 bytes
           *reinterpret_cast<uint4*>(Ahi + idx) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
@@ -423,6 +457,7 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
         mma_pending = true;
       }
       if (!ok) break;
+      const float yy = __fadd_rn(yy2.x, yy2.y);
       nrm[r] = yy;
       const float yup = __fmul_ru(yy, 1.0f + (float)(d + 4) * 0x1p-23f);
       ynm[r] = __fsqrt_ru(yup);
@@ -459,14 +494,14 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
       th.init();
 #pragma unroll 1
       for (int c0 = lo; c0 < hi; c0 += 8) {
-        float g[8];
+        float g[8], D[8];
         rpf_tmem_ld8(tlane + (uint32_t)c0, g);
+        tc_dist8(g, nr, nrm, c0, D);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int c = c0 + j;
-          const float D = __fmaf_rn(-2.0f, g[j], __fadd_rn(nr, nrm[c < ROWS ? c : 0]));
           const bool use = tc_row && c >= lb && c < le && c != r;
-          th.insert(use ? D : INFINITY);
+          th.insert(use ? D[j] : INFINITY);
         }
       }
       if (tc_row) {
@@ -483,14 +518,14 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
       const int cl = tc_row ? lb : 0, ch = tc_row ? le : 0;
 #pragma unroll 1
       for (int c0 = lo; c0 < hi; c0 += 8) {
-        float g[8];
+        float g[8], D[8];
         rpf_tmem_ld8(tlane + (uint32_t)c0, g);
+        tc_dist8(g, nr, nrm, c0, D);
         uint32_t msk = 0u;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int c = c0 + j;
-          const float D = __fmaf_rn(-2.0f, g[j], __fadd_rn(nr, nrm[c < ROWS ? c : 0]));
-          const bool take = c >= cl && c < ch && c != r && D <= tau2;
+          const bool take = c >= cl && c < ch && c != r && D[j] <= tau2;
           msk |= (uint32_t)take << j;
         }
         while (msk) {
@@ -506,6 +541,7 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
       for (int c = lb; c < le; ++c)
         if (c != r) my[ns++] = (unsigned char)c;
     }
+    if (tile + gridDim.x < thi) fetch_rows(tl_c, prow_c, start_c);
     // (5) exact re-rank of the candidates
     Top64<KK> ex;
     ex.init();

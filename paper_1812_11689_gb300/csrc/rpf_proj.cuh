@@ -118,25 +118,6 @@ __device__ __forceinline__ void rpf_stage_rows(const float* __restrict__ X, int 
   }
 }
 
-// Packed FP32 pair arithmetic (one instruction, two lanes of work each, each
-// half rounded exactly as the scalar operation would round it).
-__device__ __forceinline__ float2 rpf_sub2(float2 a, float2 b) {
-  float2 r;
-  asm("{\n\t.reg .b64 a, b, r;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
-      "sub.rn.f32x2 r, a, b;\n\tmov.b64 {%0, %1}, r;\n\t}"
-      : "=f"(r.x), "=f"(r.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return r;
-}
-__device__ __forceinline__ float2 rpf_fma2(float2 a, float2 b, float2 c) {
-  float2 r;
-  asm("{\n\t.reg .b64 a, b, c, r;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
-      "mov.b64 c, {%6, %7};\n\tfma.rn.f32x2 r, a, b, c;\n\tmov.b64 {%0, %1}, r;\n\t}"
-      : "=f"(r.x), "=f"(r.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return r;
-}
-
 // Chains of the lane's row over coordinates [k0, k0 + kc) from the tile.
 // Every dot product (and the sum of squares) runs as two FP32 chains, one
 // over the even and one over the odd coordinates, in packed pair
