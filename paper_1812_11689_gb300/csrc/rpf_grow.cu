@@ -215,7 +215,9 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
       // batches of 32 positions, one per lane, rows staged through row
       // tiles, kPaStages units in flight per warp
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      rpf_warp_project<TG, RPF_TILE_DC, kPaStages>(
+      // TG is nTry itself when nTry <= 5 (the launch picks it so): one pass
+      // then covers every try, with the sum of squares
+      rpf_warp_project<TG, RPF_TILE_DC, kPaStages, (TG <= 5)>(
           X, d, perm_cur + base, len, warp, kBlock / 32, tiles + warp * kPaStages * RPF_TILE_FLOATS,
           so, sr + j0 * d, nj, j0 == 0, lane, j0 == 0 ? xnorm : nullptr,
           [&](int pos, int gid, const float(&acc)[TG], float nn, float xn) {

@@ -124,10 +124,12 @@ __device__ __forceinline__ void rpf_stage_rows(const float* __restrict__ X, int 
 // instructions; the caller adds the halves.  Each half has at most d / 2
 // terms, so the computed value obeys the error bound of a d-term sequential
 // chain that the radius and the statistics bounds assume.
-template <int TG, int DC = RPF_TILE_DC>
+// FULL: all TG tries and the sum of squares (the caller guarantees nj == TG
+// and want_nn), so that no per-try predicate is kept across the loop.
+template <int TG, int DC, bool FULL>
 __device__ __forceinline__ void rpf_tile_chunk(const float* tile, int lane, int k0, int kc,
-                                               const float* so, const float* sr, int d, int nj,
-                                               float2 (&acc)[TG], float2& nn, bool want_nn) {
+                                                 const float* so, const float* sr, int d, int nj,
+                                                 float2 (&acc)[TG], float2& nn, bool want_nn) {
   const float* xr = tile + lane * (DC + 4);
 #pragma unroll 4
   for (int k = 0; k < kc; k += 4) {
@@ -135,13 +137,13 @@ __device__ __forceinline__ void rpf_tile_chunk(const float* tile, int lane, int 
     const float4 o4 = *reinterpret_cast<const float4*>(so + k0 + k);
     const float2 e01 = rpf_sub2(make_float2(x4.x, x4.y), make_float2(o4.x, o4.y));
     const float2 e23 = rpf_sub2(make_float2(x4.z, x4.w), make_float2(o4.z, o4.w));
-    if (want_nn) {
+    if (FULL || want_nn) {
       nn = rpf_fma2(e01, e01, nn);
       nn = rpf_fma2(e23, e23, nn);
     }
 #pragma unroll
     for (int q = 0; q < TG; ++q) {
-      if (q < nj) {
+      if (FULL || q < nj) {
         const float4 r4 = *reinterpret_cast<const float4*>(sr + q * d + k0 + k);
         acc[q] = rpf_fma2(e23, make_float2(r4.z, r4.w),
                           rpf_fma2(e01, make_float2(r4.x, r4.y), acc[q]));
@@ -157,8 +159,9 @@ __device__ __forceinline__ void rpf_tile_chunk(const float* tile, int lane, int 
 // unit u is computed (NS tiles of 32 rows x (DC + 4) floats at `tiles`).
 // After a batch's last chunk fin(position, id, acc, nn, xn) runs on every
 // lane whose position holds a point, xn = xnorm[id] (0 when xnorm is null).
-// Point ids and their norms are read NS batches ahead.
-template <int TG, int DC, int NS, typename IdT, typename Fin>
+// Point ids and their norms are read NS batches ahead.  FULL: nj == TG and
+// want_nn on every call (one pass over all tries).
+template <int TG, int DC, int NS, bool FULL, typename IdT, typename Fin>
 __device__ __forceinline__ void rpf_warp_project(const float* __restrict__ X, int d, const IdT* ids,
                                                  int npos, int bfirst, int bstride, float* tiles,
                                                  const float* so, const float* sr, int nj,
@@ -208,8 +211,8 @@ __device__ __forceinline__ void rpf_warp_project(const float* __restrict__ X, in
       rpf_cp_wait<NS - 1>();  // this unit's copies are done
       __syncwarp();
       if (g[0] >= 0)
-        rpf_tile_chunk<TG, DC>(tiles + cs * TF, lane, c * DC, min(DC, d - c * DC), so, sr, d, nj,
-                               acc2, nn2, want_nn);
+        rpf_tile_chunk<TG, DC, FULL>(tiles + cs * TF, lane, c * DC, min(DC, d - c * DC), so, sr,
+                                     d, nj, acc2, nn2, want_nn);
       __syncwarp();  // before this tile takes a later unit
       cs = cs + 1 == NS ? 0 : cs + 1;
     }

@@ -300,7 +300,9 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 16 : 4) k_subtree(
           // units (batch, kTDC-coordinate chunk) ahead into row tiles held in
           // the partition scratch
           float* tb = reinterpret_cast<float*>(smraw + lay.sT) + warp * kTStages * 32 * (kTDC + 4);
-          rpf_warp_project<TG, kTDC, kTStages>(
+          // TG is nTry itself when nTry <= 5 (the launch picks it so): one pass
+          // then covers every try, with the sum of squares
+          rpf_warp_project<TG, kTDC, kTStages, (TG <= 5)>(
               X, d, sP + nb, m, warp, NT / 32, tb, so, r32 + j0 * d, nj, j0 == 0, lane,
               j0 == 0 ? xnorm : nullptr,
               [&](int pos, int gid, const float(&acc)[TG], float nn, float xn) {
