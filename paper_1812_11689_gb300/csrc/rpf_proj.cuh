@@ -273,7 +273,7 @@ __device__ __forceinline__ void rpf_block_stats(int nj, float (&s1)[TG], float (
   }
 #pragma unroll
   for (int q = 0; q < TG; ++q) {
-    if (q >= nj) continue;
+    if (!(TG <= 5 || q < nj)) continue;  // TG <= 5: nj == TG (the callers' launch)
     float a = s1[q], b = s2[q], c = a1[q], lo = mn[q], hi = mx[q];
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {

@@ -306,15 +306,15 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 16 : 4) k_subtree(
               X, d, sP + nb, m, warp, NT / 32, tb, so, r32 + j0 * d, nj, j0 == 0, lane,
               j0 == 0 ? xnorm : nullptr,
               [&](int pos, int gid, const float(&acc)[TG], float nn, float xn) {
-                if (j0 == 0) {
+                if (TG <= 5 || j0 == 0) {
                   const float r = rpf_point_rad(d, nn, xn, on);
                   radmax = fmaxf(radmax, r);
                   rad2 = __fmaf_ru(r, r, rad2);
                 }
 #pragma unroll
                 for (int q = 0; q < TG; ++q) {
-                  if (q < nj) {
-                    p32[(int64_t)(j0 + q) * Tn + pbase + nb + pos] = acc[q];
+                  if (TG <= 5 || q < nj) {
+                    p32[(int64_t)((TG <= 5 ? 0 : j0) + q) * Tn + pbase + nb + pos] = acc[q];
                     rpf_stat_add(acc[q], s1[q], s2[q], a1[q], mn[q], mx[q]);
                   }
                 }
