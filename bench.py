@@ -278,7 +278,7 @@ def work_model(fo, w, n):
     return {
         "k_subtree": {"bytes": pl_bb * (4 * d + 4) + rb},
         "k_subtree_w": {"bytes": pl_bw * (4 * d + 4) + rw},
-        "k_proj_a": {"bytes": pl_a * (4 * d + 4 + 4 + 4 * nt)},
+        "k_proj_a": {"bytes": pl_a * (4 * d + 4 + 4 + 4 * nt), "units": pl_a},
         "k_side_count": {"bytes": pl_a * (4 + 4 + 1)},
         "k_scatter": {"bytes": pl_a * (1 + 4 + 4)},
         "k_leaf_plain": {"bytes": n * T * (4 * d + 4 + 8 * K),
@@ -293,9 +293,12 @@ def work_model(fo, w, n):
     }
 
 
-def traffic_record(kernel, workload):
+def traffic_record(kernel, workload, units_per_launch=None):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current source of the kernel (the summary states the source digest)."""
+    the current source of the kernel (the summary states the source digest).
+    A summary of one launch of a kernel whose launches differ in size states
+    the units (point-levels) of the captured launch; its bytes are scaled to
+    units_per_launch."""
     import hashlib
     import re
     p = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
@@ -314,6 +317,9 @@ def traffic_record(kernel, workload):
         h.update(open(f, "rb").read())
     if h.hexdigest() != src.group(1):
         return None
+    u = re.search(r"captured_units:\s*([0-9]+)", txt)
+    if u and units_per_launch:
+        return int(int(m.group(1)) * units_per_launch / int(u.group(1)))
     return int(m.group(1))
 
 
@@ -330,7 +336,8 @@ def rooflines(trace, work, hbm_peak, peak_kind, steps, workload):
         ach = per_launch / (ms_launch * 1e-3) / 1e9
         r = {"kernel": k, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
              "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
-             "peak_source": peak_kind, "traffic": traffic_record(k, workload),
+             "peak_source": peak_kind,
+             "traffic": traffic_record(k, workload, work[k].get("units", 0) * steps / t["launches"]),
              "algorithmic_bytes_per_launch": int(per_launch),
              "ms_per_launch": round(ms_launch, 5), "launches_per_step": t["launches"] // steps,
              "share": round(t["ms"] / tot, 4)}
