@@ -33,6 +33,8 @@
 //  Afterwards the node table is compacted (phase B reserves id ranges) and
 //  the chosen direction of every split node is regenerated into it.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 #include <math.h>
 
 #include <algorithm>
@@ -217,23 +219,28 @@ __global__ void __launch_bounds__(kBlock) k_proj_a(
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
       // TG is nTry itself when nTry <= 5 (the launch picks it so): one pass
       // then covers every try, with the sum of squares
-      rpf_warp_project<TG, RPF_TILE_DC, kPaStages, (TG <= 5)>(
-          X, d, perm_cur + base, len, warp, kBlock / 32, tiles + warp * kPaStages * RPF_TILE_FLOATS,
-          so, sr + j0 * d, nj, j0 == 0, lane, j0 == 0 ? xnorm : nullptr,
-          [&](int pos, int gid, const float(&acc)[TG], float nn, float xn) {
-            if (TG <= 5 || j0 == 0) {
-              const float r = rpf_point_rad(d, nn, xn, on);
-              radmax = fmaxf(radmax, r);
-              rad2 = __fmaf_ru(r, r, rad2);
-            }
-#pragma unroll
-            for (int q = 0; q < TG; ++q) {
-              if (TG <= 5 || q < nj) {
-                p32[(int64_t)((TG <= 5 ? 0 : j0) + q) * Tn + base + pos] = acc[q];
-                rpf_stat_add(acc[q], s1[q], s2[q], a1[q], mn[q], mx[q]);
+      auto project = [&](auto dfull) {
+        rpf_warp_project<TG, RPF_TILE_DC, kPaStages, (TG <= 5), decltype(dfull)::value>(
+            X, d, perm_cur + base, len, warp, kBlock / 32, tiles + warp * kPaStages * RPF_TILE_FLOATS,
+            so, sr + j0 * d, nj, j0 == 0, lane, j0 == 0 ? xnorm : nullptr,
+            [&](int pos, int gid, const float(&acc)[TG], float nn, float xn) {
+              if (TG <= 5 || j0 == 0) {
+                const float r = rpf_point_rad(d, nn, xn, on);
+                radmax = fmaxf(radmax, r);
+                rad2 = __fmaf_ru(r, r, rad2);
               }
-            }
-          });
+#pragma unroll
+              for (int q = 0; q < TG; ++q) {
+                if (TG <= 5 || q < nj) {
+                  p32[(int64_t)((TG <= 5 ? 0 : j0) + q) * Tn + base + pos] = acc[q];
+                  rpf_stat_add(acc[q], s1[q], s2[q], a1[q], mn[q], mx[q]);
+                }
+              }
+            });
+      };
+      // whole chunks when d is a multiple of the chunk width
+      if (d % RPF_TILE_DC == 0) project(std::true_type{});
+      else project(std::false_type{});
     } else {
       for (int u0 = 0; u0 * kBlock < len; u0 += 4) {
         int gid[4], pos[4];

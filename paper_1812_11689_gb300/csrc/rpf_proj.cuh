@@ -104,7 +104,8 @@ __device__ __forceinline__ void rpf_cp_wait() {
 
 // Warp-collective: copy coordinates [k0, k0 + DC) of the 32 rows gid (lane
 // l's row to tile row l; gid < 0: none) into the tile (DC / 4 lanes per row).
-template <int DC = RPF_TILE_DC>
+// DFULL: d is a multiple of DC (every chunk is whole).
+template <int DC = RPF_TILE_DC, bool DFULL = false>
 __device__ __forceinline__ void rpf_stage_rows(const float* __restrict__ X, int d, int gid, int k0,
                                                float* tile, int lane) {
   constexpr int LPR = DC / 4, RPI = 32 / LPR;  // lanes per row, rows per instruction
@@ -114,7 +115,8 @@ __device__ __forceinline__ void rpf_stage_rows(const float* __restrict__ X, int 
   for (int i = 0; i < 32 / RPI; ++i) {
     const int row = RPI * i + lane / LPR;
     const int g = __shfl_sync(RPF_FULL, gid, row);
-    if (g >= 0 && c4 < kc) rpf_cp16(tile + row * (DC + 4) + c4, X + (int64_t)g * d + k0 + c4);
+    if (g >= 0 && (DFULL || c4 < kc))
+      rpf_cp16(tile + row * (DC + 4) + c4, X + (int64_t)g * d + k0 + c4);
   }
 }
 
@@ -126,13 +128,14 @@ __device__ __forceinline__ void rpf_stage_rows(const float* __restrict__ X, int 
 // chain that the radius and the statistics bounds assume.
 // FULL: all TG tries and the sum of squares (the caller guarantees nj == TG
 // and want_nn), so that no per-try predicate is kept across the loop.
-template <int TG, int DC, bool FULL>
+template <int TG, int DC, bool FULL, bool DFULL>
 __device__ __forceinline__ void rpf_tile_chunk(const float* tile, int lane, int k0, int kc,
                                                  const float* so, const float* sr, int d, int nj,
                                                  float2 (&acc)[TG], float2& nn, bool want_nn) {
   const float* xr = tile + lane * (DC + 4);
-#pragma unroll 4
-  for (int k = 0; k < kc; k += 4) {
+  const int kcc = DFULL ? DC : kc;
+#pragma unroll(DFULL ? DC / 4 : 4)
+  for (int k = 0; k < kcc; k += 4) {
     const float4 x4 = *reinterpret_cast<const float4*>(xr + k);
     const float4 o4 = *reinterpret_cast<const float4*>(so + k0 + k);
     const float2 e01 = rpf_sub2(make_float2(x4.x, x4.y), make_float2(o4.x, o4.y));
@@ -160,8 +163,8 @@ __device__ __forceinline__ void rpf_tile_chunk(const float* tile, int lane, int 
 // After a batch's last chunk fin(position, id, acc, nn, xn) runs on every
 // lane whose position holds a point, xn = xnorm[id] (0 when xnorm is null).
 // Point ids and their norms are read NS batches ahead.  FULL: nj == TG and
-// want_nn on every call (one pass over all tries).
-template <int TG, int DC, int NS, bool FULL, typename IdT, typename Fin>
+// want_nn on every call (one pass over all tries).  DFULL: d % DC == 0.
+template <int TG, int DC, int NS, bool FULL, bool DFULL, typename IdT, typename Fin>
 __device__ __forceinline__ void rpf_warp_project(const float* __restrict__ X, int d, const IdT* ids,
                                                  int npos, int bfirst, int bstride, float* tiles,
                                                  const float* so, const float* sr, int nj,
@@ -188,7 +191,7 @@ __device__ __forceinline__ void rpf_warp_project(const float* __restrict__ X, in
 #pragma unroll
     for (int kk = 1; kk < NS; ++kk)
       if (sk == kk) gs = g[kk];
-    if (i + sk < nbw) rpf_stage_rows<DC>(X, d, gs, sc * DC, tiles + ss * TF, lane);
+    if (i + sk < nbw) rpf_stage_rows<DC, DFULL>(X, d, gs, sc * DC, tiles + ss * TF, lane);
     ss = ss + 1 == NS ? 0 : ss + 1;
     if (++sc == nch) {
       sc = 0;
@@ -211,7 +214,7 @@ __device__ __forceinline__ void rpf_warp_project(const float* __restrict__ X, in
       rpf_cp_wait<NS - 1>();  // this unit's copies are done
       __syncwarp();
       if (g[0] >= 0)
-        rpf_tile_chunk<TG, DC, FULL>(tiles + cs * TF, lane, c * DC, min(DC, d - c * DC), so, sr,
+        rpf_tile_chunk<TG, DC, FULL, DFULL>(tiles + cs * TF, lane, c * DC, min(DC, d - c * DC), so, sr,
                                      d, nj, acc2, nn2, want_nn);
       __syncwarp();  // before this tile takes a later unit
       cs = cs + 1 == NS ? 0 : cs + 1;

@@ -24,6 +24,8 @@
 // m leaf slots for m points), so the layout is deterministic.  CTAs have 128
 // threads (at most 32 points per thread in the statistics).
 #include <cuda_runtime.h>
+
+#include <type_traits>
 #include <math.h>
 
 #include <algorithm>
@@ -302,23 +304,28 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 16 : 4) k_subtree(
           float* tb = reinterpret_cast<float*>(smraw + lay.sT) + warp * kTStages * 32 * (kTDC + 4);
           // TG is nTry itself when nTry <= 5 (the launch picks it so): one pass
           // then covers every try, with the sum of squares
-          rpf_warp_project<TG, kTDC, kTStages, (TG <= 5)>(
-              X, d, sP + nb, m, warp, NT / 32, tb, so, r32 + j0 * d, nj, j0 == 0, lane,
-              j0 == 0 ? xnorm : nullptr,
-              [&](int pos, int gid, const float(&acc)[TG], float nn, float xn) {
-                if (TG <= 5 || j0 == 0) {
-                  const float r = rpf_point_rad(d, nn, xn, on);
-                  radmax = fmaxf(radmax, r);
-                  rad2 = __fmaf_ru(r, r, rad2);
-                }
-#pragma unroll
-                for (int q = 0; q < TG; ++q) {
-                  if (TG <= 5 || q < nj) {
-                    p32[(int64_t)((TG <= 5 ? 0 : j0) + q) * Tn + pbase + nb + pos] = acc[q];
-                    rpf_stat_add(acc[q], s1[q], s2[q], a1[q], mn[q], mx[q]);
+          auto project = [&](auto dfull) {
+            rpf_warp_project<TG, kTDC, kTStages, (TG <= 5), decltype(dfull)::value>(
+                X, d, sP + nb, m, warp, NT / 32, tb, so, r32 + j0 * d, nj, j0 == 0, lane,
+                j0 == 0 ? xnorm : nullptr,
+                [&](int pos, int gid, const float(&acc)[TG], float nn, float xn) {
+                  if (TG <= 5 || j0 == 0) {
+                    const float r = rpf_point_rad(d, nn, xn, on);
+                    radmax = fmaxf(radmax, r);
+                    rad2 = __fmaf_ru(r, r, rad2);
                   }
-                }
-              });
+#pragma unroll
+                  for (int q = 0; q < TG; ++q) {
+                    if (TG <= 5 || q < nj) {
+                      p32[(int64_t)((TG <= 5 ? 0 : j0) + q) * Tn + pbase + nb + pos] = acc[q];
+                      rpf_stat_add(acc[q], s1[q], s2[q], a1[q], mn[q], mx[q]);
+                    }
+                  }
+                });
+          };
+          // whole chunks when d is a multiple of the chunk width
+          if (d % kTDC == 0) project(std::true_type{});
+          else project(std::false_type{});
         } else {
           for (int u0 = 0; u0 * NT < m; u0 += 4) {
             int gid[4], pos[4];
