@@ -18,11 +18,14 @@
 //      and split into BF16 pairs y ~ hi + lo; G = hi hi^T + hi lo^T + lo hi^T
 //      is accumulated by tcgen05.mma (kind::f16, M = 128, N = rows padded to
 //      16, FP32 in TMEM) over chunks of at most 128 coordinates.
-//   4. Row r reads its Gram row from TMEM (tcgen05.ld) twice: first to find
-//      tau, the K-th smallest approximate squared distance
-//      D~_rj = n_r + n_j - 2 G_rj (n = FP32 squared norm of y) with a
-//      branch-free min/max network; then to collect every j with
-//      D~_rj <= tau', a certified margin above tau.
+//   4. Row r reads its Gram row from TMEM (tcgen05.ld) and keeps the K + 2
+//      smallest keys of the approximate squared distances
+//      D~_rj = n_r + n_j - 2 G_rj (n = FP32 squared norm of y) with their
+//      columns (a branch-free min/max network); tau, an upper bound of the
+//      K-th smallest D~, comes from the K-th key, and every j with
+//      D~_rj <= tau' (a certified margin above tau) from the kept keys, or
+//      from a second pass over the row when the kept keys may not hold
+//      them all.
 //   5. The collected candidates are re-ranked with the canonical FP32 d32
 //      (the plain form's exact key) into a sorted list of 64-bit keys
 //      (d32 bits << 32 | index), which orders exactly like (d32, index).
@@ -142,6 +145,27 @@ struct TopF {
     float r = INFINITY;
 #pragma unroll
     for (int q = 0; q < KK; ++q) r = fminf(r, q >= K - 1 ? v[q] : INFINITY);
+    return r;
+  }
+};
+
+// Sorted list of the KK smallest 32-bit keys offered (branch-free network).
+template <int KK>
+struct TopU {
+  uint32_t v[KK];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int q = 0; q < KK; ++q) v[q] = 0xffffffffu;
+  }
+  __device__ __forceinline__ void insert(uint32_t x) {
+#pragma unroll
+    for (int q = KK - 1; q >= 1; --q) v[q] = max(v[q - 1], min(v[q], x));
+    v[0] = min(v[0], x);
+  }
+  __device__ __forceinline__ uint32_t kth(int K) const {  // sorted: min over q >= K - 1
+    uint32_t r = 0xffffffffu;
+#pragma unroll
+    for (int q = 0; q < KK; ++q) r = min(r, q >= K - 1 ? v[q] : 0xffffffffu);
     return r;
   }
 };
@@ -490,7 +514,15 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
       }
       lo &= ~7;
       const float nr = nrm[r];
-      TopF<KK> th;
+      // One pass keeps the KK + 2 smallest keys (D~ bits with the low 8 bits
+      // replaced by the column; D~ >= 0 after clamping, which moves no
+      // value away from its bound): a key's bucket [lower, upper] holds its
+      // D~, keys order like buckets, so the K-th key's upper edge is an
+      // upper bound tau of the K-th smallest D~.  The margin's columns are
+      // the kept keys whose lower edge is <= tau'; when the last kept key's
+      // lower edge is also <= tau', further columns may lie within the
+      // margin and the row collects them in a second pass.
+      TopU<KK + 2> th;
       th.init();
 #pragma unroll 1
       for (int c0 = lo; c0 < hi; c0 += 8) {
@@ -501,38 +533,56 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
         for (int j = 0; j < 8; ++j) {
           const int c = c0 + j;
           const bool use = tc_row && c >= lb && c < le && c != r;
-          th.insert(use ? D[j] : INFINITY);
+          const uint32_t key = (__float_as_uint(fmaxf(D[j], 0.0f)) & 0xffffff00u) | (uint32_t)c;
+          th.insert(use ? key : 0xffffffffu);
         }
       }
+      bool more = false;  // the kept keys may not hold every margin column
       if (tc_row) {
-        const float tau = th.kth(K);
+        const uint32_t kk = th.kth(K);
+        const float tlow = __uint_as_float(kk & 0xffffff00u);
+        const float tau = kk == 0xffffffffu || isinf(tlow) ? INFINITY : __uint_as_float(kk | 0xffu);
         const float Nm = __uint_as_float(nmax_bits[bslot]);
         eps = __fmul_ru(ce, __fadd_ru(nr, Nm));
         eta = __fmul_ru(0x1p-23f, __fadd_ru(ynm[r], __fsqrt_ru(Nm)));
         const float s = __fadd_ru(__fmul_ru(__fsqrt_ru(__fadd_ru(tau, eps)), 1.0f + 4.0f * gam),
                                   2.0f * eta);
         tau2 = __fadd_ru(eps, __fmul_ru(s, s));
-      }
-      // the columns within the margin, eight at a time as a bit mask; the
-      // few set bits are then written out (no divergent store per column)
-      const int cl = tc_row ? lb : 0, ch = tc_row ? le : 0;
-#pragma unroll 1
-      for (int c0 = lo; c0 < hi; c0 += 8) {
-        float g[8], D[8];
-        rpf_tmem_ld8(tlane + (uint32_t)c0, g);
-        tc_dist8(g, nr, nrm, c0, D);
-        uint32_t msk = 0u;
+        const uint32_t last = th.v[KK + 1];
+        more = last != 0xffffffffu && !(__uint_as_float(last & 0xffffff00u) > tau2);
+        if (!more) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int c = c0 + j;
-          const bool take = c >= cl && c < ch && c != r && D[j] <= tau2;
-          msk |= (uint32_t)take << j;
+          for (int q = 0; q < KK + 2; ++q) {
+            const uint32_t v = th.v[q];
+            if (v != 0xffffffffu && __uint_as_float(v & 0xffffff00u) <= tau2) {
+              if (ns < TC_SLOTS) my[ns] = (unsigned char)(v & 0xffu);
+              ++ns;
+            }
+          }
         }
-        while (msk) {
-          const int j = __ffs(msk) - 1;
-          msk &= msk - 1u;
-          if (ns < TC_SLOTS) my[ns] = (unsigned char)(c0 + j);
-          ++ns;
+      }
+      if (__any_sync(RPF_FULL, more)) {
+        // the columns within the margin, eight at a time as a bit mask; the
+        // few set bits are then written out (no divergent store per column)
+        const int cl = more ? lb : 0, ch = more ? le : 0;
+#pragma unroll 1
+        for (int c0 = lo; c0 < hi; c0 += 8) {
+          float g[8], D[8];
+          rpf_tmem_ld8(tlane + (uint32_t)c0, g);
+          tc_dist8(g, nr, nrm, c0, D);
+          uint32_t msk = 0u;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int c = c0 + j;
+            const bool take = c >= cl && c < ch && c != r && D[j] <= tau2;
+            msk |= (uint32_t)take << j;
+          }
+          while (msk) {
+            const int j = __ffs(msk) - 1;
+            msk &= msk - 1u;
+            if (ns < TC_SLOTS) my[ns] = (unsigned char)(c0 + j);
+            ++ns;
+          }
         }
       }
     }

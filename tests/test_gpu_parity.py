@@ -299,6 +299,23 @@ def test_chosen_form_certificate_fallback_is_exact(shape):
     assert c.counters()["bf16_fallback_rows"] > 0
 
 
+def test_chosen_form_margin_wider_than_the_kept_keys():
+    # groups of 16 near-equidistant points (regular simplices, edge ~1.4, far
+    # apart): a row's 15 group-mates all lie within the certified margin, more
+    # than the K + 2 keys the selection keeps, so the row collects its margin
+    # columns in a second pass; the lists must equal the oracle's
+    rng = np.random.default_rng(4)
+    d, g, ng = 64, 16, 150
+    centres = 50.0 * rng.standard_normal((ng, d))
+    X = np.concatenate([c + np.eye(g, d) for c in centres])
+    X = (X + 1e-6 * rng.standard_normal(X.shape)).astype(np.float32)
+    o = oracle.Forest(X, 3, 100, 5, seed=2)
+    oi, od = o.all_knn(10)
+    c = gpu_forest(X, 3, 100, 5, seed=2, form=1)
+    ci, cd = c.all_knn(10)
+    assert np.array_equal(ci.cpu().numpy(), oi) and np.array_equal(cd.cpu().numpy(), od)
+
+
 @pytest.mark.parametrize("form", [0, 1])
 def test_all_knn_over_tree_prefixes_equals_the_smaller_forests(form):
     # nested ensembles: the first T' trees of a forest are the T'-tree forest
