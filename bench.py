@@ -323,7 +323,10 @@ def traffic_record(kernel, workload, units_per_launch=None):
     return int(m.group(1))
 
 
-def rooflines(trace, work, hbm_peak, peak_kind, steps, workload):
+GROWTH_KERNELS = ("k_proj_a", "k_subtree", "k_subtree_w")
+
+
+def rooflines(trace, work, hbm_peak, peak_kind, steps, workload, gather_peak=None):
     """Per-kernel roofline fractions; the kernel with the largest share first."""
     tot = sum(v["ms"] for v in trace.values()) or 1.0
     fp32_peak = 2 * FP32_LANES * SM_MAX_GHZ * 1e9 / 1e12  # TFLOP/s, FMA = 2
@@ -341,6 +344,13 @@ def rooflines(trace, work, hbm_peak, peak_kind, steps, workload):
              "algorithmic_bytes_per_launch": int(per_launch),
              "ms_per_launch": round(ms_launch, 5), "launches_per_step": t["launches"] // steps,
              "share": round(t["ms"] / tot, 4)}
+        if gather_peak and k in GROWTH_KERNELS:
+            # the growth kernels read X from L2: their own ceiling is the
+            # rate of random whole-row reads (rpf_gather_probe, this run)
+            r["l2_row_gather"] = {"achieved": round(ach, 1), "peak": gather_peak, "unit": "GB/s",
+                                  "frac": round(ach / gather_peak, 4),
+                                  "peak_source": "rpf_gather_probe on the workload's matrix, "
+                                                 "timed in this run"}
         if "tensor_flops" in work[k]:
             tf = work[k]["tensor_flops"] * steps / t["launches"] / (ms_launch * 1e-3) / 1e12
             bp, bsrc = bf16_peak()
@@ -557,8 +567,9 @@ def run_gb300(args, rank, world, local_rank):
 
     hbm_peak, peak_kind = peaks()
     work = work_model(fc, w, n)
-    roofs = rooflines(trace, work, hbm_peak, peak_kind, args.steps, args.workload)
-    roofs_p = rooflines(trace_p, work, hbm_peak, peak_kind, args.steps, args.workload)
+    gpk = round(forest.gather_rate(Xd), 1)
+    roofs = rooflines(trace, work, hbm_peak, peak_kind, args.steps, args.workload, gpk)
+    roofs_p = rooflines(trace_p, work, hbm_peak, peak_kind, args.steps, args.workload, gpk)
     roof = None
     if roofs:
         top = roofs[0]

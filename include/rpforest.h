@@ -334,6 +334,20 @@ int64_t rpf_launch_count(void);
 int rpf_trace_read(int32_t max_names, char* names, int64_t* launches, double* ms,
                    int32_t* n_names);
 
+/*
+ * rpf_gather_probe -- the row-gather reference of the growth kernels:
+ * gathers `rows` rows of X (n x d FP32, device, 16-byte aligned, d a
+ * multiple of 4) in a fixed pseudo-random order (seeded by `seed`), d / 4
+ * lanes per row (at most 32) reading each row as one coalesced read, and
+ * keeps nothing of them (`out`, one device float, is never written in
+ * practice).  Only enqueues the kernel on `stream`; the caller times it.
+ * rows * d * 4 bytes over the elapsed time is the rate of random whole-row
+ * reads that the growth kernels' own row gathers are compared with.
+ * Errors: RPF_EINVAL, RPF_ECUDA.
+ */
+int rpf_gather_probe(const float* X, int64_t n, int32_t d, int64_t rows, int64_t seed, float* out,
+                     void* stream);
+
 /* ---- inspection (host outputs; used by tests and tools) ------------------ */
 
 /* Sizes: n, d, T, total node count, leaf count, max depth, and the number of

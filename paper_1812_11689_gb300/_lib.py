@@ -99,6 +99,8 @@ def lib() -> ctypes.CDLL:
             L.rpf_forest_counters.restype = ctypes.c_int
             L.rpf_brute_knn.argtypes = [_vp, _i64, _i32, _vp, _i64, _vp, _i32, _vp, _vp, _vp]
             L.rpf_brute_knn.restype = ctypes.c_int
+            L.rpf_gather_probe.argtypes = [_vp, _i64, _i32, _i64, _i64, _vp, _vp]
+            L.rpf_gather_probe.restype = ctypes.c_int
             L.rpf_trace_enable.argtypes = [ctypes.c_int]
             L.rpf_trace_enable.restype = ctypes.c_int
             L.rpf_launch_count.argtypes = []
@@ -129,5 +131,5 @@ EXPORTED = ("rpf_default_params", "rpf_build", "rpf_build_shard", "rpf_all_knn",
             "rpf_set_query_scan",
             "rpf_workspace_bytes", "rpf_free", "rpf_error_string", "rpf_forest_info",
             "rpf_forest_perm", "rpf_forest_leaves", "rpf_forest_nodes", "rpf_directions",
-            "rpf_brute_knn", "rpf_trace_enable", "rpf_launch_count", "rpf_trace_read",
+            "rpf_brute_knn", "rpf_gather_probe", "rpf_trace_enable", "rpf_launch_count", "rpf_trace_read",
             "rpf_forest_counters")

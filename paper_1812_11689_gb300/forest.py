@@ -314,6 +314,29 @@ def brute_knn(X, Q, K: int, self_idx=None, stream=None):
     return idx, dist
 
 
+def gather_rate(X, rows: int = 1 << 24, reps: int = 10, seed: int = 1) -> float:
+    """rpf_gather_probe timed with CUDA events on the current stream: GB/s of
+    random whole rows of the device matrix X (n x d FP32)."""
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32
+            and X.is_contiguous() and X.dim() == 2):
+        raise ValueError("X must be a contiguous 2-D float32 CUDA tensor")
+    out = torch.zeros(1, dtype=torch.float32, device=X.device)
+    s = torch.cuda.current_stream(X.device)
+    L = _lib.lib()
+    n, d = int(X.shape[0]), int(X.shape[1])
+    for r in range(2):  # warm-up
+        check(L.rpf_gather_probe(_ptr(X), n, d, rows, seed + r, _ptr(out), s.cuda_stream),
+              "rpf_gather_probe")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for r in range(reps):
+        check(L.rpf_gather_probe(_ptr(X), n, d, rows, seed + 2 + r, _ptr(out), s.cuda_stream),
+              "rpf_gather_probe")
+    e1.record(s)
+    e1.synchronize()
+    return rows * d * 4 / (e0.elapsed_time(e1) * 1e-3 / reps) / 1e9
+
+
 def merge_keys(lists, K: int, idx=None, dist=None, stream=None):
     """rpf_merge_keys: lists (G, n, K, 2) int32 (d32 bits, index) -> final
     (idx, dist) of the n points (the union over the G groups of trees)."""

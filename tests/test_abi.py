@@ -65,4 +65,5 @@ def test_build_rejects_bad_arguments_before_touching_the_gpu(L):
     assert L.rpf_query(None, None, 1, 5, None, None, None, 0, None) == -1
     assert L.rpf_workspace_bytes(None, 10, 5, 1) == 0
     assert L.rpf_set_query_scan(None, 0) == -1
+    assert L.rpf_gather_probe(None, 10, 4, 1, 0, None, None) == -1
     L.rpf_free(None)

@@ -555,3 +555,15 @@ def test_set_form_switches_a_built_forest_and_keeps_the_lists():
     f.set_form(0)
     ai, ad = f.all_knn(10)
     assert torch.equal(pi, ai) and torch.equal(pd, ad)
+
+
+def test_gather_probe_rate_is_positive_and_checks_its_arguments():
+    from paper_1812_11689_gb300 import _lib, forest
+    X = torch.from_numpy(synth.make("aniso20_d64", n=50000)).cuda()
+    assert forest.gather_rate(X, rows=1 << 18, reps=2) > 0
+    with pytest.raises(ValueError):
+        forest.gather_rate(X.cpu())
+    out = torch.zeros(1, device="cuda")
+    L = _lib.lib()
+    assert L.rpf_gather_probe(X.data_ptr(), X.shape[0], 6, 1, 0, out.data_ptr(), None) == -1
+    assert out.item() == 0.0
