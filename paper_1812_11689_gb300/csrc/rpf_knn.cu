@@ -414,6 +414,85 @@ __global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, in
   if (sub == 0) qleaf[g] = node;
 }
 
+// The same walk with the query's coordinates held in registers and the next
+// node's direction requested together with its routing record (PM >=
+// ceil(d / 8) coordinates per lane), so a level costs one round trip even
+// though the loop first tests the record.  The sums run in the same order as
+// k_route_w's, so the decisions are the same.
+template <int PM>
+__global__ void __launch_bounds__(256) k_route_p(const float* __restrict__ Q, int64_t m, int d,
+                                                 int T, const int4* __restrict__ node_route,
+                                                 const float* __restrict__ node_dir32,
+                                                 int32_t* qleaf) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / RW;
+  const int lane = threadIdx.x & 31, sub = lane & (RW - 1);
+  const unsigned gmask = ((1u << RW) - 1u) << (lane & ~(RW - 1));
+  if (g >= m * T) return;  // whole group
+  const int64_t q = g / T;
+  const int t = (int)(g % T);
+  const float* x = Q + q * d;
+  const int per = (d + RW - 1) / RW;
+  const float kerr = (float)(per + 7) * 0x1p-24f;
+  const float kA = 1.0f + (float)(per + 6) * 0x1p-23f;
+  float xv[PM], rv[PM];
+#pragma unroll
+  for (int i = 0; i < PM; ++i) {
+    const int k = sub + RW * i;
+    xv[i] = k < d ? __ldg(x + k) : 0.0f;
+  }
+  int node = t;
+  int4 rec = __ldg(node_route + node);
+#pragma unroll
+  for (int i = 0; i < PM; ++i) {
+    const int k = sub + RW * i;
+    rv[i] = k < d ? __ldg(node_dir32 + (int64_t)node * d + k) : 0.0f;
+  }
+  while (rec.z >= 0) {
+    const double c = __hiloint2double(rec.y, rec.x);
+    float sacc = 0.0f, aacc = 0.0f;
+#pragma unroll
+    for (int i = 0; i < PM; ++i) {
+      if (sub + RW * i < d) {
+        sacc = __fmaf_rn(xv[i], rv[i], sacc);
+        aacc = __fmaf_rn(fabsf(xv[i]), fabsf(rv[i]), aacc);
+      }
+    }
+#pragma unroll
+    for (int off = RW / 2; off >= 1; off >>= 1) {
+      sacc = __fadd_rn(sacc, __shfl_xor_sync(gmask, sacc, off, RW));
+      aacc = __fadd_rn(aacc, __shfl_xor_sync(gmask, aacc, off, RW));
+    }
+    int go_left;
+    if (rec.z == rec.w) {  // rank split: every query goes left
+      go_left = 1;
+    } else {
+      const float e = __fmul_ru(kerr, __fmul_ru(aacc, kA));
+      if (__fadd_ru(sacc, e) < __double2float_rd(c)) {
+        go_left = 1;
+      } else if (__fsub_rd(sacc, e) >= __double2float_ru(c)) {
+        go_left = 0;
+      } else {  // undecided by the bound: the canonical FP64 chain
+        int v = 0;
+        if (sub == 0) {
+          const float* r32 = node_dir32 + (int64_t)node * d;
+          double p = 0.0;
+          for (int k = 0; k < d; ++k) p = __fma_rn((double)__ldg(x + k), (double)__ldg(r32 + k), p);
+          v = p < c;
+        }
+        go_left = __shfl_sync(gmask, v, 0, RW);
+      }
+    }
+    node = go_left ? rec.z : rec.w;
+    rec = __ldg(node_route + node);
+#pragma unroll
+    for (int i = 0; i < PM; ++i) {
+      const int k = sub + RW * i;
+      rv[i] = k < d ? __ldg(node_dir32 + (int64_t)node * d + k) : 0.0f;
+    }
+  }
+  if (sub == 0) qleaf[g] = node;
+}
+
 // Ascending bitonic sort of one 64-bit key per lane (all 32 lanes).
 __device__ __forceinline__ unsigned long long rpf_warp_sort(unsigned long long v, int lane) {
 #pragma unroll
@@ -850,8 +929,20 @@ size_t rpf_query_ws(const rpf_forest* f, int64_t m, int K) {
 // Leaf ids of m queries in every tree (k_route_w) into qleaf (m x T).
 int rpf_route_dev(const rpf_forest* f, const float* Q, int64_t m, int32_t* qleaf, cudaStream_t s) {
   const int T = f->prm.n_trees;
-  RPF_LAUNCH("k_route_w", s, k_route_w<<<nblk(m * T * RW, 256), 256, 0, s>>>(
-      Q, m, f->d, T, f->node_route, f->node_dir32, qleaf));
+  const int per = (f->d + RW - 1) / RW;
+  const unsigned grid = nblk(m * T * RW, 256);
+#define RPF_ROUTE_P(PMV)                                                             \
+  RPF_LAUNCH("k_route_w", s, k_route_p<PMV><<<grid, 256, 0, s>>>(Q, m, f->d, T,       \
+                                                                  f->node_route,      \
+                                                                  f->node_dir32, qleaf))
+  if (per <= 4) RPF_ROUTE_P(4);
+  else if (per <= 8) RPF_ROUTE_P(8);
+  else if (per <= 12) RPF_ROUTE_P(12);
+  else if (per <= 16) RPF_ROUTE_P(16);
+  else
+    RPF_LAUNCH("k_route_w", s, k_route_w<<<grid, 256, 0, s>>>(
+        Q, m, f->d, T, f->node_route, f->node_dir32, qleaf));
+#undef RPF_ROUTE_P
   RPF_CU(cudaGetLastError());
   return RPF_OK;
 }
