@@ -187,7 +187,7 @@ int rpf_query(const rpf_forest* f, const float* Q, int64_t m, int32_t K, int32_t
  *   idx,dist : m x K outputs in DEVICE memory, owned by the caller.
  *   stream   : cudaStream_t (NULL = legacy default stream).
  * Scratch: one fixed array of RPF_STATIC_SCRATCH_BYTES per device, inside
- * the library.  A call needs 256 + align256(4 m T) + align256(8 T m K) bytes
+ * the library.  A call needs 256 + align256(8 m T) + align256(8 T m K) bytes
  * of it (T = trees of the forest; at T = 32, K = 10 that allows m <= 3120);
  * larger requests return RPF_EINVAL without launching anything -- split
  * them.  Nothing in the scratch has to start at zero: the call clears its

@@ -1232,12 +1232,17 @@ __global__ void __launch_bounds__(128) k_node_dirs(int64_t N, int d, uint64_t se
 // Routing record of every node: c (two words), left child, and the right
 // child -- or the left one for a rank split, which sends every query left.
 __global__ void k_route_table(int64_t N, const int32_t* left, const int32_t* right,
-                              const int32_t* flag, const double* c, int4* out) {
+                              const int32_t* flag, const double* c, const int32_t* begin,
+                              const int32_t* len, int4* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const double cc = c[i];
   const int l = left[i];
-  const int r = (l >= 0 && (flag[i] & 1)) ? l : right[i];
+  if (l < 0) {  // a leaf: its segment of the tree's permutation
+    out[i] = make_int4(begin[i], len[i], -1, -1);
+    return;
+  }
+  const double cc = c[i];
+  const int r = (flag[i] & 1) ? l : right[i];
   out[i] = make_int4(__double2loint(cc), __double2hiint(cc), l, r);
 }
 
@@ -1251,7 +1256,8 @@ int rpf_build_route(rpf_forest* f, cudaStream_t s) {
     return RPF_ENOMEM;
   if (N > 0)
     RPF_LAUNCH("k_route_table", s, k_route_table<<<nblk(N, 256), 256, 0, s>>>(
-        N, f->node_left, f->node_right, f->node_flag, f->node_c, f->node_route));
+        N, f->node_left, f->node_right, f->node_flag, f->node_c, f->node_begin, f->node_len,
+        f->node_route));
   RPF_CU(cudaGetLastError());
   return RPF_OK;
 }

@@ -392,12 +392,12 @@ int rpf_build_route(rpf_forest* f, cudaStream_t s);
 // scan covers (f, K), and the launch over m x T (query, tree) leaves
 int rpf_build_x16(rpf_forest* f, cudaStream_t s);
 bool rpf_qscan_bf_ok(const rpf_forest* f, int K);
-int rpf_qscan_bf(const rpf_forest* f, const float* Q, int64_t m, int K, const int32_t* qleaf,
+int rpf_qscan_bf(const rpf_forest* f, const float* Q, int64_t m, int K, const int2* qleaf,
                  uint2* cand, int* err, cudaStream_t s);
 // the query path in parts (rpf_knn.cu): routing, and the leaf scan in the
 // BF16 (bf) or FP32 form
-int rpf_route_dev(const rpf_forest* f, const float* Q, int64_t m, int32_t* qleaf, cudaStream_t s);
-int rpf_qscan_dev(const rpf_forest* f, const float* Q, int64_t m, int K, const int32_t* qleaf,
+int rpf_route_dev(const rpf_forest* f, const float* Q, int64_t m, int2* qleaf, cudaStream_t s);
+int rpf_qscan_dev(const rpf_forest* f, const float* Q, int64_t m, int K, const int2* qleaf,
                   uint2* cand, int* qerr, bool bf, cudaStream_t s);
 // the query scan the autotuner kept for (d, leaf bound, K): 1 = BF16 rows,
 // 0 = FP32 rows, -1 = not tuned

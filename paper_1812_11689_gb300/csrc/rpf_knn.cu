@@ -320,17 +320,15 @@ __global__ void k_merge(int64_t n, int K, int G, const uint2* cand, const uint2*
 }
 
 template <int KMAX>
-__global__ void k_qscan(const float* Q, int64_t m, int d, int T, int K, const int32_t* qleaf,
-                        const int32_t* node_tree, const int32_t* node_begin,
-                        const int32_t* node_len, const int32_t* perm, const float* X, int64_t n,
-                        uint2* cand) {
+__global__ void k_qscan(const float* Q, int64_t m, int d, int T, int K, const int2* qleaf,
+                        const int32_t* perm, const float* X, int64_t n, uint2* cand) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= m * T) return;
   const int64_t q = g / T;
   const int t = (int)(g % T);
-  const int leaf = qleaf[g];
-  const int b = node_begin[leaf], ln = node_len[leaf];
-  const int32_t* mem = perm + (int64_t)node_tree[leaf] * n + b;
+  const int2 lf = qleaf[g];  // the leaf's (begin, length) in tree t's permutation
+  const int b = lf.x, ln = lf.y;
+  const int32_t* mem = perm + (int64_t)t * n + b;
   const float* x = Q + q * d;
   TopK<KMAX> tk;
   tk.init();
@@ -360,7 +358,7 @@ __global__ void k_qscan(const float* Q, int64_t m, int d, int T, int K, const in
 __global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, int64_t m, int d,
                                                  int T, const int4* __restrict__ node_route,
                                                  const float* __restrict__ node_dir32,
-                                                 int32_t* qleaf) {
+                                                 int2* qleaf) {
   const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / RW;
   const int lane = threadIdx.x & 31, sub = lane & (RW - 1);
   const unsigned gmask = ((1u << RW) - 1u) << (lane & ~(RW - 1));
@@ -411,7 +409,7 @@ __global__ void __launch_bounds__(256) k_route_w(const float* __restrict__ Q, in
     node = go_left ? rec.z : rec.w;
     rec = __ldg(node_route + node);
   }
-  if (sub == 0) qleaf[g] = node;
+  if (sub == 0) qleaf[g] = make_int2(rec.x, rec.y);  // the leaf's (begin, length)
 }
 
 // The same walk with the query's coordinates held in registers and the next
@@ -423,7 +421,7 @@ template <int PM>
 __global__ void __launch_bounds__(256) k_route_p(const float* __restrict__ Q, int64_t m, int d,
                                                  int T, const int4* __restrict__ node_route,
                                                  const float* __restrict__ node_dir32,
-                                                 int32_t* qleaf) {
+                                                 int2* qleaf) {
   const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / RW;
   const int lane = threadIdx.x & 31, sub = lane & (RW - 1);
   const unsigned gmask = ((1u << RW) - 1u) << (lane & ~(RW - 1));
@@ -490,7 +488,7 @@ __global__ void __launch_bounds__(256) k_route_p(const float* __restrict__ Q, in
       rv[i] = k < d ? __ldg(node_dir32 + (int64_t)node * d + k) : 0.0f;
     }
   }
-  if (sub == 0) qleaf[g] = node;
+  if (sub == 0) qleaf[g] = make_int2(rec.x, rec.y);  // the leaf's (begin, length)
 }
 
 // Ascending bitonic sort of one 64-bit key per lane (all 32 lanes).
@@ -529,10 +527,7 @@ __device__ __forceinline__ unsigned long long rpf_warp_merge_min(unsigned long l
 // warps' lists).  Leaves of at most QS_T points.
 #define QS_T 128
 __global__ void __launch_bounds__(QS_T) k_qscan_cta(const float* __restrict__ Q, int64_t m, int d,
-                                                    int dp, int T, int K, const int32_t* qleaf,
-                                                    const int32_t* node_tree,
-                                                    const int32_t* node_begin,
-                                                    const int32_t* node_len,
+                                                    int dp, int T, int K, const int2* qleaf,
                                                     const int32_t* __restrict__ perm,
                                                     const float* __restrict__ X, int64_t n,
                                                     uint2* cand, int* err, uint64_t wlim) {
@@ -544,9 +539,9 @@ __global__ void __launch_bounds__(QS_T) k_qscan_cta(const float* __restrict__ Q,
   const int64_t q = g / T;
   const int t = (int)(g % T);
   const int tid = threadIdx.x;
-  const int leaf = qleaf[g];
-  const int len = node_len[leaf];
-  const int32_t* mem = perm + (int64_t)node_tree[leaf] * n + node_begin[leaf];
+  const int2 lf = qleaf[g];  // the leaf's (begin, length) in tree t's permutation
+  const int len = lf.y;
+  const int32_t* mem = perm + (int64_t)t * n + lf.x;
   float* qv = qs_rows + QS_T * dp;
   if (tid < len) pid[tid] = mem[tid];
   for (int k = tid; k < dp; k += QS_T) qv[k] = k < d ? Q[q * d + k] : 0.0f;
@@ -756,12 +751,11 @@ void launch_merge(int64_t n, int K, int G, const uint2* cand, const uint2* run_i
 }
 
 template <int KMAX>
-void launch_qscan(const rpf_forest* f, const float* Q, int64_t m, int K, const int32_t* qleaf,
+void launch_qscan(const rpf_forest* f, const float* Q, int64_t m, int K, const int2* qleaf,
                   uint2* cand, cudaStream_t s) {
   const int T = f->prm.n_trees;
-  RPF_LAUNCH("k_qscan", s, k_qscan<KMAX><<<nblk(m * T, 128), 128, 0, s>>>(Q, m, f->d, T, K, qleaf, f->node_tree,
-                                                 f->node_begin, f->node_len, f->perm, f->X, f->n,
-                                                 cand));
+  RPF_LAUNCH("k_qscan", s, k_qscan<KMAX><<<nblk(m * T, 128), 128, 0, s>>>(
+      Q, m, f->d, T, K, qleaf, f->perm, f->X, f->n, cand));
 }
 
 #define RPF_KDISPATCH(K, FN, ...)                 \
@@ -918,7 +912,7 @@ int rpf_all_knn_dev(rpf_forest* f, int T, int K, int32_t* idx, float* dist, void
 }
 
 size_t rpf_query_core_ws(int64_t m, int T, int K) {
-  return RPF_QERR_BYTES + align256((size_t)m * T * 4) + align256((size_t)T * m * K * 8);
+  return RPF_QERR_BYTES + align256((size_t)m * T * 8) + align256((size_t)T * m * K * 8);
 }
 
 size_t rpf_query_ws(const rpf_forest* f, int64_t m, int K) {
@@ -926,8 +920,9 @@ size_t rpf_query_ws(const rpf_forest* f, int64_t m, int K) {
          align256((size_t)m * K * 4) + align256((size_t)m * K * 4);
 }
 
-// Leaf ids of m queries in every tree (k_route_w) into qleaf (m x T).
-int rpf_route_dev(const rpf_forest* f, const float* Q, int64_t m, int32_t* qleaf, cudaStream_t s) {
+// The leaf of each of m queries in every tree, as its (begin, length) in the
+// tree's permutation, into qleaf (m x T).
+int rpf_route_dev(const rpf_forest* f, const float* Q, int64_t m, int2* qleaf, cudaStream_t s) {
   const int T = f->prm.n_trees;
   const int per = (f->d + RW - 1) / RW;
   const unsigned grid = nblk(m * T * RW, 256);
@@ -949,7 +944,7 @@ int rpf_route_dev(const rpf_forest* f, const float* Q, int64_t m, int32_t* qleaf
 
 // Per-tree lists of the leaves in qleaf: the chosen form's BF16 scan when
 // `bf` (and the scan covers (f, K)), else the FP32 scan.
-int rpf_qscan_dev(const rpf_forest* f, const float* Q, int64_t m, int K, const int32_t* qleaf,
+int rpf_qscan_dev(const rpf_forest* f, const float* Q, int64_t m, int K, const int2* qleaf,
                   uint2* cand, int* qerr, bool bf, cudaStream_t s) {
   const int T = f->prm.n_trees;
   const int dp = ((f->d + 3) & ~3) + 4;
@@ -960,7 +955,7 @@ int rpf_qscan_dev(const rpf_forest* f, const float* Q, int64_t m, int K, const i
   } else if (f->prm.leaf_max <= QS_T && (f->d % 4) == 0 && qsm <= 200 * 1024) {
     RPF_CU(cudaFuncSetAttribute(k_qscan_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
     RPF_LAUNCH("k_qscan_cta", s, k_qscan_cta<<<(unsigned)(m * T), QS_T, qsm, s>>>(
-        Q, m, f->d, dp, T, K, qleaf, f->node_tree, f->node_begin, f->node_len, f->perm, f->X,
+        Q, m, f->d, dp, T, K, qleaf, f->perm, f->X,
         f->n, cand, qerr, rpf_wait_limit_ns()));
   } else {
     RPF_KDISPATCH(K, launch_qscan, f, Q, m, K, qleaf, cand, s);
@@ -981,8 +976,8 @@ int rpf_query_dev(const rpf_forest* f, const float* Q, int64_t m, int K, int32_t
   if (ws_bytes < rpf_query_core_ws(m, T, K)) return RPF_EINVAL;
   int* qerr = (int*)ws;
   RPF_CU(cudaMemsetAsync(qerr, 0, sizeof(int), s));
-  int32_t* qleaf = (int32_t*)((char*)ws + RPF_QERR_BYTES);
-  uint2* cand = (uint2*)((char*)qleaf + align256((size_t)m * T * 4));
+  int2* qleaf = (int2*)((char*)ws + RPF_QERR_BYTES);
+  uint2* cand = (uint2*)((char*)qleaf + align256((size_t)m * T * 8));
   int rc = rpf_route_dev(f, Q, m, qleaf, s);
   if (rc) return rc;
   const bool bf = f->prm.form == 1 && (f->qscan_mode >= 0 ? f->qscan_mode == 1

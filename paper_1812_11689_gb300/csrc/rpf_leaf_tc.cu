@@ -980,10 +980,10 @@ int rpf_tc_autotune(rpf_forest* f, int K, cudaStream_t s, int32_t* chosen) {
     if (!rc && rpf_qscan_bf_ok(f, K)) {
       const int T = f->prm.n_trees;
       const int64_t mq = std::min<int64_t>(f->n, 4096);
-      int32_t* qleaf = nullptr;
+      int2* qleaf = nullptr;
       uint2* qc = nullptr;
       int* qe = nullptr;
-      if (rpf_alloc((void**)&qleaf, 4 * (size_t)mq * T, s) ||
+      if (rpf_alloc((void**)&qleaf, 8 * (size_t)mq * T, s) ||
           rpf_alloc((void**)&qc, 8 * (size_t)mq * T * K, s) || rpf_alloc((void**)&qe, 4, s)) {
         rc = RPF_ENOMEM;
       } else {

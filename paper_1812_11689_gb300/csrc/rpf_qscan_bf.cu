@@ -107,8 +107,7 @@ __device__ __forceinline__ float qb_d32(const float* qv, const float* __restrict
 
 __global__ void __launch_bounds__(QB_T) k_qscan_bf(
     const float* __restrict__ Q, int64_t m, int d, int d8, int dp16, int T, int K,
-    const int32_t* qleaf, const int32_t* node_tree, const int32_t* node_begin,
-    const int32_t* node_len, const int32_t* __restrict__ perm, const float* __restrict__ X,
+    const int2* qleaf, const int32_t* __restrict__ perm, const float* __restrict__ X,
     const uint16_t* __restrict__ X16, const float* __restrict__ xnorm, int64_t n, uint2* cand,
     int* err, unsigned long long* fallbacks, uint64_t wlim) {
   extern __shared__ __align__(16) unsigned char qb_raw[];
@@ -125,9 +124,9 @@ __global__ void __launch_bounds__(QB_T) k_qscan_bf(
   const int64_t q = g / T;
   const int t = (int)(g % T);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int leaf = qleaf[g];
-  const int len = node_len[leaf];
-  const int32_t* mem = perm + (int64_t)node_tree[leaf] * n + node_begin[leaf];
+  const int2 lf = qleaf[g];  // the leaf's (begin, length) in tree t's permutation
+  const int len = lf.y;
+  const int32_t* mem = perm + (int64_t)t * n + lf.x;
   uint2* out = cand + ((int64_t)t * m + q) * K;
   float xn = 0.0f;
   if (tid < len) {
@@ -285,7 +284,7 @@ bool rpf_qscan_bf_ok(const rpf_forest* f, int K) {
   return (size_t)QB_T * dp16 * 2 + (size_t)f->d8 * 4 <= 200 * 1024;
 }
 
-int rpf_qscan_bf(const rpf_forest* f, const float* Q, int64_t m, int K, const int32_t* qleaf,
+int rpf_qscan_bf(const rpf_forest* f, const float* Q, int64_t m, int K, const int2* qleaf,
                  uint2* cand, int* err, cudaStream_t s) {
   const int T = f->prm.n_trees, d8 = f->d8;
   // row stride: an odd number of 16-byte units, so 16-byte row reads of
@@ -294,7 +293,7 @@ int rpf_qscan_bf(const rpf_forest* f, const float* Q, int64_t m, int K, const in
   const size_t smem = (size_t)QB_T * dp16 * 2 + (size_t)d8 * 4;
   RPF_CU(cudaFuncSetAttribute(k_qscan_bf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   RPF_LAUNCH("k_qscan_bf", s, k_qscan_bf<<<(unsigned)(m * T), QB_T, smem, s>>>(
-      Q, m, f->d, d8, dp16, T, K, qleaf, f->node_tree, f->node_begin, f->node_len, f->perm, f->X,
+      Q, m, f->d, d8, dp16, T, K, qleaf, f->perm, f->X,
       f->X16, f->xnorm, f->n, cand, err, f->d_fallback, rpf_wait_limit_ns()));
   RPF_CU(cudaGetLastError());
   return RPF_OK;

@@ -45,7 +45,7 @@ def test_query_static_rejects_oversized_and_host_requests():
     import torch
     f = _forest()
     K = 10
-    # need = 256 + align256(4 m T) + align256(8 T m K) > 8 MiB at T = 8, K = 10
+    # need = 256 + align256(8 m T) + align256(8 T m K) > 8 MiB at T = 8, K = 10
     m = 13000
     Qd = torch.zeros((m, 96), dtype=torch.float32, device="cuda")
     idx = torch.full((m, K), -7, dtype=torch.int32, device="cuda")
