@@ -188,14 +188,14 @@ int rpf_query(const rpf_forest* f, const float* Q, int64_t m, int32_t K, int32_t
  *   stream   : cudaStream_t (NULL = legacy default stream).
  * Scratch: one fixed array of RPF_STATIC_SCRATCH_BYTES per device, inside
  * the library.  A call needs 256 + align256(8 m T) + align256(8 T m K) bytes
- * of it (T = trees of the forest; at T = 32, K = 10 that allows m <= 3120);
+ * of it (T = trees of the forest; at T = 32, K = 10 that allows m <= 2978);
  * larger requests return RPF_EINVAL without launching anything -- split
  * them.  Nothing in the scratch has to start at zero: the call clears its
  * error word and every other byte it reads was written earlier in the call.
  * Set-up: the first call on a device (that device current, the forest's
  * device) looks the array up once (cudaGetSymbolAddress) and caches its
- * address; make that first call before any stream capture starts.  The
- * cached address does not survive a device reset (cudaDeviceReset).
+ * address.  The cached address does not survive a device reset
+ * (cudaDeviceReset).
  * Races: the scratch is shared by every call on the device.  Calls that may
  * overlap in time (different streams, different host threads) race on it and
  * corrupt each other's results: issue them on one stream, or serialise them.

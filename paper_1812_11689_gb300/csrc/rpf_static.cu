@@ -11,9 +11,8 @@
 // The scratch is one file-scope __device__ array per device (its backing is
 // set up by the CUDA runtime when this module is loaded, not by this call).
 // The first call on a device, with that device current, looks the array up
-// with cudaGetSymbolAddress and caches the address; that first call should be
-// made before any stream capture begins.  Later calls on the device only
-// reuse the cached address.  The cache does not survive a device reset
+// with cudaGetSymbolAddress and caches the address; later calls on the
+// device only reuse it.  The cache does not survive a device reset
 // (cudaDeviceReset, or the primary context released and created again): the
 // array may then live at another address, so a process that resets a device
 // must not call rpf_query_static on it afterwards.
