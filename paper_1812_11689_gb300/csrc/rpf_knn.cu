@@ -32,6 +32,18 @@ namespace {
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// acc + the squares of a - v over four coordinates, added one at a time in
+// coordinate order (the canonical d32 chain); the differences are taken in
+// packed pairs, each lane rounding like __fsub_rn
+__device__ __forceinline__ float sq_chain4(const float4 a, const float4 v, float acc) {
+  const float2 e01 = rpf_sub2(make_float2(a.x, a.y), make_float2(v.x, v.y));
+  const float2 e23 = rpf_sub2(make_float2(a.z, a.w), make_float2(v.z, v.w));
+  acc = __fmaf_rn(e01.x, e01.x, acc);
+  acc = __fmaf_rn(e01.y, e01.y, acc);
+  acc = __fmaf_rn(e23.x, e23.x, acc);
+  return __fmaf_rn(e23.y, e23.y, acc);
+}
+
 // Register-resident sorted list of the KMAX smallest (d, idx) offered so far
 // (ascending; empty slots are (+inf, -1)).  Every caller needs the K <= KMAX
 // smallest, which the first K entries are.  The length is a compile-time
@@ -209,11 +221,7 @@ __global__ void __launch_bounds__(128, 4) k_leaf_plain(const int32_t* tile_cnt,
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const float4 v = *reinterpret_cast<const float4*>(xs + cc[j] * dp + k);
-            float e;
-            e = __fsub_rn(xr[k], v.x); acc[j] = __fmaf_rn(e, e, acc[j]);
-            e = __fsub_rn(xr[k + 1], v.y); acc[j] = __fmaf_rn(e, e, acc[j]);
-            e = __fsub_rn(xr[k + 2], v.z); acc[j] = __fmaf_rn(e, e, acc[j]);
-            e = __fsub_rn(xr[k + 3], v.w); acc[j] = __fmaf_rn(e, e, acc[j]);
+            acc[j] = sq_chain4(make_float4(xr[k], xr[k + 1], xr[k + 2], xr[k + 3]), v, acc[j]);
           }
         }
       } else if (STAGE) {
@@ -223,11 +231,7 @@ __global__ void __launch_bounds__(128, 4) k_leaf_plain(const int32_t* tile_cnt,
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const float4 v = *reinterpret_cast<const float4*>(xs + cc[j] * dp + k);
-            float e;
-            e = __fsub_rn(a.x, v.x); acc[j] = __fmaf_rn(e, e, acc[j]);
-            e = __fsub_rn(a.y, v.y); acc[j] = __fmaf_rn(e, e, acc[j]);
-            e = __fsub_rn(a.z, v.z); acc[j] = __fmaf_rn(e, e, acc[j]);
-            e = __fsub_rn(a.w, v.w); acc[j] = __fmaf_rn(e, e, acc[j]);
+            acc[j] = sq_chain4(a, v, acc[j]);
           }
         }
       } else {
@@ -261,11 +265,7 @@ __device__ __forceinline__ void rpf_row_exact(const float* xs, int dp, int d4, i
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float4 v = *reinterpret_cast<const float4*>(xs + cc[j] * dp + k);
-        float e;
-        e = __fsub_rn(a.x, v.x); acc[j] = __fmaf_rn(e, e, acc[j]);
-        e = __fsub_rn(a.y, v.y); acc[j] = __fmaf_rn(e, e, acc[j]);
-        e = __fsub_rn(a.z, v.z); acc[j] = __fmaf_rn(e, e, acc[j]);
-        e = __fsub_rn(a.w, v.w); acc[j] = __fmaf_rn(e, e, acc[j]);
+        acc[j] = sq_chain4(a, v, acc[j]);
       }
     }
 #pragma unroll
@@ -568,11 +568,7 @@ __global__ void __launch_bounds__(QS_T) k_qscan_cta(const float* __restrict__ Q,
     for (int k = 0; k < d; k += 4) {
       const float4 a = *reinterpret_cast<const float4*>(qv + k);
       const float4 b = *reinterpret_cast<const float4*>(y + k);
-      float e;
-      e = __fsub_rn(a.x, b.x); acc = __fmaf_rn(e, e, acc);
-      e = __fsub_rn(a.y, b.y); acc = __fmaf_rn(e, e, acc);
-      e = __fsub_rn(a.z, b.z); acc = __fmaf_rn(e, e, acc);
-      e = __fsub_rn(a.w, b.w); acc = __fmaf_rn(e, e, acc);
+      acc = sq_chain4(a, b, acc);
     }
     key = ((unsigned long long)__float_as_uint(acc) << 32) | (unsigned)pid[tid];
   }

@@ -181,12 +181,15 @@ __device__ __forceinline__ void d32x4(const float* xs, int dp, int d4, int r, co
     const float4 a = *reinterpret_cast<const float4*>(x + k);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
+      // the differences in packed pairs (each lane rounds like __fsub_rn);
+      // the squares still go into one chain in coordinate order
       const float4 v = *reinterpret_cast<const float4*>(xs + c[j] * dp + k);
-      float e;
-      e = __fsub_rn(a.x, v.x); acc[j] = __fmaf_rn(e, e, acc[j]);
-      e = __fsub_rn(a.y, v.y); acc[j] = __fmaf_rn(e, e, acc[j]);
-      e = __fsub_rn(a.z, v.z); acc[j] = __fmaf_rn(e, e, acc[j]);
-      e = __fsub_rn(a.w, v.w); acc[j] = __fmaf_rn(e, e, acc[j]);
+      const float2 e01 = rpf_sub2(make_float2(a.x, a.y), make_float2(v.x, v.y));
+      const float2 e23 = rpf_sub2(make_float2(a.z, a.w), make_float2(v.z, v.w));
+      acc[j] = __fmaf_rn(e01.x, e01.x, acc[j]);
+      acc[j] = __fmaf_rn(e01.y, e01.y, acc[j]);
+      acc[j] = __fmaf_rn(e23.x, e23.x, acc[j]);
+      acc[j] = __fmaf_rn(e23.y, e23.y, acc[j]);
     }
   }
 }
