@@ -21,11 +21,13 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "rpf_internal.cuh"
 #include "rpf_tma.cuh"
 #include "rpf_scan.cuh"
+#include "rpf_select.cuh"
 
 namespace {
 
@@ -196,7 +198,10 @@ __global__ void __launch_bounds__(128, 4) k_leaf_plain(const int32_t* tile_cnt,
     const int r = lb + 32 * (it - item_off[lo]) + lane;
     const bool live = r < le;
     const int rr = live ? r : lb;
-    TopK<KMAX> tk;
+    // up to 16 entries: 64-bit keys (d32 bits, index), which order like
+    // (d32, index), inserted four at a time; longer lists keep one insertion
+    // per column (the batched merge would not fit in registers beside the row)
+    std::conditional_t<(KMAX <= 16), Top64<KMAX>, TopK<KMAX>> tk;
     tk.init();
     float xr[REG ? 64 : 1];
     if (REG) {
@@ -239,10 +244,20 @@ __global__ void __launch_bounds__(128, 4) k_leaf_plain(const int32_t* tile_cnt,
         for (int j = 0; j < 4; ++j)
           acc[j] = rpf_d32(X + (int64_t)prow[rr] * d, X + (int64_t)prow[cc[j]] * d, d);
       }
+      if constexpr (KMAX <= 16) {
+        unsigned long long kb[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = c0 + j;
-        if (c < le && c != r) tk.offer(acc[j], prow[c]);
+        for (int j = 0; j < 4; ++j) {
+          const int c = c0 + j;
+          kb[j] = c < le && c != r ? key64(acc[j], prow[cc[j]]) : ~0ull;
+        }
+        tk.insert4(kb);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = c0 + j;
+          if (c < le && c != r) tk.offer(acc[j], prow[c]);
+        }
       }
     }
     if (live) tk.store(K, cand + ((int64_t)(t - t0) * n + prow[r]) * K);

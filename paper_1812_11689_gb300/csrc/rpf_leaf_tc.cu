@@ -61,6 +61,7 @@
 
 #include "rpf_internal.cuh"
 #include "rpf_scan.cuh"
+#include "rpf_select.cuh"
 #include "rpf_tma.cuh"
 #include "rpf_umma.cuh"
 
@@ -76,40 +77,6 @@ namespace {
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-// Sorted list of the KK smallest 64-bit keys offered (ascending; empty slots
-// are all-ones).  Insertion is a branch-free min/max network.
-template <int KK>
-struct Top64 {
-  unsigned long long k[KK];
-  __device__ __forceinline__ void init() {
-#pragma unroll
-    for (int q = 0; q < KK; ++q) k[q] = ~0ull;
-  }
-  __device__ __forceinline__ void insert(unsigned long long x) {
-#pragma unroll
-    for (int q = KK - 1; q >= 1; --q) k[q] = max(k[q - 1], min(k[q], x));
-    k[0] = min(k[0], x);
-  }
-  // d32 of the K-th entry: the list is sorted, so it is the smallest key at
-  // or after position K - 1 (a reduction keeps the list in registers)
-  __device__ __forceinline__ float kth_d32(int K) const {
-    unsigned long long m = ~0ull;
-#pragma unroll
-    for (int q = 0; q < KK; ++q) m = min(m, q >= K - 1 ? k[q] : ~0ull);
-    return __uint_as_float((unsigned)(m >> 32));
-  }
-  // first K entries as (d32 bits, index); empty slots as (+inf, -1)
-  __device__ __forceinline__ void store(int K, uint2* out) const {
-#pragma unroll
-    for (int q = 0; q < KK; ++q)
-      if (q < K) {
-        const bool e = k[q] == ~0ull;
-        out[q] = e ? make_uint2(0x7f800000u, 0xffffffffu)
-                   : make_uint2((unsigned)(k[q] >> 32), (unsigned)k[q]);
-      }
-  }
-};
-
 // D~ = (n_r + n_c) - 2 G_rc for the eight columns c0 .. c0 + 7 (c0 a multiple
 // of 8; nrm has room for them), in packed pair instructions
 __device__ __forceinline__ void tc_dist8(const float (&g)[8], float nr, const float* nrm, int c0,
@@ -122,10 +89,6 @@ __device__ __forceinline__ void tc_dist8(const float (&g)[8], float nr, const fl
     D[j] = v.x;
     D[j + 1] = v.y;
   }
-}
-
-__device__ __forceinline__ unsigned long long key64(float d32, int idx) {
-  return ((unsigned long long)__float_as_uint(d32) << 32) | (unsigned)idx;
 }
 
 // Sorted list of the KK smallest floats offered (branch-free network).
@@ -149,64 +112,6 @@ struct TopF {
   }
 };
 
-__host__ __device__ __forceinline__ uint32_t umin32(uint32_t a, uint32_t b) { return a < b ? a : b; }
-__host__ __device__ __forceinline__ uint32_t umax32(uint32_t a, uint32_t b) { return a < b ? b : a; }
-__host__ __device__ __forceinline__ void ucmpx(uint32_t& a, uint32_t& b) {  // a <= b after
-  const uint32_t lo = umin32(a, b);
-  b = umax32(a, b);
-  a = lo;
-}
-__host__ __device__ constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
-
-// Sorted list of the KK smallest 32-bit keys offered (branch-free networks).
-template <int KK>
-struct TopU {
-  uint32_t v[KK];
-  __host__ __device__ __forceinline__ void init() {
-#pragma unroll
-    for (int q = 0; q < KK; ++q) v[q] = 0xffffffffu;
-  }
-  __host__ __device__ __forceinline__ void insert(uint32_t x) {
-#pragma unroll
-    for (int q = KK - 1; q >= 1; --q) v[q] = umax32(v[q - 1], umin32(v[q], x));
-    v[0] = umin32(v[0], x);
-  }
-  // The same list as eight insert() calls, in fewer operations: the batch is
-  // sorted (a 19-comparator network); the elementwise minimum of the list and
-  // the reversed batch holds the KK smallest of both and rises then falls;
-  // a bitonic merge sorts it.  The merge runs over a power of two P >= KK
-  // with P - KK leading zeros (no key is smaller), whose comparisons fold
-  // away.
-  __host__ __device__ __forceinline__ void insert8(uint32_t (&b)[8]) {
-    ucmpx(b[0], b[2]); ucmpx(b[1], b[3]); ucmpx(b[4], b[6]); ucmpx(b[5], b[7]);
-    ucmpx(b[0], b[4]); ucmpx(b[1], b[5]); ucmpx(b[2], b[6]); ucmpx(b[3], b[7]);
-    ucmpx(b[0], b[1]); ucmpx(b[2], b[3]); ucmpx(b[4], b[5]); ucmpx(b[6], b[7]);
-    ucmpx(b[2], b[4]); ucmpx(b[3], b[5]);
-    ucmpx(b[1], b[4]); ucmpx(b[3], b[6]);
-    ucmpx(b[1], b[2]); ucmpx(b[3], b[4]); ucmpx(b[5], b[6]);
-    constexpr int P = pow2_at_least(KK);
-    uint32_t s[P];
-#pragma unroll
-    for (int i = 0; i < P - KK; ++i) s[i] = 0u;
-#pragma unroll
-    for (int i = 0; i < KK; ++i)
-      s[P - KK + i] = KK - 1 - i < 8 ? umin32(v[i], b[KK - 1 - i < 8 ? KK - 1 - i : 0]) : v[i];
-#pragma unroll
-    for (int st = P / 2; st >= 1; st >>= 1) {
-#pragma unroll
-      for (int i = 0; i < P; ++i)
-        if ((i & st) == 0) ucmpx(s[i], s[i + st]);
-    }
-#pragma unroll
-    for (int i = 0; i < KK; ++i) v[i] = s[P - KK + i];
-  }
-  __host__ __device__ __forceinline__ uint32_t kth(int K) const {  // sorted: min over q >= K - 1
-    uint32_t r = 0xffffffffu;
-#pragma unroll
-    for (int q = 0; q < KK; ++q) r = umin32(r, q >= K - 1 ? v[q] : 0xffffffffu);
-    return r;
-  }
-};
 
 // Exact d32 of tile row r against up to four tile rows c[0..3] (canonical
 // chains over k in order; rows padded with zeros to d4).
@@ -648,9 +553,10 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
         for (int j = 0; j < 4; ++j) cc[j] = my[e0 + j < nc ? e0 + j : e0];
         float acc[4];
         d32x4(xs, dp, d4, r, cc, acc);
+        unsigned long long kb[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (e0 + j < nc) ex.insert(key64(acc[j], prow_s[cc[j]]));
+        for (int j = 0; j < 4; ++j) kb[j] = e0 + j < nc ? key64(acc[j], prow_s[cc[j]]) : ~0ull;
+        ex.insert4(kb);
       }
       if (tc_row) {
         // (6) certificate
@@ -673,9 +579,11 @@ __global__ void __launch_bounds__(ROWS, ROWS == 128 ? 4 : 1) k_leaf_tc(
         for (int j = 0; j < 4; ++j) cc[j] = min(c0 + j, le - 1);
         float acc[4];
         d32x4(xs, dp, d4, r, cc, acc);
+        unsigned long long kb[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          if (c0 + j < le && c0 + j != r) ex.insert(key64(acc[j], prow_s[c0 + j]));
+          kb[j] = c0 + j < le && c0 + j != r ? key64(acc[j], prow_s[c0 + j]) : ~0ull;
+        ex.insert4(kb);
       }
       if (redo) atomicAdd(fallbacks, 1ULL);
     }
