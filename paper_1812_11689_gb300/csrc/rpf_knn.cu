@@ -198,10 +198,12 @@ __global__ void __launch_bounds__(128, 4) k_leaf_plain(const int32_t* tile_cnt,
     const int r = lb + 32 * (it - item_off[lo]) + lane;
     const bool live = r < le;
     const int rr = live ? r : lb;
-    // up to 16 entries: 64-bit keys (d32 bits, index), which order like
-    // (d32, index), inserted four at a time; longer lists keep one insertion
-    // per column (the batched merge would not fit in registers beside the row)
-    std::conditional_t<(KMAX <= 16), Top64<KMAX>, TopK<KMAX>> tk;
+    // up to 16 entries (32 when the row is not held in registers): 64-bit
+    // keys (d32 bits, index), which order like (d32, index), merged in four
+    // at a time; longer lists keep one insertion per column (the batched
+    // merge would not fit in registers)
+    constexpr bool kBatch = KMAX <= 16 || (!REG && KMAX <= 32);
+    std::conditional_t<kBatch, Top64<KMAX>, TopK<KMAX>> tk;
     tk.init();
     float xr[REG ? 64 : 1];
     if (REG) {
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(128, 4) k_leaf_plain(const int32_t* tile_cnt,
         for (int j = 0; j < 4; ++j)
           acc[j] = rpf_d32(X + (int64_t)prow[rr] * d, X + (int64_t)prow[cc[j]] * d, d);
       }
-      if constexpr (KMAX <= 16) {
+      if constexpr (kBatch) {
         unsigned long long kb[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -777,6 +779,17 @@ void launch_qscan(const rpf_forest* f, const float* Q, int64_t m, int K, const i
     else if ((K) <= 64) FN<64>(__VA_ARGS__);      \
     else FN<128>(__VA_ARGS__);                    \
   } while (0)
+// the plain leaf tiles also get lists of exactly 10 and 20 (the common K)
+#define RPF_LEAF_KDISPATCH(K, FN, ...)            \
+  do {                                            \
+    if ((K) <= 8) FN<8>(__VA_ARGS__);             \
+    else if ((K) <= 10) FN<10>(__VA_ARGS__);      \
+    else if ((K) <= 16) FN<16>(__VA_ARGS__);      \
+    else if ((K) <= 20) FN<20>(__VA_ARGS__);      \
+    else if ((K) <= 32) FN<32>(__VA_ARGS__);      \
+    else if ((K) <= 64) FN<64>(__VA_ARGS__);      \
+    else FN<128>(__VA_ARGS__);                    \
+  } while (0)
 
 }  // namespace
 
@@ -869,7 +882,7 @@ size_t rpf_all_knn_ws(const rpf_forest* f, int K) {
 
 int rpf_leaf_plain(const rpf_forest* f, int t0, int g, int K, uint2* cand, cudaStream_t s) {
   const int64_t tb = (int64_t)t0 * f->tiles_per_tree, nt = (int64_t)g * f->tiles_per_tree;
-  if (nt > 0) RPF_KDISPATCH(K, launch_leaf, f, tb, nt, K, t0, cand, f->d_err, s);
+  if (nt > 0) RPF_LEAF_KDISPATCH(K, launch_leaf, f, tb, nt, K, t0, cand, f->d_err, s);
   RPF_CU(cudaGetLastError());
   return RPF_OK;
 }
@@ -901,7 +914,7 @@ int rpf_all_knn_dev(rpf_forest* f, int T, int K, int32_t* idx, float* dist, void
         if (rc) return rc;
       } else {
         if (f->prm.form == 1) ++f->plain_groups;  // chosen form not available here
-        RPF_KDISPATCH(K, launch_leaf, f, tb, nt, K, t0, cand, f->d_err, s);
+        RPF_LEAF_KDISPATCH(K, launch_leaf, f, tb, nt, K, t0, cand, f->d_err, s);
       }
     }
     const bool first = t0 == 0, last = t0 + g >= T;
