@@ -126,6 +126,26 @@ int rpf_all_knn_trees(rpf_forest* f, int32_t n_trees, int32_t K, int32_t* idx, f
                       void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * rpf_all_knn_async -- the lists of rpf_all_knn (Algorithm 3 with Q = U),
+ * only enqueued on `stream`: the call allocates nothing, does not
+ * synchronise and reads no device memory on the host, so the sequence (a
+ * persistent launch over every (tree, leaf) tile per group of trees, then
+ * the cross-tree merge) can be recorded into a CUDA graph and replayed.
+ *   K        : 1 <= K <= 128.
+ *   idx,dist : n x K outputs in DEVICE memory.
+ *   workspace: DEVICE scratch of at least rpf_workspace_bytes(f, 0, K, 1)
+ *              bytes, owned by the caller; its first word receives the
+ *              outcome of the device work.
+ * Once the work is done, rpf_query_status(workspace, stream) returns
+ * RPF_OK, or RPF_ETIMEOUT if a bounded device wait gave up (the lists are
+ * then unspecified).  Calls on one forest share its error word: issue them
+ * on one stream.  Errors at enqueue: RPF_EINVAL (host pointer, small
+ * workspace), RPF_ECUDA.
+ */
+int rpf_all_knn_async(rpf_forest* f, int32_t K, int32_t* idx, float* dist, void* workspace,
+                      size_t ws_bytes, void* stream);
+
+/*
  * rpf_all_knn_keys -- the lists of rpf_all_knn with the ranking key itself:
  * for every point, its K nearest in the union of its leaves over this
  * forest's trees, as n x K pairs of int32 (bits of the FP32 squared distance
@@ -208,15 +228,17 @@ int rpf_query_static(const rpf_forest* f, const float* Q, int64_t m, int32_t K, 
                      float* dist, void* stream);
 
 /*
- * rpf_query_status -- outcome of the device work of the last rpf_query that
- * used `workspace` (or, with workspace NULL, of the last rpf_query_static on
- * the current device): synchronises `stream` (the stream that query ran on),
- * then returns RPF_OK, or RPF_ETIMEOUT if one of its bounded device waits
- * gave up.  Errors: RPF_EINVAL (host pointer), RPF_ECUDA.
+ * rpf_query_status -- outcome of the device work of the last rpf_query or
+ * rpf_all_knn_async that used `workspace` (or, with workspace NULL, of the
+ * last rpf_query_static on the current device): synchronises `stream` (the
+ * stream that call ran on), then returns RPF_OK, or RPF_ETIMEOUT if one of
+ * its bounded device waits gave up.  Errors: RPF_EINVAL (host pointer),
+ * RPF_ECUDA.
  */
 int rpf_query_status(const void* workspace, void* stream);
 
-/* Scratch bytes rpf_all_knn (for_all_knn = 1, m ignored) or rpf_query needs. */
+/* Scratch bytes rpf_all_knn / rpf_all_knn_async (for_all_knn = 1, m ignored)
+ * or rpf_query needs. */
 size_t rpf_workspace_bytes(const rpf_forest* f, int64_t m, int32_t K, int32_t for_all_knn);
 
 /*

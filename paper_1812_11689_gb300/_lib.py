@@ -61,6 +61,8 @@ def lib() -> ctypes.CDLL:
             L.rpf_all_knn.restype = ctypes.c_int
             L.rpf_all_knn_trees.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp, _sz, _vp]
             L.rpf_all_knn_trees.restype = ctypes.c_int
+            L.rpf_all_knn_async.argtypes = [_vp, _i32, _vp, _vp, _vp, _sz, _vp]
+            L.rpf_all_knn_async.restype = ctypes.c_int
             L.rpf_query.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _sz, _vp]
             L.rpf_query.restype = ctypes.c_int
             L.rpf_query_static.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp]
@@ -125,7 +127,8 @@ def check(code: int, what: str) -> None:
 
 # names of every symbol include/rpforest.h declares (checked by the CPU tests)
 EXPORTED = ("rpf_default_params", "rpf_build", "rpf_build_shard", "rpf_all_knn",
-            "rpf_all_knn_keys", "rpf_merge_keys", "rpf_all_knn_trees", "rpf_query",
+            "rpf_all_knn_keys", "rpf_merge_keys", "rpf_all_knn_trees", "rpf_all_knn_async",
+            "rpf_query",
             "rpf_query_static", "rpf_query_status", "rpf_add_trees", "rpf_autotune",
             "rpf_set_wait_limit", "rpf_wait_selftest", "rpf_debug_fail_alloc", "rpf_set_form",
             "rpf_set_query_scan",

@@ -10,6 +10,7 @@
 
 #include <atomic>
 
+#include "rpf_allknn.cuh"
 #include "rpf_internal.cuh"
 #include "rpf_tma.cuh"
 
@@ -480,6 +481,23 @@ int rpf_all_knn_trees(rpf_forest* f, int32_t n_trees, int32_t K, int32_t* idx, f
     RPF_CU(cudaStreamSynchronize(s));
   }
   RPF_CU(cudaGetLastError());
+  return RPF_OK;
+}
+
+int rpf_all_knn_async(rpf_forest* f, int32_t K, int32_t* idx, float* dist, void* workspace,
+                      size_t ws_bytes, void* stream) {
+  if (!f || !idx || !dist || !workspace || K < 1 || K > RPF_MAX_K) return RPF_EINVAL;
+  if (!rpf_is_device_ptr(idx) || !rpf_is_device_ptr(dist) || !rpf_is_device_ptr(workspace))
+    return RPF_EINVAL;
+  if (ws_bytes < rpf_all_knn_ws(f, K)) return RPF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  RPF_CU(cudaMemsetAsync(f->d_err, 0, sizeof(int), s));
+  const int rc = rpf_all_knn_enqueue(f, f->prm.n_trees, K, idx, dist,
+                                     (char*)workspace + RPF_QERR_BYTES,
+                                     ws_bytes - RPF_QERR_BYTES, s, nullptr);
+  if (rc) return rc;
+  // this call's outcome, for rpf_query_status(workspace, stream)
+  RPF_CU(cudaMemcpyAsync(workspace, f->d_err, sizeof(int), cudaMemcpyDeviceToDevice, s));
   return RPF_OK;
 }
 

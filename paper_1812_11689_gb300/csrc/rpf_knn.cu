@@ -24,6 +24,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "rpf_allknn.cuh"
 #include "rpf_internal.cuh"
 #include "rpf_tma.cuh"
 #include "rpf_scan.cuh"
@@ -874,10 +875,12 @@ int rpf_build_tiles(rpf_forest* f, cudaStream_t s, int R_force) {
   return RPF_OK;
 }
 
+// [error word of an enqueue-only call (RPF_QERR_BYTES)][running lists]
+// [per-tree lists of every tree]
 size_t rpf_all_knn_ws(const rpf_forest* f, int K) {
   const int64_t n = f->n;
   const int T = f->prm.n_trees;
-  return align256((size_t)T * n * K * 8) + align256((size_t)n * K * 8);
+  return RPF_QERR_BYTES + align256((size_t)T * n * K * 8) + align256((size_t)n * K * 8);
 }
 
 int rpf_leaf_plain(const rpf_forest* f, int t0, int g, int K, uint2* cand, cudaStream_t s) {
@@ -894,8 +897,8 @@ int rpf_merge_dev(int64_t n, int K, int G, const uint2* lists, int32_t* idx, flo
   return RPF_OK;
 }
 
-int rpf_all_knn_dev(rpf_forest* f, int T, int K, int32_t* idx, float* dist, void* ws,
-                    size_t ws_bytes, cudaStream_t s, uint2* keys) {
+int rpf_all_knn_enqueue(rpf_forest* f, int T, int K, int32_t* idx, float* dist, void* ws,
+                        size_t ws_bytes, cudaStream_t s, uint2* keys) {
   const int64_t n = f->n;
   const size_t run_b = align256((size_t)n * K * 8);
   const size_t per_tree = (size_t)n * K * 8;
@@ -924,6 +927,13 @@ int rpf_all_knn_dev(rpf_forest* f, int T, int K, int32_t* idx, float* dist, void
                   s);
   }
   RPF_CU(cudaGetLastError());
+  return RPF_OK;
+}
+
+int rpf_all_knn_dev(rpf_forest* f, int T, int K, int32_t* idx, float* dist, void* ws,
+                    size_t ws_bytes, cudaStream_t s, uint2* keys) {
+  const int rc = rpf_all_knn_enqueue(f, T, K, idx, dist, ws, ws_bytes, s, keys);
+  if (rc) return rc;
   // a bounded device wait that gave up is reported here
   int herr = 0;
   RPF_CU(cudaMemcpyAsync(&herr, f->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -148,6 +148,25 @@ class Forest:
                   "rpf_all_knn_trees")
         return idx, dist
 
+    def all_knn_async(self, K: int, idx, dist, workspace, stream=None):
+        """rpf_all_knn_async: the lists of all_knn, only enqueued (nothing
+        allocated, no synchronisation), so the call can be recorded into a
+        CUDA graph.  idx (n x K int32), dist (n x K float32) and workspace
+        (at least workspace_bytes(K) bytes) are caller-owned contiguous CUDA
+        tensors, checked here before anything is launched;
+        query_status(workspace) reports the outcome once the work is done."""
+        _check_buffer("idx", idx, (self.n, K), torch.int32, self.device)
+        _check_buffer("dist", dist, (self.n, K), torch.float32, self.device)
+        if (not isinstance(workspace, torch.Tensor) or not workspace.is_cuda
+                or not workspace.is_contiguous()):
+            raise ValueError("workspace must be a contiguous CUDA tensor")
+        wsb = workspace.numel() * workspace.element_size()
+        if wsb < self.workspace_bytes(K):
+            raise ValueError("workspace needs %d bytes, not %d" % (self.workspace_bytes(K), wsb))
+        check(_lib.lib().rpf_all_knn_async(self._h, K, _ptr(idx), _ptr(dist), _ptr(workspace),
+                                           wsb, _stream_handle(stream)), "rpf_all_knn_async")
+        return idx, dist
+
     def all_knn_keys(self, K: int, keys=None, workspace=None, stream=None):
         """rpf_all_knn_keys: (n, K, 2) int32 pairs (d32 bits, index) per point."""
         if keys is None:
@@ -219,8 +238,8 @@ class Forest:
 
     def query_status(self, workspace=None, stream=None) -> None:
         """rpf_query_status: waits for the stream and raises if a bounded
-        device wait of the last query on `workspace` (None: the last
-        query_static on this device) gave up."""
+        device wait of the last query or all_knn_async on `workspace` (None:
+        the last query_static on this device) gave up."""
         check(_lib.lib().rpf_query_status(None if workspace is None else _ptr(workspace),
                                           _stream_handle(stream)), "rpf_query_status")
 
