@@ -62,6 +62,7 @@ def test_build_rejects_bad_arguments_before_touching_the_gpu(L):
     q = _lib.rpf_params(3, 50, 5, 0, 0, 0, 0)
     assert L.rpf_build(buf, 1 << 30, 2, ctypes.byref(q), None, ctypes.byref(out)) == -1
     assert L.rpf_all_knn(None, 5, None, None, None, 0, None) == -1
+    assert L.rpf_all_knn_async(None, 5, None, None, None, 0, None) == -1
     assert L.rpf_query(None, None, 1, 5, None, None, None, 0, None) == -1
     assert L.rpf_workspace_bytes(None, 10, 5, 1) == 0
     assert L.rpf_set_query_scan(None, 0) == -1
