@@ -68,3 +68,19 @@ def test_build_rejects_bad_arguments_before_touching_the_gpu(L):
     assert L.rpf_set_query_scan(None, 0) == -1
     assert L.rpf_gather_probe(None, 10, 4, 1, 0, None, None) == -1
     L.rpf_free(None)
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary is a C ABI: include/rpforest.h compiles as C99 with no
+    C++ or CUDA types, and every declaration has C linkage."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "h.c"
+    src.write_text('#include "rpforest.h"\nint main(void) { return 0; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-c", str(src), "-o", str(tmp_path / "h.o")],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
